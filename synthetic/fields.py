@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs: SU(3) gauge fields, Gaussian and point sources.
+
+This module is the one piece shared by the oracle side and the CUDA side: it
+draws inputs and holds none of the Wilson-Dirac arithmetic.  Everything is
+numpy complex128 in the canonical layout
+
+* gauge field ``[V, 4, 3, 3]`` (site lex with x fastest; mu = x, y, z, t; row; col)
+* spinor      ``[V, 3, 4]``    (colour, spin)
+
+The paper measures on real gauge configurations that are not available;
+these seeded fields stand in for them:
+
+* links ``U = exp(i eps H)``, ``H = sum_a c_a lambda_a / 2`` over the eight
+  Gell-Mann matrices, ``c_a ~ N(0, 1)``, then re-unitarised (Gram-Schmidt of
+  rows 0 and 1, row 2 = conj(row0 x row1)) so that det U = 1 to rounding;
+* sources: complex Gaussian with E|z|^2 = 1 (real and imaginary parts
+  N(0, 1/2)), or unit point sources.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_CHUNK = 1 << 18  # matrices per chunk, bounds temporary memory
+
+
+def volume(dims) -> int:
+    return int(np.prod([int(d) for d in dims]))
+
+
+def gell_mann() -> np.ndarray:
+    """The eight Gell-Mann matrices, shape (8, 3, 3)."""
+    lam = np.zeros((8, 3, 3), dtype=np.complex128)
+    lam[0][0, 1] = lam[0][1, 0] = 1
+    lam[1][0, 1], lam[1][1, 0] = -1j, 1j
+    lam[2][0, 0], lam[2][1, 1] = 1, -1
+    lam[3][0, 2] = lam[3][2, 0] = 1
+    lam[4][0, 2], lam[4][2, 0] = -1j, 1j
+    lam[5][1, 2] = lam[5][2, 1] = 1
+    lam[6][1, 2], lam[6][2, 1] = -1j, 1j
+    lam[7][0, 0] = lam[7][1, 1] = 1 / np.sqrt(3)
+    lam[7][2, 2] = -2 / np.sqrt(3)
+    return lam
+
+
+def _expm_antihermitian(X: np.ndarray) -> np.ndarray:
+    """exp(X) for a batch of small matrices: scaling and squaring (2^-4) with a
+    degree-8 Taylor polynomial; for ||X|| < 2 the truncation is below 1e-14
+    and the re-unitarisation that follows removes it from the group."""
+    s = 4
+    Y = X / (1 << s)
+    n = X.shape[-1]
+    eye = np.broadcast_to(np.eye(n, dtype=X.dtype), X.shape)
+    E = eye.copy()
+    term = eye.copy()
+    for k in range(1, 9):
+        term = np.matmul(term, Y) / k
+        E = E + term
+    for _ in range(s):
+        E = np.matmul(E, E)
+    return E
+
+
+def reunitarise(U: np.ndarray) -> np.ndarray:
+    """Project a batch of near-SU(3) matrices onto SU(3): orthonormalise
+    rows 0 and 1, then row 2 = conj(row0 x row1)."""
+    r0 = U[..., 0, :]
+    r0 = r0 / np.linalg.norm(r0, axis=-1, keepdims=True)
+    r1 = U[..., 1, :]
+    r1 = r1 - np.sum(np.conj(r0) * r1, axis=-1, keepdims=True) * r0
+    r1 = r1 / np.linalg.norm(r1, axis=-1, keepdims=True)
+    r2 = np.conj(np.cross(r0, r1))
+    return np.stack([r0, r1, r2], axis=-2)
+
+
+def su3_links(dims, eps: float = 0.3, seed: int = 1) -> np.ndarray:
+    """Seeded gauge field U_mu(x) = exp(i eps sum_a c_a lambda_a / 2), [V, 4, 3, 3]."""
+    V = volume(dims)
+    n = 4 * V
+    rng = np.random.default_rng(seed)
+    lam = gell_mann() / 2
+    out = np.empty((n, 3, 3), dtype=np.complex128)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        c = rng.standard_normal((b - a, 8))
+        H = np.einsum("na,aij->nij", c, lam)
+        out[a:b] = reunitarise(_expm_antihermitian(1j * eps * H))
+    return out.reshape(V, 4, 3, 3)
+
+
+def unit_links(dims) -> np.ndarray:
+    """Free field: every link is the identity."""
+    V = volume(dims)
+    U = np.zeros((V, 4, 3, 3), dtype=np.complex128)
+    U[..., 0, 0] = U[..., 1, 1] = U[..., 2, 2] = 1
+    return U
+
+
+def random_su3(n: int, seed: int) -> np.ndarray:
+    """n Haar-like random SU(3) matrices (QR of complex Gaussians, phase-fixed)."""
+    rng = np.random.default_rng(seed)
+    Z = (rng.standard_normal((n, 3, 3)) + 1j * rng.standard_normal((n, 3, 3))) / np.sqrt(2)
+    Q, R = np.linalg.qr(Z)
+    d = np.diagonal(R, axis1=-2, axis2=-1)
+    Q = Q * (d / np.abs(d))[:, None, :]
+    det = np.linalg.det(Q)
+    Q[:, :, 2] = Q[:, :, 2] / det[:, None]  # det 1; column scale by a unit phase keeps unitarity
+    return Q
+
+
+def gaussian_spinor(n_sites: int, seed: int) -> np.ndarray:
+    """Complex Gaussian spinor field [n_sites, 3, 4] with E|z|^2 = 1."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal((n_sites, 3, 4))
+    im = rng.standard_normal((n_sites, 3, 4))
+    return (re + 1j * im) / np.sqrt(2)
+
+
+def point_source(dims, site: int, colour: int, spin: int) -> np.ndarray:
+    """delta_{x, site} delta_{c, colour} delta_{s, spin}, [V, 3, 4]."""
+    b = np.zeros((volume(dims), 3, 4), dtype=np.complex128)
+    b[site, colour, spin] = 1
+    return b
+
+
+def coords(dims) -> np.ndarray:
+    """Coordinates (x, y, z, t) of every lex site, shape [V, 4]."""
+    Lx, Ly, Lz, Lt = (int(d) for d in dims)
+    t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly), np.arange(Lx),
+                             indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel(), t.ravel()], axis=1)
+
+
+def parity_sites(dims, parity: int) -> np.ndarray:
+    """Lex indices of the sites of one parity, in half-lattice order (lex // 2)."""
+    c = coords(dims)
+    return np.nonzero(c.sum(axis=1) % 2 == parity)[0]
+
+
+def to_half(full: np.ndarray, dims, parity: int) -> np.ndarray:
+    return np.ascontiguousarray(full[parity_sites(dims, parity)])
+
+
+def from_halves(even: np.ndarray, odd: np.ndarray, dims) -> np.ndarray:
+    out = np.empty((volume(dims),) + even.shape[1:], dtype=even.dtype)
+    out[parity_sites(dims, 0)] = even
+    out[parity_sites(dims, 1)] = odd
+    return out

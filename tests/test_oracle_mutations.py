@@ -1,0 +1,49 @@
+"""The oracle's pins have teeth: plant a plausible mistake in a copy of the
+oracle source (on the CPU, in a temporary directory), build it, and check
+that the pins of ``test_oracle_pins.py`` reject it.  The real oracle is
+never modified."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "wilson_oracle.c")
+
+# (description, original text, planted text)
+MUTANTS = [
+    ("projector sign swapped", "double sf = dagger ? +1.0 : -1.0;",
+     "double sf = dagger ? -1.0 : +1.0;"),
+    ("backward hop uses U instead of U^dag", "sum += wb * conj(Ub[3 * b + a])",
+     "sum += wb * Ub[3 * a + b]"),
+    ("backward phase not conjugated", "wb = conj(ph);", "wb = ph;"),
+    ("forward link taken at x+mu", "const cplx *Uf = U + (site * 4 + mu) * 9;",
+     "const cplx *Uf = U + (lf * 4 + mu) * 9;"),
+    ("kappa^2 dropped in the Schur operator", "out[i] = in[i] - kappa * kappa * t[i];",
+     "out[i] = in[i] - kappa * t[i];"),
+    ("literal 2 kappa in the schur reconstruction", "xq[i] = bq[i] + kappa * hx[i];",
+     "xq[i] = 2 * kappa * bq[i] + kappa * hx[i];"),
+    ("CGNR beta inverted", "double beta = nz1 / nz;", "double beta = nz / nz1;"),
+    ("gamma_x sign slip", "g[0][3] = I;  g[1][2] = I;", "g[0][3] = -I;  g[1][2] = I;"),
+]
+
+FAST_PINS = ("test_gamma_basis_clifford or test_free_field_plane_waves or "
+             "test_gamma5_hermiticity or test_gauge_covariance or "
+             "test_schur_blocks_dense or test_cgnr_schur_solve_matches_lu")
+
+
+@pytest.mark.parametrize("desc,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_mutant(tmp_path, desc, orig, planted):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation anchor not found: {orig}"
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(orig, planted))
+    lib = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", str(mut), "-o",
+                    str(lib), "-lm"], check=True)
+    env = dict(os.environ, WD_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", FAST_PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and "1 failed" in r.stdout, (desc, r.stdout[-2000:])
