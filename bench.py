@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the Wilson-Dirac hot path on GB300.
+
+One step = one complete even-odd solve D x = b to an FP64 true residual
+||b - D x|| / ||b|| <= 1e-10 (Schur preparation, CGNR with FP64 reliable
+updates in the workload's storage precision, reconstruction, FP64 true
+residual) on a 32^3 x 64 lattice with inputs resident in HBM.
+
+Printed as one JSON line:
+  value         whole-solve throughput: algorithmic bytes of every kernel of
+                the solve / solve time (GB/s); ms_per_step is the time to a
+                1e-10 residual
+  roofline      the hopping-term kernel alone (launched back to back through
+                wd_dslash_resident, CUDA events on its stream) against the
+                measured HBM copy bandwidth
+  fp64_cg_ms    the same solve with plain FP64 even-odd CGNR on the same GPU
+  e2e           the solve through wd_solve_cg_host: b and x in pinned host
+                memory, host<->device copies inside the timed region
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+
+Multi-GPU (torchrun): independent replicas, one per GPU, each with its own
+source (there is no data exchange on this path); value sums the ranks' bytes
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as syn  # noqa: E402
+
+METRIC = "Dslash GB/s vs HBM peak; time to 1e-10 residual, chosen vs plain FP64 CG"
+DEFAULT_WORKLOAD = "wilson_32x32x32x64_f16r12"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(syn.WORKLOADS))
+    ap.add_argument("--dslash-launches", type=int, default=200)
+    ap.add_argument("--no-fp64-cg", action="store_true",
+                    help="skip the plain FP64 CG comparison solve (reported as null)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def combine_ranks(elapsed_ms: float, bytes_total: float, launches: int):
+    """Replicas-only aggregation: the slowest rank's time, the sum of every
+    rank's bytes and kernel launches (no data moves between ranks)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return elapsed_ms, bytes_total, launches
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([bytes_total, float(launches)], device=dev, dtype=torch.float64)
+    dist.all_reduce(s)
+    return float(t.item()), float(s[0].item()), int(s[1].item())
+
+
+def fp64_schur_bytes(vh: int) -> float:
+    """Compulsory bytes of one FP64 Schur application: two hops (in 24 + out 24 +
+    8 links x 18 reals per site, plus 24 for the xpay input on the second)."""
+    return 8.0 * vh * ((48 + 144) + (48 + 144 + 24))
+
+
+def cpu_baseline(w, U, b, seconds_target=15.0):
+    """Time the FP64 oracle's Schur operator on the host cores (bounded sample)."""
+    import oracle
+    half = syn.to_half(b, w.dims, 1)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle.apply_eo(half, U, w.dims, w.kappa, w.phase, 1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds_target or n >= 8 or el * (n + 1) / n > 2 * seconds_target:
+            break
+    return {"value": fp64_schur_bytes(w.vh) * n / el / 1e9, "unit": "GB/s",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} FP64 Schur-operator applications (2 hops each) of the oracle on "
+                      f"{'x'.join(map(str, w.dims))}, {el:.1f} s; bytes counted as the FP64 "
+                      f"compulsory traffic"}
+
+
+def run_reference(args, w, rank, world):
+    """The oracle arm: the same metric and unit from the FP64 CPU oracle."""
+    if rank != 0:
+        return
+    import oracle
+    U = syn.su3_links(w.dims, eps=w.eps, seed=w.gauge_seed)
+    b = syn.gaussian_spinor(w.volume, w.source_seed)
+    half = syn.to_half(b, w.dims, 1)
+    for _ in range(args.warmup):
+        oracle.apply_eo(half, U, w.dims, w.kappa, w.phase, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply_eo(half, U, w.dims, w.kappa, w.phase, 1)
+    el = time.perf_counter() - t0
+    value = fp64_schur_bytes(w.vh) * args.steps / el / 1e9
+    sample = (f"each step one FP64 Schur-operator application (two hops) of the oracle on "
+              f"{'x'.join(map(str, w.dims))}; a full solve needs ~4 per CGNR iteration")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lattice": "x".join(map(str, w.dims)),
+                       "kappa": w.kappa},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse_args()
+    w = syn.WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1401_2039_gb300 import WilsonDirac
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # inputs: the gauge field is shared, each replica solves its own source
+    U_np = syn.su3_links(w.dims, eps=w.eps, seed=w.gauge_seed)
+    b_np = syn.gaussian_spinor(w.volume, w.source_seed + rank)
+    U = torch.from_numpy(U_np).cuda()
+    b = torch.from_numpy(b_np).cuda()
+    stream = torch.cuda.Stream()
+    op = WilsonDirac(w.dims, w.kappa, w.phase, prec=w.prec, recon=w.recon, stream=stream)
+    op.set_gauge(U)
+    del U
+
+    def solve():
+        return op.solve(b, tol=w.tol, maxiter=20000)
+
+    for _ in range(args.warmup):
+        res = solve()
+    try:
+        dev_id = str(torch.cuda.get_device_properties(local).uuid)
+        dev_id = dev_id if dev_id.startswith("GPU-") else "GPU-" + dev_id
+    except Exception:
+        dev_id = None
+
+    # ---- timed region: K solves
+    infos = []
+    with ClockSampler(dev_id) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            infos.append(solve().info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        host_s = time.perf_counter() - t0
+        barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    bytes_total = sum(i["bytes"] for i in infos)
+    launches = int(sum(i["launches"] for i in infos))
+    worst_resid = max(i["true_rel_resid"] for i in infos)
+    elapsed_ms, bytes_total, launches = combine_ranks(elapsed_ms, bytes_total, launches)
+    value = bytes_total / (elapsed_ms / 1e3) / 1e9
+
+    # ---- hopping term alone: back-to-back launches on the handle's work stream
+    peak, peak_kind = peaks()
+    ws = torch.cuda.ExternalStream(op.work_stream)
+    half = torch.from_numpy(syn.to_half(b_np, w.dims, 0)).cuda()
+    op.field_load(0, half)
+    op.field_load(1, half)
+    for i in range(10):
+        op.dslash_resident(i & 1, 1 - (i & 1))
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(ws)
+    n_d = args.dslash_launches
+    for i in range(n_d):   # ping-pong: slot i%2 -> slot 1 - i%2, parity alternating
+        op.dslash_resident(i & 1, 1 - (i & 1))
+    d1.record(ws)
+    torch.cuda.synchronize()
+    dslash_us = d0.elapsed_time(d1) * 1e3 / n_d
+    achieved = op.dslash_bytes / (dslash_us * 1e-6) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        traffic = tr.get(f"{w.name}")
+
+    # ---- plain FP64 even-odd CGNR on the same GPU, same problem
+    fp64_ms = None
+    fp64_iters = None
+    if not args.no_fp64_cg:
+        op64 = WilsonDirac(w.dims, w.kappa, w.phase, prec="f64", recon=18, stream=stream)
+        op64.set_gauge(torch.from_numpy(U_np).cuda())
+        op64.solve(b, tol=w.tol, maxiter=40000)            # warm-up (graphs, caches)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        r64 = op64.solve(b, tol=w.tol, maxiter=40000)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = f0.elapsed_time(f1)
+        fp64_iters = r64.info["iters"]
+        op64.close()
+
+    # ---- end to end through the host-memory entry point
+    bh = torch.from_numpy(b_np).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    op.solve_host(xh, bh, tol=w.tol)
+    torch.cuda.synchronize()
+    n_e2e = max(1, min(args.steps, 3))
+    e_bytes = 0.0
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        xh.zero_()
+        e_bytes += op.solve_host(xh, bh, tol=w.tol).info["bytes"]
+    e2e_s = time.perf_counter() - t0
+    e2e_value = e_bytes / e2e_s / 1e9
+    spinor_bytes = w.volume * 12 * 16
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, U_np, b_np)
+
+    if rank == 0:
+        ms = elapsed_ms / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if w.prec != "f64" else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lattice": "x".join(map(str, w.dims)),
+                       "kappa": w.kappa, "storage": w.prec, "link_reals": w.recon,
+                       "solver": "even-odd CGNR, FP64 reliable updates",
+                       "tol": w.tol, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (gauge field and spinors > 129 MB)"},
+            "time_to_solution_ms": ms,
+            "iters": infos[-1]["iters"], "reliable_updates": infos[-1]["reliable_updates"],
+            "true_rel_resid": worst_resid,
+            "fp64_cg_ms": fp64_ms, "fp64_cg_iters": fp64_iters,
+            "speedup_vs_fp64_cg": (fp64_ms / ms) if fp64_ms else None,
+            "host_wall_ms_per_step": host_s / args.steps * 1e3,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": f"k_dslash<{w.prec},{w.recon}> (plain hop)",
+                         "launch_us": dslash_us, "peak_kind": peak_kind,
+                         "bytes_per_launch": op.dslash_bytes},
+            "dslash_gflops": 1320.0 * w.vh / (dslash_us * 1e-6) / 1e9,
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 2 * spinor_bytes,
+                    "d2h_bytes_per_step": spinor_bytes, "ms_per_step": e2e_s / n_e2e * 1e3},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    op.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * libwd: Wilson-Dirac operator, its even-odd Schur form and the CGNR solve
+ * on one GB300 GPU (sm_103a).
+ *
+ * The operation (Barthou et al., arXiv:1401.2039):
+ *   D = I - kappa * H                                       Fig. "dirac", mu = 0
+ *   (H psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x)       phi_mu  psi(x+mu)
+ *                        + (1 + gamma_mu) U_mu(x-mu)^dag phi_mu* psi(x-mu) ]
+ * with 4x4 gamma matrices in the DeGrand-Rossi basis (the paper fixes only
+ * their algebra, Fig. "id"), 3x3 SU(3) links U (U[s x d]^dag = U[(s+d) x -d],
+ * Fig. "id") and a complex boundary phase phi_mu applied to hops that wrap
+ * around the lattice in direction mu (conjugated on backward hops; the
+ * paper's isPeriodic(L) = true is phi = 1).
+ *   Schur operator on parity p (Alg. "schur", D11 = D22 = I):
+ *     Mhat_p = I - kappa^2 P_p H P_q^t P_q H P_p^t,  q = 1 - p
+ *   Solve (goal "xx = Dirac^-1 bb" with templates "CGNR schur"):
+ *     bhat_p = b_p + kappa P_p H b_q; CGNR (Alg. "CGNR") on Mhat_p x_p = bhat_p;
+ *     x_q = b_q + kappa P_q H x_p.
+ *
+ * Canonical layout of every array crossing this boundary (complex128 =
+ * two doubles, re then im), all of them DEVICE pointers unless a function
+ * says otherwise:
+ *   site index  lex = ((t*Lz + z)*Ly + y)*Lx + x;  parity (x+y+z+t) % 2
+ *   spinor      [V][3 colour][4 spin] complex128   (full lattice, V sites)
+ *   half spinor [V/2][3][4] complex128, entry lex/2 of each site of one parity
+ *   gauge field [V][4 mu][3 row][3 col] complex128, mu = x, y, z, t
+ * The caller owns every array it passes; calls never keep a pointer to
+ * them.  The operator handle owns its packed copies (structure-of-arrays,
+ * even-odd ordered, in its storage precision) and all workspace, allocated
+ * by wd_op_create; apply and solve calls allocate nothing.
+ *
+ * Streams: every call is ordered after the work already queued on the
+ * stream given to wd_op_create (NULL = the legacy default stream) and the
+ * work it queues completes before later work on that stream.  Calls on one
+ * handle must not run concurrently from several host threads.
+ *
+ * Errors: every int-returning call returns a wd_status; none aborts or
+ * exits.  wd_last_error() describes the last failure of the calling thread.
+ */
+#ifndef WD_H
+#define WD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_op wd_op;
+
+typedef enum {
+    WD_OK = 0,
+    WD_ERR_ARG = 1,            /* null pointer, bad parity/flag/precision/recon   */
+    WD_ERR_DIMS = 2,           /* a lattice extent odd or < 2, or too large       */
+    WD_ERR_CUDA = 3,           /* a CUDA runtime call failed                      */
+    WD_ERR_NOMEM = 4,          /* device allocation failed                        */
+    WD_ERR_NOT_CONVERGED = 5,  /* solver reached maxiter                          */
+    WD_ERR_BREAKDOWN = 6,      /* NaN/Inf or a zero denominator in the solver     */
+    WD_ERR_TIMEOUT = 7,        /* a bounded device wait gave up                   */
+    WD_ERR_STATE = 8           /* call out of order (e.g. no gauge field loaded)  */
+} wd_status;
+
+typedef enum { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_BF16 = 3 } wd_prec;
+
+/* Create an operator for a Lx x Ly x Lz x Lt lattice.
+ *   dims   host int[4] {Lx, Ly, Lz, Lt}; every extent even and >= 2
+ *   kappa  hopping parameter (any real; kappa = 0 gives D = I)
+ *   phase  host double[8]: (re, im) of phi_mu for mu = x, y, z, t
+ *   prec   storage precision of the operator applications and of the
+ *          inner solver iterations (WD_F64: plain FP64 throughout;
+ *          WD_F32/F16/BF16: low-precision storage, FP32 arithmetic,
+ *          FP64 reliable updates in wd_solve_cg)
+ *   recon  18 (full links) or 12 (two rows stored, third row rebuilt as
+ *          conj(row0 x row1), valid for SU(3) links)
+ *   stream cudaStream_t to order work on, or NULL for the legacy stream
+ * Allocates every device buffer the handle will need. */
+int wd_op_create(wd_op **op, const int dims[4], double kappa, const double phase[8],
+                 int prec, int recon, void *stream);
+void wd_op_destroy(wd_op *op);
+
+/* Load (copy, pack, convert) the gauge field; U is a device pointer in the
+ * canonical [V][4][3][3] complex128 layout.  With recon = 12 the links must
+ * be SU(3) for the results to match the 18-real operator. */
+int wd_op_set_gauge(wd_op *op, const double *U);
+
+/* out = D in (dagger: D^dag in), full lattice, canonical spinors (Fig. "dirac"). */
+int wd_apply(wd_op *op, double *out, const double *in, int dagger);
+
+/* out = Mhat_p in (dagger: Mhat_p^dag in) on half-lattice spinors of parity p
+ * (Alg. "schur": D22 - D21 D11^-1 D12 for p = 1). */
+int wd_apply_eo(wd_op *op, double *out, const double *in, int parity, int dagger);
+
+/* out = P_p H P_q^t in (dagger: the same with H^dag): the hopping term from
+ * parity q = 1 - p onto parity p, half-lattice canonical spinors. */
+int wd_dslash_eo(wd_op *op, double *out, const double *in, int out_parity, int dagger);
+
+typedef struct {
+    int iters;               /* inner CGNR iterations                             */
+    int reliable_updates;    /* FP64 residual recomputations                      */
+    double true_rel_resid;   /* ||b - D x|| / ||b|| in FP64 on the full lattice    */
+    double seconds;          /* host wall time of the call                         */
+    double dslash_lo;        /* hopping-term applications in storage precision     */
+    double dslash_hi;        /* hopping-term applications in FP64                  */
+    double bytes;            /* algorithmic device bytes moved by the solve        */
+    double launches;         /* kernels launched (directly or inside CUDA graphs)  */
+} wd_solve_info;
+
+/* Solve D x = b (goal "xx = Dirac^-1 bb", templates "CGNR schur") to
+ * ||b - D x|| / ||b|| <= tol, judged by an FP64 true residual.
+ *   x       device, full canonical spinor; on entry its parity-p part is the
+ *           initial guess (zeros for none), on exit the solution
+ *   b       device, full canonical spinor
+ *   parity  the parity CGNR works on (1 = odd, as in Alg. "schur")
+ *   info    may be NULL
+ * Returns WD_OK, WD_ERR_NOT_CONVERGED (x holds the last iterate) or
+ * WD_ERR_BREAKDOWN.  Blocks the calling thread until the solve is done. */
+int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, int maxiter,
+                int parity, wd_solve_info *info);
+
+/* The same solve with x and b in HOST memory (pageable or pinned); the
+ * host<->device copies go through buffers the handle owns. */
+int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
+                     int maxiter, int parity, wd_solve_info *info);
+
+/* Resident fields for timing the hopping term alone: slot 0 and 1 are two
+ * half-lattice spinors the handle owns, in its internal layout and storage
+ * precision.  wd_field_load packs a canonical half spinor (device) into a
+ * slot, wd_field_store unpacks it, wd_dslash_resident computes
+ * slot[1 - in_slot] = P_p H P_q^t slot[in_slot] with no layout conversion. */
+int wd_field_load(wd_op *op, int slot, const double *half_in);
+int wd_field_store(wd_op *op, int slot, double *half_out);
+int wd_dslash_resident(wd_op *op, int in_slot, int out_parity, int dagger);
+
+/* Stream the handle queues its work on (a cudaStream_t). */
+void *wd_op_stream(wd_op *op);
+
+/* Algorithmic (compulsory) bytes of one single-parity hopping-term launch in
+ * the handle's storage precision: Vh * (24 in + 24 out + 8 links * recon)
+ * reals. */
+double wd_dslash_bytes(const wd_op *op);
+
+const char *wd_status_string(int status);
+const char *wd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WD_H */

@@ -27,7 +27,7 @@ import numpy as np
 from .build import build_oracle, library_path
 
 __all__ = [
-    "gamma", "hop", "apply", "apply_eo", "hop_eo", "schur_prepare",
+    "gamma", "hop", "hop_sites", "apply", "apply_eo", "hop_eo", "schur_prepare",
     "schur_reconstruct", "cgnr", "solve", "dense_matrix", "num_threads",
     "build_oracle",
 ]
@@ -44,6 +44,8 @@ def _load():
         ip = ctypes.POINTER(ctypes.c_int)
         lib.oracle_gamma.argtypes = [ctypes.c_int, dp]
         lib.oracle_hop.argtypes = [dp, dp, dp, ip, dp, ctypes.c_int]
+        lib.oracle_hop_sites.argtypes = [dp, dp, dp, ip, dp, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_long), ctypes.c_long]
         lib.oracle_apply.argtypes = [dp, dp, dp, ip, ctypes.c_double, dp, ctypes.c_int]
         lib.oracle_apply_eo.argtypes = [dp, dp, dp, ip, ctypes.c_double, dp, ctypes.c_int, ctypes.c_int]
         lib.oracle_hop_eo.argtypes = [dp, dp, dp, ip, dp, ctypes.c_int, ctypes.c_int]
@@ -101,6 +103,17 @@ def hop(psi, U, dims, phase, dagger=False) -> np.ndarray:
     out = np.empty_like(psi)
     ph = _phase(phase)
     _load().oracle_hop(_dp(out), _dp(psi), _dp(U), _dims(dims), _dp(ph), int(bool(dagger)))
+    return out
+
+
+def hop_sites(psi, U, dims, phase, sites, dagger=False) -> np.ndarray:
+    """(H psi)(x) at the listed lex sites only, shape [len(sites), 3, 4]."""
+    psi, U = _c128(psi), _c128(U)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 3, 4), dtype=np.complex128)
+    ph = _phase(phase)
+    _load().oracle_hop_sites(_dp(out), _dp(psi), _dp(U), _dims(dims), _dp(ph), int(bool(dagger)),
+                             sites.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), len(sites))
     return out
 
 

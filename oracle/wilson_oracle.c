@@ -112,16 +112,11 @@ static long coord_to_lex(const geom *g, const int c[4]) {
 static int parity_of(const int c[4]) { return (c[0] + c[1] + c[2] + c[3]) & 1; }
 
 /* ---------------------------------------------------------------------- */
-/* Hopping term, full lattice: out = H in (dagger = 0) or H^dag in.        */
+/* Hopping term at one site: acc = (H in)(site) (or (H^dag in)(site)).     */
 /* H^dag swaps the projectors: (1 - gamma) <-> (1 + gamma) (gamma hermitian,
  * the adjoint of a forward hop is a backward hop with the adjoint link).   */
-void oracle_hop(double *out_, const double *in_, const double *U_,
-                const int *dims, const double *phase, int dagger) {
-    geom g = make_geom(dims);
-    cplx *out = (cplx *)out_;
-    const cplx *in = (const cplx *)in_;
-    const cplx *U = (const cplx *)U_;
-
+static void hop_site(const geom *g, long site, cplx acc[3][4], const cplx *in, const cplx *U,
+                     const double *phase, int dagger) {
     cplx proj_fwd[4][4][4], proj_bwd[4][4][4]; /* [mu][s][s'] */
     for (int mu = 0; mu < 4; ++mu) {
         cplx gm[4][4];
@@ -134,42 +129,60 @@ void oracle_hop(double *out_, const double *in_, const double *U_,
                 proj_bwd[mu][s][t] = id - sf * gm[s][t];
             }
     }
+    int c[4];
+    lex_to_coord(g, site, c);
+    memset(acc, 0, 12 * sizeof(cplx));
+    for (int mu = 0; mu < 4; ++mu) {
+        cplx ph = phase[2 * mu] + I * phase[2 * mu + 1];
+        /* forward neighbour x + mu */
+        int cf[4] = {c[0], c[1], c[2], c[3]};
+        cplx wf = 1.0;
+        cf[mu] += 1;
+        if (cf[mu] == g->L[mu]) { cf[mu] = 0; wf = ph; }
+        /* backward neighbour x - mu */
+        int cb[4] = {c[0], c[1], c[2], c[3]};
+        cplx wb = 1.0;
+        cb[mu] -= 1;
+        if (cb[mu] < 0) { cb[mu] = g->L[mu] - 1; wb = conj(ph); }
+        long lf = coord_to_lex(g, cf), lb = coord_to_lex(g, cb);
+        const cplx *Uf = U + (site * 4 + mu) * 9; /* U_mu(x)      */
+        const cplx *Ub = U + (lb * 4 + mu) * 9;   /* U_mu(x - mu) */
+        const cplx *pf = in + lf * 12, *pb = in + lb * 12;
+        /* (U (x) P) V = U . V . P^t, V = 3x4 colour-by-spin matrix */
+        for (int a = 0; a < 3; ++a)
+            for (int s = 0; s < 4; ++s) {
+                cplx sum = 0;
+                for (int b = 0; b < 3; ++b)
+                    for (int t = 0; t < 4; ++t) {
+                        sum += wf * Uf[3 * a + b] * proj_fwd[mu][s][t] * pf[4 * b + t];
+                        sum += wb * conj(Ub[3 * b + a]) * proj_bwd[mu][s][t] * pb[4 * b + t];
+                    }
+                acc[a][s] += sum;
+            }
+    }
+}
 
+/* Hopping term, full lattice: out = H in (dagger = 0) or H^dag in.        */
+void oracle_hop(double *out_, const double *in_, const double *U_,
+                const int *dims, const double *phase, int dagger) {
+    geom g = make_geom(dims);
 #pragma omp parallel for schedule(static)
     for (long site = 0; site < g.vol; ++site) {
-        int c[4];
-        lex_to_coord(&g, site, c);
         cplx acc[3][4];
-        memset(acc, 0, sizeof(acc));
-        for (int mu = 0; mu < 4; ++mu) {
-            cplx ph = phase[2 * mu] + I * phase[2 * mu + 1];
-            /* forward neighbour x + mu */
-            int cf[4] = {c[0], c[1], c[2], c[3]};
-            cplx wf = 1.0;
-            cf[mu] += 1;
-            if (cf[mu] == g.L[mu]) { cf[mu] = 0; wf = ph; }
-            /* backward neighbour x - mu */
-            int cb[4] = {c[0], c[1], c[2], c[3]};
-            cplx wb = 1.0;
-            cb[mu] -= 1;
-            if (cb[mu] < 0) { cb[mu] = g.L[mu] - 1; wb = conj(ph); }
-            long lf = coord_to_lex(&g, cf), lb = coord_to_lex(&g, cb);
-            const cplx *Uf = U + (site * 4 + mu) * 9; /* U_mu(x)      */
-            const cplx *Ub = U + (lb * 4 + mu) * 9;   /* U_mu(x - mu) */
-            const cplx *pf = in + lf * 12, *pb = in + lb * 12;
-            /* (U (x) P) V = U . V . P^t, V = 3x4 colour-by-spin matrix */
-            for (int a = 0; a < 3; ++a)
-                for (int s = 0; s < 4; ++s) {
-                    cplx sum = 0;
-                    for (int b = 0; b < 3; ++b)
-                        for (int t = 0; t < 4; ++t) {
-                            sum += wf * Uf[3 * a + b] * proj_fwd[mu][s][t] * pf[4 * b + t];
-                            sum += wb * conj(Ub[3 * b + a]) * proj_bwd[mu][s][t] * pb[4 * b + t];
-                        }
-                    acc[a][s] += sum;
-                }
-        }
-        memcpy(out + site * 12, acc, sizeof(acc));
+        hop_site(&g, site, acc, (const cplx *)in_, (const cplx *)U_, phase, dagger);
+        memcpy((cplx *)out_ + site * 12, acc, sizeof(acc));
+    }
+}
+
+/* The same at the n listed lex sites only: out[k] = (H in)(sites[k]).      */
+void oracle_hop_sites(double *out_, const double *in_, const double *U_, const int *dims,
+                      const double *phase, int dagger, const long *sites, long n) {
+    geom g = make_geom(dims);
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < n; ++k) {
+        cplx acc[3][4];
+        hop_site(&g, sites[k], acc, (const cplx *)in_, (const cplx *)U_, phase, dagger);
+        memcpy((cplx *)out_ + k * 12, acc, sizeof(acc));
     }
 }
 

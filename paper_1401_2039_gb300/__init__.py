@@ -1,0 +1,9 @@
+"""GB300-native Wilson-Dirac hot path (arXiv:1401.2039): hopping term,
+even-odd Schur operator and CGNR solve with mixed-precision reliable
+updates, all in the CUDA library libwd (include/wd.h)."""
+from .build import build_library  # noqa: F401
+from .wd import (PRECISIONS, SolveInfo, SolveResult, WDError, WilsonDirac,  # noqa: F401
+                 load_library)
+
+__all__ = ["WilsonDirac", "WDError", "SolveInfo", "SolveResult", "PRECISIONS", "build_library",
+           "load_library"]

@@ -1,0 +1,255 @@
+// Vector kernels of the Krylov solver (Alg. "CGNR" lines on x, r, p and
+// the norms), fused so that each touches every vector once, plus the
+// precision conversions of the reliable updates.
+//
+// Spinor fields are whole 16-byte planes (no tail), so the element-wise
+// kernels walk the flat array of 16-byte chunks (NF * stride of them;
+// the zero padding of each plane stays zero under every update).  Norms
+// accumulate in FP64 and finish with the deterministic last-block sum.
+#include "wd_internal.cuh"
+
+namespace wd {
+
+constexpr int BLAS_BLOCK = 256;
+constexpr int BLAS_MAX_GRID = 152 * 8;
+
+template <typename S, typename R> struct Chunk {
+    static constexpr int K = 16 / (int)sizeof(S);  // reals per 16-byte chunk
+    __device__ __forceinline__ static void load(const void *base, long i, R *r) {
+        uint4 v = ld_v4((const char *)base + i * 16);
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        Words<S, R>::unpack(w, r, K);
+    }
+    __device__ __forceinline__ static void store(void *base, long i, const R *r) {
+        uint32_t w[4];
+        Words<S, R>::pack(r, w, K);
+        st_v4((char *)base + i * 16, make_uint4(w[0], w[1], w[2], w[3]));
+    }
+};
+
+inline long spinor_chunks(int prec, const Geom &g) {
+    return (long)(24 * prec_bytes(prec) / 16) * g.stride;
+}
+
+inline unsigned blas_grid(long n) {
+    long b = (n + BLAS_BLOCK - 1) / BLAS_BLOCK;
+    if (b > BLAS_MAX_GRID) b = BLAS_MAX_GRID;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+int reduction_blocks(const Geom &g) {
+    long d = (g.vh + 127) / 128;
+    return (int)(d > BLAS_MAX_GRID ? d : BLAS_MAX_GRID);
+}
+
+// x += alpha p;  r -= alpha Ap;  ||r||^2  (alpha from the device scalars)
+template <typename S, typename R>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_cg_update_xr(long n, void *x, void *r, const void *p, const void *Ap, Reduction red) {
+    using C = Chunk<S, R>;
+    const R alpha = (R)red.scalars->alpha;
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        R xv[C::K], rv[C::K], pv[C::K], av[C::K];
+        C::load(x, i, xv);
+        C::load(r, i, rv);
+        C::load(p, i, pv);
+        C::load(Ap, i, av);
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < C::K; ++k) {
+            xv[k] += alpha * pv[k];
+            rv[k] -= alpha * av[k];
+            s += rv[k] * rv[k];
+        }
+        C::store(x, i, xv);
+        C::store(r, i, rv);
+        acc += (double)s;
+    }
+    block_reduce_finish<BLAS_BLOCK>(acc, red);
+}
+
+// p = z + beta p
+template <typename S, typename R>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_cg_update_p(long n, void *p, const void *z, const SolverScalars *sc) {
+    using C = Chunk<S, R>;
+    const R beta = (R)sc->beta;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        R pv[C::K], zv[C::K];
+        C::load(p, i, pv);
+        C::load(z, i, zv);
+#pragma unroll
+        for (int k = 0; k < C::K; ++k) pv[k] = zv[k] + beta * pv[k];
+        C::store(p, i, pv);
+    }
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_norm2(long n, const void *v, Reduction red) {
+    using C = Chunk<S, R>;
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        R a[C::K];
+        C::load(v, i, a);
+#pragma unroll
+        for (int k = 0; k < C::K; ++k) acc += (double)a[k] * (double)a[k];
+    }
+    block_reduce_finish<BLAS_BLOCK>(acc, red);
+}
+
+// out = x - y and ||out||^2, FP64
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_xmy_norm(long n, double *out, const double *x, const double *y, Reduction red) {
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        double2 a = reinterpret_cast<const double2 *>(x)[i];
+        double2 b = reinterpret_cast<const double2 *>(y)[i];
+        double2 d = {a.x - b.x, a.y - b.y};
+        reinterpret_cast<double2 *>(out)[i] = d;
+        acc += d.x * d.x + d.y * d.y;
+    }
+    block_reduce_finish<BLAS_BLOCK>(acc, red);
+}
+
+// out (precision SO) = scale * in (precision SI), one site per thread.
+template <typename SO, typename SI>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_convert_scaled(long vh, long stride, void *out, const void *in, const double *scale_dev,
+                 double scale_host) {
+    const double sc = scale_dev ? *scale_dev : scale_host;
+    for (long h = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; h < vh;
+         h += (long)gridDim.x * BLAS_BLOCK) {
+        double v[24];
+        Rec<SI, 24>::template load_coherent<double>(in, stride, h, v);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[i] *= sc;
+        Rec<SO, 24>::store(out, stride, h, v);
+    }
+}
+
+// x_hi += inv_scale * x_lo;  x_lo = 0
+template <typename S>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_fold_x(long vh, long stride, double *x_hi, void *x_lo, const double *inv_scale) {
+    const double is = *inv_scale;
+    for (long h = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; h < vh;
+         h += (long)gridDim.x * BLAS_BLOCK) {
+        double lo[24], hi[24];
+        Rec<S, 24>::template load_coherent<double>(x_lo, stride, h, lo);
+        Rec<double, 24>::template load_coherent<double>(x_hi, stride, h, hi);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            hi[i] += is * lo[i];
+            lo[i] = 0.0;
+        }
+        Rec<double, 24>::store(x_hi, stride, h, hi);
+        Rec<S, 24>::store(x_lo, stride, h, lo);
+    }
+}
+
+// p *= ratio and nz *= ratio^2: the Krylov direction follows a change of
+// the residual's scale.
+template <typename S, typename R>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_rescale(long n, void *p, SolverScalars *sc, const double *ratio_dev) {
+    using C = Chunk<S, R>;
+    const double ratio = *ratio_dev;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        R v[C::K];
+        C::load(p, i, v);
+#pragma unroll
+        for (int k = 0; k < C::K; ++k) v[k] *= (R)ratio;
+        C::store(p, i, v);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->nz *= ratio * ratio;
+}
+
+// ------------------------------------------------------------------ launchers
+#define WD_PREC_DISPATCH(prec, CALL)                                                    \
+    switch (prec) {                                                                     \
+    case WD_F64: { using S = double; using R = double; CALL; break; }                   \
+    case WD_F32: { using S = float; using R = float; CALL; break; }                     \
+    case WD_F16: { using S = __half; using R = float; CALL; break; }                    \
+    case WD_BF16: { using S = __nv_bfloat16; using R = float; CALL; break; }            \
+    default: return cudaErrorInvalidValue;                                              \
+    }
+
+cudaError_t launch_cg_update_xr(int prec, const Geom &g, void *x, void *r, const void *p,
+                                const void *Ap, const Reduction &red, cudaStream_t s) {
+    const long n = spinor_chunks(prec, g);
+    WD_PREC_DISPATCH(prec, (k_cg_update_xr<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(
+                               n, x, r, p, Ap, red)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update_p(int prec, const Geom &g, void *p, const void *z,
+                               const SolverScalars *sc, cudaStream_t s) {
+    const long n = spinor_chunks(prec, g);
+    WD_PREC_DISPATCH(prec, (k_cg_update_p<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, p, z, sc)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction &red,
+                         cudaStream_t s) {
+    const long n = spinor_chunks(prec, g);
+    WD_PREC_DISPATCH(prec, (k_norm2<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, v, red)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xmy_norm(const Geom &g, double *out, const double *x, const double *y,
+                            const Reduction &red, cudaStream_t s) {
+    const long n = spinor_chunks(WD_F64, g);
+    k_xmy_norm<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, out, x, y, red);
+    return cudaGetLastError();
+}
+
+template <typename SO>
+static cudaError_t convert_from(int prec_in, void *out, const void *in, const Geom &g,
+                                const double *sd, double sh, cudaStream_t s) {
+    const unsigned grid = blas_grid(g.vh);
+    switch (prec_in) {
+    case WD_F64: k_convert_scaled<SO, double><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, out, in, sd, sh); break;
+    case WD_F32: k_convert_scaled<SO, float><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, out, in, sd, sh); break;
+    case WD_F16: k_convert_scaled<SO, __half><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, out, in, sd, sh); break;
+    case WD_BF16: k_convert_scaled<SO, __nv_bfloat16><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, out, in, sd, sh); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const void *in,
+                                  const Geom &g, const double *scale_dev, double scale_host,
+                                  cudaStream_t s) {
+    switch (prec_out) {
+    case WD_F64: return convert_from<double>(prec_in, out, in, g, scale_dev, scale_host, s);
+    case WD_F32: return convert_from<float>(prec_in, out, in, g, scale_dev, scale_host, s);
+    case WD_F16: return convert_from<__half>(prec_in, out, in, g, scale_dev, scale_host, s);
+    case WD_BF16: return convert_from<__nv_bfloat16>(prec_in, out, in, g, scale_dev, scale_host, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fold_x(int prec_lo, const Geom &g, double *x_hi, void *x_lo,
+                          const double *inv_scale_dev, cudaStream_t s) {
+    const unsigned grid = blas_grid(g.vh);
+    WD_PREC_DISPATCH(prec_lo, (k_fold_x<S><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo,
+                                                                         inv_scale_dev)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescale_lo(int prec_lo, const Geom &g, void *p, SolverScalars *sc,
+                              const double *ratio_dev, cudaStream_t s) {
+    const long n = spinor_chunks(prec_lo, g);
+    WD_PREC_DISPATCH(prec_lo, (k_rescale<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, p, sc,
+                                                                                     ratio_dev)));
+    return cudaGetLastError();
+}
+
+}  // namespace wd

@@ -1,0 +1,282 @@
+// Hopping term (Dslash) of the Wilson-Dirac operator, one output parity.
+//
+//   out(x) = sum_mu [ (1 + s_f gamma_mu) U_mu(x)        phi_mu  in(x+mu)
+//                   + (1 + s_b gamma_mu) U_mu(x-mu)^dag  phi_mu* in(x-mu) ]
+//   s_f = -1, s_b = +1 for H (Fig. "dirac"); swapped for H^dag.
+//
+// One thread per output site.  Each of the eight hops
+//   1. loads the neighbour's 24 reals (read-only path, L1/L2 reuse between
+//      the eight sites that read it),
+//   2. projects them onto the two independent spin rows of (1 +- gamma_mu)
+//      (rank 2, two entries per row from {+-1, +-i}, Sec. 4.2),
+//   3. multiplies the 3x2 half spinor by the link (streamed, not cached in
+//      L1; 12-real links rebuild the third row as conj(row0 x row1)),
+//   4. applies the boundary phase if the hop wrapped,
+//   5. expands back to four spin rows and accumulates.
+// Gamma matrices: DeGrand-Rossi basis (gamma_5 = diag(1, 1, -1, -1)).
+// Arithmetic type R = double for FP64 storage, float otherwise.
+#pragma once
+
+#include "wd_internal.cuh"
+
+namespace wd {
+
+template <typename R> struct cx { R re, im; };
+
+template <typename R>
+__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+// i * a
+template <typename R>
+__device__ __forceinline__ cx<R> cmuli(cx<R> a) { return {-a.im, a.re}; }
+
+// Half spinor h[spin row k][colour] from the 24 reals of a site, projector
+// 1 + SGN * gamma_MU.  psi real index = 2 * (4 * colour + spin) + (0 re | 1 im).
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void project(const R *psi, cx<R> h[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cx<R> p0 = {psi[8 * c + 0], psi[8 * c + 1]};
+        cx<R> p1 = {psi[8 * c + 2], psi[8 * c + 3]};
+        cx<R> p2 = {psi[8 * c + 4], psi[8 * c + 5]};
+        cx<R> p3 = {psi[8 * c + 6], psi[8 * c + 7]};
+        if (MU == 0) {          // gamma_x: rows (3, i) (2, i) (1, -i) (0, -i)
+            h[0][c] = SGN > 0 ? cadd(p0, cmuli(p3)) : csub(p0, cmuli(p3));
+            h[1][c] = SGN > 0 ? cadd(p1, cmuli(p2)) : csub(p1, cmuli(p2));
+        } else if (MU == 1) {   // gamma_y: rows (3, -1) (2, 1) (1, 1) (0, -1)
+            h[0][c] = SGN > 0 ? csub(p0, p3) : cadd(p0, p3);
+            h[1][c] = SGN > 0 ? cadd(p1, p2) : csub(p1, p2);
+        } else if (MU == 2) {   // gamma_z: rows (2, i) (3, -i) (0, -i) (1, i)
+            h[0][c] = SGN > 0 ? cadd(p0, cmuli(p2)) : csub(p0, cmuli(p2));
+            h[1][c] = SGN > 0 ? csub(p1, cmuli(p3)) : cadd(p1, cmuli(p3));
+        } else {                // gamma_t: rows (2, 1) (3, 1) (0, 1) (1, 1)
+            h[0][c] = SGN > 0 ? cadd(p0, p2) : csub(p0, p2);
+            h[1][c] = SGN > 0 ? cadd(p1, p3) : csub(p1, p3);
+        }
+    }
+}
+
+// acc += (1 + SGN gamma_MU) expanded from the transported half spinor u:
+// rows 0, 1 are u itself, rows 2, 3 are fixed multiples of u rows.
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void accumulate(R *acc, const cx<R> u[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cx<R> r2, r3;
+        if (MU == 0) {          // r2 = -SGN i u1, r3 = -SGN i u0
+            r2 = cmuli(u[1][c]); r3 = cmuli(u[0][c]);
+            if (SGN > 0) { r2 = {-r2.re, -r2.im}; r3 = {-r3.re, -r3.im}; }
+        } else if (MU == 1) {   // r2 = SGN u1, r3 = -SGN u0
+            r2 = u[1][c]; r3 = u[0][c];
+            if (SGN > 0) r3 = {-r3.re, -r3.im}; else r2 = {-r2.re, -r2.im};
+        } else if (MU == 2) {   // r2 = -SGN i u0, r3 = SGN i u1
+            r2 = cmuli(u[0][c]); r3 = cmuli(u[1][c]);
+            if (SGN > 0) r2 = {-r2.re, -r2.im}; else r3 = {-r3.re, -r3.im};
+        } else {                // r2 = SGN u0, r3 = SGN u1
+            r2 = u[0][c]; r3 = u[1][c];
+            if (SGN < 0) { r2 = {-r2.re, -r2.im}; r3 = {-r3.re, -r3.im}; }
+        }
+        acc[8 * c + 0] += u[0][c].re; acc[8 * c + 1] += u[0][c].im;
+        acc[8 * c + 2] += u[1][c].re; acc[8 * c + 3] += u[1][c].im;
+        acc[8 * c + 4] += r2.re;      acc[8 * c + 5] += r2.im;
+        acc[8 * c + 6] += r3.re;      acc[8 * c + 7] += r3.im;
+    }
+}
+
+// Link as 18 reals (row-major, re/im); 12-real records rebuild row 2.
+template <typename S, typename R, int RECON>
+__device__ __forceinline__ void load_link(const void *base, long stride, long h, R *U) {
+    Rec<S, RECON>::template load<R, 1>(base, stride, h, U);
+    if (RECON == 12) {
+        // row2 = conj(row0 x row1)
+        const R a0r = U[0], a0i = U[1], a1r = U[2], a1i = U[3], a2r = U[4], a2i = U[5];
+        const R b0r = U[6], b0i = U[7], b1r = U[8], b1i = U[9], b2r = U[10], b2i = U[11];
+        // (a1 b2 - a2 b1)^*
+        U[12] = (a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i);
+        U[13] = -((a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r));
+        // (a2 b0 - a0 b2)^*
+        U[14] = (a2r * b0r - a2i * b0i) - (a0r * b2r - a0i * b2i);
+        U[15] = -((a2r * b0i + a2i * b0r) - (a0r * b2i + a0i * b2r));
+        // (a0 b1 - a1 b0)^*
+        U[16] = (a0r * b1r - a0i * b1i) - (a1r * b0r - a1i * b0i);
+        U[17] = -((a0r * b1i + a0i * b1r) - (a1r * b0i + a1i * b0r));
+    }
+}
+
+// u[k][a] = sum_b U[a][b] h[k][b]
+template <typename R>
+__device__ __forceinline__ void su3_mul(const R *U, const cx<R> h[2][3], cx<R> u[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
+                re += ur * h[k][b].re - ui * h[k][b].im;
+                im += ur * h[k][b].im + ui * h[k][b].re;
+            }
+            u[k][a] = {re, im};
+        }
+}
+
+// u[k][a] = sum_b conj(U[b][a]) h[k][b]
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul(const R *U, const cx<R> h[2][3], cx<R> u[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R ur = U[2 * (3 * b + a)], ui = U[2 * (3 * b + a) + 1];
+                re += ur * h[k][b].re + ui * h[k][b].im;
+                im += ur * h[k][b].im - ui * h[k][b].re;
+            }
+            u[k][a] = {re, im};
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void phase_mul(cx<R> u[2][3], R pr, R pi) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R re = u[k][a].re * pr - u[k][a].im * pi;
+            const R im = u[k][a].re * pi + u[k][a].im * pr;
+            u[k][a] = {re, im};
+        }
+}
+
+template <typename R> struct DslashArgs {
+    Geom g;
+    const char *gauge_out;   // links of the output parity (4 direction blocks)
+    const char *gauge_in;    // links of the input parity
+    size_t dir_bytes;
+    void *out;
+    const void *in;
+    const void *x;
+    R scale;
+    R ph[8];
+    int parity;              // output parity
+    Reduction red;
+};
+
+template <typename S, typename R, int RECON, int MU, int DAG>
+__device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4], long h, R *acc) {
+    constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
+    constexpr int SB = -SF;
+    // forward hop: U_mu(x) in(x + mu)
+    {
+        int n[4] = {c[0], c[1], c[2], c[3]};
+        n[MU] += 1;
+        const bool wrap = (n[MU] == a.g.L[MU]);
+        if (wrap) n[MU] = 0;
+        const long hn = half_index(a.g, n);
+        R psi[24];
+        Rec<S, 24>::template load<R, 0>(a.in, a.g.stride, hn, psi);
+        cx<R> hs[2][3], u[2][3];
+        project<MU, SF>(psi, hs);
+        R U[18];
+        load_link<S, R, RECON>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, U);
+        su3_mul(U, hs, u);
+        if (wrap) phase_mul(u, a.ph[2 * MU], a.ph[2 * MU + 1]);
+        accumulate<MU, SF>(acc, u);
+    }
+    // backward hop: U_mu(x - mu)^dag in(x - mu)
+    {
+        int n[4] = {c[0], c[1], c[2], c[3]};
+        n[MU] -= 1;
+        const bool wrap = (n[MU] < 0);
+        if (wrap) n[MU] = a.g.L[MU] - 1;
+        const long hn = half_index(a.g, n);
+        R psi[24];
+        Rec<S, 24>::template load<R, 0>(a.in, a.g.stride, hn, psi);
+        cx<R> hs[2][3], u[2][3];
+        project<MU, SB>(psi, hs);
+        R U[18];
+        load_link<S, R, RECON>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, U);
+        su3_adj_mul(U, hs, u);
+        if (wrap) phase_mul(u, a.ph[2 * MU], -a.ph[2 * MU + 1]);
+        accumulate<MU, SB>(acc, u);
+    }
+}
+
+template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_dslash(const DslashArgs<R> a) {
+    const long h = (long)blockIdx.x * BLOCK + threadIdx.x;
+    double nrm = 0.0;
+    if (h < a.g.vh) {
+        int c[4];
+        site_coords(a.g, h, a.parity, c);
+        R acc[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) acc[i] = 0;
+        hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
+        hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
+        hop_pair<S, R, RECON, 2, DAG>(a, c, h, acc);
+        hop_pair<S, R, RECON, 3, DAG>(a, c, h, acc);
+        if (EPI == EPI_XPAY) {
+            R xv[24];
+            Rec<S, 24>::template load<R, 0>(a.x, a.g.stride, h, xv);
+#pragma unroll
+            for (int i = 0; i < 24; ++i) acc[i] = xv[i] + a.scale * acc[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) acc[i] *= a.scale;
+        }
+        Rec<S, 24>::store(a.out, a.g.stride, h, acc);
+        if (NORM) {
+            R s = 0;
+#pragma unroll
+            for (int i = 0; i < 24; ++i) s += acc[i] * acc[i];
+            nrm = (double)s;
+        }
+    }
+    if (NORM) block_reduce_finish<BLOCK>(nrm, a.red);
+}
+
+constexpr int DSLASH_BLOCK = 128;
+
+template <typename S, typename R, int RECON>
+cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
+    DslashArgs<R> a;
+    a.g = L.g;
+    const int q = 1 - L.out_parity;
+    a.gauge_out = (const char *)L.gauge->ptr[L.out_parity];
+    a.gauge_in = (const char *)L.gauge->ptr[q];
+    a.dir_bytes = L.gauge->dir_bytes;
+    a.out = L.out;
+    a.in = L.in;
+    a.x = L.x;
+    a.scale = (R)L.scale;
+    for (int i = 0; i < 8; ++i) a.ph[i] = (R)L.phase[i];
+    a.parity = L.out_parity;
+    if (L.red) a.red = *L.red;
+    else a.red = Reduction{nullptr, nullptr, nullptr, FIN_NONE};
+    const unsigned grid = (unsigned)((L.g.vh + DSLASH_BLOCK - 1) / DSLASH_BLOCK);
+    const bool norm = L.red != nullptr;
+#define WD_LAUNCH(DAG, EPI, NORM)                                                         \
+    k_dslash<S, R, RECON, DAG, EPI, NORM, DSLASH_BLOCK><<<grid, DSLASH_BLOCK, 0, s>>>(a)
+    if (L.epi == EPI_PLAIN) {
+        if (L.dagger) WD_LAUNCH(1, EPI_PLAIN, 0); else WD_LAUNCH(0, EPI_PLAIN, 0);
+    } else if (!norm) {
+        if (L.dagger) WD_LAUNCH(1, EPI_XPAY, 0); else WD_LAUNCH(0, EPI_XPAY, 0);
+    } else {
+        if (L.dagger) WD_LAUNCH(1, EPI_XPAY, 1); else WD_LAUNCH(0, EPI_XPAY, 1);
+    }
+#undef WD_LAUNCH
+    return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_dslash_prec(const DslashLaunch &L, cudaStream_t s) {
+    return L.gauge->recon == 12 ? launch_dslash_t<S, R, 12>(L, s)
+                                : launch_dslash_t<S, R, 18>(L, s);
+}
+
+}  // namespace wd

@@ -1,0 +1,144 @@
+// Conversions between the canonical boundary layout (FP64 complex,
+// array-of-structures, lexicographic sites) and the internal layout
+// (structure-of-arrays planes, one array per parity, storage precision).
+#include "wd_internal.cuh"
+
+namespace wd {
+
+constexpr int LAYOUT_BLOCK = 128;
+
+inline unsigned layout_grid(long n) {
+    long b = (n + LAYOUT_BLOCK - 1) / LAYOUT_BLOCK;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ void load_canonical(const double *src, long site, double *v, int n) {
+    const double2 *p = reinterpret_cast<const double2 *>(src + (long)site * n);
+    for (int i = 0; i < n / 2; ++i) {
+        double2 d = p[i];
+        v[2 * i] = d.x;
+        v[2 * i + 1] = d.y;
+    }
+}
+
+__device__ __forceinline__ void store_canonical(double *dst, long site, const double *v, int n) {
+    double2 *p = reinterpret_cast<double2 *>(dst + (long)site * n);
+    for (int i = 0; i < n / 2; ++i) p[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
+template <typename S>
+__global__ void k_pack_half(Geom g, void *dst, const double *src) {
+    const long h = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
+    if (h >= g.vh) return;
+    double v[24];
+    load_canonical(src, h, v, 24);
+    Rec<S, 24>::store(dst, g.stride, h, v);
+}
+
+template <typename S>
+__global__ void k_unpack_half(Geom g, double *dst, const void *src) {
+    const long h = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
+    if (h >= g.vh) return;
+    double v[24];
+    Rec<S, 24>::template load_coherent<double>(src, g.stride, h, v);
+    store_canonical(dst, h, v, 24);
+}
+
+__device__ __forceinline__ int lex_parity(const Geom &g, long lex) {
+    long r = lex;
+    int x = (int)(r % g.L[0]); r /= g.L[0];
+    int y = (int)(r % g.L[1]); r /= g.L[1];
+    int z = (int)(r % g.L[2]);
+    int t = (int)(r / g.L[2]);
+    return (x + y + z + t) & 1;
+}
+
+template <typename S>
+__global__ void k_pack_full(Geom g, void *even, void *odd, const double *src) {
+    const long lex = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
+    if (lex >= 2 * g.vh) return;
+    double v[24];
+    load_canonical(src, lex, v, 24);
+    Rec<S, 24>::store(lex_parity(g, lex) ? odd : even, g.stride, lex >> 1, v);
+}
+
+template <typename S>
+__global__ void k_unpack_full(Geom g, double *dst, const void *even, const void *odd) {
+    const long lex = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
+    if (lex >= 2 * g.vh) return;
+    double v[24];
+    Rec<S, 24>::template load_coherent<double>(lex_parity(g, lex) ? odd : even, g.stride,
+                                                lex >> 1, v);
+    store_canonical(dst, lex, v, 24);
+}
+
+// One thread per (site, direction): the link's first RECON reals (row-major,
+// so 12 keeps rows 0 and 1).
+template <typename S, int RECON>
+__global__ void k_pack_gauge(Geom g, char *even, char *odd, size_t dir_bytes, const double *U) {
+    const long i = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
+    if (i >= 8 * g.vh) return;
+    const long lex = i >> 2;
+    const int mu = (int)(i & 3);
+    double v[18];
+    load_canonical(U, i, v, 18);
+    char *base = (lex_parity(g, lex) ? odd : even) + mu * dir_bytes;
+    Rec<S, RECON>::store(base, g.stride, lex >> 1, v);
+}
+
+#define WD_STORE_DISPATCH(prec, KERNEL, ...)                                              \
+    switch (prec) {                                                                       \
+    case WD_F64: KERNEL<double><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;        \
+    case WD_F32: KERNEL<float><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;         \
+    case WD_F16: KERNEL<__half><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;        \
+    case WD_BF16: KERNEL<__nv_bfloat16><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;\
+    default: return cudaErrorInvalidValue;                                                \
+    }
+
+cudaError_t launch_pack_half(int prec, const Geom &g, void *dst, const double *src,
+                             cudaStream_t s) {
+    const unsigned grid = layout_grid(g.vh);
+    WD_STORE_DISPATCH(prec, k_pack_half, g, dst, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_half(int prec, const Geom &g, double *dst, const void *src,
+                               cudaStream_t s) {
+    const unsigned grid = layout_grid(g.vh);
+    WD_STORE_DISPATCH(prec, k_unpack_half, g, dst, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_full(int prec, const Geom &g, void *dst_even, void *dst_odd,
+                             const double *src, cudaStream_t s) {
+    const unsigned grid = layout_grid(2 * g.vh);
+    WD_STORE_DISPATCH(prec, k_pack_full, g, dst_even, dst_odd, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_full(int prec, const Geom &g, double *dst, const void *src_even,
+                               const void *src_odd, cudaStream_t s) {
+    const unsigned grid = layout_grid(2 * g.vh);
+    WD_STORE_DISPATCH(prec, k_unpack_full, g, dst, src_even, src_odd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_gauge(const GaugeSet &gs, const Geom &g, const double *U,
+                              cudaStream_t s) {
+    const unsigned grid = layout_grid(8 * g.vh);
+    char *e = (char *)gs.ptr[0], *o = (char *)gs.ptr[1];
+#define WD_G(S)                                                                              \
+    if (gs.recon == 12) k_pack_gauge<S, 12><<<grid, LAYOUT_BLOCK, 0, s>>>(g, e, o, gs.dir_bytes, U); \
+    else k_pack_gauge<S, 18><<<grid, LAYOUT_BLOCK, 0, s>>>(g, e, o, gs.dir_bytes, U)
+    switch (gs.prec) {
+    case WD_F64: WD_G(double); break;
+    case WD_F32: WD_G(float); break;
+    case WD_F16: WD_G(__half); break;
+    case WD_BF16: WD_G(__nv_bfloat16); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef WD_G
+    return cudaGetLastError();
+}
+
+}  // namespace wd

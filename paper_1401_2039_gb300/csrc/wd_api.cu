@@ -1,0 +1,660 @@
+// C ABI of libwd: operator handle, operator applications and the CGNR
+// solve of the even-odd Schur system (arXiv:1401.2039, Fig. "dirac",
+// Alg. "schur", Alg. "CGNR").
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wd_internal.cuh"
+
+namespace wd {
+cudaError_t launch_dslash_f64(const DslashLaunch &L, cudaStream_t s);
+cudaError_t launch_dslash_f32(const DslashLaunch &L, cudaStream_t s);
+cudaError_t launch_dslash_f16(const DslashLaunch &L, cudaStream_t s);
+cudaError_t launch_dslash_bf16(const DslashLaunch &L, cudaStream_t s);
+
+cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s) {
+    switch (prec) {
+    case WD_F64: return launch_dslash_f64(L, s);
+    case WD_F32: return launch_dslash_f32(L, s);
+    case WD_F16: return launch_dslash_f16(L, s);
+    case WD_BF16: return launch_dslash_bf16(L, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace wd
+
+using namespace wd;
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define WD_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? WD_ERR_NOMEM : WD_ERR_CUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+#define WD_TRY(call)                                                                       \
+    do {                                                                                   \
+        int rc_ = (call);                                                                  \
+        if (rc_ != WD_OK) return rc_;                                                      \
+    } while (0)
+
+// Parameters of the reliable-update scheme (Clark et al. 2010): refresh the
+// FP64 residual whenever the iterated residual has fallen by DELTA since
+// the last refresh.
+static const double RU_DELTA = 0.1;
+static const int MAX_BATCH_LOG2 = 5;  // graph batches of 1, 2, ..., 32 iterations
+
+struct wd_op {
+    Geom g{};
+    double kappa = 0;
+    double phase[8] = {};
+    int prec = WD_F64, recon = 18;
+    cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy)
+    cudaStream_t stream = nullptr; // work stream owned by the handle
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool gauge_loaded = false;
+
+    GaugeSet gauge_lo;             // storage precision, recon
+    GaugeSet gauge_hi;             // FP64, 18 reals (shares gauge_lo when identical)
+    bool hi_shared = false;
+
+    // storage-precision fields
+    void *fa[2] = {}, *fc[2] = {}, *ftmp = nullptr, *slot[2] = {};
+    void *xl = nullptr, *rl = nullptr, *pl = nullptr, *zl = nullptr, *apl = nullptr,
+         *tl = nullptr;
+    // FP64 fields
+    double *hb[2] = {}, *bh = nullptr, *xh = nullptr, *rh = nullptr, *axh = nullptr,
+           *th = nullptr, *xq = nullptr;
+    // canonical staging for the host-memory solve
+    double *stage_x = nullptr, *stage_b = nullptr;
+
+    // reductions
+    double *partials = nullptr;
+    unsigned int *counter = nullptr;
+    SolverScalars *sc = nullptr;      // device
+    SolverScalars *sc_host = nullptr; // pinned mirror
+    double *dev_consts = nullptr;     // [0] scale, [1] 1/scale, [2] ratio
+    double *host_consts = nullptr;    // pinned staging of dev_consts
+
+    // CUDA graphs of 2^k CGNR iterations, per solved parity
+    cudaGraphExec_t graphs[2][MAX_BATCH_LOG2 + 1] = {};
+
+    std::vector<void *> allocations;
+
+    size_t lo_field_bytes() const { return field_bytes(prec, g.stride, 24); }
+    size_t hi_field_bytes() const { return field_bytes(WD_F64, g.stride, 24); }
+};
+
+// ------------------------------------------------------------------ helpers
+static int dev_alloc(wd_op *op, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(WD_ERR_NOMEM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                      "): " + cudaGetErrorString(e));
+    }
+    op->allocations.push_back(*p);
+    WD_CUDA(cudaMemset(*p, 0, bytes));
+    return WD_OK;
+}
+
+static int fork(wd_op *op) {
+    WD_CUDA(cudaEventRecord(op->ev_fork, op->user));
+    WD_CUDA(cudaStreamWaitEvent(op->stream, op->ev_fork, 0));
+    return WD_OK;
+}
+
+static int join(wd_op *op) {
+    WD_CUDA(cudaEventRecord(op->ev_join, op->stream));
+    WD_CUDA(cudaStreamWaitEvent(op->user, op->ev_join, 0));
+    return WD_OK;
+}
+
+static Reduction reduction(wd_op *op, int fin) {
+    return Reduction{op->partials, op->counter, op->sc, fin};
+}
+
+// out = scale * H_{p,q} in  (PLAIN) or  x + scale * H_{p,q} in  (XPAY), optional norm
+static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, const void *in,
+                  const void *x, double scale, const Reduction *red) {
+    DslashLaunch L;
+    L.g = op->g;
+    L.gauge = hi ? &op->gauge_hi : &op->gauge_lo;
+    L.out_parity = out_parity;
+    L.dagger = dagger;
+    memcpy(L.phase, op->phase, sizeof(L.phase));
+    L.out = out;
+    L.in = in;
+    L.x = x;
+    L.scale = scale;
+    L.epi = x ? EPI_XPAY : EPI_PLAIN;
+    L.red = red;
+    WD_CUDA(launch_dslash(L, hi ? WD_F64 : op->prec, op->stream));
+    return WD_OK;
+}
+
+// out_p = in_p - kappa^2 H_pq H_qp in_p  (Mhat_p, or Mhat_p^dag with H^dag)
+static int schur(wd_op *op, bool hi, int p, int dagger, void *out, const void *in, void *tmp,
+                 const Reduction *red) {
+    WD_TRY(dslash(op, hi, 1 - p, dagger, tmp, in, nullptr, 1.0, nullptr));
+    WD_TRY(dslash(op, hi, p, dagger, out, tmp, in, -op->kappa * op->kappa, red));
+    return WD_OK;
+}
+
+static int check_op(const wd_op *op) {
+    if (!op) return fail(WD_ERR_ARG, "null operator handle");
+    if (!op->gauge_loaded) return fail(WD_ERR_STATE, "no gauge field loaded (wd_op_set_gauge)");
+    return WD_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *wd_status_string(int s) {
+    switch (s) {
+    case WD_OK: return "ok";
+    case WD_ERR_ARG: return "invalid argument";
+    case WD_ERR_DIMS: return "invalid lattice dimensions";
+    case WD_ERR_CUDA: return "CUDA error";
+    case WD_ERR_NOMEM: return "out of device memory";
+    case WD_ERR_NOT_CONVERGED: return "solver did not converge";
+    case WD_ERR_BREAKDOWN: return "solver breakdown";
+    case WD_ERR_TIMEOUT: return "device wait timed out";
+    case WD_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+const char *wd_last_error(void) { return g_last_error.c_str(); }
+
+void *wd_op_stream(wd_op *op) { return op ? (void *)op->stream : nullptr; }
+
+double wd_dslash_bytes(const wd_op *op) {
+    if (!op) return 0.0;
+    return (double)op->g.vh * (48.0 + 8.0 * op->recon) * (double)prec_bytes(op->prec);
+}
+
+void wd_op_destroy(wd_op *op) {
+    if (!op) return;
+    if (op->stream) cudaStreamSynchronize(op->stream);
+    for (auto &row : op->graphs)
+        for (auto &ge : row)
+            if (ge) cudaGraphExecDestroy(ge);
+    for (void *p : op->allocations) cudaFree(p);
+    if (op->sc_host) cudaFreeHost(op->sc_host);
+    if (op->host_consts) cudaFreeHost(op->host_consts);
+    if (op->ev_fork) cudaEventDestroy(op->ev_fork);
+    if (op->ev_join) cudaEventDestroy(op->ev_join);
+    if (op->stream) cudaStreamDestroy(op->stream);
+    delete op;
+}
+
+static int create_impl(wd_op *op) {
+    WD_CUDA(cudaStreamCreateWithFlags(&op->stream, cudaStreamNonBlocking));
+    WD_CUDA(cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming));
+    WD_CUDA(cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming));
+
+    const Geom &g = op->g;
+    // gauge fields
+    op->gauge_lo.prec = op->prec;
+    op->gauge_lo.recon = op->recon;
+    op->gauge_lo.dir_bytes = field_bytes(op->prec, g.stride, op->recon);
+    for (int p = 0; p < 2; ++p)
+        WD_TRY(dev_alloc(op, &op->gauge_lo.ptr[p], 4 * op->gauge_lo.dir_bytes));
+    op->hi_shared = (op->prec == WD_F64 && op->recon == 18);
+    if (op->hi_shared) {
+        op->gauge_hi = op->gauge_lo;
+    } else {
+        op->gauge_hi.prec = WD_F64;
+        op->gauge_hi.recon = 18;
+        op->gauge_hi.dir_bytes = field_bytes(WD_F64, g.stride, 18);
+        for (int p = 0; p < 2; ++p)
+            WD_TRY(dev_alloc(op, &op->gauge_hi.ptr[p], 4 * op->gauge_hi.dir_bytes));
+    }
+    // fields
+    const size_t lo = op->lo_field_bytes(), hi = op->hi_field_bytes();
+    void **lo_fields[] = {&op->fa[0], &op->fa[1], &op->fc[0], &op->fc[1], &op->ftmp,
+                          &op->slot[0], &op->slot[1], &op->xl, &op->rl, &op->pl, &op->zl,
+                          &op->apl, &op->tl};
+    for (void **f : lo_fields) WD_TRY(dev_alloc(op, f, lo));
+    double **hi_fields[] = {&op->hb[0], &op->hb[1], &op->bh, &op->xh, &op->rh, &op->axh,
+                            &op->th, &op->xq};
+    for (double **f : hi_fields) WD_TRY(dev_alloc(op, (void **)f, hi));
+    const size_t canon = (size_t)2 * g.vh * 24 * sizeof(double);
+    WD_TRY(dev_alloc(op, (void **)&op->stage_x, canon));
+    WD_TRY(dev_alloc(op, (void **)&op->stage_b, canon));
+    // reductions
+    WD_TRY(dev_alloc(op, (void **)&op->partials, sizeof(double) * reduction_blocks(g)));
+    WD_TRY(dev_alloc(op, (void **)&op->counter, sizeof(unsigned int) * 4));
+    WD_TRY(dev_alloc(op, (void **)&op->sc, sizeof(SolverScalars)));
+    WD_TRY(dev_alloc(op, (void **)&op->dev_consts, sizeof(double) * 4));
+    WD_CUDA(cudaMallocHost((void **)&op->sc_host, sizeof(SolverScalars)));
+    WD_CUDA(cudaMallocHost((void **)&op->host_consts, sizeof(double) * 4));
+    WD_CUDA(cudaDeviceSynchronize());
+    return WD_OK;
+}
+
+int wd_op_create(wd_op **out, const int dims[4], double kappa, const double phase[8],
+                 int prec, int recon, void *stream) {
+    if (!out || !dims || !phase) return fail(WD_ERR_ARG, "null argument to wd_op_create");
+    *out = nullptr;
+    long V = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (dims[m] < 2 || dims[m] % 2)
+            return fail(WD_ERR_DIMS, "every lattice extent must be even and >= 2");
+        if (dims[m] > (1 << 14)) return fail(WD_ERR_DIMS, "lattice extent too large");
+        V *= dims[m];
+    }
+    if (V > (1L << 31)) return fail(WD_ERR_DIMS, "lattice volume above 2^31 sites");
+    if (prec < WD_F64 || prec > WD_BF16) return fail(WD_ERR_ARG, "unknown precision");
+    if (recon != 18 && recon != 12) return fail(WD_ERR_ARG, "recon must be 18 or 12");
+    if (!std::isfinite(kappa)) return fail(WD_ERR_ARG, "kappa must be finite");
+    for (int i = 0; i < 8; ++i)
+        if (!std::isfinite(phase[i])) return fail(WD_ERR_ARG, "phases must be finite");
+
+    wd_op *op = new wd_op();
+    for (int m = 0; m < 4; ++m) op->g.L[m] = dims[m];
+    op->g.hx = dims[0] / 2;
+    op->g.vh = V / 2;
+    op->g.stride = pad_stride(op->g.vh);
+    op->kappa = kappa;
+    memcpy(op->phase, phase, sizeof(op->phase));
+    op->prec = prec;
+    op->recon = recon;
+    op->user = (cudaStream_t)stream;
+    int rc = create_impl(op);
+    if (rc != WD_OK) {
+        std::string msg = g_last_error;
+        wd_op_destroy(op);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = op;
+    return WD_OK;
+}
+
+int wd_op_set_gauge(wd_op *op, const double *U) {
+    if (!op || !U) return fail(WD_ERR_ARG, "null argument to wd_op_set_gauge");
+    WD_TRY(fork(op));
+    WD_CUDA(launch_pack_gauge(op->gauge_lo, op->g, U, op->stream));
+    if (!op->hi_shared) WD_CUDA(launch_pack_gauge(op->gauge_hi, op->g, U, op->stream));
+    WD_TRY(join(op));
+    op->gauge_loaded = true;
+    return WD_OK;
+}
+
+int wd_apply(wd_op *op, double *out, const double *in, int dagger) {
+    WD_TRY(check_op(op));
+    if (!out || !in) return fail(WD_ERR_ARG, "null spinor");
+    if (dagger != 0 && dagger != 1) return fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    WD_TRY(fork(op));
+    WD_CUDA(launch_pack_full(op->prec, op->g, op->fa[0], op->fa[1], in, op->stream));
+    for (int p = 0; p < 2; ++p)   // out_p = in_p - kappa H_pq in_q
+        WD_TRY(dslash(op, false, p, dagger, op->fc[p], op->fa[1 - p], op->fa[p], -op->kappa,
+                      nullptr));
+    WD_CUDA(launch_unpack_full(op->prec, op->g, out, op->fc[0], op->fc[1], op->stream));
+    return join(op);
+}
+
+int wd_apply_eo(wd_op *op, double *out, const double *in, int parity, int dagger) {
+    WD_TRY(check_op(op));
+    if (!out || !in) return fail(WD_ERR_ARG, "null spinor");
+    if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (dagger != 0 && dagger != 1) return fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    WD_TRY(fork(op));
+    WD_CUDA(launch_pack_half(op->prec, op->g, op->fa[0], in, op->stream));
+    WD_TRY(schur(op, false, parity, dagger, op->fc[0], op->fa[0], op->ftmp, nullptr));
+    WD_CUDA(launch_unpack_half(op->prec, op->g, out, op->fc[0], op->stream));
+    return join(op);
+}
+
+int wd_dslash_eo(wd_op *op, double *out, const double *in, int out_parity, int dagger) {
+    WD_TRY(check_op(op));
+    if (!out || !in) return fail(WD_ERR_ARG, "null spinor");
+    if (out_parity != 0 && out_parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (dagger != 0 && dagger != 1) return fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    WD_TRY(fork(op));
+    WD_CUDA(launch_pack_half(op->prec, op->g, op->fa[0], in, op->stream));
+    WD_TRY(dslash(op, false, out_parity, dagger, op->fc[0], op->fa[0], nullptr, 1.0, nullptr));
+    WD_CUDA(launch_unpack_half(op->prec, op->g, out, op->fc[0], op->stream));
+    return join(op);
+}
+
+int wd_field_load(wd_op *op, int slot, const double *half_in) {
+    if (!op || !half_in) return fail(WD_ERR_ARG, "null argument");
+    if (slot != 0 && slot != 1) return fail(WD_ERR_ARG, "slot must be 0 or 1");
+    WD_TRY(fork(op));
+    WD_CUDA(launch_pack_half(op->prec, op->g, op->slot[slot], half_in, op->stream));
+    return join(op);
+}
+
+int wd_field_store(wd_op *op, int slot, double *half_out) {
+    if (!op || !half_out) return fail(WD_ERR_ARG, "null argument");
+    if (slot != 0 && slot != 1) return fail(WD_ERR_ARG, "slot must be 0 or 1");
+    WD_TRY(fork(op));
+    WD_CUDA(launch_unpack_half(op->prec, op->g, half_out, op->slot[slot], op->stream));
+    return join(op);
+}
+
+int wd_dslash_resident(wd_op *op, int in_slot, int out_parity, int dagger) {
+    WD_TRY(check_op(op));
+    if (in_slot != 0 && in_slot != 1) return fail(WD_ERR_ARG, "slot must be 0 or 1");
+    if (out_parity != 0 && out_parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (dagger != 0 && dagger != 1) return fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    WD_TRY(fork(op));
+    WD_TRY(dslash(op, false, out_parity, dagger, op->slot[1 - in_slot], op->slot[in_slot],
+                  nullptr, 1.0, nullptr));
+    return join(op);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ solver
+namespace {
+
+struct SolveState {
+    int p, q;
+    double target;      // absolute FP64 residual norm to reach
+    double nb;          // ||b||
+    double scale;       // r_lo = scale * r_hi
+    double r_hi;        // ||r_hi|| at the last refresh
+    int ru;             // reliable updates
+    double dslash_lo, dslash_hi, bytes, launches;
+};
+
+double field_b(const wd_op *op, int prec) { return (double)op->g.vh * 24 * prec_bytes(prec); }
+double dslash_b(const wd_op *op, bool hi, bool xpay) {
+    const int pr = hi ? WD_F64 : op->prec;
+    const int rc = hi ? 18 : op->recon;
+    return (double)op->g.vh * (48.0 + 8.0 * rc + (xpay ? 24.0 : 0.0)) * (double)prec_bytes(pr);
+}
+
+// One CGNR iteration on Mhat_p in storage precision, with the residual
+// checkpoint at its end:
+//   z = A^dag r; beta = |z|^2 / nz; nz = |z|^2; p = z + beta p;
+//   Ap = A p; alpha = nz / |Ap|^2; x += alpha p; r -= alpha Ap; nr = |r|^2
+// (Alg. "CGNR", rotated so that the host may refresh r between iterations).
+int cg_iteration(wd_op *op, int p) {
+    Reduction rb = reduction(op, FIN_BETA), ra = reduction(op, FIN_ALPHA),
+              rn = reduction(op, FIN_NR);
+    WD_TRY(schur(op, false, p, 1, op->zl, op->rl, op->tl, &rb));
+    WD_CUDA(launch_cg_update_p(op->prec, op->g, op->pl, op->zl, op->sc, op->stream));
+    WD_TRY(schur(op, false, p, 0, op->apl, op->pl, op->tl, &ra));
+    WD_CUDA(launch_cg_update_xr(op->prec, op->g, op->xl, op->rl, op->pl, op->apl, rn,
+                                op->stream));
+    return WD_OK;
+}
+
+int graph_for(wd_op *op, int p, int lg, cudaGraphExec_t *out) {
+    if (!op->graphs[p][lg]) {
+        cudaGraph_t graph = nullptr;
+        WD_CUDA(cudaStreamBeginCapture(op->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = WD_OK;
+        for (int i = 0; i < (1 << lg) && rc == WD_OK; ++i) rc = cg_iteration(op, p);
+        cudaError_t e = cudaStreamEndCapture(op->stream, &graph);
+        if (rc != WD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        WD_CUDA(e);
+        cudaError_t ei = cudaGraphInstantiate(&op->graphs[p][lg], graph, 0);
+        cudaGraphDestroy(graph);
+        WD_CUDA(ei);
+    }
+    *out = op->graphs[p][lg];
+    return WD_OK;
+}
+
+int run_iterations(wd_op *op, int p, int n) {
+    for (int lg = MAX_BATCH_LOG2; lg >= 0; --lg) {
+        while (n >= (1 << lg)) {
+            cudaGraphExec_t ge;
+            WD_TRY(graph_for(op, p, lg, &ge));
+            WD_CUDA(cudaGraphLaunch(ge, op->stream));
+            n -= 1 << lg;
+        }
+    }
+    return WD_OK;
+}
+
+int read_scalars(wd_op *op) {
+    WD_CUDA(cudaMemcpyAsync(op->sc_host, op->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost,
+                            op->stream));
+    WD_CUDA(cudaStreamSynchronize(op->stream));
+    return WD_OK;
+}
+
+// r_hi = bhat - Mhat x_hi in FP64 and ||r_hi||^2 -> scratch[0]
+int true_residual(wd_op *op, SolveState &st) {
+    Reduction r0 = reduction(op, FIN_STORE0);
+    WD_TRY(schur(op, true, st.p, 0, op->axh, op->xh, op->th, nullptr));
+    WD_CUDA(launch_xmy_norm(op->g, op->rh, op->bh, op->axh, r0, op->stream));
+    st.dslash_hi += 2;
+    st.launches += 3;
+    st.bytes += dslash_b(op, true, false) + dslash_b(op, true, true) + 3 * field_b(op, WD_F64);
+    return WD_OK;
+}
+
+int set_consts(wd_op *op, double scale, double inv_scale, double ratio) {
+    op->host_consts[0] = scale;
+    op->host_consts[1] = inv_scale;
+    op->host_consts[2] = ratio;
+    WD_CUDA(cudaMemcpyAsync(op->dev_consts, op->host_consts, 3 * sizeof(double),
+                            cudaMemcpyHostToDevice, op->stream));
+    return WD_OK;
+}
+
+int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, int parity,
+               wd_solve_info *info) {
+    SolveState st{};
+    st.p = parity;
+    st.q = 1 - parity;
+    const Geom &g = op->g;
+    const double n_real = 24.0 * (double)g.vh;
+    const bool mixed = op->prec != WD_F64;
+
+    // Alg. schur: split b and the initial guess by parity, bhat_p = b_p + kappa H_pq b_q
+    WD_CUDA(launch_pack_full(WD_F64, g, op->hb[0], op->hb[1], b, op->stream));
+    {
+        double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
+        WD_CUDA(launch_pack_full(WD_F64, g, xe, xo, x, op->stream));
+    }
+    WD_TRY(dslash(op, true, st.p, 0, op->bh, op->hb[st.q], op->hb[st.p], op->kappa, nullptr));
+    Reduction r1 = reduction(op, FIN_STORE1), r0 = reduction(op, FIN_STORE0);
+    WD_CUDA(launch_norm2(WD_F64, g, op->hb[st.q], r1, op->stream));
+    WD_TRY(read_scalars(op));
+    double nb2 = op->sc_host->scratch[1];
+    WD_CUDA(launch_norm2(WD_F64, g, op->hb[st.p], r0, op->stream));
+    WD_TRY(read_scalars(op));
+    nb2 += op->sc_host->scratch[0];
+    st.nb = std::sqrt(nb2);
+    st.target = tol * st.nb;
+    st.dslash_hi += 1;
+    st.launches += 5;   // two packs, the bhat hop, two norms
+    st.bytes += dslash_b(op, true, true) + 5 * field_b(op, WD_F64);
+
+    WD_TRY(true_residual(op, st));
+    WD_TRY(read_scalars(op));
+    st.r_hi = std::sqrt(op->sc_host->scratch[0]);
+
+    int status = WD_OK;
+    int iters = 0;
+    if (st.nb == 0.0) {
+        WD_CUDA(cudaMemsetAsync(op->xh, 0, op->hi_field_bytes(), op->stream));
+        st.r_hi = 0.0;
+    } else if (st.r_hi > st.target) {
+        // inner system: r_lo = scale r_hi, x_lo = 0, p = 0, nz = +inf
+        st.scale = (mixed && st.r_hi > 0) ? std::sqrt(n_real) / st.r_hi : 1.0;
+        WD_TRY(set_consts(op, st.scale, 1.0 / st.scale, 1.0));
+        WD_CUDA(launch_convert_scaled(op->prec, op->rl, WD_F64, op->rh, g, op->dev_consts, 0,
+                                      op->stream));
+        WD_CUDA(cudaMemsetAsync(op->xl, 0, op->lo_field_bytes(), op->stream));
+        WD_CUDA(cudaMemsetAsync(op->pl, 0, op->lo_field_bytes(), op->stream));
+        SolverScalars init{};
+        init.nz = INFINITY;
+        *op->sc_host = init;
+        WD_CUDA(cudaMemcpyAsync(op->sc, op->sc_host, sizeof(SolverScalars),
+                                cudaMemcpyHostToDevice, op->stream));
+        WD_CUDA(cudaStreamSynchronize(op->stream));
+        st.bytes += field_b(op, WD_F64) + field_b(op, op->prec) * 3;
+        st.launches += 1;
+
+        const double per_iter_bytes =
+            2 * (dslash_b(op, false, false) + dslash_b(op, false, true)) +
+            9 * field_b(op, op->prec);
+        double r_max_lo = st.r_hi * st.scale;   // iterated residual at the last refresh
+        double last_lognr = 2 * std::log(r_max_lo);
+        int last_it = 0;
+        int batch = 8;
+        for (;;) {
+            int n = std::min(batch, maxiter - iters);
+            if (n > 0) {
+                WD_TRY(run_iterations(op, st.p, n));
+                WD_TRY(read_scalars(op));
+                iters = op->sc_host->iter;
+                st.dslash_lo += 4.0 * n;
+                st.launches += 6.0 * n;
+                st.bytes += per_iter_bytes * n;
+            }
+            const SolverScalars &h = *op->sc_host;
+            if (h.flags & 1) { status = WD_ERR_BREAKDOWN; break; }
+            const double r_lo = std::sqrt(h.nr);
+            const bool want_conv = r_lo <= st.target * st.scale;
+            const bool want_ru = mixed && r_lo < RU_DELTA * r_max_lo;
+            const bool out_of_iters = iters >= maxiter;
+            if (want_conv || want_ru || out_of_iters) {
+                // reliable update: fold x_lo into x_hi, recompute r_hi in FP64
+                WD_CUDA(launch_fold_x(op->prec, g, op->xh, op->xl, op->dev_consts + 1,
+                                      op->stream));
+                st.bytes += field_b(op, op->prec) * 2 + field_b(op, WD_F64) * 2;
+                st.launches += 1;
+                WD_TRY(true_residual(op, st));
+                WD_TRY(read_scalars(op));
+                st.r_hi = std::sqrt(op->sc_host->scratch[0]);
+                st.ru += 1;
+                if (!(st.r_hi == st.r_hi)) { status = WD_ERR_BREAKDOWN; break; }
+                if (st.r_hi <= st.target) break;
+                if (out_of_iters) { status = WD_ERR_NOT_CONVERGED; break; }
+                const double new_scale = mixed ? std::sqrt(n_real) / st.r_hi : 1.0;
+                const double ratio = new_scale / st.scale;
+                WD_TRY(set_consts(op, new_scale, 1.0 / new_scale, ratio));
+                WD_CUDA(launch_convert_scaled(op->prec, op->rl, WD_F64, op->rh, g,
+                                              op->dev_consts, 0, op->stream));
+                if (ratio != 1.0)
+                    WD_CUDA(launch_rescale_lo(op->prec, g, op->pl, op->sc, op->dev_consts + 2,
+                                              op->stream));
+                st.bytes += field_b(op, WD_F64) + field_b(op, op->prec) * 3;
+                st.launches += ratio != 1.0 ? 2 : 1;
+                st.scale = new_scale;
+                r_max_lo = st.r_hi * st.scale;
+                last_lognr = 2 * std::log(r_max_lo);
+                last_it = iters;
+                batch = 4;
+                continue;
+            }
+            // predict the iterations to the next event from the convergence rate
+            const double lognr = std::log(h.nr);
+            const int di = iters - last_it;
+            int next = 8;
+            if (di > 0 && lognr < last_lognr) {
+                const double rate = (lognr - last_lognr) / di;   // < 0
+                double thr = 2 * std::log(st.target * st.scale);
+                if (mixed) thr = std::max(thr, 2 * std::log(RU_DELTA * r_max_lo));
+                next = (int)std::ceil((thr - lognr) / rate);
+            }
+            last_lognr = lognr;
+            last_it = iters;
+            batch = std::max(1, std::min(next, 1 << MAX_BATCH_LOG2));
+        }
+    }
+
+    // reconstruction x_q = b_q + kappa H_qp x_p, then the FP64 true residual
+    // of the full system: r_p = b_p - (x_p - kappa H_pq x_q), r_q likewise.
+    WD_TRY(dslash(op, true, st.q, 0, op->xq, op->xh, op->hb[st.q], op->kappa, nullptr));
+    WD_TRY(dslash(op, true, st.p, 0, op->axh, op->xq, op->xh, -op->kappa, nullptr));
+    WD_CUDA(launch_xmy_norm(g, op->rh, op->hb[st.p], op->axh, r0, op->stream));
+    WD_TRY(dslash(op, true, st.q, 0, op->axh, op->xh, op->xq, -op->kappa, nullptr));
+    WD_CUDA(launch_xmy_norm(g, op->th, op->hb[st.q], op->axh, r1, op->stream));
+    {
+        double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
+        WD_CUDA(launch_unpack_full(WD_F64, g, x, xe, xo, op->stream));
+    }
+    WD_TRY(read_scalars(op));
+    st.dslash_hi += 3;
+    st.launches += 6;
+    st.bytes += 2 * dslash_b(op, true, true) + dslash_b(op, true, true) + 6 * field_b(op, WD_F64) +
+                4 * field_b(op, WD_F64);
+    const double rfull = std::sqrt(op->sc_host->scratch[0] + op->sc_host->scratch[1]);
+    if (info) {
+        info->iters = iters;
+        info->reliable_updates = st.ru;
+        info->true_rel_resid = st.nb > 0 ? rfull / st.nb : 0.0;
+        info->dslash_lo = st.dslash_lo;
+        info->dslash_hi = st.dslash_hi;
+        info->bytes = st.bytes;
+        info->launches = st.launches;
+    }
+    if (status == WD_OK && st.nb > 0 && rfull > st.target * 1.0000001) {
+        // the Schur residual met the target but rounding of the
+        // reconstruction did not: report it rather than hide it
+        status = WD_ERR_NOT_CONVERGED;
+    }
+    if (status != WD_OK) fail(status, wd_status_string(status));
+    return status;
+}
+
+}  // namespace
+
+extern "C" int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, int maxiter,
+                           int parity, wd_solve_info *info) {
+    auto t0 = std::chrono::steady_clock::now();
+    WD_TRY(check_op(op));
+    if (!x || !b) return fail(WD_ERR_ARG, "null spinor");
+    if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (!(tol > 0) || maxiter < 0) return fail(WD_ERR_ARG, "tol must be > 0, maxiter >= 0");
+    if (info) memset(info, 0, sizeof(*info));
+    WD_TRY(fork(op));
+    int rc = solve_impl(op, x, b, tol, maxiter, parity, info);
+    int rj = join(op);
+    if (info)
+        info->seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc != WD_OK ? rc : rj;
+}
+
+extern "C" int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
+                                int maxiter, int parity, wd_solve_info *info) {
+    auto t0 = std::chrono::steady_clock::now();
+    WD_TRY(check_op(op));
+    if (!x_host || !b_host) return fail(WD_ERR_ARG, "null spinor");
+    if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (!(tol > 0) || maxiter < 0) return fail(WD_ERR_ARG, "tol must be > 0, maxiter >= 0");
+    if (info) memset(info, 0, sizeof(*info));
+    const size_t bytes = (size_t)2 * op->g.vh * 24 * sizeof(double);
+    WD_TRY(fork(op));
+    WD_CUDA(cudaMemcpyAsync(op->stage_b, b_host, bytes, cudaMemcpyHostToDevice, op->stream));
+    WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
+    int rc = solve_impl(op, op->stage_x, op->stage_b, tol, maxiter, parity, info);
+    if (rc == WD_OK || rc == WD_ERR_NOT_CONVERGED) {
+        WD_CUDA(cudaMemcpyAsync(x_host, op->stage_x, bytes, cudaMemcpyDeviceToHost, op->stream));
+        WD_CUDA(cudaStreamSynchronize(op->stream));
+    }
+    int rj = join(op);
+    if (info)
+        info->seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc != WD_OK ? rc : rj;
+}

@@ -1,0 +1,407 @@
+// Internal declarations of libwd: storage-precision traits, the
+// structure-of-arrays field layout, vectorised loads/stores and lattice
+// geometry shared by the kernels.
+//
+// Field layout (one parity, Vh sites, site index h = lex / 2):
+//   a record of N reals of storage type S occupies N*sizeof(S) bytes split
+//   into NF = bytes / 16 planes of 16-byte vectors followed by one tail plane
+//   of (bytes % 16) bytes per site; plane j of site h lives at
+//   base + j * stride * 16 + h * 16 and the tail at base + NF * stride * 16 +
+//   h * tail.  Consecutive threads (consecutive h) therefore read consecutive
+//   16-byte words: every load of a warp is one fully-used 512-byte request.
+//   stride = Vh rounded up to a multiple of 64 sites; padding stays zero.
+//   Spinor records are 24 reals ([colour][spin][re,im]); link records are 18
+//   reals (3x3, row-major) or 12 (rows 0 and 1).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wd.h"
+
+namespace wd {
+
+// ---------------------------------------------------------------- precision
+template <int P> struct Prec;
+template <> struct Prec<WD_F64> { using S = double;        using R = double; };
+template <> struct Prec<WD_F32> { using S = float;         using R = float;  };
+template <> struct Prec<WD_F16> { using S = __half;        using R = float;  };
+template <> struct Prec<WD_BF16> { using S = __nv_bfloat16; using R = float; };
+
+inline size_t prec_bytes(int p) { return p == WD_F64 ? 8 : p == WD_F32 ? 4 : 2; }
+
+// Bytes of one field of Vh records of nreal reals in precision p.
+inline size_t field_bytes(int p, long stride, int nreal) {
+    size_t rec = (size_t)nreal * prec_bytes(p);
+    size_t nf = rec / 16, tail = rec % 16;
+    return nf * stride * 16 + tail * stride;
+}
+
+inline long pad_stride(long vh) { return (vh + 63) / 64 * 64; }
+
+// ---------------------------------------------------------------- loads
+__device__ __forceinline__ uint4 ld_nc_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+// Streaming load that is not kept in L1 (links: each is read once per launch).
+__device__ __forceinline__ uint4 ld_stream_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_stream_v2(const void *p) {
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+                 : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const void *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_v4(const void *p) {
+    return *reinterpret_cast<const uint4 *>(p);
+}
+__device__ __forceinline__ void st_v4(void *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+__device__ __forceinline__ void st_v2(void *p, uint2 v) { *reinterpret_cast<uint2 *>(p) = v; }
+__device__ __forceinline__ void st_u32(void *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
+
+// ---------------------------------------------------------------- word <-> real
+template <typename S, typename R> struct Words;
+template <> struct Words<double, double> {
+    static constexpr int per_word = 0;  // two words per real
+    __device__ static void unpack(const uint32_t *w, double *r, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) r[i] = __hiloint2double((int)w[2 * i + 1], (int)w[2 * i]);
+    }
+    __device__ static void pack(const double *r, uint32_t *w, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            w[2 * i] = (uint32_t)__double2loint(r[i]);
+            w[2 * i + 1] = (uint32_t)__double2hiint(r[i]);
+        }
+    }
+};
+template <> struct Words<float, float> {
+    __device__ static void unpack(const uint32_t *w, float *r, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) r[i] = __uint_as_float(w[i]);
+    }
+    __device__ static void pack(const float *r, uint32_t *w, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) w[i] = __float_as_uint(r[i]);
+    }
+};
+template <> struct Words<__half, float> {
+    __device__ static void unpack(const uint32_t *w, float *r, int n) {
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&w[i]);
+            float2 f = __half22float2(h);
+            r[2 * i] = f.x;
+            r[2 * i + 1] = f.y;
+        }
+    }
+    __device__ static void pack(const float *r, uint32_t *w, int n) {
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            __half2 h = __floats2half2_rn(r[2 * i], r[2 * i + 1]);
+            w[i] = *reinterpret_cast<uint32_t *>(&h);
+        }
+    }
+};
+template <> struct Words<__nv_bfloat16, float> {
+    __device__ static void unpack(const uint32_t *w, float *r, int n) {
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[i]);
+            float2 f = __bfloat1622float2(h);
+            r[2 * i] = f.x;
+            r[2 * i + 1] = f.y;
+        }
+    }
+    __device__ static void pack(const float *r, uint32_t *w, int n) {
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
+            w[i] = *reinterpret_cast<uint32_t *>(&h);
+        }
+    }
+};
+
+// Low-precision storage read into / written from FP64 registers (layout
+// conversions and the reliable-update kernels): go through the FP32 form;
+// FP32 -> FP64 is exact and FP64 -> FP16/BF16 rounds once via FP32.
+template <typename S> struct WordsViaFloat {
+    __device__ static void unpack(const uint32_t *w, double *r, int n) {
+        float f[24];
+        Words<S, float>::unpack(w, f, n);
+#pragma unroll
+        for (int i = 0; i < n; ++i) r[i] = (double)f[i];
+    }
+    __device__ static void pack(const double *r, uint32_t *w, int n) {
+        float f[24];
+#pragma unroll
+        for (int i = 0; i < n; ++i) f[i] = (float)r[i];
+        Words<S, float>::pack(f, w, n);
+    }
+};
+template <> struct Words<float, double> : WordsViaFloat<float> {};
+template <> struct Words<__half, double> : WordsViaFloat<__half> {};
+template <> struct Words<__nv_bfloat16, double> : WordsViaFloat<__nv_bfloat16> {};
+
+// A record of N reals of storage type S in the SoA layout described above.
+template <typename S, int N> struct Rec {
+    static constexpr int BYTES = N * (int)sizeof(S);
+    static constexpr int NF = BYTES / 16;
+    static constexpr int TAIL = BYTES % 16;
+    static constexpr int WORDS = BYTES / 4;
+    static_assert(TAIL == 0 || TAIL == 4 || TAIL == 8, "unsupported record");
+
+    // LoadKind: 0 = read-only cached (spinors), 1 = streaming (links).
+    template <int KIND>
+    __device__ __forceinline__ static void load_words(const char *base, long stride, long h,
+                                                      uint32_t *w) {
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            const char *p = base + ((long)j * stride + h) * 16;
+            uint4 v = KIND ? ld_stream_v4(p) : ld_nc_v4(p);
+            w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
+        }
+        if (TAIL == 8) {
+            uint2 v = ld_stream_v2(base + (long)NF * stride * 16 + h * 8);
+            w[4 * NF] = v.x; w[4 * NF + 1] = v.y;
+        } else if (TAIL == 4) {
+            w[4 * NF] = ld_stream_u32(base + (long)NF * stride * 16 + h * 4);
+        }
+    }
+    template <typename R, int KIND = 0>
+    __device__ __forceinline__ static void load(const void *base, long stride, long h, R *r) {
+        uint32_t w[WORDS];
+        load_words<KIND>((const char *)base, stride, h, w);
+        Words<S, R>::unpack(w, r, N);
+    }
+    // Plain (coherent) load, for fields the same kernel may have written.
+    template <typename R>
+    __device__ __forceinline__ static void load_coherent(const void *base, long stride, long h,
+                                                         R *r) {
+        static_assert(TAIL == 0, "coherent loads only for whole 16-byte records");
+        uint32_t w[WORDS];
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            uint4 v = ld_v4((const char *)base + ((long)j * stride + h) * 16);
+            w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
+        }
+        Words<S, R>::unpack(w, r, N);
+    }
+    template <typename R>
+    __device__ __forceinline__ static void store(void *base, long stride, long h, const R *r) {
+        uint32_t w[WORDS];
+        Words<S, R>::pack(r, w, N);
+        char *b = (char *)base;
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+            st_v4(b + ((long)j * stride + h) * 16,
+                  make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]));
+        if (TAIL == 8) st_v2(b + (long)NF * stride * 16 + h * 8, make_uint2(w[4 * NF], w[4 * NF + 1]));
+        else if (TAIL == 4) st_u32(b + (long)NF * stride * 16 + h * 4, w[4 * NF]);
+    }
+};
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+    int L[4];       // Lx, Ly, Lz, Lt
+    int hx;         // Lx / 2
+    long vh;        // V / 2
+    long stride;    // padded plane stride (sites)
+};
+
+// Coordinates of half-lattice site h of parity p.
+__device__ __forceinline__ void site_coords(const Geom &g, long h, int p, int c[4]) {
+    long r = h / g.hx;
+    int xh = (int)(h - r * g.hx);
+    c[1] = (int)(r % g.L[1]);
+    r /= g.L[1];
+    c[2] = (int)(r % g.L[2]);
+    c[3] = (int)(r / g.L[2]);
+    c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
+}
+
+__device__ __forceinline__ long half_index(const Geom &g, const int c[4]) {
+    return ((((long)c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0]) >> 1;
+}
+
+// ---------------------------------------------------------------- reductions
+// Scalars of the Krylov solver, resident in device memory so that kernels
+// chain without host round trips.
+struct SolverScalars {
+    double nz;          // ||z||^2 of the current z = A^dag r
+    double pAp;         // ||A p||^2
+    double alpha, beta;
+    double nr;          // ||r||^2 of the iterated residual
+    double scratch[4];  // results of plain reductions
+    int iter;           // iterations completed
+    int flags;          // bit 0: breakdown (zero or non-finite denominator)
+    double hist[64];    // ||r||^2 after iteration k at hist[k % 64]
+};
+
+enum FinalOp {
+    FIN_NONE = 0,
+    FIN_STORE0 = 1,   // scratch[0] = sum
+    FIN_STORE1 = 2,   // scratch[1] = sum
+    FIN_ALPHA = 3,    // pAp = sum; alpha = nz / pAp
+    FIN_BETA = 4,     // beta = sum / nz; nz = sum
+    FIN_NR = 5,       // nr = sum; hist[iter % 64] = sum; ++iter
+};
+
+// Partial sums of one reduction: one double per block, plus the arrival
+// counter of the last-block-done pattern (reset by the last block).
+struct Reduction {
+    double *partials;
+    unsigned int *counter;
+    SolverScalars *scalars;
+    int op;
+};
+
+__device__ __forceinline__ void apply_final(SolverScalars *s, int op, double sum) {
+    switch (op) {
+    case FIN_STORE0: s->scratch[0] = sum; break;
+    case FIN_STORE1: s->scratch[1] = sum; break;
+    case FIN_ALPHA: {
+        s->pAp = sum;
+        double a = 0.0;                   // z = 0: the residual vanished exactly
+        if (s->nz != 0.0) {
+            a = s->nz / sum;
+            if (!(sum > 0.0) || !isfinite(a)) { s->flags |= 1; a = 0.0; }
+        }
+        s->alpha = a;
+        break;
+    }
+    case FIN_BETA: {
+        // nz = +inf before the first iteration gives beta = 0; so does z = 0
+        double b = sum == 0.0 ? 0.0 : sum / s->nz;
+        if (!isfinite(sum) || isnan(b)) { s->flags |= 1; b = 0.0; }
+        s->beta = b;
+        s->nz = sum;
+        break;
+    }
+    case FIN_NR:
+        s->nr = sum;
+        s->hist[s->iter & 63] = sum;
+        s->iter += 1;
+        if (!isfinite(sum)) s->flags |= 1;
+        break;
+    default: break;
+    }
+}
+
+// Block-wide sum of v (every thread of the block must call), then the
+// deterministic grid-wide finish: the last block to arrive adds the
+// per-block partials in block order and applies the final operation.
+template <int BLOCK>
+__device__ __forceinline__ void block_reduce_finish(double v, const Reduction &red) {
+    __shared__ double warp_sums[BLOCK / 32];
+    __shared__ bool is_last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_sums[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+#pragma unroll
+        for (int i = 0; i < BLOCK / 32; ++i) s += warp_sums[i];
+        red.partials[blockIdx.x] = s;
+        __threadfence();
+        unsigned int prev = atomicAdd(red.counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double s = 0;
+    for (unsigned int i = threadIdx.x; i < gridDim.x; i += BLOCK)
+        s += __ldcg(&red.partials[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) warp_sums[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+#pragma unroll
+        for (int i = 0; i < BLOCK / 32; ++i) t += warp_sums[i];
+        apply_final(red.scalars, red.op, t);
+        *red.counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+struct Field {          // one parity spinor field in the internal layout
+    void *ptr = nullptr;
+    int prec = WD_F64;
+};
+
+struct GaugeSet {       // links of both parities, one precision/reconstruction
+    void *ptr[2] = {nullptr, nullptr};  // [parity] -> 4 direction blocks
+    size_t dir_bytes = 0;               // bytes of one direction block
+    int prec = WD_F64;
+    int recon = 18;
+};
+
+enum Epilogue { EPI_PLAIN = 0, EPI_XPAY = 1 };
+
+struct DslashLaunch {
+    Geom g;
+    const GaugeSet *gauge;
+    int out_parity;
+    int dagger;
+    double phase[8];
+    void *out;
+    const void *in;
+    const void *x;       // EPI_XPAY: out = x + scale * H in
+    double scale;
+    int epi;
+    const Reduction *red;  // optional ||out||^2
+};
+
+// dslash.cu
+cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s);
+
+// blas.cu
+cudaError_t launch_cg_update_xr(int prec, const Geom &g, void *x, void *r, const void *p,
+                                const void *Ap, const Reduction &red, cudaStream_t s);
+cudaError_t launch_cg_update_p(int prec, const Geom &g, void *p, const void *z,
+                               const SolverScalars *sc, cudaStream_t s);
+cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction &red,
+                         cudaStream_t s);
+cudaError_t launch_xmy_norm(const Geom &g, double *out, const double *x, const double *y,
+                            const Reduction &red, cudaStream_t s);
+cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const void *in,
+                                  const Geom &g, const double *scale_dev, double scale_host,
+                                  cudaStream_t s);
+cudaError_t launch_fold_x(int prec_lo, const Geom &g, double *x_hi, void *x_lo,
+                          const double *inv_scale_dev, cudaStream_t s);
+cudaError_t launch_rescale_lo(int prec_lo, const Geom &g, void *p, SolverScalars *sc,
+                              const double *ratio_dev, cudaStream_t s);
+int reduction_blocks(const Geom &g);
+
+// layout.cu
+cudaError_t launch_pack_half(int prec, const Geom &g, void *dst, const double *src,
+                             cudaStream_t s);
+cudaError_t launch_unpack_half(int prec, const Geom &g, double *dst, const void *src,
+                               cudaStream_t s);
+cudaError_t launch_pack_full(int prec, const Geom &g, void *dst_even, void *dst_odd,
+                             const double *src, cudaStream_t s);
+cudaError_t launch_unpack_full(int prec, const Geom &g, double *dst, const void *src_even,
+                               const void *src_odd, cudaStream_t s);
+cudaError_t launch_pack_gauge(const GaugeSet &gs, const Geom &g, const double *U,
+                              cudaStream_t s);
+
+}  // namespace wd

@@ -1,0 +1,224 @@
+"""ctypes binding of libwd (include/wd.h): argument marshalling only.
+
+Every operation runs in the CUDA kernels of libwd; PyTorch provides device
+memory and streams.  There is no CPU fallback: constructing an operator
+without a CUDA device, or without the compiled library, raises.
+
+Arrays are torch complex128 tensors in the canonical layout of the C ABI:
+full spinors ``[V, 3, 4]``, half-lattice spinors ``[V/2, 3, 4]`` (entry
+``lex // 2`` of each site of one parity), gauge fields ``[V, 4, 3, 3]``.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+WD_OK, WD_ERR_ARG, WD_ERR_DIMS, WD_ERR_CUDA, WD_ERR_NOMEM = 0, 1, 2, 3, 4
+WD_ERR_NOT_CONVERGED, WD_ERR_BREAKDOWN, WD_ERR_TIMEOUT, WD_ERR_STATE = 5, 6, 7, 8
+PRECISIONS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+
+
+class WDError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libwd status {status}: {message}")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("dslash_lo", ctypes.c_double), ("dslash_hi", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("launches", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library() -> ctypes.CDLL:
+    """Load (building first if stale) libwd.so from the package's _build directory."""
+    global _lib
+    if _lib is None:
+        path = _build.build_library()
+        lib = ctypes.CDLL(path)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        i, d = ctypes.c_int, ctypes.c_double
+        sig = {
+            "wd_op_create": (i, [ctypes.POINTER(vp), ip, d, dp, i, i, vp]),
+            "wd_op_destroy": (None, [vp]),
+            "wd_op_set_gauge": (i, [vp, vp]),
+            "wd_apply": (i, [vp, vp, vp, i]),
+            "wd_apply_eo": (i, [vp, vp, vp, i, i]),
+            "wd_dslash_eo": (i, [vp, vp, vp, i, i]),
+            "wd_solve_cg": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
+            "wd_solve_cg_host": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
+            "wd_field_load": (i, [vp, i, vp]),
+            "wd_field_store": (i, [vp, i, vp]),
+            "wd_dslash_resident": (i, [vp, i, i, i]),
+            "wd_op_stream": (vp, [vp]),
+            "wd_dslash_bytes": (d, [vp]),
+            "wd_status_string": (ctypes.c_char_p, [i]),
+            "wd_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != WD_OK:
+        lib = load_library()
+        raise WDError(rc, lib.wd_last_error().decode() or lib.wd_status_string(rc).decode())
+
+
+def _dev(t: torch.Tensor, shape, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.complex128 or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous complex128 tensor of shape {tuple(shape)}")
+    return t
+
+
+def phases_array(phase) -> ctypes.Array:
+    ph = [complex(p) for p in phase]
+    if len(ph) != 4:
+        raise ValueError("phase needs one complex number per direction")
+    flat = []
+    for p in ph:
+        flat += [p.real, p.imag]
+    return (ctypes.c_double * 8)(*flat)
+
+
+@dataclass
+class SolveResult:
+    x: torch.Tensor
+    status: int
+    info: dict
+
+
+class WilsonDirac:
+    """Wilson-Dirac operator D = 1 - kappa H on one GPU (handle on a wd_op)."""
+
+    def __init__(self, dims, kappa: float, phase=(1, 1, 1, -1), prec: str = "f64",
+                 recon: int = 18, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("WilsonDirac needs a CUDA device; there is no CPU fallback")
+        self.lib = load_library()
+        self.dims = tuple(int(v) for v in dims)
+        self.V = 1
+        for v in self.dims:
+            self.V *= v
+        self.Vh = self.V // 2
+        self.kappa = float(kappa)
+        self.prec = prec
+        self.recon = int(recon)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        handle = ctypes.c_void_p()
+        dims_c = (ctypes.c_int * 4)(*self.dims)
+        rc = self.lib.wd_op_create(ctypes.byref(handle), dims_c, self.kappa, phases_array(phase),
+                                   PRECISIONS[prec], self.recon,
+                                   ctypes.c_void_p(self.stream.cuda_stream))
+        _check(rc)
+        self.handle = handle
+
+    # ------------------------------------------------------------------ life cycle
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.wd_op_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def work_stream(self) -> int:
+        """cudaStream_t (as an int) that libwd queues this operator's kernels on."""
+        return int(self.lib.wd_op_stream(self.handle) or 0)
+
+    @property
+    def dslash_bytes(self) -> float:
+        return float(self.lib.wd_dslash_bytes(self.handle))
+
+    # ------------------------------------------------------------------ operations
+    def set_gauge(self, U: torch.Tensor):
+        _dev(U, (self.V, 4, 3, 3), "U")
+        _check(self.lib.wd_op_set_gauge(self.handle, ctypes.c_void_p(U.data_ptr())))
+
+    def apply(self, psi: torch.Tensor, dagger: bool = False, out=None) -> torch.Tensor:
+        _dev(psi, (self.V, 3, 4), "psi")
+        out = torch.empty_like(psi) if out is None else _dev(out, (self.V, 3, 4), "out")
+        _check(self.lib.wd_apply(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(psi.data_ptr()), int(bool(dagger))))
+        return out
+
+    def apply_eo(self, psi: torch.Tensor, parity: int = 1, dagger: bool = False,
+                 out=None) -> torch.Tensor:
+        _dev(psi, (self.Vh, 3, 4), "psi")
+        out = torch.empty_like(psi) if out is None else _dev(out, (self.Vh, 3, 4), "out")
+        _check(self.lib.wd_apply_eo(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(psi.data_ptr()), int(parity),
+                                    int(bool(dagger))))
+        return out
+
+    def dslash_eo(self, psi: torch.Tensor, out_parity: int, dagger: bool = False,
+                  out=None) -> torch.Tensor:
+        _dev(psi, (self.Vh, 3, 4), "psi")
+        out = torch.empty_like(psi) if out is None else _dev(out, (self.Vh, 3, 4), "out")
+        _check(self.lib.wd_dslash_eo(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(psi.data_ptr()), int(out_parity),
+                                     int(bool(dagger))))
+        return out
+
+    def solve(self, b: torch.Tensor, tol: float = 1e-10, maxiter: int = 20000, parity: int = 1,
+              x0: torch.Tensor | None = None, check: bool = True) -> SolveResult:
+        _dev(b, (self.V, 3, 4), "b")
+        x = torch.zeros_like(b) if x0 is None else _dev(x0, (self.V, 3, 4), "x0").clone()
+        info = SolveInfo()
+        rc = self.lib.wd_solve_cg(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(b.data_ptr()), float(tol), int(maxiter),
+                                  int(parity), ctypes.byref(info))
+        if check and rc not in (WD_OK,):
+            _check(rc)
+        return SolveResult(x, rc, info.as_dict())
+
+    def solve_host(self, x_host: torch.Tensor, b_host: torch.Tensor, tol: float = 1e-10,
+                   maxiter: int = 20000, parity: int = 1) -> SolveResult:
+        """Solve with x and b in host memory (pinned for asynchronous copies)."""
+        for t, n in ((x_host, "x"), (b_host, "b")):
+            if t.is_cuda or t.dtype != torch.complex128 or tuple(t.shape) != (self.V, 3, 4) \
+                    or not t.is_contiguous():
+                raise ValueError(f"{n} must be a contiguous complex128 host tensor [V, 3, 4]")
+        info = SolveInfo()
+        rc = self.lib.wd_solve_cg_host(self.handle, ctypes.c_void_p(x_host.data_ptr()),
+                                       ctypes.c_void_p(b_host.data_ptr()), float(tol),
+                                       int(maxiter), int(parity), ctypes.byref(info))
+        _check(rc)
+        return SolveResult(x_host, rc, info.as_dict())
+
+    # resident fields, for timing the hopping term alone
+    def field_load(self, slot: int, half: torch.Tensor):
+        _dev(half, (self.Vh, 3, 4), "half")
+        _check(self.lib.wd_field_load(self.handle, int(slot), ctypes.c_void_p(half.data_ptr())))
+
+    def field_store(self, slot: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.Vh, 3, 4), dtype=torch.complex128, device="cuda")
+        _dev(out, (self.Vh, 3, 4), "out")
+        _check(self.lib.wd_field_store(self.handle, int(slot), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def dslash_resident(self, in_slot: int, out_parity: int, dagger: bool = False):
+        _check(self.lib.wd_dslash_resident(self.handle, int(in_slot), int(out_parity),
+                                           int(bool(dagger))))

@@ -18,9 +18,11 @@ these seeded fields stand in for them:
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
-_CHUNK = 1 << 18  # matrices per chunk, bounds temporary memory
+_CHUNK = 1 << 16  # matrices per generator chunk (part of the field's definition)
 
 
 def volume(dims) -> int:
@@ -72,18 +74,34 @@ def reunitarise(U: np.ndarray) -> np.ndarray:
     return np.stack([r0, r1, r2], axis=-2)
 
 
-def su3_links(dims, eps: float = 0.3, seed: int = 1) -> np.ndarray:
-    """Seeded gauge field U_mu(x) = exp(i eps sum_a c_a lambda_a / 2), [V, 4, 3, 3]."""
+def _links_chunk(args):
+    seed, k, n, eps = args
+    rng = np.random.default_rng((seed, k))
+    c = rng.standard_normal((n, 8))
+    H = np.einsum("na,aij->nij", c, gell_mann() / 2)
+    return reunitarise(_expm_antihermitian(1j * eps * H))
+
+
+def su3_links(dims, eps: float = 0.3, seed: int = 1, workers: int | None = None) -> np.ndarray:
+    """Seeded gauge field U_mu(x) = exp(i eps sum_a c_a lambda_a / 2), [V, 4, 3, 3].
+
+    The 4V matrices are drawn in fixed chunks of 2^16, chunk k from the
+    generator seeded by (seed, k), so the field does not depend on how many
+    worker processes build it (large lattices use a spawn-started pool)."""
     V = volume(dims)
     n = 4 * V
-    rng = np.random.default_rng(seed)
-    lam = gell_mann() / 2
+    jobs = [(seed, k, min(_CHUNK, n - a), eps) for k, a in enumerate(range(0, n, _CHUNK))]
     out = np.empty((n, 3, 3), dtype=np.complex128)
-    for a in range(0, n, _CHUNK):
-        b = min(n, a + _CHUNK)
-        c = rng.standard_normal((b - a, 8))
-        H = np.einsum("na,aij->nij", c, lam)
-        out[a:b] = reunitarise(_expm_antihermitian(1j * eps * H))
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1) if len(jobs) >= 32 else 1
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for k, blk in enumerate(pool.imap(_links_chunk, jobs, chunksize=4)):
+                out[k * _CHUNK:k * _CHUNK + len(blk)] = blk
+    else:
+        for k, job in enumerate(jobs):
+            out[k * _CHUNK:k * _CHUNK + job[2]] = _links_chunk(job)
     return out.reshape(V, 4, 3, 3)
 
 

@@ -1,0 +1,107 @@
+"""The C ABI library builds, loads and exports every function include/wd.h
+declares, and rejects bad arguments before touching a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1401_2039_gb300 import load_library
+    return load_library()
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(wd_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("wd_apply", "wd_apply_eo", "wd_solve_cg", "wd_op_create",
+                     "wd_op_set_gauge", "wd_dslash_eo"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    lib.wd_status_string.restype = ctypes.c_char_p
+    assert lib.wd_status_string(0) == b"ok"
+    assert lib.wd_status_string(2) == b"invalid lattice dimensions"
+    assert lib.wd_status_string(99) == b"unknown status"
+
+
+def _create(lib, dims, prec=0, recon=18, kappa=0.12, phase=(1, 0, 1, 0, 1, 0, -1, 0)):
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*dims)
+    ph = (ctypes.c_double * 8)(*phase)
+    lib.wd_op_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_void_p]
+    return lib.wd_op_create(ctypes.byref(h), d, kappa, ph, prec, recon, None), h
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 4, 4), (4, 4, 5, 4), (4, 4, 4, 0), (0, 2, 2, 2),
+                                  (4, -2, 4, 4), (4, 4, 4, 1)])
+def test_create_rejects_bad_dims(lib, dims):
+    rc, h = _create(lib, dims)
+    assert rc == 2 and not h.value
+
+
+@pytest.mark.parametrize("prec,recon", [(7, 18), (-1, 18), (0, 13), (1, 0)])
+def test_create_rejects_bad_precision_or_recon(lib, prec, recon):
+    rc, h = _create(lib, (4, 4, 4, 4), prec, recon)
+    assert rc == 1 and not h.value
+
+
+def test_create_rejects_non_finite(lib):
+    rc, _ = _create(lib, (4, 4, 4, 4), kappa=float("nan"))
+    assert rc == 1
+    rc, _ = _create(lib, (4, 4, 4, 4), phase=(1, 0, 1, 0, 1, float("inf"), -1, 0))
+    assert rc == 1
+
+
+def test_null_handles_are_rejected(lib):
+    lib.wd_apply.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int]
+    lib.wd_apply_eo.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int]
+    lib.wd_solve_cg.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                        ctypes.c_int, ctypes.c_void_p]
+    assert lib.wd_apply(None, None, None, 0) == 1
+    assert lib.wd_apply_eo(None, None, None, 1, 0) == 1
+    assert lib.wd_solve_cg(None, None, None, 1e-10, 100, 1, None) == 1
+    lib.wd_last_error.restype = ctypes.c_char_p
+    assert b"null" in lib.wd_last_error()
+    lib.wd_op_destroy(None)   # no-op
+
+
+def test_product_path_has_no_cpu_fallback():
+    import torch
+    from paper_1401_2039_gb300 import WilsonDirac
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError, match="CUDA"):
+        WilsonDirac((4, 4, 4, 4), 0.12)
+
+
+def test_product_package_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1401_2039_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in src.lower(), f

@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Norm-wise relative tolerances ||gpu - oracle|| / ||oracle|| by storage
+precision: FP64 1e-13, FP32 1e-6, FP16/BF16 2e-2.  Solves are judged by
+the FP64 true residual ||b - D x|| / ||b|| the oracle computes, and by the
+distance to the oracle's solution.
+
+Lattices span several 128-site thread blocks with a ragged last block
+(e.g. 6x6x2x4: Vh = 144), the 2^4 lattice where x+mu and x-mu coincide,
+anisotropic shapes and both boundary-phase kinds.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-2, "bf16": 2e-2}
+PRECS = ["f64", "f32", "f16", "bf16"]
+DIMS = [(4, 4, 4, 4), (6, 6, 2, 4), (2, 2, 2, 2), (16, 8, 8, 8), (8, 4, 6, 10)]
+PHASES = {"apbc": syn.workloads.APBC_T,
+          "twisted": tuple(np.exp(1j * np.array([0.3, 0.0, -0.9, np.pi])))}
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+_fields = {}
+
+
+def fields(dims, seed=1):
+    key = (dims, seed)
+    if key not in _fields:
+        U = syn.su3_links(dims, eps=0.3, seed=seed)
+        psi = syn.gaussian_spinor(syn.volume(dims), seed + 100)
+        _fields[key] = (U, psi)
+    return _fields[key]
+
+
+def make_op(dims, kappa, phase, prec, recon, U):
+    from paper_1401_2039_gb300 import WilsonDirac
+    op = WilsonDirac(dims, kappa, phase, prec=prec, recon=recon)
+    op.set_gauge(cuda(U))
+    return op
+
+
+# --------------------------------------------------------------------- hopping term
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("recon", [18, 12])
+def test_dslash_eo(dims, prec, recon):
+    U, psi = fields(dims)
+    for phname, phase in PHASES.items():
+        op = make_op(dims, 0.12, phase, prec, recon, U)
+        for out_parity in (0, 1):
+            src = syn.to_half(psi, dims, 1 - out_parity)
+            for dagger in (False, True):
+                ref = oracle.hop_eo(src, U, dims, phase, out_parity, dagger)
+                got = host(op.dslash_eo(cuda(src), out_parity, dagger))
+                e = rel(got, ref)
+                assert e < TOL[prec], (phname, out_parity, dagger, e)
+        op.close()
+
+
+def test_dslash_generic_links_f64():
+    """18-real links need not be unitary: random complex matrices."""
+    dims = (6, 4, 2, 4)
+    rng = np.random.default_rng(5)
+    V = syn.volume(dims)
+    U = (rng.standard_normal((V, 4, 3, 3)) + 1j * rng.standard_normal((V, 4, 3, 3)))
+    psi = syn.gaussian_spinor(V, 6)
+    op = make_op(dims, 0.1, PHASES["twisted"], "f64", 18, U)
+    for par in (0, 1):
+        for dag in (False, True):
+            src = syn.to_half(psi, dims, 1 - par)
+            assert rel(host(op.dslash_eo(cuda(src), par, dag)),
+                       oracle.hop_eo(src, U, dims, PHASES["twisted"], par, dag)) < 1e-13
+
+
+# --------------------------------------------------------------------- operators
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 2, 4), (8, 4, 6, 10)])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("recon", [18, 12])
+def test_apply_full(dims, prec, recon):
+    U, psi = fields(dims)
+    kappa = 0.124
+    phase = PHASES["apbc"]
+    op = make_op(dims, kappa, phase, prec, recon, U)
+    for dagger in (False, True):
+        ref = oracle.apply(psi, U, dims, kappa, phase, dagger)
+        got = host(op.apply(cuda(psi), dagger))
+        assert rel(got, ref) < TOL[prec], dagger
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 2, 4), (2, 2, 2, 2)])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("recon", [18, 12])
+def test_apply_eo(dims, prec, recon):
+    U, psi = fields(dims)
+    kappa = 0.13
+    phase = PHASES["twisted"]
+    op = make_op(dims, kappa, phase, prec, recon, U)
+    for parity in (0, 1):
+        src = syn.to_half(psi, dims, parity)
+        for dagger in (False, True):
+            ref = oracle.apply_eo(src, U, dims, kappa, phase, parity, dagger)
+            got = host(op.apply_eo(cuda(src), parity, dagger))
+            assert rel(got, ref) < TOL[prec], (parity, dagger)
+
+
+def test_kappa_zero_is_identity():
+    dims = (4, 4, 2, 2)
+    U, psi = fields(dims)
+    op = make_op(dims, 0.0, PHASES["apbc"], "f64", 18, U)
+    assert np.array_equal(host(op.apply(cuda(psi))), psi)
+    half = syn.to_half(psi, dims, 1)
+    assert np.array_equal(host(op.apply_eo(cuda(half), 1)), half)
+
+
+# --------------------------------------------------------------------- solves
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dims,kappa,recon", [((4, 4, 4, 4), 0.12, 18),
+                                              ((8, 8, 8, 8), 0.124, 18),
+                                              ((8, 8, 8, 8), 0.124, 12),
+                                              ((6, 6, 2, 4), 0.124, 12)])
+def test_solve_matches_oracle(prec, dims, kappa, recon):
+    U, _ = fields(dims)
+    phase = PHASES["apbc"]
+    b = syn.gaussian_spinor(syn.volume(dims), 2)
+    op = make_op(dims, kappa, phase, prec, recon, U)
+    res = op.solve(cuda(b), tol=1e-10, maxiter=5000, parity=1)
+    x = host(res.x)
+    r_true = np.linalg.norm(b - oracle.apply(x, U, dims, kappa, phase)) / np.linalg.norm(b)
+    assert r_true <= 1.05e-10, (r_true, res.info)
+    assert abs(res.info["true_rel_resid"] - r_true) <= 1e-3 * r_true + 1e-15
+    x_ref, _, ok = oracle.solve(b, U, dims, kappa, phase, parity=1, tol=1e-13)
+    assert ok
+    assert rel(x, x_ref) < 1e-8
+    if prec != "f64":
+        assert res.info["reliable_updates"] >= 2
+
+
+def test_solve_even_parity_and_initial_guess():
+    dims, kappa = (6, 6, 2, 4), 0.124
+    U, _ = fields(dims)
+    phase = PHASES["twisted"]
+    b = syn.gaussian_spinor(syn.volume(dims), 3)
+    op = make_op(dims, kappa, phase, "f32", 18, U)
+    res = op.solve(cuda(b), tol=1e-10, parity=0)
+    x = host(res.x)
+    assert np.linalg.norm(b - oracle.apply(x, U, dims, kappa, phase)) <= 1.05e-10 * np.linalg.norm(b)
+    # starting from the solution needs no iteration
+    res2 = op.solve(cuda(b), tol=1e-8, parity=0, x0=res.x)
+    assert res2.info["iters"] == 0 and res2.status == 0
+
+
+def test_solve_zero_rhs_and_kappa_zero():
+    dims = (4, 4, 4, 4)
+    U, psi = fields(dims)
+    op = make_op(dims, 0.12, PHASES["apbc"], "f32", 18, U)
+    res = op.solve(cuda(np.zeros_like(psi)), tol=1e-10)
+    assert res.status == 0 and np.count_nonzero(host(res.x)) == 0
+    op0 = make_op(dims, 0.0, PHASES["apbc"], "f64", 18, U)
+    res0 = op0.solve(cuda(psi), tol=1e-12)
+    assert res0.status == 0 and res0.info["iters"] <= 1
+    assert rel(host(res0.x), psi) < 1e-15
+
+
+def test_solve_reports_not_converged():
+    from paper_1401_2039_gb300.wd import WD_ERR_NOT_CONVERGED
+    dims = (8, 8, 8, 8)
+    U, _ = fields(dims)
+    b = syn.gaussian_spinor(syn.volume(dims), 2)
+    op = make_op(dims, 0.124, PHASES["apbc"], "f32", 18, U)
+    res = op.solve(cuda(b), tol=1e-10, maxiter=5, check=False)
+    assert res.status == WD_ERR_NOT_CONVERGED
+    assert res.info["iters"] == 5
+    assert 1e-10 < res.info["true_rel_resid"] < 1.0
+
+
+def test_host_memory_solve_matches_device_solve():
+    dims, kappa = (8, 8, 8, 8), 0.124
+    U, _ = fields(dims)
+    b = syn.gaussian_spinor(syn.volume(dims), 2)
+    op = make_op(dims, kappa, PHASES["apbc"], "f32", 18, U)
+    dev = op.solve(cuda(b), tol=1e-10)
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    res = op.solve_host(xh, bh, tol=1e-10)
+    assert np.array_equal(res.x.numpy(), host(dev.x))   # same kernels, same order: bitwise
+    assert res.info["iters"] == dev.info["iters"]
+
+
+def test_resident_dslash_matches_canonical():
+    dims = (8, 4, 6, 10)
+    U, psi = fields(dims)
+    for prec, recon in (("f32", 18), ("f16", 12)):
+        op = make_op(dims, 0.12, PHASES["apbc"], prec, recon, U)
+        src = syn.to_half(psi, dims, 0)
+        op.field_load(0, cuda(src))
+        op.dslash_resident(0, 1)
+        got = host(op.field_store(1))
+        assert rel(got, oracle.hop_eo(src, U, dims, PHASES["apbc"], 1)) < TOL[prec]
+        assert op.dslash_bytes == syn.volume(dims) // 2 * (48 + 8 * recon) * (4 if prec == "f32" else 2)
