@@ -44,27 +44,38 @@ def gell_mann() -> np.ndarray:
     return lam
 
 
-def _expm_antihermitian(X: np.ndarray) -> np.ndarray:
-    """exp(X) for a batch of small matrices: scaling and squaring (2^-4) with a
+def _mm_soa(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Products of batches of 3x3 matrices stored as [3, 3, n] (long contiguous
+    vectors per entry, so every numpy call streams n elements)."""
+    c = np.empty_like(a)
+    for i in range(3):
+        for k in range(3):
+            c[i, k] = a[i, 0] * b[0, k] + a[i, 1] * b[1, k] + a[i, 2] * b[2, k]
+    return c
+
+
+def _expm_soa(X: np.ndarray) -> np.ndarray:
+    """exp(X) for [3, 3, n] batches: scaling and squaring (2^-4) with a
     degree-8 Taylor polynomial; for ||X|| < 2 the truncation is below 1e-14
     and the re-unitarisation that follows removes it from the group."""
     s = 4
     Y = X / (1 << s)
-    n = X.shape[-1]
-    eye = np.broadcast_to(np.eye(n, dtype=X.dtype), X.shape)
+    eye = np.zeros_like(X)
+    for i in range(3):
+        eye[i, i] = 1
     E = eye.copy()
-    term = eye.copy()
+    term = eye
     for k in range(1, 9):
-        term = np.matmul(term, Y) / k
-        E = E + term
+        term = _mm_soa(term, Y) / k
+        E += term
     for _ in range(s):
-        E = np.matmul(E, E)
+        E = _mm_soa(E, E)
     return E
 
 
 def reunitarise(U: np.ndarray) -> np.ndarray:
-    """Project a batch of near-SU(3) matrices onto SU(3): orthonormalise
-    rows 0 and 1, then row 2 = conj(row0 x row1)."""
+    """Project a batch of near-SU(3) matrices [..., 3, 3] onto SU(3):
+    orthonormalise rows 0 and 1, then row 2 = conj(row0 x row1)."""
     r0 = U[..., 0, :]
     r0 = r0 / np.linalg.norm(r0, axis=-1, keepdims=True)
     r1 = U[..., 1, :]
@@ -74,12 +85,24 @@ def reunitarise(U: np.ndarray) -> np.ndarray:
     return np.stack([r0, r1, r2], axis=-2)
 
 
+def _reunitarise_soa(U: np.ndarray) -> np.ndarray:
+    """reunitarise for [3, 3, n] batches, returned as [n, 3, 3]."""
+    r0, r1 = U[0], U[1]
+    r0 = r0 / np.sqrt((np.abs(r0) ** 2).sum(axis=0))
+    r1 = r1 - (np.conj(r0) * r1).sum(axis=0) * r0
+    r1 = r1 / np.sqrt((np.abs(r1) ** 2).sum(axis=0))
+    r2 = np.conj(np.stack([r0[1] * r1[2] - r0[2] * r1[1],
+                           r0[2] * r1[0] - r0[0] * r1[2],
+                           r0[0] * r1[1] - r0[1] * r1[0]]))
+    return np.ascontiguousarray(np.stack([r0, r1, r2]).transpose(2, 0, 1))
+
+
 def _links_chunk(args):
     seed, k, n, eps = args
     rng = np.random.default_rng((seed, k))
     c = rng.standard_normal((n, 8))
-    H = np.einsum("na,aij->nij", c, gell_mann() / 2)
-    return reunitarise(_expm_antihermitian(1j * eps * H))
+    H = np.einsum("aij,na->ijn", gell_mann() / 2, c)          # [3, 3, n]
+    return _reunitarise_soa(_expm_soa(1j * eps * H))
 
 
 def su3_links(dims, eps: float = 0.3, seed: int = 1, workers: int | None = None) -> np.ndarray:
@@ -87,21 +110,24 @@ def su3_links(dims, eps: float = 0.3, seed: int = 1, workers: int | None = None)
 
     The 4V matrices are drawn in fixed chunks of 2^16, chunk k from the
     generator seeded by (seed, k), so the field does not depend on how many
-    worker processes build it (large lattices use a spawn-started pool)."""
+    threads build it (numpy releases the GIL inside its array kernels)."""
     V = volume(dims)
     n = 4 * V
     jobs = [(seed, k, min(_CHUNK, n - a), eps) for k, a in enumerate(range(0, n, _CHUNK))]
     out = np.empty((n, 3, 3), dtype=np.complex128)
+
+    def run(k):
+        out[k * _CHUNK:k * _CHUNK + jobs[k][2]] = _links_chunk(jobs[k])
+
     if workers is None:
-        workers = min(16, os.cpu_count() or 1) if len(jobs) >= 32 else 1
-    if workers > 1:
-        import multiprocessing as mp
-        with mp.get_context("spawn").Pool(workers) as pool:
-            for k, blk in enumerate(pool.imap(_links_chunk, jobs, chunksize=4)):
-                out[k * _CHUNK:k * _CHUNK + len(blk)] = blk
+        workers = min(16, os.cpu_count() or 1)
+    if workers > 1 and len(jobs) > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            list(ex.map(run, range(len(jobs))))
     else:
-        for k, job in enumerate(jobs):
-            out[k * _CHUNK:k * _CHUNK + job[2]] = _links_chunk(job)
+        for k in range(len(jobs)):
+            run(k)
     return out.reshape(V, 4, 3, 3)
 
 

@@ -177,7 +177,9 @@ def test_solve_zero_rhs_and_kappa_zero():
     assert res.status == 0 and np.count_nonzero(host(res.x)) == 0
     op0 = make_op(dims, 0.0, PHASES["apbc"], "f64", 18, U)
     res0 = op0.solve(cuda(psi), tol=1e-12)
-    assert res0.status == 0 and res0.info["iters"] <= 1
+    # D = I: the first iteration is exact; the rest of its graph batch is a no-op
+    assert res0.status == 0 and res0.info["true_rel_resid"] == 0.0
+    assert res0.info["iters"] <= 8
     assert rel(host(res0.x), psi) < 1e-15
 
 
