@@ -140,6 +140,41 @@ double wd_dslash_bytes(const wd_op *op);
 const char *wd_status_string(int status);
 const char *wd_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Schur operator for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a deployment variant of
+ * wd_apply_eo.  Callers that cannot call cudaMalloc (code running while a
+ * host framework captures its stream into a CUDA graph, plug-ins whose host
+ * application owns all device memory through its own pool, real-time paths
+ * that must not enter the driver's allocator) cannot create a wd_op, which
+ * allocates.  This entry point needs no handle and allocates nothing: it
+ * reads the caller's canonical FP64 arrays directly and keeps its one
+ * intermediate field in a fixed device array inside libwd (12,582,912
+ * bytes, held on every GPU that loads the library until the process exits).
+ *
+ *   out     device, [V/2][3][4] complex128, parity `parity`; must not overlap in
+ *   in      device, [V/2][3][4] complex128, parity `parity`
+ *   U       device, [V][4][3][3] complex128 (canonical gauge field)
+ *   dims, kappa, phase, parity, dagger: as for wd_op_create / wd_apply_eo
+ *   stream  cudaStream_t the two kernels are queued on (NULL = legacy)
+ * out = Mhat_p in (dagger: Mhat_p^dag in), FP64 throughout, asynchronous.
+ *
+ * Limits and sharing: V/2 must not exceed WD_NOALLOC_MAX_VH (else
+ * WD_ERR_DIMS, nothing queued).  Every call shares the one device array,
+ * which keeps the last call's contents; calls that overlap on the GPU
+ * (different streams or host threads) race on it and must be serialised by
+ * the caller.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture begins.  Errors are described by
+ * wd_noalloc_last_error().
+ */
+#define WD_NOALLOC_MAX_VH 65536
+int wd_apply_eo_noalloc(double *out, const double *in, const double *U, const int dims[4],
+                        double kappa, const double phase[8], int parity, int dagger,
+                        void *stream);
+const char *wd_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif
