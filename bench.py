@@ -145,6 +145,27 @@ def combine_ranks(elapsed_ms: float, bytes_total: float, launches: int):
     return float(t.item()), float(s[0].item()), int(s[1].item())
 
 
+def kernel_source_sha() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1401_2039_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read()
+                   for f in ("dslash.cuh", "wd_internal.cuh"))
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def captured_traffic(workload: str):
+    """ncu DRAM bytes (read + write) per launch of the hopping term from the
+    committed capture, or None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        tr = json.load(f)
+    if tr.get("kernel_source_sha256_16") != kernel_source_sha() or workload not in tr:
+        return None
+    return tr[workload]["traffic_bytes_per_launch"]
+
+
 def fp64_schur_bytes(vh: int) -> float:
     """Compulsory bytes of one FP64 Schur application: two hops (in 24 + out 24 +
     8 links x 18 reals per site, plus 24 for the xpay input on the second)."""
@@ -284,12 +305,7 @@ def main():
     torch.cuda.synchronize()
     dslash_us = d0.elapsed_time(d1) * 1e3 / n_d
     achieved = op.dslash_bytes / (dslash_us * 1e-6) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "dslash_traffic.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            tr = json.load(f)
-        traffic = tr.get(f"{w.name}")
+    traffic = captured_traffic(w.name)
 
     # ---- plain FP64 even-odd CGNR on the same GPU, same problem
     fp64_ms = None

@@ -101,6 +101,7 @@ typedef struct {
     double dslash_hi;        /* hopping-term applications in FP64                  */
     double bytes;            /* algorithmic device bytes moved by the solve        */
     double launches;         /* kernels launched (directly or inside CUDA graphs)  */
+    int restarts;            /* Krylov restarts after a stagnating residual        */
 } wd_solve_info;
 
 /* Solve D x = b (goal "xx = Dirac^-1 bb", templates "CGNR schur") to
@@ -115,6 +116,14 @@ typedef struct {
 int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, int maxiter,
                 int parity, wd_solve_info *info);
 
+/* Reliable-update parameters of the mixed-precision solve (ignored for
+ * WD_F64): the FP64 residual is recomputed whenever the iterated residual
+ * has fallen by ru_delta (0 < ru_delta < 1; default 0.01 for WD_F32, 0.1
+ * for WD_F16/WD_BF16) since the last
+ * recomputation, and the Krylov direction restarts when the iterated residual
+ * has not improved for stall_iters iterations (default 200). */
+int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters);
+
 /* The same solve with x and b in HOST memory (pageable or pinned); the
  * host<->device copies go through buffers the handle owns. */
 int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
@@ -128,6 +137,16 @@ int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol
 int wd_field_load(wd_op *op, int slot, const double *half_in);
 int wd_field_store(wd_op *op, int slot, double *half_out);
 int wd_dslash_resident(wd_op *op, int in_slot, int out_parity, int dagger);
+
+/* Launch configuration of the hopping term picked by the autotuner when the
+ * gauge field was loaded (hi = 0: storage precision, hi = 1: the FP64
+ * kernels of the reliable updates).  us (optional, n entries) receives the
+ * measured microseconds per launch of every candidate; block, min_blocks and
+ * sites_per_thread (optional) describe the chosen one.  Returns its index,
+ * or -1 for a null handle.  Setting WD_DSLASH_CFG=k in the environment
+ * forces candidate k, WD_TUNE=0 keeps candidate 0. */
+int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,
+                     int *sites_per_thread);
 
 /* Stream the handle queues its work on (a cudaStream_t). */
 void *wd_op_stream(wd_op *op);

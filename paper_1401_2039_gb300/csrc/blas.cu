@@ -117,6 +117,17 @@ k_xmy_norm(long n, double *out, const double *x, const double *y, Reduction red)
     block_reduce_finish<BLAS_BLOCK>(acc, red);
 }
 
+// out = y + a x, FP64
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_xpay_f64(long n, double *out, const double *y, double a, const double *x) {
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        const double2 yv = reinterpret_cast<const double2 *>(y)[i];
+        const double2 xv = reinterpret_cast<const double2 *>(x)[i];
+        reinterpret_cast<double2 *>(out)[i] = make_double2(yv.x + a * xv.x, yv.y + a * xv.y);
+    }
+}
+
 // out (precision SO) = scale * in (precision SI), one site per thread.
 template <typename SO, typename SI>
 __global__ void __launch_bounds__(BLAS_BLOCK)
@@ -207,6 +218,13 @@ cudaError_t launch_xmy_norm(const Geom &g, double *out, const double *x, const d
                             const Reduction &red, cudaStream_t s) {
     const long n = spinor_chunks(WD_F64, g);
     k_xmy_norm<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, out, x, y, red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xpay_f64(const Geom &g, double *out, const double *y, double a,
+                            const double *x, cudaStream_t s) {
+    const long n = spinor_chunks(WD_F64, g);
+    k_xpay_f64<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, out, y, a, x);
     return cudaGetLastError();
 }
 

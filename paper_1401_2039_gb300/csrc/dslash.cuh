@@ -89,34 +89,38 @@ template <typename S, typename R, int RECON>
 __device__ __forceinline__ void load_link(const void *base, long stride, long h, R *U) {
     Rec<S, RECON>::template load<R, 1>(base, stride, h, U);
     if (RECON == 12) {
-        // row2 = conj(row0 x row1)
+        // row2 = conj(row0 x row1): (a1 b2 - a2 b1)^*, (a2 b0 - a0 b2)^*, (a0 b1 - a1 b0)^*
         const R a0r = U[0], a0i = U[1], a1r = U[2], a1i = U[3], a2r = U[4], a2i = U[5];
         const R b0r = U[6], b0i = U[7], b1r = U[8], b1i = U[9], b2r = U[10], b2i = U[11];
-        // (a1 b2 - a2 b1)^*
-        U[12] = (a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i);
-        U[13] = -((a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r));
-        // (a2 b0 - a0 b2)^*
-        U[14] = (a2r * b0r - a2i * b0i) - (a0r * b2r - a0i * b2i);
-        U[15] = -((a2r * b0i + a2i * b0r) - (a0r * b2i + a0i * b2r));
-        // (a0 b1 - a1 b0)^*
-        U[16] = (a0r * b1r - a0i * b1i) - (a1r * b0r - a1i * b0i);
-        U[17] = -((a0r * b1i + a0i * b1r) - (a1r * b0i + a1i * b0r));
+        R t;
+        t = a1r * b2r; t -= a1i * b2i; t -= a2r * b1r; t += a2i * b1i; U[12] = t;
+        t = a2r * b1i; t += a2i * b1r; t -= a1r * b2i; t -= a1i * b2r; U[13] = t;
+        t = a2r * b0r; t -= a2i * b0i; t -= a0r * b2r; t += a0i * b2i; U[14] = t;
+        t = a0r * b2i; t += a0i * b2r; t -= a2r * b0i; t -= a2i * b0r; U[15] = t;
+        t = a0r * b1r; t -= a0i * b1i; t -= a1r * b0r; t += a1i * b0i; U[16] = t;
+        t = a1r * b0i; t += a1i * b0r; t -= a0r * b1i; t -= a0i * b1r; U[17] = t;
     }
 }
 
-// u[k][a] = sum_b U[a][b] h[k][b]
+// u[k][a] = sum_b U[a][b] h[k][b], written as chains of single
+// multiply-adds so that every real product becomes one FMA.
 template <typename R>
 __device__ __forceinline__ void su3_mul(const R *U, const cx<R> h[2][3], cx<R> u[2][3]) {
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            R re = 0, im = 0;
+            R re = U[6 * a] * h[k][0].re;
+            R im = U[6 * a] * h[k][0].im;
+            re -= U[6 * a + 1] * h[k][0].im;
+            im += U[6 * a + 1] * h[k][0].re;
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
+            for (int b = 1; b < 3; ++b) {
                 const R ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
-                re += ur * h[k][b].re - ui * h[k][b].im;
-                im += ur * h[k][b].im + ui * h[k][b].re;
+                re += ur * h[k][b].re;
+                re -= ui * h[k][b].im;
+                im += ur * h[k][b].im;
+                im += ui * h[k][b].re;
             }
             u[k][a] = {re, im};
         }
@@ -129,12 +133,17 @@ __device__ __forceinline__ void su3_adj_mul(const R *U, const cx<R> h[2][3], cx<
     for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            R re = 0, im = 0;
+            R re = U[2 * a] * h[k][0].re;
+            R im = U[2 * a] * h[k][0].im;
+            re += U[2 * a + 1] * h[k][0].im;
+            im -= U[2 * a + 1] * h[k][0].re;
 #pragma unroll
-            for (int b = 0; b < 3; ++b) {
+            for (int b = 1; b < 3; ++b) {
                 const R ur = U[2 * (3 * b + a)], ui = U[2 * (3 * b + a) + 1];
-                re += ur * h[k][b].re + ui * h[k][b].im;
-                im += ur * h[k][b].im - ui * h[k][b].re;
+                re += ur * h[k][b].re;
+                re += ui * h[k][b].im;
+                im += ur * h[k][b].im;
+                im -= ui * h[k][b].re;
             }
             u[k][a] = {re, im};
         }
@@ -166,17 +175,32 @@ template <typename R> struct DslashArgs {
     Reduction red;
 };
 
+// Half-lattice index of the neighbour x +- mu of site h (coordinates c),
+// from offsets: h = ((t*Lz + z)*Ly + y)*(Lx/2) + x/2.
+template <int MU, int DIR>
+__device__ __forceinline__ long neighbour(const Geom &g, long h, const int c[4], bool &wrap) {
+    if (MU == 0) {
+        int xn = c[0] + DIR;
+        wrap = DIR > 0 ? (xn == g.L[0]) : (xn < 0);
+        if (wrap) xn = DIR > 0 ? 0 : g.L[0] - 1;
+        return h + ((xn >> 1) - (c[0] >> 1));
+    }
+    long step = g.hx;
+    if (MU >= 2) step *= g.L[1];
+    if (MU >= 3) step *= g.L[2];
+    wrap = DIR > 0 ? (c[MU] == g.L[MU] - 1) : (c[MU] == 0);
+    if (DIR > 0) return wrap ? h - (long)(g.L[MU] - 1) * step : h + step;
+    return wrap ? h + (long)(g.L[MU] - 1) * step : h - step;
+}
+
 template <typename S, typename R, int RECON, int MU, int DAG>
 __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4], long h, R *acc) {
     constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
     constexpr int SB = -SF;
     // forward hop: U_mu(x) in(x + mu)
     {
-        int n[4] = {c[0], c[1], c[2], c[3]};
-        n[MU] += 1;
-        const bool wrap = (n[MU] == a.g.L[MU]);
-        if (wrap) n[MU] = 0;
-        const long hn = half_index(a.g, n);
+        bool wrap;
+        const long hn = neighbour<MU, +1>(a.g, h, c, wrap);
         R psi[24];
         Rec<S, 24>::template load<R, 0>(a.in, a.g.stride, hn, psi);
         cx<R> hs[2][3], u[2][3];
@@ -189,11 +213,8 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
     }
     // backward hop: U_mu(x - mu)^dag in(x - mu)
     {
-        int n[4] = {c[0], c[1], c[2], c[3]};
-        n[MU] -= 1;
-        const bool wrap = (n[MU] < 0);
-        if (wrap) n[MU] = a.g.L[MU] - 1;
-        const long hn = half_index(a.g, n);
+        bool wrap;
+        const long hn = neighbour<MU, -1>(a.g, h, c, wrap);
         R psi[24];
         Rec<S, 24>::template load<R, 0>(a.in, a.g.stride, hn, psi);
         cx<R> hs[2][3], u[2][3];
@@ -206,41 +227,73 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
     }
 }
 
-template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_dslash(const DslashArgs<R> a) {
-    const long h = (long)blockIdx.x * BLOCK + threadIdx.x;
+// One output site per (thread, i < SPT): site h = block base + i * BLOCK +
+// thread, so each of a warp's loads stays one contiguous request.
+template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK, int MINB,
+          int SPT>
+__global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
     double nrm = 0.0;
-    if (h < a.g.vh) {
-        int c[4];
-        site_coords(a.g, h, a.parity, c);
-        R acc[24];
 #pragma unroll
-        for (int i = 0; i < 24; ++i) acc[i] = 0;
-        hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
-        hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
-        hop_pair<S, R, RECON, 2, DAG>(a, c, h, acc);
-        hop_pair<S, R, RECON, 3, DAG>(a, c, h, acc);
-        if (EPI == EPI_XPAY) {
-            R xv[24];
-            Rec<S, 24>::template load<R, 0>(a.x, a.g.stride, h, xv);
+    for (int i = 0; i < SPT; ++i) {
+        const long h = (long)blockIdx.x * (BLOCK * SPT) + i * BLOCK + threadIdx.x;
+        if (h < a.g.vh) {
+            int c[4];
+            site_coords(a.g, h, a.parity, c);
+            R acc[24];
 #pragma unroll
-            for (int i = 0; i < 24; ++i) acc[i] = xv[i] + a.scale * acc[i];
-        } else {
+            for (int k = 0; k < 24; ++k) acc[k] = 0;
+            hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
+            hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
+            hop_pair<S, R, RECON, 2, DAG>(a, c, h, acc);
+            hop_pair<S, R, RECON, 3, DAG>(a, c, h, acc);
+            if (EPI == EPI_XPAY) {
+                R xv[24];
+                Rec<S, 24>::template load<R, 0>(a.x, a.g.stride, h, xv);
 #pragma unroll
-            for (int i = 0; i < 24; ++i) acc[i] *= a.scale;
-        }
-        Rec<S, 24>::store(a.out, a.g.stride, h, acc);
-        if (NORM) {
-            R s = 0;
+                for (int k = 0; k < 24; ++k) acc[k] = xv[k] + a.scale * acc[k];
+            } else {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) s += acc[i] * acc[i];
-            nrm = (double)s;
+                for (int k = 0; k < 24; ++k) acc[k] *= a.scale;
+            }
+            Rec<S, 24>::store(a.out, a.g.stride, h, acc);
+            if (NORM) {
+                R sq = 0;
+#pragma unroll
+                for (int k = 0; k < 24; ++k) sq += acc[k] * acc[k];
+                nrm += (double)sq;
+            }
         }
     }
     if (NORM) block_reduce_finish<BLOCK>(nrm, a.red);
 }
 
-constexpr int DSLASH_BLOCK = 128;
+// Launch configurations the tuner chooses from: threads per block, the
+// minimum resident blocks per SM handed to the register allocator, and
+// output sites per thread.  Kernels that fuse a norm always use entry 0 so
+// that reductions add in one fixed order.
+struct DslashCfg { int block, minb, spt; };
+constexpr int N_DSLASH_CFG = 5;
+constexpr DslashCfg DSLASH_CFGS[N_DSLASH_CFG] = {
+    {128, 1, 1}, {128, 8, 1}, {256, 1, 1}, {256, 4, 1}, {128, 1, 2}};
+
+template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int CFG>
+void launch_cfg(const DslashArgs<R> &a, cudaStream_t s) {
+    constexpr DslashCfg C = DSLASH_CFGS[CFG];
+    const long per_block = (long)C.block * C.spt;
+    const unsigned grid = (unsigned)((a.g.vh + per_block - 1) / per_block);
+    k_dslash<S, R, RECON, DAG, EPI, NORM, C.block, C.minb, C.spt><<<grid, C.block, 0, s>>>(a);
+}
+
+template <typename S, typename R, int RECON, int DAG, int EPI>
+void launch_any_cfg(int cfg, const DslashArgs<R> &a, cudaStream_t s) {
+    switch (cfg) {
+    case 1: launch_cfg<S, R, RECON, DAG, EPI, 0, 1>(a, s); break;
+    case 2: launch_cfg<S, R, RECON, DAG, EPI, 0, 2>(a, s); break;
+    case 3: launch_cfg<S, R, RECON, DAG, EPI, 0, 3>(a, s); break;
+    case 4: launch_cfg<S, R, RECON, DAG, EPI, 0, 4>(a, s); break;
+    default: launch_cfg<S, R, RECON, DAG, EPI, 0, 0>(a, s); break;
+    }
+}
 
 template <typename S, typename R, int RECON>
 cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
@@ -258,25 +311,18 @@ cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
     a.parity = L.out_parity;
     if (L.red) a.red = *L.red;
     else a.red = Reduction{nullptr, nullptr, nullptr, FIN_NONE};
-    const unsigned grid = (unsigned)((L.g.vh + DSLASH_BLOCK - 1) / DSLASH_BLOCK);
-    const bool norm = L.red != nullptr;
-#define WD_LAUNCH(DAG, EPI, NORM)                                                         \
-    k_dslash<S, R, RECON, DAG, EPI, NORM, DSLASH_BLOCK><<<grid, DSLASH_BLOCK, 0, s>>>(a)
-    if (L.epi == EPI_PLAIN) {
-        if (L.dagger) WD_LAUNCH(1, EPI_PLAIN, 0); else WD_LAUNCH(0, EPI_PLAIN, 0);
-    } else if (!norm) {
-        if (L.dagger) WD_LAUNCH(1, EPI_XPAY, 0); else WD_LAUNCH(0, EPI_XPAY, 0);
+    const int cfg = L.cfg;
+    if (L.red) {   // fused norm: fixed configuration, fixed summation order
+        if (L.dagger) launch_cfg<S, R, RECON, 1, EPI_XPAY, 1, 0>(a, s);
+        else launch_cfg<S, R, RECON, 0, EPI_XPAY, 1, 0>(a, s);
+    } else if (L.epi == EPI_PLAIN) {
+        if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_PLAIN>(cfg, a, s);
+        else launch_any_cfg<S, R, RECON, 0, EPI_PLAIN>(cfg, a, s);
     } else {
-        if (L.dagger) WD_LAUNCH(1, EPI_XPAY, 1); else WD_LAUNCH(0, EPI_XPAY, 1);
+        if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_XPAY>(cfg, a, s);
+        else launch_any_cfg<S, R, RECON, 0, EPI_XPAY>(cfg, a, s);
     }
-#undef WD_LAUNCH
     return cudaGetLastError();
-}
-
-template <typename S, typename R>
-cudaError_t launch_dslash_prec(const DslashLaunch &L, cudaStream_t s) {
-    return L.gauge->recon == 12 ? launch_dslash_t<S, R, 12>(L, s)
-                                : launch_dslash_t<S, R, 18>(L, s);
 }
 
 }  // namespace wd

@@ -1,0 +1,9 @@
+// Hopping-term kernels with __nv_bfloat16 storage and 18-real links, in their own
+// translation unit so the precision/link-format variants compile in parallel.
+#include "dslash.cuh"
+
+namespace wd {
+cudaError_t launch_dslash_bf16_r18(const DslashLaunch &L, cudaStream_t s) {
+    return launch_dslash_t<__nv_bfloat16, float, 18>(L, s);
+}
+}  // namespace wd

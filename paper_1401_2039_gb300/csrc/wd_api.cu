@@ -4,24 +4,27 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
-#include "wd_internal.cuh"
+#include "dslash.cuh"
 
 namespace wd {
-cudaError_t launch_dslash_f64(const DslashLaunch &L, cudaStream_t s);
-cudaError_t launch_dslash_f32(const DslashLaunch &L, cudaStream_t s);
-cudaError_t launch_dslash_f16(const DslashLaunch &L, cudaStream_t s);
-cudaError_t launch_dslash_bf16(const DslashLaunch &L, cudaStream_t s);
+#define WD_DECL(P)                                                                         \
+    cudaError_t launch_dslash_##P##_r18(const DslashLaunch &L, cudaStream_t s);            \
+    cudaError_t launch_dslash_##P##_r12(const DslashLaunch &L, cudaStream_t s);
+WD_DECL(f64) WD_DECL(f32) WD_DECL(f16) WD_DECL(bf16)
+#undef WD_DECL
 
 cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s) {
+    const bool r12 = L.gauge->recon == 12;
     switch (prec) {
-    case WD_F64: return launch_dslash_f64(L, s);
-    case WD_F32: return launch_dslash_f32(L, s);
-    case WD_F16: return launch_dslash_f16(L, s);
-    case WD_BF16: return launch_dslash_bf16(L, s);
+    case WD_F64: return r12 ? launch_dslash_f64_r12(L, s) : launch_dslash_f64_r18(L, s);
+    case WD_F32: return r12 ? launch_dslash_f32_r12(L, s) : launch_dslash_f32_r18(L, s);
+    case WD_F16: return r12 ? launch_dslash_f16_r12(L, s) : launch_dslash_f16_r18(L, s);
+    case WD_BF16: return r12 ? launch_dslash_bf16_r12(L, s) : launch_dslash_bf16_r18(L, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -50,10 +53,12 @@ static int fail(int code, const std::string &msg) {
         if (rc_ != WD_OK) return rc_;                                                      \
     } while (0)
 
-// Parameters of the reliable-update scheme (Clark et al. 2010): refresh the
-// FP64 residual whenever the iterated residual has fallen by DELTA since
-// the last refresh.
-static const double RU_DELTA = 0.1;
+// Defaults of the reliable-update scheme (Clark et al. 2010): refresh the
+// FP64 residual whenever the iterated residual has fallen by delta since
+// the last refresh; restart the Krylov direction when the iterated residual
+// has not improved for stall_iters iterations.
+static const double RU_DELTA_DEFAULT = 0.1;
+static const int STALL_ITERS_DEFAULT = 200;
 static const int MAX_BATCH_LOG2 = 5;  // graph batches of 1, 2, ..., 32 iterations
 
 struct wd_op {
@@ -87,6 +92,16 @@ struct wd_op {
     SolverScalars *sc_host = nullptr; // pinned mirror
     double *dev_consts = nullptr;     // [0] scale, [1] 1/scale, [2] ratio
     double *host_consts = nullptr;    // pinned staging of dev_consts
+
+    // solver parameters (FP32 inner iterations stay accurate over a deeper
+    // residual drop than FP16/BF16 ones)
+    double ru_delta = RU_DELTA_DEFAULT;
+    int stall_iters = STALL_ITERS_DEFAULT;
+
+    // tuned launch configuration of the hopping term: [0] storage precision, [1] FP64
+    int cfg[2] = {0, 0};
+    double tune_us[2][8] = {};
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
 
     // CUDA graphs of 2^k CGNR iterations, per solved parity
     cudaGraphExec_t graphs[2][MAX_BATCH_LOG2 + 1] = {};
@@ -142,6 +157,7 @@ static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, con
     L.scale = scale;
     L.epi = x ? EPI_XPAY : EPI_PLAIN;
     L.red = red;
+    L.cfg = op->cfg[hi ? 1 : 0];
     WD_CUDA(launch_dslash(L, hi ? WD_F64 : op->prec, op->stream));
     return WD_OK;
 }
@@ -160,8 +176,67 @@ static int check_op(const wd_op *op) {
     return WD_OK;
 }
 
+// Autotuner: time every launch configuration of the plain hopping term on
+// this operator's lattice (two warm-up and five timed launches each, CUDA
+// events on the work stream) and keep the fastest.  WD_DSLASH_CFG=k forces
+// configuration k, WD_TUNE=0 keeps configuration 0.
+static int tune_dslash(wd_op *op, bool hi) {
+    const int slot = hi ? 1 : 0;
+    const char *force = getenv("WD_DSLASH_CFG");
+    const char *tune = getenv("WD_TUNE");
+    if (force) {
+        int k = atoi(force);
+        op->cfg[slot] = (k >= 0 && k < N_DSLASH_CFG) ? k : 0;
+        return WD_OK;
+    }
+    if (tune && tune[0] == '0') {
+        op->cfg[slot] = 0;
+        return WD_OK;
+    }
+    void *in = hi ? (void *)op->th : op->slot[0];
+    void *out = hi ? (void *)op->axh : op->slot[1];
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int k = 0; k < N_DSLASH_CFG; ++k) {
+        op->cfg[slot] = k;
+        for (int w = 0; w < 2; ++w)
+            WD_TRY(dslash(op, hi, w & 1, 0, out, in, nullptr, 1.0, nullptr));
+        WD_CUDA(cudaEventRecord(op->ev_t0, op->stream));
+        for (int r = 0; r < 5; ++r)
+            WD_TRY(dslash(op, hi, r & 1, 0, out, in, nullptr, 1.0, nullptr));
+        WD_CUDA(cudaEventRecord(op->ev_t1, op->stream));
+        WD_CUDA(cudaEventSynchronize(op->ev_t1));
+        float ms = 0;
+        WD_CUDA(cudaEventElapsedTime(&ms, op->ev_t0, op->ev_t1));
+        op->tune_us[slot][k] = ms * 1e3 / 5;
+        if (ms < best_ms) { best_ms = ms; best = k; }
+    }
+    op->cfg[slot] = best;
+    return WD_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
+
+int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters) {
+    if (!op) return fail(WD_ERR_ARG, "null operator handle");
+    if (!(ru_delta > 0.0 && ru_delta < 1.0) || stall_iters < 1)
+        return fail(WD_ERR_ARG, "ru_delta must lie in (0, 1) and stall_iters be >= 1");
+    op->ru_delta = ru_delta;
+    op->stall_iters = stall_iters;
+    return WD_OK;
+}
+
+int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,
+                     int *sites_per_thread) {
+    if (!op || (hi != 0 && hi != 1)) return -1;
+    const int k = op->cfg[hi];
+    for (int i = 0; us && i < n && i < N_DSLASH_CFG; ++i) us[i] = op->tune_us[hi][i];
+    if (block) *block = DSLASH_CFGS[k].block;
+    if (min_blocks) *min_blocks = DSLASH_CFGS[k].minb;
+    if (sites_per_thread) *sites_per_thread = DSLASH_CFGS[k].spt;
+    return k;
+}
 
 const char *wd_status_string(int s) {
     switch (s) {
@@ -196,6 +271,8 @@ void wd_op_destroy(wd_op *op) {
     for (void *p : op->allocations) cudaFree(p);
     if (op->sc_host) cudaFreeHost(op->sc_host);
     if (op->host_consts) cudaFreeHost(op->host_consts);
+    if (op->ev_t0) cudaEventDestroy(op->ev_t0);
+    if (op->ev_t1) cudaEventDestroy(op->ev_t1);
     if (op->ev_fork) cudaEventDestroy(op->ev_fork);
     if (op->ev_join) cudaEventDestroy(op->ev_join);
     if (op->stream) cudaStreamDestroy(op->stream);
@@ -206,6 +283,8 @@ static int create_impl(wd_op *op) {
     WD_CUDA(cudaStreamCreateWithFlags(&op->stream, cudaStreamNonBlocking));
     WD_CUDA(cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming));
     WD_CUDA(cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming));
+    WD_CUDA(cudaEventCreate(&op->ev_t0));
+    WD_CUDA(cudaEventCreate(&op->ev_t1));
 
     const Geom &g = op->g;
     // gauge fields
@@ -274,6 +353,7 @@ int wd_op_create(wd_op **out, const int dims[4], double kappa, const double phas
     memcpy(op->phase, phase, sizeof(op->phase));
     op->prec = prec;
     op->recon = recon;
+    op->ru_delta = prec == WD_F32 ? 0.01 : RU_DELTA_DEFAULT;
     op->user = (cudaStream_t)stream;
     int rc = create_impl(op);
     if (rc != WD_OK) {
@@ -291,6 +371,9 @@ int wd_op_set_gauge(wd_op *op, const double *U) {
     WD_TRY(fork(op));
     WD_CUDA(launch_pack_gauge(op->gauge_lo, op->g, U, op->stream));
     if (!op->hi_shared) WD_CUDA(launch_pack_gauge(op->gauge_hi, op->g, U, op->stream));
+    WD_TRY(tune_dslash(op, false));
+    if (!op->hi_shared) WD_TRY(tune_dslash(op, true));
+    else op->cfg[1] = op->cfg[0];
     WD_TRY(join(op));
     op->gauge_loaded = true;
     return WD_OK;
@@ -373,6 +456,8 @@ struct SolveState {
     double r_hi;        // ||r_hi|| at the last refresh
     int ru;             // reliable updates
     double dslash_lo, dslash_hi, bytes, launches;
+    int restarts;
+    bool th_valid;      // th holds H_qp x_hi for the current x_hi
 };
 
 double field_b(const wd_op *op, int prec) { return (double)op->g.vh * 24 * prec_bytes(prec); }
@@ -442,6 +527,7 @@ int true_residual(wd_op *op, SolveState &st) {
     Reduction r0 = reduction(op, FIN_STORE0);
     WD_TRY(schur(op, true, st.p, 0, op->axh, op->xh, op->th, nullptr));
     WD_CUDA(launch_xmy_norm(op->g, op->rh, op->bh, op->axh, r0, op->stream));
+    st.th_valid = true;
     st.dslash_hi += 2;
     st.launches += 3;
     st.bytes += dslash_b(op, true, false) + dslash_b(op, true, true) + 3 * field_b(op, WD_F64);
@@ -473,27 +559,37 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
         WD_CUDA(launch_pack_full(WD_F64, g, xe, xo, x, op->stream));
     }
     WD_TRY(dslash(op, true, st.p, 0, op->bh, op->hb[st.q], op->hb[st.p], op->kappa, nullptr));
-    Reduction r1 = reduction(op, FIN_STORE1), r0 = reduction(op, FIN_STORE0);
+    Reduction r1 = reduction(op, FIN_STORE1), r0 = reduction(op, FIN_STORE0),
+              r2 = reduction(op, FIN_STORE2), r3 = reduction(op, FIN_STORE3);
     WD_CUDA(launch_norm2(WD_F64, g, op->hb[st.q], r1, op->stream));
-    WD_TRY(read_scalars(op));
-    double nb2 = op->sc_host->scratch[1];
     WD_CUDA(launch_norm2(WD_F64, g, op->hb[st.p], r0, op->stream));
+    WD_CUDA(launch_norm2(WD_F64, g, op->xh, r2, op->stream));
+    WD_CUDA(launch_norm2(WD_F64, g, op->bh, r3, op->stream));
     WD_TRY(read_scalars(op));
-    nb2 += op->sc_host->scratch[0];
+    const double nb2 = op->sc_host->scratch[0] + op->sc_host->scratch[1];
     st.nb = std::sqrt(nb2);
     st.target = tol * st.nb;
     st.dslash_hi += 1;
-    st.launches += 5;   // two packs, the bhat hop, two norms
-    st.bytes += dslash_b(op, true, true) + 5 * field_b(op, WD_F64);
+    st.launches += 7;   // two packs, the bhat hop, four norms
+    st.bytes += dslash_b(op, true, true) + 8 * field_b(op, WD_F64);
 
-    WD_TRY(true_residual(op, st));
-    WD_TRY(read_scalars(op));
-    st.r_hi = std::sqrt(op->sc_host->scratch[0]);
+    if (op->sc_host->scratch[2] == 0.0) {
+        // zero initial guess: r = bhat exactly, no operator application
+        WD_CUDA(cudaMemcpyAsync(op->rh, op->bh, op->hi_field_bytes(), cudaMemcpyDeviceToDevice,
+                                op->stream));
+        st.r_hi = std::sqrt(op->sc_host->scratch[3]);
+        st.bytes += 2 * field_b(op, WD_F64);
+    } else {
+        WD_TRY(true_residual(op, st));
+        WD_TRY(read_scalars(op));
+        st.r_hi = std::sqrt(op->sc_host->scratch[0]);
+    }
 
     int status = WD_OK;
     int iters = 0;
     if (st.nb == 0.0) {
         WD_CUDA(cudaMemsetAsync(op->xh, 0, op->hi_field_bytes(), op->stream));
+        st.th_valid = false;
         st.r_hi = 0.0;
     } else if (st.r_hi > st.target) {
         // inner system: r_lo = scale r_hi, x_lo = 0, p = 0, nz = +inf
@@ -519,6 +615,8 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
         double last_lognr = 2 * std::log(r_max_lo);
         int last_it = 0;
         int batch = 8;
+        double best_lo = r_max_lo;              // smallest iterated residual since then
+        int best_it = 0;
         for (;;) {
             int n = std::min(batch, maxiter - iters);
             if (n > 0) {
@@ -532,13 +630,16 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
             const SolverScalars &h = *op->sc_host;
             if (h.flags & 1) { status = WD_ERR_BREAKDOWN; break; }
             const double r_lo = std::sqrt(h.nr);
+            if (r_lo < best_lo) { best_lo = r_lo; best_it = iters; }
             const bool want_conv = r_lo <= st.target * st.scale;
-            const bool want_ru = mixed && r_lo < RU_DELTA * r_max_lo;
+            const bool want_ru = mixed && r_lo < op->ru_delta * r_max_lo;
+            const bool stalled = mixed && iters - best_it >= op->stall_iters;
             const bool out_of_iters = iters >= maxiter;
-            if (want_conv || want_ru || out_of_iters) {
+            if (want_conv || want_ru || stalled || out_of_iters) {
                 // reliable update: fold x_lo into x_hi, recompute r_hi in FP64
                 WD_CUDA(launch_fold_x(op->prec, g, op->xh, op->xl, op->dev_consts + 1,
                                       op->stream));
+                st.th_valid = false;
                 st.bytes += field_b(op, op->prec) * 2 + field_b(op, WD_F64) * 2;
                 st.launches += 1;
                 WD_TRY(true_residual(op, st));
@@ -553,15 +654,26 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
                 WD_TRY(set_consts(op, new_scale, 1.0 / new_scale, ratio));
                 WD_CUDA(launch_convert_scaled(op->prec, op->rl, WD_F64, op->rh, g,
                                               op->dev_consts, 0, op->stream));
-                if (ratio != 1.0)
+                if (stalled) {
+                    // restart: p = 0 and nz = +inf make the next direction z itself
+                    WD_CUDA(cudaMemsetAsync(op->pl, 0, op->lo_field_bytes(), op->stream));
+                    op->host_consts[3] = INFINITY;
+                    WD_CUDA(cudaMemcpyAsync(&op->sc->nz, &op->host_consts[3], sizeof(double),
+                                            cudaMemcpyHostToDevice, op->stream));
+                    st.restarts += 1;
+                } else if (ratio != 1.0) {
                     WD_CUDA(launch_rescale_lo(op->prec, g, op->pl, op->sc, op->dev_consts + 2,
                                               op->stream));
+                    st.launches += 1;
+                }
                 st.bytes += field_b(op, WD_F64) + field_b(op, op->prec) * 3;
-                st.launches += ratio != 1.0 ? 2 : 1;
+                st.launches += 1;
                 st.scale = new_scale;
                 r_max_lo = st.r_hi * st.scale;
                 last_lognr = 2 * std::log(r_max_lo);
                 last_it = iters;
+                best_lo = r_max_lo;
+                best_it = iters;
                 batch = 4;
                 continue;
             }
@@ -572,7 +684,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
             if (di > 0 && lognr < last_lognr) {
                 const double rate = (lognr - last_lognr) / di;   // < 0
                 double thr = 2 * std::log(st.target * st.scale);
-                if (mixed) thr = std::max(thr, 2 * std::log(RU_DELTA * r_max_lo));
+                if (mixed) thr = std::max(thr, 2 * std::log(op->ru_delta * r_max_lo));
                 next = (int)std::ceil((thr - lognr) / rate);
             }
             last_lognr = lognr;
@@ -581,9 +693,16 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
         }
     }
 
-    // reconstruction x_q = b_q + kappa H_qp x_p, then the FP64 true residual
-    // of the full system: r_p = b_p - (x_p - kappa H_pq x_q), r_q likewise.
-    WD_TRY(dslash(op, true, st.q, 0, op->xq, op->xh, op->hb[st.q], op->kappa, nullptr));
+    // reconstruction x_q = b_q + kappa H_qp x_p (reusing H_qp x_p from the last
+    // FP64 residual when x_p has not changed since), then the FP64 true
+    // residual of the full system: r_p = b_p - (x_p - kappa H_pq x_q), r_q likewise.
+    if (st.th_valid) {
+        WD_CUDA(launch_xpay_f64(g, op->xq, op->hb[st.q], op->kappa, op->th, op->stream));
+        st.bytes += 3 * field_b(op, WD_F64);
+        st.dslash_hi -= 1;
+    } else {
+        WD_TRY(dslash(op, true, st.q, 0, op->xq, op->xh, op->hb[st.q], op->kappa, nullptr));
+    }
     WD_TRY(dslash(op, true, st.p, 0, op->axh, op->xq, op->xh, -op->kappa, nullptr));
     WD_CUDA(launch_xmy_norm(g, op->rh, op->hb[st.p], op->axh, r0, op->stream));
     WD_TRY(dslash(op, true, st.q, 0, op->axh, op->xh, op->xq, -op->kappa, nullptr));
@@ -606,6 +725,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
         info->dslash_hi = st.dslash_hi;
         info->bytes = st.bytes;
         info->launches = st.launches;
+        info->restarts = st.restarts;
     }
     if (status == WD_OK && st.nb > 0 && rfull > st.target * 1.0000001) {
         // the Schur residual met the target but rounding of the

@@ -259,6 +259,8 @@ enum FinalOp {
     FIN_ALPHA = 3,    // pAp = sum; alpha = nz / pAp
     FIN_BETA = 4,     // beta = sum / nz; nz = sum
     FIN_NR = 5,       // nr = sum; hist[iter % 64] = sum; ++iter
+    FIN_STORE2 = 6,   // scratch[2] = sum
+    FIN_STORE3 = 7,   // scratch[3] = sum
 };
 
 // Partial sums of one reduction: one double per block, plus the arrival
@@ -274,6 +276,8 @@ __device__ __forceinline__ void apply_final(SolverScalars *s, int op, double sum
     switch (op) {
     case FIN_STORE0: s->scratch[0] = sum; break;
     case FIN_STORE1: s->scratch[1] = sum; break;
+    case FIN_STORE2: s->scratch[2] = sum; break;
+    case FIN_STORE3: s->scratch[3] = sum; break;
     case FIN_ALPHA: {
         s->pAp = sum;
         double a = 0.0;                   // z = 0: the residual vanished exactly
@@ -369,6 +373,7 @@ struct DslashLaunch {
     double scale;
     int epi;
     const Reduction *red;  // optional ||out||^2
+    int cfg = 0;           // launch configuration (tuned per operator)
 };
 
 // dslash.cu
@@ -383,6 +388,8 @@ cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction
                          cudaStream_t s);
 cudaError_t launch_xmy_norm(const Geom &g, double *out, const double *x, const double *y,
                             const Reduction &red, cudaStream_t s);
+cudaError_t launch_xpay_f64(const Geom &g, double *out, const double *y, double a,
+                            const double *x, cudaStream_t s);
 cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const void *in,
                                   const Geom &g, const double *scale_dev, double scale_host,
                                   cudaStream_t s);

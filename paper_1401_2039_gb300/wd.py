@@ -32,7 +32,8 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
                 ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("dslash_lo", ctypes.c_double), ("dslash_hi", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("launches", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("launches", ctypes.c_double),
+                ("restarts", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -62,6 +63,8 @@ def load_library() -> ctypes.CDLL:
             "wd_field_store": (i, [vp, i, vp]),
             "wd_dslash_resident": (i, [vp, i, i, i]),
             "wd_op_stream": (vp, [vp]),
+            "wd_op_set_solver": (i, [vp, d, i]),
+            "wd_dslash_tuning": (i, [vp, i, dp, i, ip, ip, ip]),
             "wd_dslash_bytes": (d, [vp]),
             "wd_status_string": (ctypes.c_char_p, [i]),
             "wd_last_error": (ctypes.c_char_p, []),
@@ -206,6 +209,19 @@ class WilsonDirac:
                                        int(maxiter), int(parity), ctypes.byref(info))
         _check(rc)
         return SolveResult(x_host, rc, info.as_dict())
+
+    def set_solver(self, ru_delta: float = 0.1, stall_iters: int = 200):
+        """Reliable-update threshold and stagnation restart of the mixed-precision solve."""
+        _check(self.lib.wd_op_set_solver(self.handle, float(ru_delta), int(stall_iters)))
+
+    def dslash_tuning(self, hi: bool = False) -> dict:
+        """The autotuner's choice for the hopping term and its per-candidate timings (us)."""
+        us = (ctypes.c_double * 8)()
+        blk, mb, spt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        k = self.lib.wd_dslash_tuning(self.handle, int(bool(hi)), us, 8, ctypes.byref(blk),
+                                      ctypes.byref(mb), ctypes.byref(spt))
+        return {"index": k, "block": blk.value, "min_blocks": mb.value,
+                "sites_per_thread": spt.value, "us": [round(v, 2) for v in us[:5]]}
 
     # resident fields, for timing the hopping term alone
     def field_load(self, slot: int, half: torch.Tensor):
