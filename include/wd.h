@@ -129,6 +129,33 @@ int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters);
 int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
                      int maxiter, int parity, wd_solve_info *info);
 
+/* ---------------------------------------------------------------------------
+ * Batches: several operators (lattices of any size, one storage precision
+ * and link format, FP64/FP32/FP16) with nrhs[k] right-hand sides each, at
+ * most 8 operators and 64 systems.  A batch owns the fields of all its
+ * systems (right-hand-side index innermost, so the links of a site are read
+ * once for all of its right-hand sides) and advances every system in
+ * lockstep with persistent kernels that walk a table of tiles over all
+ * lattices; each system keeps its own CGNR scalars, reliable updates are
+ * taken together, and converged systems are frozen.  The operators must
+ * outlive the batch.  Not in the paper: it batches the paper's solve (goal
+ * with templates "CGNR schur") over many right-hand sides and lattices. */
+typedef struct wd_batch wd_batch;
+int wd_batch_create(wd_batch **bt, wd_op *const *ops, const int *nrhs, int nops);
+void wd_batch_destroy(wd_batch *bt);
+/* out[k], in[k]: device, [nrhs[k]][V_k/2][3][4] complex128, hopping term
+ * P_p H P_q^t of every system (storage precision of the operators). */
+int wd_batch_dslash(wd_batch *bt, double *const *out, const double *const *in, int out_parity,
+                    int dagger);
+/* The same on the batch's resident fields (last inputs of wd_batch_dslash). */
+int wd_batch_dslash_resident(wd_batch *bt, int out_parity, int dagger);
+/* x[k] (in: initial guesses or zeros, out: solutions), b[k]: device,
+ * [nrhs[k]][V_k][3][4] complex128; info: sum(nrhs) entries or NULL, in
+ * system order (operator 0's right-hand sides first). */
+int wd_batch_solve(wd_batch *bt, double *const *x, const double *const *b, double tol,
+                   int maxiter, int parity, wd_solve_info *info);
+const char *wd_batch_last_error(void);
+
 /* Resident fields for timing the hopping term alone: slot 0 and 1 are two
  * half-lattice spinors the handle owns, in its internal layout and storage
  * precision.  wd_field_load packs a canonical half spinor (device) into a

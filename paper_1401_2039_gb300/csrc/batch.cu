@@ -1,0 +1,988 @@
+// Batched solves: many right-hand sides on one lattice and several lattices
+// of different sizes, advanced in lockstep by persistent kernels.
+//
+// A batch holds P problems (an operator handle each, up to BT_MAX_PROB) with
+// n_p right-hand sides each.  Every (problem, rhs) pair is one "system" with
+// its own solver scalars (slot).  Fields of a problem store the n_p
+// right-hand sides with the rhs index innermost: element (plane j, site h,
+// rhs r) sits at ((j * stride + h) * n_p + r) * 16 bytes.  That is the
+// single-field layout with plane stride stride * n_p and site index
+// h * n_p + r, so the record loads of the single-field kernels apply as they
+// are, consecutive threads (consecutive r, then h) read consecutive 16-byte
+// words, and the n_p threads of one site read its eight links once from
+// DRAM (the duplicates are served by the same warp request or by L1/L2).
+//
+// Work is cut into tiles of BT_BLOCK items that never straddle two
+// problems; a persistent grid walks the tile table.  Reductions are
+// deterministic: each tile sums its items per rhs in a fixed order, each
+// block accumulates its tiles per slot in tile order, and the last block to
+// finish adds the per-block partials per slot in block order.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dslash.cuh"
+
+namespace wd {
+
+constexpr int BT_BLOCK = 128;
+constexpr int BT_MAX_PROB = 8;
+constexpr int BT_MAX_SLOTS = 64;
+constexpr int BT_GRID = 152 * 8;
+
+struct BtProb {
+    Geom g;                  // stride = plane stride of one right-hand side
+    const char *gauge_out;   // links of the output parity
+    const char *gauge_in;    // links of the input parity
+    size_t dir_bytes;
+    void *f[4];              // fields of this launch (meaning set by the kernel)
+    double scale;            // per-problem coefficient
+    double ph[8];            // boundary phases
+    int nrhs;
+    int slot0;               // first solver slot of the problem
+    long tile0;              // first tile of the problem
+    long nitems;             // work items of the problem
+};
+
+struct BtArgs {
+    BtProb p[BT_MAX_PROB];
+    int nprob;
+    long ntiles;
+    int parity;              // output parity of hopping terms
+    int fin;                 // final operation applied per slot
+    int nslots;
+    double *partials;        // [grid][BT_MAX_SLOTS]
+    unsigned int *counter;
+    SolverScalars *scalars;  // [nslots]
+    const double *consts;    // per-slot constants, [4][BT_MAX_SLOTS]
+};
+
+__device__ __forceinline__ int bt_problem(const BtArgs &a, long t) {
+    int pi = 0;
+#pragma unroll 1
+    for (int k = 1; k < a.nprob; ++k)
+        if (t >= a.p[k].tile0) pi = k;
+    return pi;
+}
+
+// Per-tile sum of v over the items of each rhs (fixed order), added to the
+// block's slot accumulators.  Every thread of the block must call.
+__device__ __forceinline__ void bt_tile_sums(double v, const BtProb &P, long item0, double *tv,
+                                             double *sacc) {
+    tv[threadIdx.x] = v;
+    __syncthreads();
+    const int nr = P.nrhs;
+    if ((int)threadIdx.x < nr) {
+        const int j = threadIdx.x;
+        const int i0 = (int)(((long)j - item0 % nr + nr) % nr);
+        double s = 0.0;
+        for (int i = i0; i < BT_BLOCK; i += nr) s += tv[i];
+        sacc[P.slot0 + j] += s;
+    }
+    __syncthreads();
+}
+
+// Grid-wide finish: per-block slot partials, then the last block adds them
+// in block order (one warp per slot) and applies the final operation.
+__device__ __forceinline__ void bt_finish(const BtArgs &a, const double *sacc) {
+    __shared__ bool last;
+    for (int s = threadIdx.x; s < a.nslots; s += BT_BLOCK)
+        a.partials[(long)blockIdx.x * BT_MAX_SLOTS + s] = sacc[s];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = warp; s < a.nslots; s += BT_BLOCK / 32) {
+        double sum = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32)
+            sum += __ldcg(&a.partials[(long)b * BT_MAX_SLOTS + s]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) apply_final(&a.scalars[s], a.fin, sum);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// ------------------------------------------------------------------ hopping term
+template <typename S, typename R, int RECON, int MU, int DAG>
+__device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], long h, int r,
+                                            R *acc) {
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    const long ss = P.g.stride * P.nrhs;
+    {
+        bool wrap;
+        const long hn = neighbour<MU, +1>(P.g, h, c, wrap);
+        R psi[24];
+        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
+        cx<R> hs[2][3], u[2][3];
+        project<MU, SF>(psi, hs);
+        R U[18];
+        load_link<S, R, RECON>(P.gauge_out + MU * P.dir_bytes, P.g.stride, h, U);
+        su3_mul(U, hs, u);
+        if (wrap) phase_mul(u, (R)P.ph[2 * MU], (R)P.ph[2 * MU + 1]);
+        accumulate<MU, SF>(acc, u);
+    }
+    {
+        bool wrap;
+        const long hn = neighbour<MU, -1>(P.g, h, c, wrap);
+        R psi[24];
+        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
+        cx<R> hs[2][3], u[2][3];
+        project<MU, SB>(psi, hs);
+        R U[18];
+        load_link<S, R, RECON>(P.gauge_in + MU * P.dir_bytes, P.g.stride, hn, U);
+        su3_adj_mul(U, hs, u);
+        if (wrap) phase_mul(u, (R)P.ph[2 * MU], -(R)P.ph[2 * MU + 1]);
+        accumulate<MU, SB>(acc, u);
+    }
+}
+
+// f[0] = out, f[1] = in, f[2] = x:  out = scale * H in  or  x + scale * H in
+template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM>
+__global__ void __launch_bounds__(BT_BLOCK, 8) k_dslash_batch(const BtArgs a) {
+    __shared__ double tv[BT_BLOCK];
+    __shared__ double sacc[BT_MAX_SLOTS];
+    if (NORM) {
+        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = 0.0;
+        __syncthreads();
+    }
+    for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const BtProb &P = a.p[bt_problem(a, t)];
+        const long item0 = (t - P.tile0) * BT_BLOCK;
+        const long item = item0 + threadIdx.x;
+        double v = 0.0;
+        if (item < P.nitems) {
+            const int nr = P.nrhs;
+            const long h = item / nr;
+            const int r = (int)(item - h * nr);
+            int c[4];
+            site_coords(P.g, h, a.parity, c);
+            R acc[24];
+#pragma unroll
+            for (int k = 0; k < 24; ++k) acc[k] = 0;
+            bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
+            bt_hop_pair<S, R, RECON, 1, DAG>(P, c, h, r, acc);
+            bt_hop_pair<S, R, RECON, 2, DAG>(P, c, h, r, acc);
+            bt_hop_pair<S, R, RECON, 3, DAG>(P, c, h, r, acc);
+            const long ss = P.g.stride * nr;
+            const R sc = (R)P.scale;
+            if (XPAY) {
+                R xv[24];
+                Rec<S, 24>::template load<R, 0>(P.f[2], ss, item, xv);
+#pragma unroll
+                for (int k = 0; k < 24; ++k) acc[k] = xv[k] + sc * acc[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) acc[k] *= sc;
+            }
+            Rec<S, 24>::store(P.f[0], ss, item, acc);
+            if (NORM) {
+                R sq = 0;
+#pragma unroll
+                for (int k = 0; k < 24; ++k) sq += acc[k] * acc[k];
+                v = (double)sq;
+            }
+        }
+        if (NORM) bt_tile_sums(v, P, item0, tv, sacc);
+    }
+    if (NORM) bt_finish(a, sacc);
+}
+
+// ------------------------------------------------------------------ vector kernels
+// Element-wise kernels walk 16-byte chunks; chunk i of a problem belongs to
+// rhs i % nrhs (planes hold stride * nrhs chunks, a multiple of nrhs).
+enum BtOp { BT_XR = 0, BT_P = 1, BT_NORM = 2, BT_RESCALE = 3 };
+
+template <typename S, typename R, int OP>
+__global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const BtArgs a) {
+    using C = Chunk16<S, R>;
+    __shared__ double tv[BT_BLOCK];
+    __shared__ double sacc[BT_MAX_SLOTS];
+    constexpr bool RED = OP == BT_XR || OP == BT_NORM;
+    if (RED) {
+        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = 0.0;
+        __syncthreads();
+    }
+    for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const BtProb &P = a.p[bt_problem(a, t)];
+        const long item0 = (t - P.tile0) * BT_BLOCK;
+        const long i = item0 + threadIdx.x;
+        double v = 0.0;
+        if (i < P.nitems) {
+            SolverScalars *s = &a.scalars[P.slot0 + (int)(i % P.nrhs)];
+            if (OP == BT_XR) {          // f = {x, r, p, Ap}: x += a p, r -= a Ap, |r|^2
+                const R al = (R)s->alpha;
+                R xv[C::K], rv[C::K], pv[C::K], av[C::K];
+                C::load(P.f[0], i, xv);
+                C::load(P.f[1], i, rv);
+                C::load(P.f[2], i, pv);
+                C::load(P.f[3], i, av);
+                R sq = 0;
+#pragma unroll
+                for (int k = 0; k < C::K; ++k) {
+                    xv[k] += al * pv[k];
+                    rv[k] -= al * av[k];
+                    sq += rv[k] * rv[k];
+                }
+                C::store(P.f[0], i, xv);
+                C::store(P.f[1], i, rv);
+                v = (double)sq;
+            } else if (OP == BT_P) {    // f = {p, z}: p = z + b p
+                const R be = (R)s->beta;
+                R pv[C::K], zv[C::K];
+                C::load(P.f[0], i, pv);
+                C::load(P.f[1], i, zv);
+#pragma unroll
+                for (int k = 0; k < C::K; ++k) pv[k] = zv[k] + be * pv[k];
+                C::store(P.f[0], i, pv);
+            } else if (OP == BT_NORM) { // f = {v}
+                R vv[C::K];
+                C::load(P.f[0], i, vv);
+#pragma unroll
+                for (int k = 0; k < C::K; ++k) v += (double)vv[k] * (double)vv[k];
+            } else {                    // f = {p}: p *= ratio[slot]
+                const int slot = P.slot0 + (int)(i % P.nrhs);
+                const R ratio = (R)a.consts[2 * BT_MAX_SLOTS + slot];
+                R pv[C::K];
+                C::load(P.f[0], i, pv);
+#pragma unroll
+                for (int k = 0; k < C::K; ++k) pv[k] *= ratio;
+                C::store(P.f[0], i, pv);
+            }
+        }
+        if (RED) bt_tile_sums(v, P, item0, tv, sacc);
+    }
+    if (RED) bt_finish(a, sacc);
+}
+
+// FP64 kernels over (site, rhs) items:
+//   XMY:  f = {out, x, y}: out = x - y, |out|^2
+//   XPAY: f = {out, y, x}: out = y + scale x
+enum BtOp64 { BT64_XMY = 0, BT64_XPAY = 1 };
+
+template <int OP>
+__global__ void __launch_bounds__(BT_BLOCK) k_bt_f64(const BtArgs a) {
+    __shared__ double tv[BT_BLOCK];
+    __shared__ double sacc[BT_MAX_SLOTS];
+    if (OP == BT64_XMY) {
+        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = 0.0;
+        __syncthreads();
+    }
+    for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const BtProb &P = a.p[bt_problem(a, t)];
+        const long item0 = (t - P.tile0) * BT_BLOCK;
+        const long i = item0 + threadIdx.x;
+        double v = 0.0;
+        if (i < P.nitems) {
+            const double2 *x = (const double2 *)P.f[1];
+            const double2 *y = (const double2 *)P.f[2];
+            double2 *o = (double2 *)P.f[0];
+            const double2 a1 = x[i], b1 = y[i];
+            double2 d;
+            if (OP == BT64_XMY) d = make_double2(a1.x - b1.x, a1.y - b1.y);
+            else d = make_double2(a1.x + P.scale * b1.x, a1.y + P.scale * b1.y);
+            o[i] = d;
+            v = d.x * d.x + d.y * d.y;
+        }
+        if (OP == BT64_XMY) bt_tile_sums(v, P, item0, tv, sacc);
+    }
+    if (OP == BT64_XMY) bt_finish(a, sacc);
+}
+
+// Conversions over (site, rhs) items, with per-slot constants:
+//   CONV: f = {out (SO), in (SI)}: out = consts[0][slot] * in
+//   FOLD: f = {x_hi (FP64), x_lo (SI)}: x_hi += consts[1][slot] * x_lo; x_lo = 0
+template <typename SO, typename SI, int FOLD>
+__global__ void __launch_bounds__(BT_BLOCK) k_bt_conv(const BtArgs a) {
+    for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const BtProb &P = a.p[bt_problem(a, t)];
+        const long i = (t - P.tile0) * BT_BLOCK + threadIdx.x;
+        if (i >= P.nitems) continue;
+        const int slot = P.slot0 + (int)(i % P.nrhs);
+        const long ss = P.g.stride * P.nrhs;
+        double v[24];
+        Rec<SI, 24>::template load_coherent<double>(P.f[1], ss, i, v);
+        if (FOLD) {
+            double hi[24];
+            Rec<double, 24>::template load_coherent<double>(P.f[0], ss, i, hi);
+            const double is = a.consts[BT_MAX_SLOTS + slot];
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                hi[k] += is * v[k];
+                v[k] = 0.0;
+            }
+            Rec<double, 24>::store(P.f[0], ss, i, hi);
+            Rec<SI, 24>::store(P.f[1], ss, i, v);
+        } else {
+            const double sc = a.consts[slot];
+#pragma unroll
+            for (int k = 0; k < 24; ++k) v[k] *= sc;
+            Rec<SO, 24>::store(P.f[0], ss, i, v);
+        }
+    }
+}
+
+// rescale also multiplies nz by ratio^2 (one thread per slot)
+__global__ void k_bt_rescale_nz(SolverScalars *sc, const double *consts, int nslots) {
+    const int s = threadIdx.x;
+    if (s < nslots) {
+        const double r = consts[2 * BT_MAX_SLOTS + s];
+        sc[s].nz *= r * r;
+    }
+}
+
+// Canonical [nrhs][V][3][4] complex128 <-> batched FP64 parity fields.
+__global__ void k_bt_pack_full(Geom g, int nrhs, double *even, double *odd, const double *src) {
+    const long i = (long)blockIdx.x * BT_BLOCK + threadIdx.x;
+    const long V = 2 * g.vh;
+    if (i >= V * nrhs) return;
+    const int r = (int)(i / V);
+    const long lex = i - (long)r * V;
+    long q = lex;
+    const int x = (int)(q % g.L[0]); q /= g.L[0];
+    const int y = (int)(q % g.L[1]); q /= g.L[1];
+    const int z = (int)(q % g.L[2]);
+    const int t = (int)(q / g.L[2]);
+    double v[24];
+    const double2 *s2 = (const double2 *)(src + i * 24);
+    for (int k = 0; k < 12; ++k) { v[2 * k] = s2[k].x; v[2 * k + 1] = s2[k].y; }
+    Rec<double, 24>::store(((x + y + z + t) & 1) ? odd : even, g.stride * nrhs,
+                           (lex >> 1) * nrhs + r, v);
+}
+
+__global__ void k_bt_unpack_full(Geom g, int nrhs, double *dst, const double *even,
+                                 const double *odd) {
+    const long i = (long)blockIdx.x * BT_BLOCK + threadIdx.x;
+    const long V = 2 * g.vh;
+    if (i >= V * nrhs) return;
+    const int r = (int)(i / V);
+    const long lex = i - (long)r * V;
+    long q = lex;
+    const int x = (int)(q % g.L[0]); q /= g.L[0];
+    const int y = (int)(q % g.L[1]); q /= g.L[1];
+    const int z = (int)(q % g.L[2]);
+    const int t = (int)(q / g.L[2]);
+    double v[24];
+    Rec<double, 24>::template load_coherent<double>(((x + y + z + t) & 1) ? odd : even,
+                                                    g.stride * nrhs, (lex >> 1) * nrhs + r, v);
+    double2 *d2 = (double2 *)(dst + i * 24);
+    for (int k = 0; k < 12; ++k) d2[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
+// Canonical half spinors [nrhs][Vh][3][4] <-> a batched field of precision S.
+template <typename S, int UNPACK>
+__global__ void k_bt_half(Geom g, int nrhs, void *field, double *canon) {
+    const long i = (long)blockIdx.x * BT_BLOCK + threadIdx.x;
+    if (i >= g.vh * nrhs) return;
+    const int r = (int)(i / g.vh);
+    const long h = i - (long)r * g.vh;
+    double v[24];
+    double2 *c2 = (double2 *)(canon + i * 24);
+    if (UNPACK) {
+        Rec<S, 24>::template load_coherent<double>(field, g.stride * nrhs, h * nrhs + r, v);
+        for (int k = 0; k < 12; ++k) c2[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    } else {
+        for (int k = 0; k < 12; ++k) { v[2 * k] = c2[k].x; v[2 * k + 1] = c2[k].y; }
+        Rec<S, 24>::store(field, g.stride * nrhs, h * nrhs + r, v);
+    }
+}
+
+}  // namespace wd
+
+// =================================================================== host side
+#include "op.cuh"
+
+using namespace wd;
+
+static thread_local std::string g_bt_error;
+static int bt_fail(int code, const std::string &m) {
+    g_bt_error = m;
+    return code;
+}
+#define BT_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bt_fail(e_ == cudaErrorMemoryAllocation ? WD_ERR_NOMEM : WD_ERR_CUDA,    \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+#define BT_TRY(call)                                                                        \
+    do {                                                                                    \
+        int rc_ = (call);                                                                   \
+        if (rc_ != WD_OK) return rc_;                                                       \
+    } while (0)
+
+namespace {
+
+enum Fld { F_XL, F_RL, F_PL, F_ZL, F_APL, F_TL, F_HB0, F_HB1, F_BH, F_XH, F_RH, F_AXH, F_TH,
+           F_XQ, F_IO0, F_IO1, N_FLD };
+enum Items { IT_SITES, IT_LO_CHUNKS, IT_HI_CHUNKS, IT_HI_D2 };
+enum Scale { SC_ONE, SC_KAPPA, SC_MKAPPA, SC_MKAPPA2 };
+
+struct BtFields { void *f[N_FLD]; };
+
+}  // namespace
+
+struct wd_batch {
+    int nprob = 0;
+    wd_op *ops[BT_MAX_PROB] = {};
+    int nrhs[BT_MAX_PROB] = {};
+    int slot0[BT_MAX_PROB] = {};
+    int nslots = 0;
+    int prec = WD_F32, recon = 18;
+    cudaStream_t user = nullptr, stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    BtFields fl[BT_MAX_PROB];
+    double *partials = nullptr;
+    unsigned int *counter = nullptr;
+    SolverScalars *sc = nullptr, *sc_host = nullptr;
+    double *consts = nullptr, *consts_host = nullptr;
+    cudaGraphExec_t graphs[2][MAX_BATCH_LOG2 + 1] = {};
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+int bt_alloc(wd_batch *bt, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return bt_fail(WD_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    bt->allocs.push_back(*p);
+    BT_CUDA(cudaMemset(*p, 0, bytes));
+    return WD_OK;
+}
+
+long items_of(const wd_batch *bt, int p, int kind) {
+    const wd_op *op = bt->ops[p];
+    const long n = bt->nrhs[p];
+    switch (kind) {
+    case IT_SITES: return op->g.vh * n;
+    case IT_LO_CHUNKS: return (long)(24 * prec_bytes(bt->prec) / 16) * op->g.stride * n;
+    case IT_HI_CHUNKS: return 12L * op->g.stride * n;
+    default: return 12L * op->g.stride * n;   // IT_HI_D2: double2 elements
+    }
+}
+
+double scale_of(const wd_op *op, int mode) {
+    switch (mode) {
+    case SC_KAPPA: return op->kappa;
+    case SC_MKAPPA: return -op->kappa;
+    case SC_MKAPPA2: return -op->kappa * op->kappa;
+    default: return 1.0;
+    }
+}
+
+// Arguments of one batched launch: tile table, fields, per-problem scale.
+BtArgs make_args(wd_batch *bt, int kind, int fin, std::initializer_list<int> fields,
+                 int scale_mode, bool hi, int out_parity) {
+    BtArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nprob = bt->nprob;
+    long tile = 0;
+    for (int p = 0; p < bt->nprob; ++p) {
+        wd_op *op = bt->ops[p];
+        BtProb &P = a.p[p];
+        P.g = op->g;
+        const GaugeSet &gs = hi ? op->gauge_hi : op->gauge_lo;
+        P.gauge_out = (const char *)gs.ptr[out_parity];
+        P.gauge_in = (const char *)gs.ptr[1 - out_parity];
+        P.dir_bytes = gs.dir_bytes;
+        int k = 0;
+        for (int fid : fields) P.f[k++] = bt->fl[p].f[fid];
+        P.scale = scale_of(op, scale_mode);
+        memcpy(P.ph, op->phase, sizeof(P.ph));
+        P.nrhs = bt->nrhs[p];
+        P.slot0 = bt->slot0[p];
+        P.tile0 = tile;
+        P.nitems = items_of(bt, p, kind);
+        tile += (P.nitems + BT_BLOCK - 1) / BT_BLOCK;
+    }
+    a.ntiles = tile;
+    a.parity = out_parity;
+    a.fin = fin;
+    a.nslots = bt->nslots;
+    a.partials = bt->partials;
+    a.counter = bt->counter;
+    a.scalars = bt->sc;
+    a.consts = bt->consts;
+    return a;
+}
+
+unsigned grid_of(const BtArgs &a) {
+    return (unsigned)std::max<long>(1, std::min<long>(a.ntiles, BT_GRID));
+}
+
+template <typename S, typename R, int RECON>
+void launch_hop_t(const BtArgs &a, int dagger, bool xpay, bool norm, cudaStream_t s) {
+    const unsigned gr = grid_of(a);
+#define BT_H(D, X, N) k_dslash_batch<S, R, RECON, D, X, N><<<gr, BT_BLOCK, 0, s>>>(a)
+    if (dagger) {
+        if (!xpay) BT_H(1, 0, 0); else if (!norm) BT_H(1, 1, 0); else BT_H(1, 1, 1);
+    } else {
+        if (!xpay) BT_H(0, 0, 0); else if (!norm) BT_H(0, 1, 0); else BT_H(0, 1, 1);
+    }
+#undef BT_H
+}
+
+// out = scale * H_{p,q} in  or  x + scale * H_{p,q} in, for every system
+int bt_hop(wd_batch *bt, bool hi, int out_parity, int dagger, int out, int in, int x,
+           int scale_mode, int fin) {
+    BtArgs a = x >= 0 ? make_args(bt, IT_SITES, fin, {out, in, x}, scale_mode, hi, out_parity)
+                      : make_args(bt, IT_SITES, fin, {out, in}, scale_mode, hi, out_parity);
+    const bool xpay = x >= 0, norm = fin != FIN_NONE;
+    const int prec = hi ? WD_F64 : bt->prec;
+    const int recon = hi ? 18 : bt->recon;
+    if (prec == WD_F64) {
+        if (recon == 12) launch_hop_t<double, double, 12>(a, dagger, xpay, norm, bt->stream);
+        else launch_hop_t<double, double, 18>(a, dagger, xpay, norm, bt->stream);
+    } else if (prec == WD_F32) {
+        if (recon == 12) launch_hop_t<float, float, 12>(a, dagger, xpay, norm, bt->stream);
+        else launch_hop_t<float, float, 18>(a, dagger, xpay, norm, bt->stream);
+    } else {
+        if (recon == 12) launch_hop_t<__half, float, 12>(a, dagger, xpay, norm, bt->stream);
+        else launch_hop_t<__half, float, 18>(a, dagger, xpay, norm, bt->stream);
+    }
+    BT_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int bt_schur(wd_batch *bt, bool hi, int p, int dagger, int out, int in, int tmp, int fin) {
+    BT_TRY(bt_hop(bt, hi, 1 - p, dagger, tmp, in, -1, SC_ONE, FIN_NONE));
+    BT_TRY(bt_hop(bt, hi, p, dagger, out, tmp, in, SC_MKAPPA2, fin));
+    return WD_OK;
+}
+
+template <int OP>
+int bt_vec(wd_batch *bt, bool hi, int fin, std::initializer_list<int> fields) {
+    BtArgs a = make_args(bt, hi ? IT_HI_CHUNKS : IT_LO_CHUNKS, fin, fields, SC_ONE, false, 0);
+    const int prec = hi ? WD_F64 : bt->prec;
+    const unsigned gr = grid_of(a);
+    if (prec == WD_F64) k_bt_vec<double, double, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
+    else if (prec == WD_F32) k_bt_vec<float, float, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
+    else k_bt_vec<__half, float, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
+    BT_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+template <int OP>
+int bt_f64(wd_batch *bt, int fin, std::initializer_list<int> fields, int scale_mode) {
+    BtArgs a = make_args(bt, IT_HI_D2, fin, fields, scale_mode, false, 0);
+    k_bt_f64<OP><<<grid_of(a), BT_BLOCK, 0, bt->stream>>>(a);
+    BT_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// lo <- consts[0] * hi  (FOLD = 0)   or   hi += consts[1] * lo, lo = 0  (FOLD = 1)
+int bt_conv(wd_batch *bt, bool fold, int dst, int src) {
+    BtArgs a = make_args(bt, IT_SITES, FIN_NONE, {dst, src}, SC_ONE, false, 0);
+    const unsigned gr = grid_of(a);
+    cudaStream_t s = bt->stream;
+    if (fold) {
+        if (bt->prec == WD_F32) k_bt_conv<double, float, 1><<<gr, BT_BLOCK, 0, s>>>(a);
+        else k_bt_conv<double, __half, 1><<<gr, BT_BLOCK, 0, s>>>(a);
+    } else {
+        if (bt->prec == WD_F32) k_bt_conv<float, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+        else k_bt_conv<__half, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+    }
+    BT_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+int bt_read(wd_batch *bt) {
+    BT_CUDA(cudaMemcpyAsync(bt->sc_host, bt->sc, sizeof(SolverScalars) * bt->nslots,
+                            cudaMemcpyDeviceToHost, bt->stream));
+    BT_CUDA(cudaStreamSynchronize(bt->stream));
+    return WD_OK;
+}
+
+int bt_write(wd_batch *bt) {
+    BT_CUDA(cudaMemcpyAsync(bt->sc, bt->sc_host, sizeof(SolverScalars) * bt->nslots,
+                            cudaMemcpyHostToDevice, bt->stream));
+    BT_CUDA(cudaMemcpyAsync(bt->consts, bt->consts_host, sizeof(double) * 4 * BT_MAX_SLOTS,
+                            cudaMemcpyHostToDevice, bt->stream));
+    return WD_OK;
+}
+
+// one lockstep CGNR iteration for every system (see cg_iteration of the
+// single-system solver)
+int bt_iteration(wd_batch *bt, int p) {
+    BT_TRY(bt_schur(bt, false, p, 1, F_ZL, F_RL, F_TL, FIN_BETA));
+    BT_TRY(bt_vec<BT_P>(bt, false, FIN_NONE, {F_PL, F_ZL}));
+    BT_TRY(bt_schur(bt, false, p, 0, F_APL, F_PL, F_TL, FIN_ALPHA));
+    BT_TRY(bt_vec<BT_XR>(bt, false, FIN_NR, {F_XL, F_RL, F_PL, F_APL}));
+    return WD_OK;
+}
+
+int bt_run(wd_batch *bt, int p, int n) {
+    for (int lg = MAX_BATCH_LOG2; lg >= 0; --lg) {
+        while (n >= (1 << lg)) {
+            if (!bt->graphs[p][lg]) {
+                cudaGraph_t graph = nullptr;
+                BT_CUDA(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
+                int rc = WD_OK;
+                for (int i = 0; i < (1 << lg) && rc == WD_OK; ++i) rc = bt_iteration(bt, p);
+                cudaError_t e = cudaStreamEndCapture(bt->stream, &graph);
+                if (rc != WD_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return rc;
+                }
+                BT_CUDA(e);
+                cudaError_t ei = cudaGraphInstantiate(&bt->graphs[p][lg], graph, 0);
+                cudaGraphDestroy(graph);
+                BT_CUDA(ei);
+            }
+            BT_CUDA(cudaGraphLaunch(bt->graphs[p][lg], bt->stream));
+            n -= 1 << lg;
+        }
+    }
+    return WD_OK;
+}
+
+// r_hi = bhat - Mhat x_hi for every system, |r_hi|^2 -> scratch[0]
+int bt_true_residual(wd_batch *bt, int p) {
+    BT_TRY(bt_schur(bt, true, p, 0, F_AXH, F_XH, F_TH, FIN_NONE));
+    BT_TRY(bt_f64<BT64_XMY>(bt, FIN_STORE0, {F_RH, F_BH, F_AXH}, SC_ONE));
+    return WD_OK;
+}
+
+int bt_solve_impl(wd_batch *bt, double *const *x, const double *const *b, double tol,
+                  int maxiter, int par, wd_solve_info *info) {
+    const int q = 1 - par;
+    const bool mixed = bt->prec != WD_F64;
+    const int S = bt->nslots;
+    std::vector<double> nb(S), target(S), r_hi(S), scale(S, 1.0), rmax(S), best(S);
+    std::vector<int> best_it(S, 0), conv_iter(S, 0);
+    std::vector<char> active(S, 0);
+    cudaStream_t st = bt->stream;
+    // split b and x0 by parity into the FP64 batched fields
+    for (int p = 0; p < bt->nprob; ++p) {
+        const wd_op *op = bt->ops[p];
+        const long n = 2 * op->g.vh * bt->nrhs[p];
+        const unsigned gr = (unsigned)((n + BT_BLOCK - 1) / BT_BLOCK);
+        double *xe = (double *)bt->fl[p].f[par == 0 ? F_XH : F_XQ];
+        double *xo = (double *)bt->fl[p].f[par == 0 ? F_XQ : F_XH];
+        k_bt_pack_full<<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], (double *)bt->fl[p].f[F_HB0],
+                                                (double *)bt->fl[p].f[F_HB1], b[p]);
+        k_bt_pack_full<<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], xe, xo, x[p]);
+    }
+    BT_CUDA(cudaGetLastError());
+    const int HBP = par == 0 ? F_HB0 : F_HB1, HBQ = par == 0 ? F_HB1 : F_HB0;
+    BT_TRY(bt_hop(bt, true, par, 0, F_BH, HBQ, HBP, SC_KAPPA, FIN_NONE));
+    BT_TRY(bt_vec<BT_NORM>(bt, true, FIN_STORE1, {HBQ}));
+    BT_TRY(bt_vec<BT_NORM>(bt, true, FIN_STORE0, {HBP}));
+    BT_TRY(bt_vec<BT_NORM>(bt, true, FIN_STORE2, {F_XH}));
+    BT_TRY(bt_vec<BT_NORM>(bt, true, FIN_STORE3, {F_BH}));
+    BT_TRY(bt_read(bt));
+    bool any_guess = false;
+    for (int s = 0; s < S; ++s) {
+        nb[s] = std::sqrt(bt->sc_host[s].scratch[0] + bt->sc_host[s].scratch[1]);
+        target[s] = tol * nb[s];
+        any_guess |= bt->sc_host[s].scratch[2] != 0.0;
+        r_hi[s] = std::sqrt(bt->sc_host[s].scratch[3]);
+    }
+    if (any_guess) {
+        BT_TRY(bt_true_residual(bt, par));
+        BT_TRY(bt_read(bt));
+        for (int s = 0; s < S; ++s) r_hi[s] = std::sqrt(bt->sc_host[s].scratch[0]);
+    } else {
+        for (int p = 0; p < bt->nprob; ++p)
+            BT_CUDA(cudaMemcpyAsync(bt->fl[p].f[F_RH], bt->fl[p].f[F_BH],
+                                    field_bytes(WD_F64, bt->ops[p]->g.stride, 24) * bt->nrhs[p],
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    int n_active = 0;
+    for (int p = 0; p < bt->nprob; ++p)
+        for (int r = 0; r < bt->nrhs[p]; ++r) {
+            const int s = bt->slot0[p] + r;
+            const double n_real = 24.0 * bt->ops[p]->g.vh;
+            active[s] = nb[s] > 0 && r_hi[s] > target[s];
+            n_active += active[s];
+            scale[s] = (mixed && active[s]) ? std::sqrt(n_real) / r_hi[s] : 1.0;
+            rmax[s] = best[s] = r_hi[s] * scale[s];
+            SolverScalars z{};
+            z.nz = INFINITY;
+            z.frozen = !active[s];
+            bt->sc_host[s] = z;
+            bt->consts_host[s] = scale[s];
+            bt->consts_host[BT_MAX_SLOTS + s] = 1.0 / scale[s];
+            bt->consts_host[2 * BT_MAX_SLOTS + s] = 1.0;
+        }
+    BT_TRY(bt_write(bt));
+    BT_TRY(bt_conv(bt, false, F_RL, F_RH));
+    for (int p = 0; p < bt->nprob; ++p) {
+        const size_t lo = field_bytes(bt->prec, bt->ops[p]->g.stride, 24) * bt->nrhs[p];
+        BT_CUDA(cudaMemsetAsync(bt->fl[p].f[F_XL], 0, lo, st));
+        BT_CUDA(cudaMemsetAsync(bt->fl[p].f[F_PL], 0, lo, st));
+    }
+    int iters = 0, ru = 0, status = WD_OK;
+    bool th_valid = any_guess;
+    double delta = bt->ops[0]->ru_delta;
+    int batch = 8;
+    while (n_active > 0) {
+        const int n = std::min(batch, maxiter - iters);
+        if (n > 0) {
+            BT_TRY(bt_run(bt, par, n));
+            iters += n;
+        }
+        BT_TRY(bt_read(bt));
+        bool trigger = iters >= maxiter;
+        int next = 1 << MAX_BATCH_LOG2;
+        for (int s = 0; s < S; ++s) {
+            if (!active[s]) continue;
+            const SolverScalars &h = bt->sc_host[s];
+            if (h.flags & 1) { status = WD_ERR_BREAKDOWN; trigger = true; }
+            const double r = std::sqrt(h.nr);
+            if (r <= target[s] * scale[s] || (mixed && r < delta * rmax[s])) trigger = true;
+            if (r < best[s]) { best[s] = r; best_it[s] = iters; }
+        }
+        if (status != WD_OK) break;
+        if (trigger) {
+            BT_TRY(bt_conv(bt, true, F_XH, F_XL));
+            BT_TRY(bt_true_residual(bt, par));
+            BT_TRY(bt_read(bt));
+            th_valid = true;
+            ru += 1;
+            for (int s = 0; s < S; ++s) {
+                if (!active[s]) continue;
+                r_hi[s] = std::sqrt(bt->sc_host[s].scratch[0]);
+                if (!(r_hi[s] == r_hi[s])) { status = WD_ERR_BREAKDOWN; break; }
+                double ratio = 1.0;
+                if (r_hi[s] <= target[s]) {
+                    active[s] = 0;
+                    n_active -= 1;
+                    bt->sc_host[s].frozen = 1;
+                    conv_iter[s] = iters;
+                } else {
+                    int p = 0;
+                    while (p + 1 < bt->nprob && s >= bt->slot0[p + 1]) ++p;
+                    const double ns = mixed ? std::sqrt(24.0 * bt->ops[p]->g.vh) / r_hi[s] : 1.0;
+                    ratio = ns / scale[s];
+                    scale[s] = ns;
+                    rmax[s] = best[s] = r_hi[s] * ns;
+                    best_it[s] = iters;
+                }
+                bt->consts_host[s] = scale[s];
+                bt->consts_host[BT_MAX_SLOTS + s] = 1.0 / scale[s];
+                bt->consts_host[2 * BT_MAX_SLOTS + s] = ratio;
+            }
+            if (status != WD_OK) break;
+            if (n_active == 0) break;
+            if (iters >= maxiter) { status = WD_ERR_NOT_CONVERGED; break; }
+            BT_TRY(bt_write(bt));
+            BT_TRY(bt_conv(bt, false, F_RL, F_RH));
+            BT_TRY(bt_vec<BT_RESCALE>(bt, false, FIN_NONE, {F_PL}));
+            k_bt_rescale_nz<<<1, BT_MAX_SLOTS, 0, st>>>(bt->sc, bt->consts, S);
+            BT_CUDA(cudaGetLastError());
+            batch = 4;
+            continue;
+        }
+        // next checkpoint: the earliest predicted event over the active systems
+        for (int s = 0; s < S; ++s) {
+            if (!active[s]) continue;
+            const SolverScalars &h = bt->sc_host[s];
+            const int k = h.iter;
+            if (k < 2) { next = std::min(next, 8); continue; }
+            const double l1 = std::log(h.hist[(k - 1) & 63]), l0 = std::log(h.hist[(k - 2) & 63]);
+            const double rate = l1 - l0;
+            double thr = 2 * std::log(target[s] * scale[s]);
+            if (mixed) thr = std::max(thr, 2 * std::log(delta * rmax[s]));
+            const int pred = rate < 0 ? (int)std::ceil((thr - l1) / rate) : 8;
+            next = std::min(next, std::max(1, pred));
+        }
+        batch = std::max(1, std::min(next, 1 << MAX_BATCH_LOG2));
+    }
+    // reconstruction and the FP64 true residual of every full system
+    if (th_valid) BT_TRY(bt_f64<BT64_XPAY>(bt, FIN_NONE, {F_XQ, HBQ, F_TH}, SC_KAPPA));
+    else BT_TRY(bt_hop(bt, true, q, 0, F_XQ, F_XH, HBQ, SC_KAPPA, FIN_NONE));
+    BT_TRY(bt_hop(bt, true, par, 0, F_AXH, F_XQ, F_XH, SC_MKAPPA, FIN_NONE));
+    BT_TRY(bt_f64<BT64_XMY>(bt, FIN_STORE0, {F_RH, HBP, F_AXH}, SC_ONE));
+    BT_TRY(bt_hop(bt, true, q, 0, F_AXH, F_XH, F_XQ, SC_MKAPPA, FIN_NONE));
+    BT_TRY(bt_f64<BT64_XMY>(bt, FIN_STORE1, {F_TH, HBQ, F_AXH}, SC_ONE));
+    for (int p = 0; p < bt->nprob; ++p) {
+        const wd_op *op = bt->ops[p];
+        const long n = 2 * op->g.vh * bt->nrhs[p];
+        const unsigned gr = (unsigned)((n + BT_BLOCK - 1) / BT_BLOCK);
+        const double *xe = (const double *)bt->fl[p].f[par == 0 ? F_XH : F_XQ];
+        const double *xo = (const double *)bt->fl[p].f[par == 0 ? F_XQ : F_XH];
+        k_bt_unpack_full<<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], x[p], xe, xo);
+    }
+    BT_CUDA(cudaGetLastError());
+    BT_TRY(bt_read(bt));
+    bool all_ok = true;
+    for (int s = 0; s < S; ++s) {
+        const double rf = std::sqrt(bt->sc_host[s].scratch[0] + bt->sc_host[s].scratch[1]);
+        const double rel = nb[s] > 0 ? rf / nb[s] : 0.0;
+        if (nb[s] > 0 && rf > target[s] * 1.0000001) all_ok = false;
+        if (info) {
+            info[s].iters = active[s] ? iters : conv_iter[s];
+            info[s].reliable_updates = ru;
+            info[s].true_rel_resid = rel;
+        }
+    }
+    if (status == WD_OK && !all_ok) status = WD_ERR_NOT_CONVERGED;
+    if (status != WD_OK) bt_fail(status, wd_status_string(status));
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *wd_batch_last_error(void) { return g_bt_error.c_str(); }
+
+void wd_batch_destroy(wd_batch *bt) {
+    if (!bt) return;
+    if (bt->stream) cudaStreamSynchronize(bt->stream);
+    for (auto &row : bt->graphs)
+        for (auto &ge : row)
+            if (ge) cudaGraphExecDestroy(ge);
+    for (void *p : bt->allocs) cudaFree(p);
+    if (bt->sc_host) cudaFreeHost(bt->sc_host);
+    if (bt->consts_host) cudaFreeHost(bt->consts_host);
+    if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
+    if (bt->ev_join) cudaEventDestroy(bt->ev_join);
+    if (bt->stream) cudaStreamDestroy(bt->stream);
+    delete bt;
+}
+
+static int batch_create_impl(wd_batch *bt) {
+    BT_CUDA(cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking));
+    BT_CUDA(cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming));
+    BT_CUDA(cudaEventCreateWithFlags(&bt->ev_join, cudaEventDisableTiming));
+    for (int p = 0; p < bt->nprob; ++p) {
+        const wd_op *op = bt->ops[p];
+        const size_t lo = field_bytes(bt->prec, op->g.stride, 24) * bt->nrhs[p];
+        const size_t hi = field_bytes(WD_F64, op->g.stride, 24) * bt->nrhs[p];
+        for (int f = 0; f < N_FLD; ++f) {
+            const bool is_lo = f <= F_TL || f == F_IO0 || f == F_IO1;
+            BT_TRY(bt_alloc(bt, &bt->fl[p].f[f], is_lo ? lo : hi));
+        }
+    }
+    BT_TRY(bt_alloc(bt, (void **)&bt->partials, sizeof(double) * BT_GRID * BT_MAX_SLOTS));
+    BT_TRY(bt_alloc(bt, (void **)&bt->counter, sizeof(unsigned int) * 4));
+    BT_TRY(bt_alloc(bt, (void **)&bt->sc, sizeof(SolverScalars) * BT_MAX_SLOTS));
+    BT_TRY(bt_alloc(bt, (void **)&bt->consts, sizeof(double) * 4 * BT_MAX_SLOTS));
+    BT_CUDA(cudaMallocHost((void **)&bt->sc_host, sizeof(SolverScalars) * BT_MAX_SLOTS));
+    BT_CUDA(cudaMallocHost((void **)&bt->consts_host, sizeof(double) * 4 * BT_MAX_SLOTS));
+    BT_CUDA(cudaDeviceSynchronize());
+    return WD_OK;
+}
+
+int wd_batch_create(wd_batch **out, wd_op *const *ops, const int *nrhs, int nops) {
+    if (!out || !ops || !nrhs) return bt_fail(WD_ERR_ARG, "null argument to wd_batch_create");
+    *out = nullptr;
+    if (nops < 1 || nops > BT_MAX_PROB)
+        return bt_fail(WD_ERR_ARG, "a batch holds 1 to 8 operators");
+    int slots = 0;
+    for (int p = 0; p < nops; ++p) {
+        if (!ops[p] || !ops[p]->gauge_loaded)
+            return bt_fail(WD_ERR_STATE, "every operator needs its gauge field loaded");
+        if (nrhs[p] < 1) return bt_fail(WD_ERR_ARG, "nrhs must be >= 1");
+        if (ops[p]->prec != ops[0]->prec || ops[p]->recon != ops[0]->recon)
+            return bt_fail(WD_ERR_ARG, "operators of a batch share precision and recon");
+        slots += nrhs[p];
+    }
+    if (ops[0]->prec == WD_BF16) return bt_fail(WD_ERR_ARG, "batches support FP64/FP32/FP16");
+    if (slots > BT_MAX_SLOTS) return bt_fail(WD_ERR_ARG, "at most 64 systems per batch");
+    wd_batch *bt = new wd_batch();
+    bt->nprob = nops;
+    bt->prec = ops[0]->prec;
+    bt->recon = ops[0]->recon;
+    bt->user = ops[0]->user;
+    int s = 0;
+    for (int p = 0; p < nops; ++p) {
+        bt->ops[p] = ops[p];
+        bt->nrhs[p] = nrhs[p];
+        bt->slot0[p] = s;
+        s += nrhs[p];
+    }
+    bt->nslots = s;
+    int rc = batch_create_impl(bt);
+    if (rc != WD_OK) {
+        std::string m = g_bt_error;
+        wd_batch_destroy(bt);
+        g_bt_error = m;
+        return rc;
+    }
+    *out = bt;
+    return WD_OK;
+}
+
+static int bt_fork(wd_batch *bt) {
+    BT_CUDA(cudaEventRecord(bt->ev_fork, bt->user));
+    BT_CUDA(cudaStreamWaitEvent(bt->stream, bt->ev_fork, 0));
+    return WD_OK;
+}
+static int bt_join(wd_batch *bt) {
+    BT_CUDA(cudaEventRecord(bt->ev_join, bt->stream));
+    BT_CUDA(cudaStreamWaitEvent(bt->user, bt->ev_join, 0));
+    return WD_OK;
+}
+
+int wd_batch_dslash(wd_batch *bt, double *const *out, const double *const *in, int out_parity,
+                    int dagger) {
+    if (!bt || !out || !in) return bt_fail(WD_ERR_ARG, "null argument to wd_batch_dslash");
+    if (out_parity != 0 && out_parity != 1) return bt_fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (dagger != 0 && dagger != 1) return bt_fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    BT_TRY(bt_fork(bt));
+    for (int p = 0; p < bt->nprob; ++p) {
+        const wd_op *op = bt->ops[p];
+        const long n = op->g.vh * bt->nrhs[p];
+        const unsigned gr = (unsigned)((n + BT_BLOCK - 1) / BT_BLOCK);
+        void *f = bt->fl[p].f[F_IO0];
+        double *c = (double *)in[p];
+        if (bt->prec == WD_F64) k_bt_half<double, 0><<<gr, BT_BLOCK, 0, bt->stream>>>(op->g, bt->nrhs[p], f, c);
+        else if (bt->prec == WD_F32) k_bt_half<float, 0><<<gr, BT_BLOCK, 0, bt->stream>>>(op->g, bt->nrhs[p], f, c);
+        else k_bt_half<__half, 0><<<gr, BT_BLOCK, 0, bt->stream>>>(op->g, bt->nrhs[p], f, c);
+    }
+    BT_CUDA(cudaGetLastError());
+    BT_TRY(bt_hop(bt, false, out_parity, dagger, F_IO1, F_IO0, -1, SC_ONE, FIN_NONE));
+    for (int p = 0; p < bt->nprob; ++p) {
+        const wd_op *op = bt->ops[p];
+        const long n = op->g.vh * bt->nrhs[p];
+        const unsigned gr = (unsigned)((n + BT_BLOCK - 1) / BT_BLOCK);
+        void *f = bt->fl[p].f[F_IO1];
+        if (bt->prec == WD_F64) k_bt_half<double, 1><<<gr, BT_BLOCK, 0, bt->stream>>>(op->g, bt->nrhs[p], f, out[p]);
+        else if (bt->prec == WD_F32) k_bt_half<float, 1><<<gr, BT_BLOCK, 0, bt->stream>>>(op->g, bt->nrhs[p], f, out[p]);
+        else k_bt_half<__half, 1><<<gr, BT_BLOCK, 0, bt->stream>>>(op->g, bt->nrhs[p], f, out[p]);
+    }
+    BT_CUDA(cudaGetLastError());
+    return bt_join(bt);
+}
+
+int wd_batch_dslash_resident(wd_batch *bt, int out_parity, int dagger) {
+    if (!bt) return bt_fail(WD_ERR_ARG, "null batch");
+    BT_TRY(bt_fork(bt));
+    BT_TRY(bt_hop(bt, false, out_parity, dagger, F_IO1, F_IO0, -1, SC_ONE, FIN_NONE));
+    return bt_join(bt);
+}
+
+int wd_batch_solve(wd_batch *bt, double *const *x, const double *const *b, double tol,
+                   int maxiter, int parity, wd_solve_info *info) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!bt || !x || !b) return bt_fail(WD_ERR_ARG, "null argument to wd_batch_solve");
+    if (parity != 0 && parity != 1) return bt_fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (!(tol > 0) || maxiter < 0) return bt_fail(WD_ERR_ARG, "tol must be > 0, maxiter >= 0");
+    if (info) memset(info, 0, sizeof(wd_solve_info) * bt->nslots);
+    BT_TRY(bt_fork(bt));
+    const int rc = bt_solve_impl(bt, x, b, tol, maxiter, parity, info);
+    const int rj = bt_join(bt);
+    const double secs =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info)
+        for (int s = 0; s < bt->nslots; ++s) info[s].seconds = secs;
+    return rc != WD_OK ? rc : rj;
+}
+
+}  // extern "C"

@@ -13,19 +13,7 @@ namespace wd {
 constexpr int BLAS_BLOCK = 256;
 constexpr int BLAS_MAX_GRID = 152 * 8;
 
-template <typename S, typename R> struct Chunk {
-    static constexpr int K = 16 / (int)sizeof(S);  // reals per 16-byte chunk
-    __device__ __forceinline__ static void load(const void *base, long i, R *r) {
-        uint4 v = ld_v4((const char *)base + i * 16);
-        uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        Words<S, R>::unpack(w, r, K);
-    }
-    __device__ __forceinline__ static void store(void *base, long i, const R *r) {
-        uint32_t w[4];
-        Words<S, R>::pack(r, w, K);
-        st_v4((char *)base + i * 16, make_uint4(w[0], w[1], w[2], w[3]));
-    }
-};
+template <typename S, typename R> using Chunk = Chunk16<S, R>;
 
 inline long spinor_chunks(int prec, const Geom &g) {
     return (long)(24 * prec_bytes(prec) / 16) * g.stride;

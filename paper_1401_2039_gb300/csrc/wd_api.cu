@@ -53,64 +53,7 @@ static int fail(int code, const std::string &msg) {
         if (rc_ != WD_OK) return rc_;                                                      \
     } while (0)
 
-// Defaults of the reliable-update scheme (Clark et al. 2010): refresh the
-// FP64 residual whenever the iterated residual has fallen by delta since
-// the last refresh; restart the Krylov direction when the iterated residual
-// has not improved for stall_iters iterations.
-static const double RU_DELTA_DEFAULT = 0.1;
-static const int STALL_ITERS_DEFAULT = 200;
-static const int MAX_BATCH_LOG2 = 5;  // graph batches of 1, 2, ..., 32 iterations
-
-struct wd_op {
-    Geom g{};
-    double kappa = 0;
-    double phase[8] = {};
-    int prec = WD_F64, recon = 18;
-    cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy)
-    cudaStream_t stream = nullptr; // work stream owned by the handle
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    bool gauge_loaded = false;
-
-    GaugeSet gauge_lo;             // storage precision, recon
-    GaugeSet gauge_hi;             // FP64, 18 reals (shares gauge_lo when identical)
-    bool hi_shared = false;
-
-    // storage-precision fields
-    void *fa[2] = {}, *fc[2] = {}, *ftmp = nullptr, *slot[2] = {};
-    void *xl = nullptr, *rl = nullptr, *pl = nullptr, *zl = nullptr, *apl = nullptr,
-         *tl = nullptr;
-    // FP64 fields
-    double *hb[2] = {}, *bh = nullptr, *xh = nullptr, *rh = nullptr, *axh = nullptr,
-           *th = nullptr, *xq = nullptr;
-    // canonical staging for the host-memory solve
-    double *stage_x = nullptr, *stage_b = nullptr;
-
-    // reductions
-    double *partials = nullptr;
-    unsigned int *counter = nullptr;
-    SolverScalars *sc = nullptr;      // device
-    SolverScalars *sc_host = nullptr; // pinned mirror
-    double *dev_consts = nullptr;     // [0] scale, [1] 1/scale, [2] ratio
-    double *host_consts = nullptr;    // pinned staging of dev_consts
-
-    // solver parameters (FP32 inner iterations stay accurate over a deeper
-    // residual drop than FP16/BF16 ones)
-    double ru_delta = RU_DELTA_DEFAULT;
-    int stall_iters = STALL_ITERS_DEFAULT;
-
-    // tuned launch configuration of the hopping term: [0] storage precision, [1] FP64
-    int cfg[2] = {0, 0};
-    double tune_us[2][8] = {};
-    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
-
-    // CUDA graphs of 2^k CGNR iterations, per solved parity
-    cudaGraphExec_t graphs[2][MAX_BATCH_LOG2 + 1] = {};
-
-    std::vector<void *> allocations;
-
-    size_t lo_field_bytes() const { return field_bytes(prec, g.stride, 24); }
-    size_t hi_field_bytes() const { return field_bytes(WD_F64, g.stride, 24); }
-};
+#include "op.cuh"
 
 // ------------------------------------------------------------------ helpers
 static int dev_alloc(wd_op *op, void **p, size_t bytes) {

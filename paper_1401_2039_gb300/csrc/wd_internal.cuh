@@ -215,6 +215,21 @@ template <typename S, int N> struct Rec {
     }
 };
 
+// One 16-byte chunk of a spinor field as 16 / sizeof(S) reals of type R.
+template <typename S, typename R> struct Chunk16 {
+    static constexpr int K = 16 / (int)sizeof(S);
+    __device__ __forceinline__ static void load(const void *base, long i, R *r) {
+        uint4 v = ld_v4((const char *)base + i * 16);
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        Words<S, R>::unpack(w, r, K);
+    }
+    __device__ __forceinline__ static void store(void *base, long i, const R *r) {
+        uint32_t w[4];
+        Words<S, R>::pack(r, w, K);
+        st_v4((char *)base + i * 16, make_uint4(w[0], w[1], w[2], w[3]));
+    }
+};
+
 // ---------------------------------------------------------------- geometry
 struct Geom {
     int L[4];       // Lx, Ly, Lz, Lt
@@ -249,6 +264,7 @@ struct SolverScalars {
     double scratch[4];  // results of plain reductions
     int iter;           // iterations completed
     int flags;          // bit 0: breakdown (zero or non-finite denominator)
+    int frozen;         // converged system of a batch: alpha = beta = 0 from now on
     double hist[64];    // ||r||^2 after iteration k at hist[k % 64]
 };
 
@@ -281,7 +297,7 @@ __device__ __forceinline__ void apply_final(SolverScalars *s, int op, double sum
     case FIN_ALPHA: {
         s->pAp = sum;
         double a = 0.0;                   // z = 0: the residual vanished exactly
-        if (s->nz != 0.0) {
+        if (s->nz != 0.0 && !s->frozen) {
             a = s->nz / sum;
             if (!(sum > 0.0) || !isfinite(a)) { s->flags |= 1; a = 0.0; }
         }
@@ -290,6 +306,7 @@ __device__ __forceinline__ void apply_final(SolverScalars *s, int op, double sum
     }
     case FIN_BETA: {
         // nz = +inf before the first iteration gives beta = 0; so does z = 0
+        if (s->frozen) { s->beta = 0.0; break; }
         double b = sum == 0.0 ? 0.0 : sum / s->nz;
         if (!isfinite(sum) || isnan(b)) { s->flags |= 1; b = 0.0; }
         s->beta = b;
@@ -297,6 +314,7 @@ __device__ __forceinline__ void apply_final(SolverScalars *s, int op, double sum
         break;
     }
     case FIN_NR:
+        if (s->frozen) break;
         s->nr = sum;
         s->hist[s->iter & 63] = sum;
         s->iter += 1;

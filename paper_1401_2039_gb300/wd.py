@@ -238,3 +238,99 @@ class WilsonDirac:
     def dslash_resident(self, in_slot: int, out_parity: int, dagger: bool = False):
         _check(self.lib.wd_dslash_resident(self.handle, int(in_slot), int(out_parity),
                                            int(bool(dagger))))
+
+
+class WilsonBatch:
+    """Lockstep batch of systems: several operators (lattices of any size, same
+    storage precision) with nrhs right-hand sides each (handle on a wd_batch)."""
+
+    def __init__(self, ops, nrhs):
+        self.lib = load_library()
+        _setup_batch_signatures(self.lib)
+        if len(ops) != len(nrhs):
+            raise ValueError("one nrhs per operator")
+        self.ops = list(ops)
+        self.nrhs = [int(n) for n in nrhs]
+        arr = (ctypes.c_void_p * len(ops))(*[op.handle for op in ops])
+        nr = (ctypes.c_int * len(ops))(*self.nrhs)
+        handle = ctypes.c_void_p()
+        rc = self.lib.wd_batch_create(ctypes.byref(handle), arr, nr, len(ops))
+        if rc != WD_OK:
+            raise WDError(rc, self.lib.wd_batch_last_error().decode())
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.wd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nsystems(self) -> int:
+        return sum(self.nrhs)
+
+    def _ptrs(self, tensors, shapes, name):
+        if len(tensors) != len(self.ops):
+            raise ValueError(f"{name}: one tensor per operator")
+        for t, shp in zip(tensors, shapes):
+            _dev(t, shp, name)
+        return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+    def dslash(self, ins, out_parity: int, dagger: bool = False):
+        """Hopping term of every system: ins[k] is [nrhs_k, V_k/2, 3, 4] on parity 1 - out_parity."""
+        shapes = [(n, op.Vh, 3, 4) for n, op in zip(self.nrhs, self.ops)]
+        outs = [torch.empty(s, dtype=torch.complex128, device="cuda") for s in shapes]
+        rc = self.lib.wd_batch_dslash(self.handle, self._ptrs(outs, shapes, "out"),
+                                      self._ptrs(ins, shapes, "in"), int(out_parity),
+                                      int(bool(dagger)))
+        if rc != WD_OK:
+            raise WDError(rc, self.lib.wd_batch_last_error().decode())
+        return outs
+
+    def dslash_resident(self, out_parity: int, dagger: bool = False):
+        rc = self.lib.wd_batch_dslash_resident(self.handle, int(out_parity), int(bool(dagger)))
+        if rc != WD_OK:
+            raise WDError(rc, self.lib.wd_batch_last_error().decode())
+
+    def solve(self, bs, tol: float = 1e-10, maxiter: int = 20000, parity: int = 1, x0s=None,
+              check: bool = True):
+        """Solve every system; bs[k] is [nrhs_k, V_k, 3, 4].  Returns (xs, status, infos)."""
+        shapes = [(n, op.V, 3, 4) for n, op in zip(self.nrhs, self.ops)]
+        xs = [torch.zeros(s, dtype=torch.complex128, device="cuda") for s in shapes] \
+            if x0s is None else [x.clone() for x in x0s]
+        infos = (SolveInfo * self.nsystems)()
+        rc = self.lib.wd_batch_solve(self.handle, self._ptrs(xs, shapes, "x"),
+                                     self._ptrs(bs, shapes, "b"), float(tol), int(maxiter),
+                                     int(parity), infos)
+        if check and rc != WD_OK:
+            raise WDError(rc, self.lib.wd_batch_last_error().decode())
+        return xs, rc, [i.as_dict() for i in infos]
+
+
+_batch_sigs_done = False
+
+
+def _setup_batch_signatures(lib):
+    global _batch_sigs_done
+    if _batch_sigs_done:
+        return
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "wd_batch_create": (i, [ctypes.POINTER(vp), pp, ctypes.POINTER(i), i]),
+        "wd_batch_destroy": (None, [vp]),
+        "wd_batch_dslash": (i, [vp, pp, pp, i, i]),
+        "wd_batch_dslash_resident": (i, [vp, i, i]),
+        "wd_batch_solve": (i, [vp, pp, pp, d, i, i, ctypes.POINTER(SolveInfo)]),
+        "wd_batch_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _batch_sigs_done = True

@@ -1,0 +1,108 @@
+"""Batched systems (many right-hand sides, uneven lattices in one persistent
+launch) against the FP64 oracle and the single-system solver.
+
+Tolerances as in test_gpu_parity.py: hopping term norm-wise 1e-13 (FP64),
+1e-6 (FP32), 2e-2 (FP16); every solved system meets the FP64 true residual
+1e-10 computed by the oracle and lies within 1e-8 of the oracle's solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-2}
+APBC = syn.workloads.APBC_T
+# uneven lattices, ragged last tiles, 1-3 right-hand sides each
+PROBLEMS = [((4, 4, 4, 4), 3, 0.12), ((6, 6, 2, 4), 2, 0.124), ((8, 4, 6, 10), 1, 0.13)]
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def make(prec, recon, problems=PROBLEMS):
+    from paper_1401_2039_gb300 import WilsonBatch, WilsonDirac
+    ops, Us = [], []
+    for k, (dims, n, kappa) in enumerate(problems):
+        U = syn.su3_links(dims, eps=0.3, seed=40 + k)
+        op = WilsonDirac(dims, kappa, APBC, prec=prec, recon=recon)
+        op.set_gauge(torch.from_numpy(U).cuda())
+        ops.append(op)
+        Us.append(U)
+    return WilsonBatch(ops, [n for _, n, _ in problems]), ops, Us
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_batch_dslash(prec, recon):
+    bt, ops, Us = make(prec, recon)
+    for out_parity in (0, 1):
+        for dagger in (False, True):
+            ins = []
+            for k, (dims, n, _) in enumerate(PROBLEMS):
+                ins.append(np.stack([syn.gaussian_spinor(syn.volume(dims) // 2, 100 + 7 * k + r)
+                                     for r in range(n)]))
+            outs = bt.dslash([torch.from_numpy(a).cuda() for a in ins], out_parity, dagger)
+            torch.cuda.synchronize()
+            for k, (dims, n, _) in enumerate(PROBLEMS):
+                got = outs[k].cpu().numpy()
+                for r in range(n):
+                    ref = oracle.hop_eo(ins[k][r], Us[k], dims, APBC, out_parity, dagger)
+                    assert rel(got[r], ref) < TOL[prec], (k, r, out_parity, dagger)
+
+
+@pytest.mark.parametrize("prec,recon", [("f64", 18), ("f32", 18), ("f16", 12)])
+def test_batch_solve(prec, recon):
+    bt, ops, Us = make(prec, recon)
+    bs = [np.stack([syn.gaussian_spinor(syn.volume(dims), 200 + 5 * k + r) for r in range(n)])
+          for k, (dims, n, _) in enumerate(PROBLEMS)]
+    xs, rc, infos = bt.solve([torch.from_numpy(b).cuda() for b in bs], tol=1e-10, maxiter=5000)
+    assert rc == 0
+    s = 0
+    for k, (dims, n, kappa) in enumerate(PROBLEMS):
+        x = xs[k].cpu().numpy()
+        for r in range(n):
+            b = bs[k][r]
+            rt = np.linalg.norm(b - oracle.apply(x[r], Us[k], dims, kappa, APBC)) / np.linalg.norm(b)
+            assert rt <= 1.05e-10, (k, r, rt, infos[s])
+            assert abs(infos[s]["true_rel_resid"] - rt) <= 1e-3 * rt + 1e-15
+            x_ref, _, ok = oracle.solve(b, Us[k], dims, kappa, APBC, tol=1e-13)
+            assert ok and rel(x[r], x_ref) < 1e-8
+            s += 1
+
+
+def test_batch_matches_single_solves_and_freezes_converged():
+    """Twelve point sources (every spin and colour) on one lattice, plus a
+    zero right-hand side that is converged from the start."""
+    from paper_1401_2039_gb300 import WilsonBatch, WilsonDirac
+    dims, kappa = (4, 4, 4, 6), 0.124
+    U = syn.su3_links(dims, seed=3)
+    op = WilsonDirac(dims, kappa, APBC, prec="f32", recon=18)
+    op.set_gauge(torch.from_numpy(U).cuda())
+    srcs = [syn.point_source(dims, 5, c, s) for c in range(3) for s in range(4)]
+    srcs.append(np.zeros_like(srcs[0]))
+    bt = WilsonBatch([op], [len(srcs)])
+    xs, rc, infos = bt.solve([torch.from_numpy(np.stack(srcs)).cuda()], tol=1e-10)
+    assert rc == 0
+    x = xs[0].cpu().numpy()
+    assert np.count_nonzero(x[-1]) == 0 and infos[-1]["iters"] == 0
+    for k in range(12):
+        single = op.solve(torch.from_numpy(srcs[k]).cuda(), tol=1e-10).x.cpu().numpy()
+        assert rel(x[k], single) < 1e-8
+        r = np.linalg.norm(srcs[k] - oracle.apply(x[k], U, dims, kappa, APBC))
+        assert r <= 1.05e-10 * np.linalg.norm(srcs[k])
+
+
+def test_batch_rejects_mixed_precisions():
+    from paper_1401_2039_gb300 import WDError, WilsonBatch, WilsonDirac
+    U = torch.from_numpy(syn.su3_links((4, 4, 4, 4))).cuda()
+    a = WilsonDirac((4, 4, 4, 4), 0.12, APBC, prec="f32")
+    b = WilsonDirac((4, 4, 4, 4), 0.12, APBC, prec="f16")
+    a.set_gauge(U)
+    b.set_gauge(U)
+    with pytest.raises(WDError):
+        WilsonBatch([a, b], [1, 1])
