@@ -147,7 +147,7 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
 
 // f[0] = out, f[1] = in, f[2] = x:  out = scale * H in  or  x + scale * H in
 template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM>
-__global__ void __launch_bounds__(BT_BLOCK, 8) k_dslash_batch(const BtArgs a) {
+__global__ void __launch_bounds__(BT_BLOCK) k_dslash_batch(const __grid_constant__ BtArgs a) {
     __shared__ double tv[BT_BLOCK];
     __shared__ double sacc[BT_MAX_SLOTS];
     if (NORM) {
@@ -161,8 +161,9 @@ __global__ void __launch_bounds__(BT_BLOCK, 8) k_dslash_batch(const BtArgs a) {
         double v = 0.0;
         if (item < P.nitems) {
             const int nr = P.nrhs;
-            const long h = item / nr;
-            const int r = (int)(item - h * nr);
+            const unsigned hu = (unsigned)item / (unsigned)nr;   // items < 2^31
+            const long h = hu;
+            const int r = (int)((unsigned)item - hu * (unsigned)nr);
             int c[4];
             site_coords(P.g, h, a.parity, c);
             R acc[24];
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(BT_BLOCK, 8) k_dslash_batch(const BtArgs a) {
 enum BtOp { BT_XR = 0, BT_P = 1, BT_NORM = 2, BT_RESCALE = 3 };
 
 template <typename S, typename R, int OP>
-__global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const BtArgs a) {
+__global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtArgs a) {
     using C = Chunk16<S, R>;
     __shared__ double tv[BT_BLOCK];
     __shared__ double sacc[BT_MAX_SLOTS];
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const BtArgs a) {
         const long i = item0 + threadIdx.x;
         double v = 0.0;
         if (i < P.nitems) {
-            SolverScalars *s = &a.scalars[P.slot0 + (int)(i % P.nrhs)];
+            SolverScalars *s = &a.scalars[P.slot0 + (int)((unsigned)i % (unsigned)P.nrhs)];
             if (OP == BT_XR) {          // f = {x, r, p, Ap}: x += a p, r -= a Ap, |r|^2
                 const R al = (R)s->alpha;
                 R xv[C::K], rv[C::K], pv[C::K], av[C::K];
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const BtArgs a) {
 #pragma unroll
                 for (int k = 0; k < C::K; ++k) v += (double)vv[k] * (double)vv[k];
             } else {                    // f = {p}: p *= ratio[slot]
-                const int slot = P.slot0 + (int)(i % P.nrhs);
+                const int slot = P.slot0 + (int)((unsigned)i % (unsigned)P.nrhs);
                 const R ratio = (R)a.consts[2 * BT_MAX_SLOTS + slot];
                 R pv[C::K];
                 C::load(P.f[0], i, pv);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const BtArgs a) {
 enum BtOp64 { BT64_XMY = 0, BT64_XPAY = 1 };
 
 template <int OP>
-__global__ void __launch_bounds__(BT_BLOCK) k_bt_f64(const BtArgs a) {
+__global__ void __launch_bounds__(BT_BLOCK) k_bt_f64(const __grid_constant__ BtArgs a) {
     __shared__ double tv[BT_BLOCK];
     __shared__ double sacc[BT_MAX_SLOTS];
     if (OP == BT64_XMY) {
@@ -301,12 +302,12 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_f64(const BtArgs a) {
 //   CONV: f = {out (SO), in (SI)}: out = consts[0][slot] * in
 //   FOLD: f = {x_hi (FP64), x_lo (SI)}: x_hi += consts[1][slot] * x_lo; x_lo = 0
 template <typename SO, typename SI, int FOLD>
-__global__ void __launch_bounds__(BT_BLOCK) k_bt_conv(const BtArgs a) {
+__global__ void __launch_bounds__(BT_BLOCK) k_bt_conv(const __grid_constant__ BtArgs a) {
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long i = (t - P.tile0) * BT_BLOCK + threadIdx.x;
         if (i >= P.nitems) continue;
-        const int slot = P.slot0 + (int)(i % P.nrhs);
+        const int slot = P.slot0 + (int)((unsigned)i % (unsigned)P.nrhs);
         const long ss = P.g.stride * P.nrhs;
         double v[24];
         Rec<SI, 24>::template load_coherent<double>(P.f[1], ss, i, v);
@@ -589,10 +590,12 @@ int bt_conv(wd_batch *bt, bool fold, int dst, int src) {
     const unsigned gr = grid_of(a);
     cudaStream_t s = bt->stream;
     if (fold) {
-        if (bt->prec == WD_F32) k_bt_conv<double, float, 1><<<gr, BT_BLOCK, 0, s>>>(a);
+        if (bt->prec == WD_F64) k_bt_conv<double, double, 1><<<gr, BT_BLOCK, 0, s>>>(a);
+        else if (bt->prec == WD_F32) k_bt_conv<double, float, 1><<<gr, BT_BLOCK, 0, s>>>(a);
         else k_bt_conv<double, __half, 1><<<gr, BT_BLOCK, 0, s>>>(a);
     } else {
-        if (bt->prec == WD_F32) k_bt_conv<float, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+        if (bt->prec == WD_F64) k_bt_conv<double, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+        else if (bt->prec == WD_F32) k_bt_conv<float, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
         else k_bt_conv<__half, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
     }
     BT_CUDA(cudaGetLastError());

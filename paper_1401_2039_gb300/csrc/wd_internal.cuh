@@ -238,14 +238,17 @@ struct Geom {
     long stride;    // padded plane stride (sites)
 };
 
-// Coordinates of half-lattice site h of parity p.
+// Coordinates of half-lattice site h of parity p (32-bit arithmetic: the
+// volume is limited to 2^31 sites).
 __device__ __forceinline__ void site_coords(const Geom &g, long h, int p, int c[4]) {
-    long r = h / g.hx;
-    int xh = (int)(h - r * g.hx);
-    c[1] = (int)(r % g.L[1]);
-    r /= g.L[1];
-    c[2] = (int)(r % g.L[2]);
-    c[3] = (int)(r / g.L[2]);
+    const unsigned hu = (unsigned)h;
+    unsigned r = hu / (unsigned)g.hx;
+    const int xh = (int)(hu - r * (unsigned)g.hx);
+    const unsigned r1 = r / (unsigned)g.L[1];
+    c[1] = (int)(r - r1 * (unsigned)g.L[1]);
+    const unsigned r2 = r1 / (unsigned)g.L[2];
+    c[2] = (int)(r1 - r2 * (unsigned)g.L[2]);
+    c[3] = (int)r2;
     c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
 }
 
