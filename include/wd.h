@@ -124,6 +124,16 @@ int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, int maxiter,
  * has not improved for stall_iters iterations (default 200). */
 int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters);
 
+/* Arithmetic of the residual recomputations of the reliable updates, of the
+ * Schur preparation and reconstruction and of the final true residual for
+ * WD_F32/WD_F16/WD_BF16 operators: mode 0 = native FP64, mode 1 (default) =
+ * double-float (each real the unevaluated sum of two FP32 numbers, a 48-bit
+ * significand, run on the FP32 pipes; GB300's FP64 rate is a small fraction
+ * of its FP32 rate).  Either form keeps ||b - D x|| accurate far below the
+ * 1e-10 relative residuals the solver is used for.  WD_F64 operators always
+ * use FP64 (mode 1 is rejected).  Not in the paper. */
+int wd_op_set_residual_precision(wd_op *op, int mode);
+
 /* The same solve with x and b in HOST memory (pageable or pinned); the
  * host<->device copies go through buffers the handle owns. */
 int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,

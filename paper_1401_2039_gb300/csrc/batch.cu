@@ -264,13 +264,14 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtA
     if (RED) bt_finish(a, sacc);
 }
 
-// FP64 kernels over (site, rhs) items:
+// High-precision (FP64 or double-float) kernels over 16-byte chunks:
 //   XMY:  f = {out, x, y}: out = x - y, |out|^2
 //   XPAY: f = {out, y, x}: out = y + scale x
 enum BtOp64 { BT64_XMY = 0, BT64_XPAY = 1 };
 
-template <int OP>
-__global__ void __launch_bounds__(BT_BLOCK) k_bt_f64(const __grid_constant__ BtArgs a) {
+template <typename H, int OP>
+__global__ void __launch_bounds__(BT_BLOCK) k_bt_hi(const __grid_constant__ BtArgs a) {
+    using C = Chunk16<H, H>;
     __shared__ double tv[BT_BLOCK];
     __shared__ double sacc[BT_MAX_SLOTS];
     if (OP == BT64_XMY) {
@@ -283,15 +284,18 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_f64(const __grid_constant__ BtA
         const long i = item0 + threadIdx.x;
         double v = 0.0;
         if (i < P.nitems) {
-            const double2 *x = (const double2 *)P.f[1];
-            const double2 *y = (const double2 *)P.f[2];
-            double2 *o = (double2 *)P.f[0];
-            const double2 a1 = x[i], b1 = y[i];
-            double2 d;
-            if (OP == BT64_XMY) d = make_double2(a1.x - b1.x, a1.y - b1.y);
-            else d = make_double2(a1.x + P.scale * b1.x, a1.y + P.scale * b1.y);
-            o[i] = d;
-            v = d.x * d.x + d.y * d.y;
+            H xv[C::K], yv[C::K], d[C::K];
+            C::load(P.f[1], i, xv);
+            C::load(P.f[2], i, yv);
+            H sq = 0;
+#pragma unroll
+            for (int k = 0; k < C::K; ++k) {
+                if (OP == BT64_XMY) d[k] = xv[k] - yv[k];
+                else d[k] = xv[k] + H(P.scale) * yv[k];
+                sq += d[k] * d[k];
+            }
+            C::store(P.f[0], i, d);
+            v = (double)sq;
         }
         if (OP == BT64_XMY) bt_tile_sums(v, P, item0, tv, sacc);
     }
@@ -300,8 +304,8 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_f64(const __grid_constant__ BtA
 
 // Conversions over (site, rhs) items, with per-slot constants:
 //   CONV: f = {out (SO), in (SI)}: out = consts[0][slot] * in
-//   FOLD: f = {x_hi (FP64), x_lo (SI)}: x_hi += consts[1][slot] * x_lo; x_lo = 0
-template <typename SO, typename SI, int FOLD>
+//   FOLD: f = {x_hi (H), x_lo (SI)}: x_hi += consts[1][slot] * x_lo; x_lo = 0
+template <typename SO, typename SI, int FOLD, typename H = double>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_conv(const __grid_constant__ BtArgs a) {
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
@@ -312,15 +316,15 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_conv(const __grid_constant__ Bt
         double v[24];
         Rec<SI, 24>::template load_coherent<double>(P.f[1], ss, i, v);
         if (FOLD) {
-            double hi[24];
-            Rec<double, 24>::template load_coherent<double>(P.f[0], ss, i, hi);
-            const double is = a.consts[BT_MAX_SLOTS + slot];
+            H hi[24];
+            Rec<H, 24>::template load_coherent<H>(P.f[0], ss, i, hi);
+            const H is = H(a.consts[BT_MAX_SLOTS + slot]);
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
-                hi[k] += is * v[k];
+                hi[k] += is * H(v[k]);
                 v[k] = 0.0;
             }
-            Rec<double, 24>::store(P.f[0], ss, i, hi);
+            Rec<H, 24>::store(P.f[0], ss, i, hi);
             Rec<SI, 24>::store(P.f[1], ss, i, v);
         } else {
             const double sc = a.consts[slot];
@@ -341,7 +345,8 @@ __global__ void k_bt_rescale_nz(SolverScalars *sc, const double *consts, int nsl
 }
 
 // Canonical [nrhs][V][3][4] complex128 <-> batched FP64 parity fields.
-__global__ void k_bt_pack_full(Geom g, int nrhs, double *even, double *odd, const double *src) {
+template <typename H>
+__global__ void k_bt_pack_full(Geom g, int nrhs, void *even, void *odd, const double *src) {
     const long i = (long)blockIdx.x * BT_BLOCK + threadIdx.x;
     const long V = 2 * g.vh;
     if (i >= V * nrhs) return;
@@ -355,12 +360,13 @@ __global__ void k_bt_pack_full(Geom g, int nrhs, double *even, double *odd, cons
     double v[24];
     const double2 *s2 = (const double2 *)(src + i * 24);
     for (int k = 0; k < 12; ++k) { v[2 * k] = s2[k].x; v[2 * k + 1] = s2[k].y; }
-    Rec<double, 24>::store(((x + y + z + t) & 1) ? odd : even, g.stride * nrhs,
-                           (lex >> 1) * nrhs + r, v);
+    Rec<H, 24>::store(((x + y + z + t) & 1) ? odd : even, g.stride * nrhs,
+                      (lex >> 1) * nrhs + r, v);
 }
 
-__global__ void k_bt_unpack_full(Geom g, int nrhs, double *dst, const double *even,
-                                 const double *odd) {
+template <typename H>
+__global__ void k_bt_unpack_full(Geom g, int nrhs, double *dst, const void *even,
+                                 const void *odd) {
     const long i = (long)blockIdx.x * BT_BLOCK + threadIdx.x;
     const long V = 2 * g.vh;
     if (i >= V * nrhs) return;
@@ -372,8 +378,8 @@ __global__ void k_bt_unpack_full(Geom g, int nrhs, double *dst, const double *ev
     const int z = (int)(q % g.L[2]);
     const int t = (int)(q / g.L[2]);
     double v[24];
-    Rec<double, 24>::template load_coherent<double>(((x + y + z + t) & 1) ? odd : even,
-                                                    g.stride * nrhs, (lex >> 1) * nrhs + r, v);
+    Rec<H, 24>::template load_coherent<double>(((x + y + z + t) & 1) ? odd : even,
+                                               g.stride * nrhs, (lex >> 1) * nrhs + r, v);
     double2 *d2 = (double2 *)(dst + i * 24);
     for (int k = 0; k < 12; ++k) d2[k] = make_double2(v[2 * k], v[2 * k + 1]);
 }
@@ -439,6 +445,7 @@ struct wd_batch {
     int slot0[BT_MAX_PROB] = {};
     int nslots = 0;
     int prec = WD_F32, recon = 18;
+    int hi_prec = WD_F64;       // residual arithmetic shared by the operators
     cudaStream_t user = nullptr, stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     BtFields fl[BT_MAX_PROB];
@@ -542,9 +549,11 @@ int bt_hop(wd_batch *bt, bool hi, int out_parity, int dagger, int out, int in, i
     BtArgs a = x >= 0 ? make_args(bt, IT_SITES, fin, {out, in, x}, scale_mode, hi, out_parity)
                       : make_args(bt, IT_SITES, fin, {out, in}, scale_mode, hi, out_parity);
     const bool xpay = x >= 0, norm = fin != FIN_NONE;
-    const int prec = hi ? WD_F64 : bt->prec;
+    const int prec = hi ? bt->hi_prec : bt->prec;
     const int recon = hi ? 18 : bt->recon;
-    if (prec == WD_F64) {
+    if (prec == WD_DF64) {
+        launch_hop_t<df64, df64, 18>(a, dagger, xpay, norm, bt->stream);
+    } else if (prec == WD_F64) {
         if (recon == 12) launch_hop_t<double, double, 12>(a, dagger, xpay, norm, bt->stream);
         else launch_hop_t<double, double, 18>(a, dagger, xpay, norm, bt->stream);
     } else if (prec == WD_F32) {
@@ -567,9 +576,10 @@ int bt_schur(wd_batch *bt, bool hi, int p, int dagger, int out, int in, int tmp,
 template <int OP>
 int bt_vec(wd_batch *bt, bool hi, int fin, std::initializer_list<int> fields) {
     BtArgs a = make_args(bt, hi ? IT_HI_CHUNKS : IT_LO_CHUNKS, fin, fields, SC_ONE, false, 0);
-    const int prec = hi ? WD_F64 : bt->prec;
+    const int prec = hi ? bt->hi_prec : bt->prec;
     const unsigned gr = grid_of(a);
-    if (prec == WD_F64) k_bt_vec<double, double, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
+    if (prec == WD_DF64) k_bt_vec<df64, df64, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
+    else if (prec == WD_F64) k_bt_vec<double, double, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
     else if (prec == WD_F32) k_bt_vec<float, float, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
     else k_bt_vec<__half, float, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
     BT_CUDA(cudaGetLastError());
@@ -579,7 +589,8 @@ int bt_vec(wd_batch *bt, bool hi, int fin, std::initializer_list<int> fields) {
 template <int OP>
 int bt_f64(wd_batch *bt, int fin, std::initializer_list<int> fields, int scale_mode) {
     BtArgs a = make_args(bt, IT_HI_D2, fin, fields, scale_mode, false, 0);
-    k_bt_f64<OP><<<grid_of(a), BT_BLOCK, 0, bt->stream>>>(a);
+    if (bt->hi_prec == WD_DF64) k_bt_hi<df64, OP><<<grid_of(a), BT_BLOCK, 0, bt->stream>>>(a);
+    else k_bt_hi<double, OP><<<grid_of(a), BT_BLOCK, 0, bt->stream>>>(a);
     BT_CUDA(cudaGetLastError());
     return WD_OK;
 }
@@ -589,14 +600,25 @@ int bt_conv(wd_batch *bt, bool fold, int dst, int src) {
     BtArgs a = make_args(bt, IT_SITES, FIN_NONE, {dst, src}, SC_ONE, false, 0);
     const unsigned gr = grid_of(a);
     cudaStream_t s = bt->stream;
+    const bool df = bt->hi_prec == WD_DF64;
     if (fold) {
         if (bt->prec == WD_F64) k_bt_conv<double, double, 1><<<gr, BT_BLOCK, 0, s>>>(a);
-        else if (bt->prec == WD_F32) k_bt_conv<double, float, 1><<<gr, BT_BLOCK, 0, s>>>(a);
-        else k_bt_conv<double, __half, 1><<<gr, BT_BLOCK, 0, s>>>(a);
+        else if (bt->prec == WD_F32) {
+            if (df) k_bt_conv<double, float, 1, df64><<<gr, BT_BLOCK, 0, s>>>(a);
+            else k_bt_conv<double, float, 1><<<gr, BT_BLOCK, 0, s>>>(a);
+        } else {
+            if (df) k_bt_conv<double, __half, 1, df64><<<gr, BT_BLOCK, 0, s>>>(a);
+            else k_bt_conv<double, __half, 1><<<gr, BT_BLOCK, 0, s>>>(a);
+        }
     } else {
         if (bt->prec == WD_F64) k_bt_conv<double, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
-        else if (bt->prec == WD_F32) k_bt_conv<float, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
-        else k_bt_conv<__half, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+        else if (bt->prec == WD_F32) {
+            if (df) k_bt_conv<float, df64, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+            else k_bt_conv<float, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+        } else {
+            if (df) k_bt_conv<__half, df64, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+            else k_bt_conv<__half, double, 0><<<gr, BT_BLOCK, 0, s>>>(a);
+        }
     }
     BT_CUDA(cudaGetLastError());
     return WD_OK;
@@ -675,9 +697,15 @@ int bt_solve_impl(wd_batch *bt, double *const *x, const double *const *b, double
         const unsigned gr = (unsigned)((n + BT_BLOCK - 1) / BT_BLOCK);
         double *xe = (double *)bt->fl[p].f[par == 0 ? F_XH : F_XQ];
         double *xo = (double *)bt->fl[p].f[par == 0 ? F_XQ : F_XH];
-        k_bt_pack_full<<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], (double *)bt->fl[p].f[F_HB0],
-                                                (double *)bt->fl[p].f[F_HB1], b[p]);
-        k_bt_pack_full<<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], xe, xo, x[p]);
+        if (bt->hi_prec == WD_DF64) {
+            k_bt_pack_full<df64><<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], bt->fl[p].f[F_HB0],
+                                                          bt->fl[p].f[F_HB1], b[p]);
+            k_bt_pack_full<df64><<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], xe, xo, x[p]);
+        } else {
+            k_bt_pack_full<double><<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], bt->fl[p].f[F_HB0],
+                                                            bt->fl[p].f[F_HB1], b[p]);
+            k_bt_pack_full<double><<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], xe, xo, x[p]);
+        }
     }
     BT_CUDA(cudaGetLastError());
     const int HBP = par == 0 ? F_HB0 : F_HB1, HBQ = par == 0 ? F_HB1 : F_HB0;
@@ -818,7 +846,10 @@ int bt_solve_impl(wd_batch *bt, double *const *x, const double *const *b, double
         const unsigned gr = (unsigned)((n + BT_BLOCK - 1) / BT_BLOCK);
         const double *xe = (const double *)bt->fl[p].f[par == 0 ? F_XH : F_XQ];
         const double *xo = (const double *)bt->fl[p].f[par == 0 ? F_XQ : F_XH];
-        k_bt_unpack_full<<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], x[p], xe, xo);
+        if (bt->hi_prec == WD_DF64)
+            k_bt_unpack_full<df64><<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], x[p], xe, xo);
+        else
+            k_bt_unpack_full<double><<<gr, BT_BLOCK, 0, st>>>(op->g, bt->nrhs[p], x[p], xe, xo);
     }
     BT_CUDA(cudaGetLastError());
     BT_TRY(bt_read(bt));
@@ -892,8 +923,10 @@ int wd_batch_create(wd_batch **out, wd_op *const *ops, const int *nrhs, int nops
         if (!ops[p] || !ops[p]->gauge_loaded)
             return bt_fail(WD_ERR_STATE, "every operator needs its gauge field loaded");
         if (nrhs[p] < 1) return bt_fail(WD_ERR_ARG, "nrhs must be >= 1");
-        if (ops[p]->prec != ops[0]->prec || ops[p]->recon != ops[0]->recon)
-            return bt_fail(WD_ERR_ARG, "operators of a batch share precision and recon");
+        if (ops[p]->prec != ops[0]->prec || ops[p]->recon != ops[0]->recon ||
+            ops[p]->hi_prec != ops[0]->hi_prec)
+            return bt_fail(WD_ERR_ARG,
+                           "operators of a batch share precision, recon and residual precision");
         slots += nrhs[p];
     }
     if (ops[0]->prec == WD_BF16) return bt_fail(WD_ERR_ARG, "batches support FP64/FP32/FP16");
@@ -902,6 +935,7 @@ int wd_batch_create(wd_batch **out, wd_op *const *ops, const int *nrhs, int nops
     bt->nprob = nops;
     bt->prec = ops[0]->prec;
     bt->recon = ops[0]->recon;
+    bt->hi_prec = ops[0]->hi_prec;
     bt->user = ops[0]->user;
     int s = 0;
     for (int p = 0; p < nops; ++p) {

@@ -76,6 +76,108 @@ k_cg_update_p(long n, void *p, const void *z, const SolverScalars *sc) {
     }
 }
 
+// |v|^2 of a double-float field, accumulated in double-float per thread.
+__global__ void __launch_bounds__(BLAS_BLOCK) k_norm2_df(long n, const void *v, Reduction red) {
+    using C = Chunk16<df64, df64>;
+    df64 acc = 0;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        df64 a[C::K];
+        C::load(v, i, a);
+#pragma unroll
+        for (int k = 0; k < C::K; ++k) acc += a[k] * a[k];
+    }
+    block_reduce_finish<BLAS_BLOCK>((double)acc, red);
+}
+
+// out = x - y and |out|^2 in double-float
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_xmy_norm_df(long n, void *out, const void *x, const void *y, Reduction red) {
+    using C = Chunk16<df64, df64>;
+    df64 acc = 0;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        df64 a[C::K], b[C::K];
+        C::load(x, i, a);
+        C::load(y, i, b);
+#pragma unroll
+        for (int k = 0; k < C::K; ++k) {
+            a[k] = a[k] - b[k];
+            acc += a[k] * a[k];
+        }
+        C::store(out, i, a);
+    }
+    block_reduce_finish<BLAS_BLOCK>((double)acc, red);
+}
+
+// out = y + a x in double-float
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_xpay_df(long n, void *out, const void *y, df64 a, const void *x) {
+    using C = Chunk16<df64, df64>;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        df64 yv[C::K], xv[C::K];
+        C::load(y, i, yv);
+        C::load(x, i, xv);
+#pragma unroll
+        for (int k = 0; k < C::K; ++k) yv[k] += a * xv[k];
+        C::store(out, i, yv);
+    }
+}
+
+// x_hi (double-float) += inv_scale * x_lo;  x_lo = 0
+template <typename S>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_fold_x_df(long vh, long stride, void *x_hi, void *x_lo, const double *inv_scale) {
+    const df64 is = df64(*inv_scale);
+    for (long h = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; h < vh;
+         h += (long)gridDim.x * BLAS_BLOCK) {
+        float lo[24];
+        df64 hi[24];
+        Rec<S, 24>::template load_coherent<float>(x_lo, stride, h, lo);
+        Rec<df64, 24>::template load_coherent<df64>(x_hi, stride, h, hi);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            hi[i] += is * df64(lo[i], 0.0f);
+            lo[i] = 0.0f;
+        }
+        Rec<df64, 24>::store(x_hi, stride, h, hi);
+        Rec<S, 24>::store(x_lo, stride, h, lo);
+    }
+}
+
+// out (precision SO) = scale * in (double-float), in FP32: the low-precision
+// copy needs only the leading part.
+template <typename SO>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_convert_from_df(long vh, long stride, void *out, const void *in, const double *scale_dev,
+                  double scale_host) {
+    const float sc = (float)(scale_dev ? *scale_dev : scale_host);
+    for (long h = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; h < vh;
+         h += (long)gridDim.x * BLAS_BLOCK) {
+        float v[24];
+        Rec<df64, 24>::template load_coherent<float>(in, stride, h, v);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[i] *= sc;
+        Rec<SO, 24>::store(out, stride, h, v);
+    }
+}
+
+// FP64 <-> double-float, element-wise over n eight-byte reals
+__global__ void k_f64_df64(long n, void *buf, int to_df) {
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        if (to_df) {
+            const double d = reinterpret_cast<double *>(buf)[i];
+            const df64 v(d);
+            reinterpret_cast<float2 *>(buf)[i] = make_float2(v.hi, v.lo);
+        } else {
+            const float2 f = reinterpret_cast<float2 *>(buf)[i];
+            reinterpret_cast<double *>(buf)[i] = (double)f.x + (double)f.y;
+        }
+    }
+}
+
 template <typename S, typename R>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_norm2(long n, const void *v, Reduction red) {
     using C = Chunk<S, R>;
@@ -198,21 +300,38 @@ cudaError_t launch_cg_update_p(int prec, const Geom &g, void *p, const void *z,
 cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction &red,
                          cudaStream_t s) {
     const long n = spinor_chunks(prec, g);
+    if (prec == WD_DF64) {
+        k_norm2_df<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, v, red);
+        return cudaGetLastError();
+    }
     WD_PREC_DISPATCH(prec, (k_norm2<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, v, red)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_xmy_norm(const Geom &g, double *out, const double *x, const double *y,
+cudaError_t launch_xmy_norm(int prec, const Geom &g, void *out, const void *x, const void *y,
                             const Reduction &red, cudaStream_t s) {
     const long n = spinor_chunks(WD_F64, g);
-    k_xmy_norm<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, out, x, y, red);
+    if (prec == WD_DF64)
+        k_xmy_norm_df<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, out, x, y, red);
+    else
+        k_xmy_norm<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, (double *)out, (const double *)x,
+                                                       (const double *)y, red);
     return cudaGetLastError();
 }
 
-cudaError_t launch_xpay_f64(const Geom &g, double *out, const double *y, double a,
-                            const double *x, cudaStream_t s) {
+cudaError_t launch_xpay_hi(int prec, const Geom &g, void *out, const void *y, double a,
+                           const void *x, cudaStream_t s) {
     const long n = spinor_chunks(WD_F64, g);
-    k_xpay_f64<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, out, y, a, x);
+    if (prec == WD_DF64)
+        k_xpay_df<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, out, y, df64(a), x);
+    else
+        k_xpay_f64<<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, (double *)out, (const double *)y, a,
+                                                       (const double *)x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_df64(void *buf, long n_reals, int to_df, cudaStream_t s) {
+    k_f64_df64<<<blas_grid(n_reals), BLAS_BLOCK, 0, s>>>(n_reals, buf, to_df);
     return cudaGetLastError();
 }
 
@@ -233,6 +352,16 @@ static cudaError_t convert_from(int prec_in, void *out, const void *in, const Ge
 cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const void *in,
                                   const Geom &g, const double *scale_dev, double scale_host,
                                   cudaStream_t s) {
+    if (prec_in == WD_DF64 && prec_out != WD_F64) {
+        const unsigned grid = blas_grid(g.vh);
+        switch (prec_out) {
+        case WD_F32: k_convert_from_df<float><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, out, in, scale_dev, scale_host); break;
+        case WD_F16: k_convert_from_df<__half><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, out, in, scale_dev, scale_host); break;
+        case WD_BF16: k_convert_from_df<__nv_bfloat16><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, out, in, scale_dev, scale_host); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (prec_out) {
     case WD_F64: return convert_from<double>(prec_in, out, in, g, scale_dev, scale_host, s);
     case WD_F32: return convert_from<float>(prec_in, out, in, g, scale_dev, scale_host, s);
@@ -242,10 +371,20 @@ cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const vo
     }
 }
 
-cudaError_t launch_fold_x(int prec_lo, const Geom &g, double *x_hi, void *x_lo,
+cudaError_t launch_fold_x(int prec_lo, int prec_hi, const Geom &g, void *x_hi, void *x_lo,
                           const double *inv_scale_dev, cudaStream_t s) {
     const unsigned grid = blas_grid(g.vh);
-    WD_PREC_DISPATCH(prec_lo, (k_fold_x<S><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo,
+    if (prec_hi == WD_DF64) {
+        switch (prec_lo) {
+        case WD_F32: k_fold_x_df<float><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, inv_scale_dev); break;
+        case WD_F16: k_fold_x_df<__half><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, inv_scale_dev); break;
+        case WD_BF16: k_fold_x_df<__nv_bfloat16><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, inv_scale_dev); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+    WD_PREC_DISPATCH(prec_lo, (k_fold_x<S><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride,
+                                                                         (double *)x_hi, x_lo,
                                                                          inv_scale_dev)));
     return cudaGetLastError();
 }

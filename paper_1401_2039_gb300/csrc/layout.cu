@@ -92,6 +92,7 @@ __global__ void k_pack_gauge(Geom g, char *even, char *odd, size_t dir_bytes, co
     case WD_F32: KERNEL<float><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;         \
     case WD_F16: KERNEL<__half><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;        \
     case WD_BF16: KERNEL<__nv_bfloat16><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;\
+    case WD_DF64: KERNEL<df64><<<grid, LAYOUT_BLOCK, 0, s>>>(__VA_ARGS__); break;         \
     default: return cudaErrorInvalidValue;                                                \
     }
 
@@ -135,6 +136,7 @@ cudaError_t launch_pack_gauge(const GaugeSet &gs, const Geom &g, const double *U
     case WD_F32: WD_G(float); break;
     case WD_F16: WD_G(__half); break;
     case WD_BF16: WD_G(__nv_bfloat16); break;
+    case WD_DF64: WD_G(df64); break;
     default: return cudaErrorInvalidValue;
     }
 #undef WD_G

@@ -22,6 +22,7 @@ struct wd_op {
     double kappa = 0;
     double phase[8] = {};
     int prec = WD_F64, recon = 18;
+    int hi_prec = WD_F64;          // residual arithmetic: WD_F64 or wd::WD_DF64 (double-float)
     cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy)
     cudaStream_t stream = nullptr; // work stream owned by the handle
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -65,6 +66,6 @@ struct wd_op {
     std::vector<void *> allocations;
 
     size_t lo_field_bytes() const { return wd::field_bytes(prec, g.stride, 24); }
-    size_t hi_field_bytes() const { return wd::field_bytes(WD_F64, g.stride, 24); }
+    size_t hi_field_bytes() const { return wd::field_bytes(hi_prec, g.stride, 24); }
 };
 

@@ -17,6 +17,7 @@ namespace wd {
     cudaError_t launch_dslash_##P##_r12(const DslashLaunch &L, cudaStream_t s);
 WD_DECL(f64) WD_DECL(f32) WD_DECL(f16) WD_DECL(bf16)
 #undef WD_DECL
+cudaError_t launch_dslash_df64_r18(const DslashLaunch &L, cudaStream_t s);
 
 cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s) {
     const bool r12 = L.gauge->recon == 12;
@@ -25,6 +26,7 @@ cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s) {
     case WD_F32: return r12 ? launch_dslash_f32_r12(L, s) : launch_dslash_f32_r18(L, s);
     case WD_F16: return r12 ? launch_dslash_f16_r12(L, s) : launch_dslash_f16_r18(L, s);
     case WD_BF16: return r12 ? launch_dslash_bf16_r12(L, s) : launch_dslash_bf16_r18(L, s);
+    case WD_DF64: return r12 ? cudaErrorInvalidValue : launch_dslash_df64_r18(L, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -101,7 +103,7 @@ static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, con
     L.epi = x ? EPI_XPAY : EPI_PLAIN;
     L.red = red;
     L.cfg = op->cfg[hi ? 1 : 0];
-    WD_CUDA(launch_dslash(L, hi ? WD_F64 : op->prec, op->stream));
+    WD_CUDA(launch_dslash(L, hi ? op->hi_prec : op->prec, op->stream));
     return WD_OK;
 }
 
@@ -168,6 +170,27 @@ int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters) {
     op->ru_delta = ru_delta;
     op->stall_iters = stall_iters;
     return WD_OK;
+}
+
+int wd_op_set_residual_precision(wd_op *op, int mode) {
+    if (!op) return fail(WD_ERR_ARG, "null operator handle");
+    if (mode != 0 && mode != 1) return fail(WD_ERR_ARG, "mode must be 0 (FP64) or 1 (double-float)");
+    if (op->prec == WD_F64) {
+        if (mode != 0) return fail(WD_ERR_ARG, "a WD_F64 operator computes its residuals in FP64");
+        return WD_OK;
+    }
+    const int want = mode ? WD_DF64 : WD_F64;
+    if (want == op->hi_prec) return WD_OK;
+    WD_TRY(fork(op));
+    if (op->gauge_loaded) {   // both forms are 8 bytes per real: convert in place
+        const long n = (long)(4 * op->gauge_hi.dir_bytes / 8);
+        for (int p = 0; p < 2; ++p)
+            WD_CUDA(launch_f64_df64(op->gauge_hi.ptr[p], n, mode, op->stream));
+    }
+    op->hi_prec = want;
+    op->gauge_hi.prec = want;
+    if (op->gauge_loaded) WD_TRY(tune_dslash(op, true));
+    return join(op);
 }
 
 int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,
@@ -240,9 +263,9 @@ static int create_impl(wd_op *op) {
     if (op->hi_shared) {
         op->gauge_hi = op->gauge_lo;
     } else {
-        op->gauge_hi.prec = WD_F64;
+        op->gauge_hi.prec = op->hi_prec;
         op->gauge_hi.recon = 18;
-        op->gauge_hi.dir_bytes = field_bytes(WD_F64, g.stride, 18);
+        op->gauge_hi.dir_bytes = field_bytes(op->hi_prec, g.stride, 18);
         for (int p = 0; p < 2; ++p)
             WD_TRY(dev_alloc(op, &op->gauge_hi.ptr[p], 4 * op->gauge_hi.dir_bytes));
     }
@@ -296,6 +319,7 @@ int wd_op_create(wd_op **out, const int dims[4], double kappa, const double phas
     memcpy(op->phase, phase, sizeof(op->phase));
     op->prec = prec;
     op->recon = recon;
+    op->hi_prec = prec == WD_F64 ? WD_F64 : WD_DF64;
     op->ru_delta = prec == WD_F32 ? 0.01 : RU_DELTA_DEFAULT;
     op->user = (cudaStream_t)stream;
     int rc = create_impl(op);
@@ -469,7 +493,7 @@ int read_scalars(wd_op *op) {
 int true_residual(wd_op *op, SolveState &st) {
     Reduction r0 = reduction(op, FIN_STORE0);
     WD_TRY(schur(op, true, st.p, 0, op->axh, op->xh, op->th, nullptr));
-    WD_CUDA(launch_xmy_norm(op->g, op->rh, op->bh, op->axh, r0, op->stream));
+    WD_CUDA(launch_xmy_norm(op->hi_prec, op->g, op->rh, op->bh, op->axh, r0, op->stream));
     st.th_valid = true;
     st.dslash_hi += 2;
     st.launches += 3;
@@ -496,18 +520,18 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
     const bool mixed = op->prec != WD_F64;
 
     // Alg. schur: split b and the initial guess by parity, bhat_p = b_p + kappa H_pq b_q
-    WD_CUDA(launch_pack_full(WD_F64, g, op->hb[0], op->hb[1], b, op->stream));
+    WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));
     {
         double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
-        WD_CUDA(launch_pack_full(WD_F64, g, xe, xo, x, op->stream));
+        WD_CUDA(launch_pack_full(op->hi_prec, g, xe, xo, x, op->stream));
     }
     WD_TRY(dslash(op, true, st.p, 0, op->bh, op->hb[st.q], op->hb[st.p], op->kappa, nullptr));
     Reduction r1 = reduction(op, FIN_STORE1), r0 = reduction(op, FIN_STORE0),
               r2 = reduction(op, FIN_STORE2), r3 = reduction(op, FIN_STORE3);
-    WD_CUDA(launch_norm2(WD_F64, g, op->hb[st.q], r1, op->stream));
-    WD_CUDA(launch_norm2(WD_F64, g, op->hb[st.p], r0, op->stream));
-    WD_CUDA(launch_norm2(WD_F64, g, op->xh, r2, op->stream));
-    WD_CUDA(launch_norm2(WD_F64, g, op->bh, r3, op->stream));
+    WD_CUDA(launch_norm2(op->hi_prec, g, op->hb[st.q], r1, op->stream));
+    WD_CUDA(launch_norm2(op->hi_prec, g, op->hb[st.p], r0, op->stream));
+    WD_CUDA(launch_norm2(op->hi_prec, g, op->xh, r2, op->stream));
+    WD_CUDA(launch_norm2(op->hi_prec, g, op->bh, r3, op->stream));
     WD_TRY(read_scalars(op));
     const double nb2 = op->sc_host->scratch[0] + op->sc_host->scratch[1];
     st.nb = std::sqrt(nb2);
@@ -538,7 +562,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
         // inner system: r_lo = scale r_hi, x_lo = 0, p = 0, nz = +inf
         st.scale = (mixed && st.r_hi > 0) ? std::sqrt(n_real) / st.r_hi : 1.0;
         WD_TRY(set_consts(op, st.scale, 1.0 / st.scale, 1.0));
-        WD_CUDA(launch_convert_scaled(op->prec, op->rl, WD_F64, op->rh, g, op->dev_consts, 0,
+        WD_CUDA(launch_convert_scaled(op->prec, op->rl, op->hi_prec, op->rh, g, op->dev_consts, 0,
                                       op->stream));
         WD_CUDA(cudaMemsetAsync(op->xl, 0, op->lo_field_bytes(), op->stream));
         WD_CUDA(cudaMemsetAsync(op->pl, 0, op->lo_field_bytes(), op->stream));
@@ -580,7 +604,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
             const bool out_of_iters = iters >= maxiter;
             if (want_conv || want_ru || stalled || out_of_iters) {
                 // reliable update: fold x_lo into x_hi, recompute r_hi in FP64
-                WD_CUDA(launch_fold_x(op->prec, g, op->xh, op->xl, op->dev_consts + 1,
+                WD_CUDA(launch_fold_x(op->prec, op->hi_prec, g, op->xh, op->xl, op->dev_consts + 1,
                                       op->stream));
                 st.th_valid = false;
                 st.bytes += field_b(op, op->prec) * 2 + field_b(op, WD_F64) * 2;
@@ -595,7 +619,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
                 const double new_scale = mixed ? std::sqrt(n_real) / st.r_hi : 1.0;
                 const double ratio = new_scale / st.scale;
                 WD_TRY(set_consts(op, new_scale, 1.0 / new_scale, ratio));
-                WD_CUDA(launch_convert_scaled(op->prec, op->rl, WD_F64, op->rh, g,
+                WD_CUDA(launch_convert_scaled(op->prec, op->rl, op->hi_prec, op->rh, g,
                                               op->dev_consts, 0, op->stream));
                 if (stalled) {
                     // restart: p = 0 and nz = +inf make the next direction z itself
@@ -640,19 +664,19 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
     // FP64 residual when x_p has not changed since), then the FP64 true
     // residual of the full system: r_p = b_p - (x_p - kappa H_pq x_q), r_q likewise.
     if (st.th_valid) {
-        WD_CUDA(launch_xpay_f64(g, op->xq, op->hb[st.q], op->kappa, op->th, op->stream));
+        WD_CUDA(launch_xpay_hi(op->hi_prec, g, op->xq, op->hb[st.q], op->kappa, op->th, op->stream));
         st.bytes += 3 * field_b(op, WD_F64);
         st.dslash_hi -= 1;
     } else {
         WD_TRY(dslash(op, true, st.q, 0, op->xq, op->xh, op->hb[st.q], op->kappa, nullptr));
     }
     WD_TRY(dslash(op, true, st.p, 0, op->axh, op->xq, op->xh, -op->kappa, nullptr));
-    WD_CUDA(launch_xmy_norm(g, op->rh, op->hb[st.p], op->axh, r0, op->stream));
+    WD_CUDA(launch_xmy_norm(op->hi_prec, g, op->rh, op->hb[st.p], op->axh, r0, op->stream));
     WD_TRY(dslash(op, true, st.q, 0, op->axh, op->xh, op->xq, -op->kappa, nullptr));
-    WD_CUDA(launch_xmy_norm(g, op->th, op->hb[st.q], op->axh, r1, op->stream));
+    WD_CUDA(launch_xmy_norm(op->hi_prec, g, op->th, op->hb[st.q], op->axh, r1, op->stream));
     {
         double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
-        WD_CUDA(launch_unpack_full(WD_F64, g, x, xe, xo, op->stream));
+        WD_CUDA(launch_unpack_full(op->hi_prec, g, x, xe, xo, op->stream));
     }
     WD_TRY(read_scalars(op));
     st.dslash_hi += 3;

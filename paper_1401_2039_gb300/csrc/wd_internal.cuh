@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "../../include/wd.h"
+#include "df64.cuh"
 
 namespace wd {
 
@@ -30,7 +31,13 @@ template <> struct Prec<WD_F32> { using S = float;         using R = float;  };
 template <> struct Prec<WD_F16> { using S = __half;        using R = float;  };
 template <> struct Prec<WD_BF16> { using S = __nv_bfloat16; using R = float; };
 
-inline size_t prec_bytes(int p) { return p == WD_F64 ? 8 : p == WD_F32 ? 4 : 2; }
+// Internal precision code of double-float fields (FP64-sized, FP32 pipes).
+constexpr int WD_DF64 = 4;
+template <> struct Prec<WD_DF64> { using S = df64; using R = df64; };
+
+inline size_t prec_bytes(int p) {
+    return (p == WD_F64 || p == WD_DF64) ? 8 : p == WD_F32 ? 4 : 2;
+}
 
 // Bytes of one field of Vh records of nreal reals in precision p.
 inline size_t field_bytes(int p, long stride, int nreal) {
@@ -156,6 +163,51 @@ template <typename S> struct WordsViaFloat {
 template <> struct Words<float, double> : WordsViaFloat<float> {};
 template <> struct Words<__half, double> : WordsViaFloat<__half> {};
 template <> struct Words<__nv_bfloat16, double> : WordsViaFloat<__nv_bfloat16> {};
+
+// Double-float storage: word pairs (hi, lo).
+template <> struct Words<df64, df64> {
+    __device__ static void unpack(const uint32_t *w, df64 *r, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) r[i] = df64(__uint_as_float(w[2 * i]), __uint_as_float(w[2 * i + 1]));
+    }
+    __device__ static void pack(const df64 *r, uint32_t *w, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            w[2 * i] = __float_as_uint(r[i].hi);
+            w[2 * i + 1] = __float_as_uint(r[i].lo);
+        }
+    }
+};
+// ... from / to FP64 registers (layout conversions at the boundary)
+template <> struct Words<df64, double> {
+    __device__ static void unpack(const uint32_t *w, double *r, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i)
+            r[i] = (double)__uint_as_float(w[2 * i]) + (double)__uint_as_float(w[2 * i + 1]);
+    }
+    __device__ static void pack(const double *r, uint32_t *w, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const float h = __double2float_rn(r[i]);
+            w[2 * i] = __float_as_uint(h);
+            w[2 * i + 1] = __float_as_uint(__double2float_rn(r[i] - (double)h));
+        }
+    }
+};
+// ... to FP32 registers (the low-precision copy of a residual)
+template <> struct Words<df64, float> {
+    __device__ static void unpack(const uint32_t *w, float *r, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) r[i] = __uint_as_float(w[2 * i]) + __uint_as_float(w[2 * i + 1]);
+    }
+    __device__ static void pack(const float *r, uint32_t *w, int n) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            w[2 * i] = __float_as_uint(r[i]);
+            w[2 * i + 1] = 0u;
+        }
+    }
+};
 
 // A record of N reals of storage type S in the SoA layout described above.
 template <typename S, int N> struct Rec {
@@ -407,14 +459,15 @@ cudaError_t launch_cg_update_p(int prec, const Geom &g, void *p, const void *z,
                                const SolverScalars *sc, cudaStream_t s);
 cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction &red,
                          cudaStream_t s);
-cudaError_t launch_xmy_norm(const Geom &g, double *out, const double *x, const double *y,
+cudaError_t launch_xmy_norm(int prec, const Geom &g, void *out, const void *x, const void *y,
                             const Reduction &red, cudaStream_t s);
-cudaError_t launch_xpay_f64(const Geom &g, double *out, const double *y, double a,
-                            const double *x, cudaStream_t s);
+cudaError_t launch_xpay_hi(int prec, const Geom &g, void *out, const void *y, double a,
+                           const void *x, cudaStream_t s);
+cudaError_t launch_f64_df64(void *buf, long n_reals, int to_df, cudaStream_t s);
 cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const void *in,
                                   const Geom &g, const double *scale_dev, double scale_host,
                                   cudaStream_t s);
-cudaError_t launch_fold_x(int prec_lo, const Geom &g, double *x_hi, void *x_lo,
+cudaError_t launch_fold_x(int prec_lo, int prec_hi, const Geom &g, void *x_hi, void *x_lo,
                           const double *inv_scale_dev, cudaStream_t s);
 cudaError_t launch_rescale_lo(int prec_lo, const Geom &g, void *p, SolverScalars *sc,
                               const double *ratio_dev, cudaStream_t s);

@@ -64,6 +64,7 @@ def load_library() -> ctypes.CDLL:
             "wd_dslash_resident": (i, [vp, i, i, i]),
             "wd_op_stream": (vp, [vp]),
             "wd_op_set_solver": (i, [vp, d, i]),
+            "wd_op_set_residual_precision": (i, [vp, i]),
             "wd_dslash_tuning": (i, [vp, i, dp, i, ip, ip, ip]),
             "wd_dslash_bytes": (d, [vp]),
             "wd_status_string": (ctypes.c_char_p, [i]),
@@ -213,6 +214,10 @@ class WilsonDirac:
     def set_solver(self, ru_delta: float = 0.1, stall_iters: int = 200):
         """Reliable-update threshold and stagnation restart of the mixed-precision solve."""
         _check(self.lib.wd_op_set_solver(self.handle, float(ru_delta), int(stall_iters)))
+
+    def set_residual_precision(self, mode: str = "df64"):
+        """Residual arithmetic of the reliable updates: "f64" or "df64" (double-float)."""
+        _check(self.lib.wd_op_set_residual_precision(self.handle, {"f64": 0, "df64": 1}[mode]))
 
     def dslash_tuning(self, hi: bool = False) -> dict:
         """The autotuner's choice for the hopping term and its per-candidate timings (us)."""

@@ -219,3 +219,33 @@ def test_resident_dslash_matches_canonical():
         got = host(op.field_store(1))
         assert rel(got, oracle.hop_eo(src, U, dims, PHASES["apbc"], 1)) < TOL[prec]
         assert op.dslash_bytes == syn.volume(dims) // 2 * (48 + 8 * recon) * (4 if prec == "f32" else 2)
+
+
+@pytest.mark.parametrize("prec,recon", [("f32", 18), ("f16", 12)])
+def test_residual_precision_modes(prec, recon):
+    """Reliable updates in native FP64 and in double-float reach the same
+    FP64 true residual; switching converts the FP64-side links in place."""
+    dims, kappa = (8, 8, 8, 8), 0.124
+    U, _ = fields(dims)
+    b = syn.gaussian_spinor(syn.volume(dims), 2)
+    op = make_op(dims, kappa, PHASES["apbc"], prec, recon, U)
+    xs = {}
+    for mode in ("f64", "df64", "f64"):
+        op.set_residual_precision(mode)
+        res = op.solve(cuda(b), tol=1e-10)
+        x = host(res.x)
+        r = np.linalg.norm(b - oracle.apply(x, U, dims, kappa, PHASES["apbc"])) / np.linalg.norm(b)
+        assert r <= 1.05e-10, (mode, r)
+        xs.setdefault(mode, x)
+    x_ref, _, _ = oracle.solve(b, U, dims, kappa, PHASES["apbc"], tol=1e-13)
+    for mode, x in xs.items():
+        assert rel(x, x_ref) < 1e-8, mode
+
+
+def test_f64_operator_rejects_double_float_residuals():
+    from paper_1401_2039_gb300 import WDError
+    dims = (4, 4, 4, 4)
+    U, _ = fields(dims)
+    op = make_op(dims, 0.12, PHASES["apbc"], "f64", 18, U)
+    with pytest.raises(WDError):
+        op.set_residual_precision("df64")
