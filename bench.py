@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--no-fp64-cg", action="store_true",
                     help="skip the plain FP64 CG comparison solve (reported as null)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched multi-source / uneven-lattice measurement")
     return ap.parse_args()
 
 
@@ -221,6 +223,57 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_measurement(prec: str, recon: int):
+    """Batched solves against the same systems solved one at a time:
+    12 point sources (every spin and colour) on 24^3 x 48, and 4 Gaussian
+    sources on each of 8^4, 12^3 x 24, 16^3 x 32 in one persistent batch."""
+    import torch
+    from paper_1401_2039_gb300 import WilsonBatch, WilsonDirac
+    ph = syn.workloads.APBC_T
+    out = {}
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3, r
+
+    dims = (24, 24, 24, 48)
+    op = WilsonDirac(dims, 0.12, ph, prec=prec, recon=recon)
+    op.set_gauge(torch.from_numpy(syn.su3_links(dims)).cuda())
+    B = torch.from_numpy(np.stack([syn.point_source(dims, 0, c, s)
+                                   for c in range(3) for s in range(4)])).cuda()
+    bt = WilsonBatch([op], [12])
+    tb, (_, _, infos) = timed(lambda: bt.solve([B], tol=1e-10))
+    ts, _ = timed(lambda: [op.solve(B[k].contiguous(), tol=1e-10) for k in range(12)], reps=1)
+    out["point_sources_24x24x24x48"] = {
+        "systems": 12, "batched_ms": tb, "sequential_ms": ts, "speedup": ts / tb,
+        "max_true_rel_resid": max(i["true_rel_resid"] for i in infos)}
+    bt.close()
+    op.close()
+    ops, Bs = [], []
+    for k, d in enumerate([(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32)]):
+        o = WilsonDirac(d, 0.12, ph, prec=prec, recon=recon)
+        o.set_gauge(torch.from_numpy(syn.su3_links(d, seed=1 + k)).cuda())
+        ops.append(o)
+        Bs.append(torch.from_numpy(np.stack([syn.gaussian_spinor(syn.volume(d), 2 + 10 * k + r)
+                                             for r in range(4)])).cuda())
+    bt = WilsonBatch(ops, [4, 4, 4])
+    tb, (_, _, infos) = timed(lambda: bt.solve(Bs, tol=1e-10))
+    ts, _ = timed(lambda: [o.solve(b[r].contiguous(), tol=1e-10) for o, b in zip(ops, Bs)
+                           for r in range(4)], reps=1)
+    out["uneven_8^4_12^3x24_16^3x32_x4"] = {
+        "systems": 12, "batched_ms": tb, "sequential_ms": ts, "speedup": ts / tb,
+        "max_true_rel_resid": max(i["true_rel_resid"] for i in infos)}
+    bt.close()
+    for o in ops:
+        o.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 def main():
     args = parse_args()
@@ -340,6 +393,11 @@ def main():
     e2e_value = e_bytes / e2e_s / 1e9
     spinor_bytes = w.volume * 12 * 16
 
+    # ---- batched solves (the multi-source and uneven-lattice workloads)
+    batch = None
+    if rank == 0 and not args.no_batch and w.prec in ("f32", "f16"):
+        batch = batch_measurement(w.prec, w.recon)
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -373,6 +431,8 @@ def main():
                     "d2h_bytes_per_step": spinor_bytes, "ms_per_step": e2e_s / n_e2e * 1e3},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
+            "residual_arithmetic": "double-float (2 x FP32)" if w.prec != "f64" else "f64",
+            "batch": batch,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -1,0 +1,432 @@
+// Learned preconditioner: a linear, gauge-equivariant parallel-transport
+// convolution (PTC) network (Lehner & Wettig, arXiv:2302.05419).  Not in the
+// paper; it serves as the right preconditioner of the flexible GCR solve.
+//
+// Layer l maps C_in channels of spinor fields to C_out channels:
+//   out_c'(x) = sum_c sum_{k=0..8} W[c', c, k] (T_k in_c)(x)
+// W[c', c, k] complex 4x4 (spin), T_0 = 1, T_{1+mu} psi(x) = U_mu(x) phi psi(x+mu),
+// T_{5+mu} psi(x) = U_mu(x-mu)^dag phi^* psi(x-mu) (phases on wrapping hops).
+//
+// GB300 mapping.  Rows m = (site x, colour a), M = 3V.  A layer is
+//   1. gather   A[m][(part, c, k, s)] = Re/Im (T_k in_c)(x)[a][s]  (BF16,
+//      K = 2 * C_in * 36 columns, padded to a multiple of 64),
+//   2. GEMM     F_out[m][(part', c', s')] = sum A[m][.] B[(part', c', s')][.]
+//      on the tensor cores (tcgen05, FP32 accumulation), with the complex
+//      weights laid out as the real block matrix [[Wr, -Wi], [Wi, Wr]],
+// and the FP32 output rows F[m] = (Re in_c'(x)[a][s'], then Im) are directly
+// the input rows of the next layer's gather.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tc_gemm.cuh"
+#include "wd_internal.cuh"
+
+namespace wd {
+
+constexpr int PTC_NK = 9;
+constexpr int PTC_MAX_LAYERS = 8;
+constexpr int PTC_BLOCK = 128;
+
+inline long pad_to(long v, long m) { return (v + m - 1) / m * m; }
+
+// canonical complex128 [V][3][4] -> F rows (x, a): [Re s0..3, Im s0..3], row stride ld
+__global__ void k_ptc_in(long V, const double2 *__restrict__ r, float *__restrict__ F, int ld,
+                         float scale) {
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;   // (x, a)
+    if (i >= 3 * V) return;
+    float *row = F + i * ld;
+    for (int s = 0; s < 4; ++s) {
+        const double2 v = r[i * 4 + s];
+        row[s] = (float)v.x * scale;
+        row[4 + s] = (float)v.y * scale;
+    }
+}
+
+// F rows (x, a) [Re s0..3, Im s0..3] -> canonical complex128, times scale
+__global__ void k_ptc_out(long V, const float *__restrict__ F, int ld, double2 *__restrict__ y,
+                          double scale) {
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i >= 3 * V) return;
+    const float *row = F + i * ld;
+    for (int s = 0; s < 4; ++s) y[i * 4 + s] = make_double2(row[s] * scale, row[4 + s] * scale);
+}
+
+struct PtcGeom {
+    int L[4];
+    long V;
+    float ph[8];
+};
+
+__device__ __forceinline__ void lex_coords(const PtcGeom &g, long x, int c[4]) {
+    unsigned r = (unsigned)x;
+    for (int m = 0; m < 3; ++m) {
+        const unsigned q = r / (unsigned)g.L[m];
+        c[m] = (int)(r - q * (unsigned)g.L[m]);
+        r = q;
+    }
+    c[3] = (int)r;
+}
+
+__device__ __forceinline__ long lex_of(const PtcGeom &g, const int c[4]) {
+    return (((long)c[3] * g.L[2] + c[2]) * g.L[1] + c[1]) * g.L[0] + c[0];
+}
+
+// Neighbour x +- mu with its wrap flag.
+__device__ __forceinline__ long ptc_neighbour(const PtcGeom &g, const int c[4], int mu, int dir,
+                                              bool &wrap) {
+    int n[4] = {c[0], c[1], c[2], c[3]};
+    n[mu] += dir;
+    wrap = false;
+    if (n[mu] == g.L[mu]) { n[mu] = 0; wrap = true; }
+    if (n[mu] < 0) { n[mu] = g.L[mu] - 1; wrap = true; }
+    return lex_of(g, n);
+}
+
+// Gather: one thread per (site x, input channel c).  F_in row stride ldf holds
+// [Re (c, s)][Im (c, s)] blocks of 4*C_in values; A row stride lda.
+__global__ void __launch_bounds__(PTC_BLOCK)
+k_ptc_gather(PtcGeom g, int cin, const float *__restrict__ F, int ldf,
+             const float2 *__restrict__ U, __nv_bfloat16 *__restrict__ A, int lda) {
+    const long t = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (t >= g.V * cin) return;
+    const long x = t / cin;
+    const int c = (int)(t - x * cin);
+    int co[4];
+    lex_coords(g, x, co);
+    const int K = cin * 36;
+    for (int k = 0; k < PTC_NK; ++k) {
+        float2 v[3][4];
+        if (k == 0) {
+            for (int a = 0; a < 3; ++a)
+                for (int s = 0; s < 4; ++s) {
+                    const float *row = F + (x * 3 + a) * (long)ldf;
+                    v[a][s] = make_float2(row[c * 4 + s], row[4 * cin + c * 4 + s]);
+                }
+        } else {
+            const int mu = (k - 1) & 3;
+            const bool fwd = k <= 4;
+            bool wrap;
+            const long xn = ptc_neighbour(g, co, mu, fwd ? 1 : -1, wrap);
+            float2 p[3][4];
+            for (int b = 0; b < 3; ++b)
+                for (int s = 0; s < 4; ++s) {
+                    const float *row = F + (xn * 3 + b) * (long)ldf;
+                    p[b][s] = make_float2(row[c * 4 + s], row[4 * cin + c * 4 + s]);
+                }
+            const float2 *Ul = U + ((fwd ? x : xn) * 4 + mu) * 9;
+            float pr = 1.f, pi = 0.f;
+            if (wrap) { pr = g.ph[2 * mu]; pi = fwd ? g.ph[2 * mu + 1] : -g.ph[2 * mu + 1]; }
+            for (int a = 0; a < 3; ++a)
+                for (int s = 0; s < 4; ++s) {
+                    float re = 0.f, im = 0.f;
+                    for (int b = 0; b < 3; ++b) {
+                        // forward: U[a][b]; backward: conj(U[b][a])
+                        const float2 u = fwd ? Ul[3 * a + b] : Ul[3 * b + a];
+                        const float ui = fwd ? u.y : -u.y;
+                        re += u.x * p[b][s].x - ui * p[b][s].y;
+                        im += u.x * p[b][s].y + ui * p[b][s].x;
+                    }
+                    v[a][s] = make_float2(re * pr - im * pi, re * pi + im * pr);
+                }
+        }
+        for (int a = 0; a < 3; ++a) {
+            __nv_bfloat16 *row = A + (x * 3 + a) * (long)lda + (c * PTC_NK + k) * 4;
+            for (int s = 0; s < 4; ++s) {
+                row[s] = __float2bfloat16_rn(v[a][s].x);
+                row[K + s] = __float2bfloat16_rn(v[a][s].y);
+            }
+        }
+    }
+}
+
+// Real block form of the complex weights: B[(p', c', s')][(p, c, k, s)], row
+// stride ldb, from W (complex64 as float2) [cout][cin][9][4][4].
+__global__ void k_ptc_weights(int cout, int cin, const float2 *__restrict__ W,
+                              __nv_bfloat16 *__restrict__ B, int ldb) {
+    const int K = cin * 36, N = cout * 4;
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i >= (long)N * K) return;
+    const int n = (int)(i / K), kk = (int)(i - (long)n * K);
+    const int cp = n >> 2, sp = n & 3;
+    const int c = kk / 36, k = (kk % 36) >> 2, s = kk & 3;
+    const float2 w = W[((((long)cp * cin + c) * PTC_NK + k) * 4 + sp) * 4 + s];
+    B[(long)n * ldb + kk] = __float2bfloat16_rn(w.x);              // Re out <- Re in:  Wr
+    B[(long)n * ldb + K + kk] = __float2bfloat16_rn(-w.y);         // Re out <- Im in: -Wi
+    B[(long)(N + n) * ldb + kk] = __float2bfloat16_rn(w.y);        // Im out <- Re in:  Wi
+    B[(long)(N + n) * ldb + K + kk] = __float2bfloat16_rn(w.x);    // Im out <- Im in:  Wr
+}
+
+__global__ void k_c128_to_c64(long n, const double2 *in, float2 *out) {
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void k_c64_to_c128(long n, const float2 *in, double2 *out) {
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i < n) out[i] = make_double2(in[i].x, in[i].y);
+}
+
+// |v|^2 of a canonical complex128 field, one block-level partial per block
+// (deterministic final sum on the host side of the launch helper).
+__global__ void k_norm2_c128(long n, const double2 *v, double *partials) {
+    __shared__ double ws[PTC_BLOCK / 32];
+    double s = 0.0;
+    for (long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x; i < n; i += (long)gridDim.x * PTC_BLOCK)
+        s += v[i].x * v[i].x + v[i].y * v[i].y;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < PTC_BLOCK / 32; ++w) t += ws[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+}  // namespace wd
+
+// =================================================================== host side
+using namespace wd;
+
+static thread_local std::string g_ptc_error;
+static int ptc_fail(int code, const std::string &m) {
+    g_ptc_error = m;
+    return code;
+}
+#define PTC_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ptc_fail(e_ == cudaErrorMemoryAllocation ? WD_ERR_NOMEM : WD_ERR_CUDA,   \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+#define PTC_TRY(call)                                                                       \
+    do {                                                                                    \
+        int rc_ = (call);                                                                   \
+        if (rc_ != WD_OK) return rc_;                                                       \
+    } while (0)
+
+struct wd_ptc {
+    PtcGeom g{};
+    int nl = 0;
+    int ch[PTC_MAX_LAYERS + 1] = {};
+    long M = 0, Mp = 0;                       // rows 3V, padded to 128
+    int Kp[PTC_MAX_LAYERS] = {};              // gathered columns, padded to 64
+    int Np[PTC_MAX_LAYERS] = {};              // output columns, padded to 16
+    int ldF[PTC_MAX_LAYERS + 1] = {};         // activation row strides
+    float *F[PTC_MAX_LAYERS + 1] = {};        // activations, FP32
+    __nv_bfloat16 *A[PTC_MAX_LAYERS] = {};    // gathered operands, BF16
+    __nv_bfloat16 *B[PTC_MAX_LAYERS] = {};    // weight matrices, BF16
+    float2 *W[PTC_MAX_LAYERS] = {};           // complex weights (FP32 master copy)
+    long wcount[PTC_MAX_LAYERS] = {};
+    float2 *U = nullptr;                      // links, complex64 [V][4][3][3]
+    double *partials = nullptr;
+    double *partials_host = nullptr;
+    int *err = nullptr;
+    cudaStream_t stream = nullptr;
+    std::vector<void *> allocs;
+};
+
+static int ptc_alloc(wd_ptc *n, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return ptc_fail(WD_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    n->allocs.push_back(*p);
+    PTC_CUDA(cudaMemset(*p, 0, bytes));
+    return WD_OK;
+}
+
+static unsigned grid_for(long n) { return (unsigned)std::max<long>(1, (n + PTC_BLOCK - 1) / PTC_BLOCK); }
+
+// D = A * B^T on the tensor cores; N must be a multiple of 16 (tiles of 128 when possible).
+static int ptc_gemm(wd_ptc *n, const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, long M,
+                    int N, int K, int lda, int ldb, int ldd) {
+    if (M % TC_BM || K % TC_BK || N % 16)
+        return ptc_fail(WD_ERR_ARG, "GEMM shape not tile aligned");
+    if (N % 128 == 0) {
+        // 16 KB of dynamic shared memory on top of the tiles keeps at most four
+        // CTAs per SM, so their 4 x 128 TMEM columns fit the SM's 512
+        static bool attr_set = false;
+        if (!attr_set) {
+            PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<128>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 16384));
+            attr_set = true;
+        }
+        dim3 grid((unsigned)(M / TC_BM), (unsigned)(N / 128));
+        k_gemm_bf16_tc<128><<<grid, TC_THREADS, 16384, n->stream>>>(A, B, D, K, lda, ldb, ldd,
+                                                                     n->err);
+    } else {
+        dim3 grid((unsigned)(M / TC_BM), (unsigned)(N / 16));
+        k_gemm_bf16_tc<16><<<grid, TC_THREADS, 0, n->stream>>>(A, B, D, K, lda, ldb, ldd, n->err);
+    }
+    PTC_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+static int ptc_check_err(wd_ptc *n) {
+    int h = 0;
+    PTC_CUDA(cudaMemcpyAsync(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    PTC_CUDA(cudaStreamSynchronize(n->stream));
+    if (h) {
+        PTC_CUDA(cudaMemsetAsync(n->err, 0, sizeof(int), n->stream));
+        return ptc_fail(WD_ERR_TIMEOUT, "tensor-core GEMM gave up waiting for its MMAs");
+    }
+    return WD_OK;
+}
+
+// forward through every layer, activations left in F[0..nl]
+static int ptc_forward(wd_ptc *n, const double *r, double in_scale) {
+    const long V = n->g.V;
+    k_ptc_in<<<grid_for(3 * V), PTC_BLOCK, 0, n->stream>>>(V, (const double2 *)r, n->F[0],
+                                                            n->ldF[0], (float)in_scale);
+    PTC_CUDA(cudaGetLastError());
+    for (int l = 0; l < n->nl; ++l) {
+        const int cin = n->ch[l];
+        k_ptc_gather<<<grid_for(V * cin), PTC_BLOCK, 0, n->stream>>>(n->g, cin, n->F[l], n->ldF[l],
+                                                                      n->U, n->A[l], n->Kp[l]);
+        PTC_CUDA(cudaGetLastError());
+        PTC_TRY(ptc_gemm(n, n->A[l], n->B[l], n->F[l + 1], n->Mp, n->Np[l], n->Kp[l], n->Kp[l],
+                         n->Kp[l], n->ldF[l + 1]));
+    }
+    return WD_OK;
+}
+
+extern "C" {
+
+const char *wd_ptc_last_error(void) { return g_ptc_error.c_str(); }
+
+void wd_ptc_destroy(wd_ptc *n) {
+    if (!n) return;
+    if (n->stream) cudaStreamSynchronize(n->stream);
+    for (void *p : n->allocs) cudaFree(p);
+    if (n->partials_host) cudaFreeHost(n->partials_host);
+    if (n->stream) cudaStreamDestroy(n->stream);
+    delete n;
+}
+
+int wd_ptc_create(wd_ptc **out, const int dims[4], const double phase[8], int nlayers,
+                  const int *channels) {
+    if (!out || !dims || !phase || !channels) return ptc_fail(WD_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (nlayers < 1 || nlayers > PTC_MAX_LAYERS) return ptc_fail(WD_ERR_ARG, "1..8 layers");
+    long V = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (dims[m] < 2 || dims[m] % 2) return ptc_fail(WD_ERR_DIMS, "extents must be even, >= 2");
+        V *= dims[m];
+    }
+    if (channels[0] != 1 || channels[nlayers] != 1)
+        return ptc_fail(WD_ERR_ARG, "the network maps one spinor field to one");
+    for (int l = 0; l <= nlayers; ++l)
+        if (channels[l] < 1 || channels[l] > 32) return ptc_fail(WD_ERR_ARG, "1..32 channels");
+    wd_ptc *n = new wd_ptc();
+    for (int m = 0; m < 4; ++m) n->g.L[m] = dims[m];
+    n->g.V = V;
+    for (int i = 0; i < 8; ++i) n->g.ph[i] = (float)phase[i];
+    n->nl = nlayers;
+    for (int l = 0; l <= nlayers; ++l) n->ch[l] = channels[l];
+    n->M = 3 * V;
+    n->Mp = pad_to(n->M, TC_BM);
+    auto fail_free = [&](int rc) { std::string m = g_ptc_error; wd_ptc_destroy(n); g_ptc_error = m; return rc; };
+    if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail_free(ptc_fail(WD_ERR_CUDA, "stream creation failed"));
+    n->ldF[0] = 8;
+    for (int l = 0; l < nlayers; ++l) {
+        n->Kp[l] = (int)pad_to(2L * channels[l] * 36, TC_BK);
+        n->Np[l] = (int)pad_to(2L * channels[l + 1] * 4, 16);
+        n->ldF[l + 1] = n->Np[l];
+        n->wcount[l] = (long)channels[l + 1] * channels[l] * PTC_NK * 16;
+    }
+    int rc = WD_OK;
+    for (int l = 0; l <= nlayers && rc == WD_OK; ++l)
+        rc = ptc_alloc(n, (void **)&n->F[l], sizeof(float) * n->Mp * n->ldF[l]);
+    for (int l = 0; l < nlayers && rc == WD_OK; ++l) {
+        rc = ptc_alloc(n, (void **)&n->A[l], sizeof(__nv_bfloat16) * n->Mp * n->Kp[l]);
+        if (rc == WD_OK) rc = ptc_alloc(n, (void **)&n->B[l], sizeof(__nv_bfloat16) * (long)n->Np[l] * n->Kp[l]);
+        if (rc == WD_OK) rc = ptc_alloc(n, (void **)&n->W[l], sizeof(float2) * n->wcount[l]);
+    }
+    if (rc == WD_OK) rc = ptc_alloc(n, (void **)&n->U, sizeof(float2) * V * 36);
+    if (rc == WD_OK) rc = ptc_alloc(n, (void **)&n->partials, sizeof(double) * 4096);
+    if (rc == WD_OK) rc = ptc_alloc(n, (void **)&n->err, sizeof(int) * 4);
+    if (rc == WD_OK && cudaMallocHost((void **)&n->partials_host, sizeof(double) * 4096) != cudaSuccess)
+        rc = ptc_fail(WD_ERR_NOMEM, "pinned host buffer");
+    if (rc != WD_OK) return fail_free(rc);
+    *out = n;
+    return WD_OK;
+}
+
+int wd_ptc_set_gauge(wd_ptc *n, const double *U) {
+    if (!n || !U) return ptc_fail(WD_ERR_ARG, "null argument");
+    const long cnt = n->g.V * 36;
+    k_c128_to_c64<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(cnt, (const double2 *)U, n->U);
+    PTC_CUDA(cudaGetLastError());
+    PTC_CUDA(cudaStreamSynchronize(n->stream));
+    return WD_OK;
+}
+
+static int ptc_rebuild_b(wd_ptc *n) {
+    for (int l = 0; l < n->nl; ++l) {
+        const long cnt = (long)n->ch[l + 1] * 4 * n->ch[l] * 36;
+        k_ptc_weights<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(n->ch[l + 1], n->ch[l], n->W[l],
+                                                                   n->B[l], n->Kp[l]);
+        PTC_CUDA(cudaGetLastError());
+    }
+    return WD_OK;
+}
+
+long wd_ptc_weight_count(const wd_ptc *n) {
+    if (!n) return 0;
+    long t = 0;
+    for (int l = 0; l < n->nl; ++l) t += n->wcount[l];
+    return t;
+}
+
+int wd_ptc_set_weights(wd_ptc *n, const double *W) {
+    if (!n || !W) return ptc_fail(WD_ERR_ARG, "null argument");
+    long off = 0;
+    for (int l = 0; l < n->nl; ++l) {
+        k_c128_to_c64<<<grid_for(n->wcount[l]), PTC_BLOCK, 0, n->stream>>>(
+            n->wcount[l], (const double2 *)W + off, n->W[l]);
+        off += n->wcount[l];
+    }
+    PTC_CUDA(cudaGetLastError());
+    PTC_TRY(ptc_rebuild_b(n));
+    PTC_CUDA(cudaStreamSynchronize(n->stream));
+    return WD_OK;
+}
+
+int wd_ptc_get_weights(wd_ptc *n, double *W) {
+    if (!n || !W) return ptc_fail(WD_ERR_ARG, "null argument");
+    long off = 0;
+    for (int l = 0; l < n->nl; ++l) {
+        k_c64_to_c128<<<grid_for(n->wcount[l]), PTC_BLOCK, 0, n->stream>>>(
+            n->wcount[l], n->W[l], (double2 *)W + off);
+        off += n->wcount[l];
+    }
+    PTC_CUDA(cudaGetLastError());
+    PTC_CUDA(cudaStreamSynchronize(n->stream));
+    return WD_OK;
+}
+
+int wd_ptc_apply(wd_ptc *n, double *y, const double *r) {
+    if (!n || !y || !r) return ptc_fail(WD_ERR_ARG, "null argument");
+    PTC_TRY(ptc_forward(n, r, 1.0));
+    k_ptc_out<<<grid_for(3 * n->g.V), PTC_BLOCK, 0, n->stream>>>(
+        n->g.V, n->F[n->nl], n->ldF[n->nl], (double2 *)y, 1.0);
+    PTC_CUDA(cudaGetLastError());
+    return ptc_check_err(n);
+}
+
+// D = A * B^T through the tensor-core GEMM, for tests of the GEMM alone:
+// A [M x K], B [N x K] BF16 row-major (device), D [M x N] FP32.
+int wd_tc_gemm_bf16(wd_ptc *n, const void *A, const void *B, float *D, long M, int N, int K) {
+    if (!n || !A || !B || !D) return ptc_fail(WD_ERR_ARG, "null argument");
+    PTC_TRY(ptc_gemm(n, (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, D, M, N, K, K, K, N));
+    return ptc_check_err(n);
+}
+
+}  // extern "C"

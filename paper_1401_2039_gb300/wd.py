@@ -339,3 +339,102 @@ def _setup_batch_signatures(lib):
         f.restype = res
         f.argtypes = args
     _batch_sigs_done = True
+
+
+class PtcNet:
+    """Parallel-transport convolution network (handle on a wd_ptc): the learned
+    right preconditioner.  Weights are one flat complex128 vector, layers in
+    order, each [C_out, C_in, 9, 4, 4]."""
+
+    def __init__(self, dims, phase=(1, 1, 1, -1), channels=(1, 16, 16, 16, 1)):
+        if not torch.cuda.is_available():
+            raise RuntimeError("PtcNet needs a CUDA device; there is no CPU fallback")
+        self.lib = load_library()
+        _setup_ptc_signatures(self.lib)
+        self.dims = tuple(int(d) for d in dims)
+        self.V = 1
+        for d in self.dims:
+            self.V *= d
+        self.channels = tuple(int(c) for c in channels)
+        handle = ctypes.c_void_p()
+        ch = (ctypes.c_int * len(self.channels))(*self.channels)
+        rc = self.lib.wd_ptc_create(ctypes.byref(handle), (ctypes.c_int * 4)(*self.dims),
+                                    phases_array(phase), len(self.channels) - 1, ch)
+        if rc != WD_OK:
+            raise WDError(rc, self.lib.wd_ptc_last_error().decode())
+        self.handle = handle
+        self.n_weights = int(self.lib.wd_ptc_weight_count(self.handle))
+
+    def _chk(self, rc):
+        if rc != WD_OK:
+            raise WDError(rc, self.lib.wd_ptc_last_error().decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.wd_ptc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_gauge(self, U: torch.Tensor):
+        _dev(U, (self.V, 4, 3, 3), "U")
+        self._chk(self.lib.wd_ptc_set_gauge(self.handle, ctypes.c_void_p(U.data_ptr())))
+
+    def set_weights(self, W: torch.Tensor):
+        _dev(W, (self.n_weights,), "W")
+        self._chk(self.lib.wd_ptc_set_weights(self.handle, ctypes.c_void_p(W.data_ptr())))
+
+    def get_weights(self) -> torch.Tensor:
+        W = torch.empty(self.n_weights, dtype=torch.complex128, device="cuda")
+        self._chk(self.lib.wd_ptc_get_weights(self.handle, ctypes.c_void_p(W.data_ptr())))
+        return W
+
+    def apply(self, r: torch.Tensor, out=None) -> torch.Tensor:
+        _dev(r, (self.V, 3, 4), "r")
+        y = torch.empty_like(r) if out is None else out
+        torch.cuda.synchronize()
+        self._chk(self.lib.wd_ptc_apply(self.handle, ctypes.c_void_p(y.data_ptr()),
+                                        ctypes.c_void_p(r.data_ptr())))
+        return y
+
+    def gemm(self, A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+        """D = A B^T on the tensor-core GEMM (bf16 in, fp32 out), for tests."""
+        M, K = A.shape
+        N = B.shape[0]
+        D = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        self._chk(self.lib.wd_tc_gemm_bf16(self.handle, ctypes.c_void_p(A.data_ptr()),
+                                           ctypes.c_void_p(B.data_ptr()),
+                                           ctypes.c_void_p(D.data_ptr()), M, N, K))
+        return D
+
+
+_ptc_sigs_done = False
+
+
+def _setup_ptc_signatures(lib):
+    global _ptc_sigs_done
+    if _ptc_sigs_done:
+        return
+    vp, i, d, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+    sig = {
+        "wd_ptc_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(d), i,
+                              ctypes.POINTER(i)]),
+        "wd_ptc_destroy": (None, [vp]),
+        "wd_ptc_set_gauge": (i, [vp, vp]),
+        "wd_ptc_set_weights": (i, [vp, vp]),
+        "wd_ptc_get_weights": (i, [vp, vp]),
+        "wd_ptc_weight_count": (l, [vp]),
+        "wd_ptc_apply": (i, [vp, vp, vp]),
+        "wd_tc_gemm_bf16": (i, [vp, vp, vp, vp, l, i, i]),
+        "wd_ptc_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _ptc_sigs_done = True
