@@ -20,6 +20,8 @@
 #include <string>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "tc_gemm.cuh"
 #include "wd_internal.cuh"
 
@@ -185,6 +187,148 @@ __global__ void k_norm2_c128(long n, const double2 *v, double *partials) {
     }
 }
 
+
+// ------------------------------------------------------------------ backward
+// Loss gradient at the network output: G = 2 (y - e) / |e|^2 in the activation
+// layout (FP32, and a BF16 copy with row stride ldb), |y - e|^2 per block.
+__global__ void k_ptc_loss_grad(long V, const float *__restrict__ F, int ld,
+                                const double2 *__restrict__ e, double inv_ne, float *__restrict__ G,
+                                __nv_bfloat16 *__restrict__ Gb, int ldb, double *partials) {
+    __shared__ double ws[PTC_BLOCK / 32];
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;   // (x, a)
+    double d2 = 0.0;
+    if (i < 3 * V) {
+        const float *row = F + i * ld;
+        for (int s = 0; s < 4; ++s) {
+            const double2 ev = e[i * 4 + s];
+            const double dr = row[s] - ev.x, di = row[4 + s] - ev.y;
+            d2 += dr * dr + di * di;
+            const float gr = (float)(2.0 * dr * inv_ne), gi = (float)(2.0 * di * inv_ne);
+            G[i * ld + s] = gr;
+            G[i * ld + 4 + s] = gi;
+            Gb[i * ldb + s] = __float2bfloat16_rn(gr);
+            Gb[i * ldb + 4 + s] = __float2bfloat16_rn(gi);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = d2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < PTC_BLOCK / 32; ++w) t += ws[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// Adjoint of the gather: dF_c(x) = sum_k (T_k^dag dA_{c,k})(x) with
+// T_{1+mu}^dag = T_{5+mu} and T_{5+mu}^dag = T_{1+mu}; dA rows (y, a) hold
+// [Re (c, k, s)][Im (c, k, s)].  One thread per (site x, channel c).
+__global__ void __launch_bounds__(PTC_BLOCK)
+k_ptc_scatter(PtcGeom g, int cin, const float *__restrict__ dA, int lda,
+              const float2 *__restrict__ U, float *__restrict__ dF, int ldf,
+              __nv_bfloat16 *__restrict__ dFb, int ldfb) {
+    const long t = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (t >= g.V * cin) return;
+    const long x = t / cin;
+    const int c = (int)(t - x * cin);
+    int co[4];
+    lex_coords(g, x, co);
+    const int K = cin * 36;
+    float2 acc[3][4];
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 4; ++s) {
+            const float *row = dA + (x * 3 + a) * (long)lda + (c * PTC_NK) * 4;
+            acc[a][s] = make_float2(row[s], row[K + s]);
+        }
+    for (int k = 1; k < PTC_NK; ++k) {
+        const int mu = (k - 1) & 3;
+        // dA_{c,k} is transported by T_k^dag: backward hop for k <= 4, forward otherwise
+        const bool fwd = k > 4;
+        bool wrap;
+        const long xn = ptc_neighbour(g, co, mu, fwd ? 1 : -1, wrap);
+        const float2 *Ul = U + ((fwd ? x : xn) * 4 + mu) * 9;
+        float pr = 1.f, pi = 0.f;
+        if (wrap) { pr = g.ph[2 * mu]; pi = fwd ? g.ph[2 * mu + 1] : -g.ph[2 * mu + 1]; }
+        float2 p[3][4];
+        for (int b = 0; b < 3; ++b)
+            for (int s = 0; s < 4; ++s) {
+                const float *row = dA + (xn * 3 + b) * (long)lda + (c * PTC_NK + k) * 4;
+                p[b][s] = make_float2(row[s], row[K + s]);
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int s = 0; s < 4; ++s) {
+                float re = 0.f, im = 0.f;
+                for (int b = 0; b < 3; ++b) {
+                    const float2 u = fwd ? Ul[3 * a + b] : Ul[3 * b + a];
+                    const float ui = fwd ? u.y : -u.y;
+                    re += u.x * p[b][s].x - ui * p[b][s].y;
+                    im += u.x * p[b][s].y + ui * p[b][s].x;
+                }
+                acc[a][s].x += re * pr - im * pi;
+                acc[a][s].y += re * pi + im * pr;
+            }
+    }
+    for (int a = 0; a < 3; ++a) {
+        float *row = dF + (x * 3 + a) * (long)ldf;
+        __nv_bfloat16 *rb = dFb + (x * 3 + a) * (long)ldfb;
+        for (int s = 0; s < 4; ++s) {
+            row[c * 4 + s] = acc[a][s].x;
+            row[4 * cin + c * 4 + s] = acc[a][s].y;
+            rb[c * 4 + s] = __float2bfloat16_rn(acc[a][s].x);
+            rb[4 * cin + c * 4 + s] = __float2bfloat16_rn(acc[a][s].y);
+        }
+    }
+}
+
+// Transposed real block weights Bt[(p, c, k, s)][(p', c', s')], row stride ldbt.
+__global__ void k_ptc_weights_t(int cout, int cin, const float2 *__restrict__ W,
+                                __nv_bfloat16 *__restrict__ Bt, int ldbt) {
+    const int K = cin * 36, N = cout * 4;
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i >= (long)N * K) return;
+    const int n = (int)(i / K), kk = (int)(i - (long)n * K);
+    const int cp = n >> 2, sp = n & 3;
+    const int c = kk / 36, k = (kk % 36) >> 2, s = kk & 3;
+    const float2 w = W[((((long)cp * cin + c) * PTC_NK + k) * 4 + sp) * 4 + s];
+    Bt[(long)kk * ldbt + n] = __float2bfloat16_rn(w.x);
+    Bt[(long)(K + kk) * ldbt + n] = __float2bfloat16_rn(-w.y);
+    Bt[(long)kk * ldbt + N + n] = __float2bfloat16_rn(w.y);
+    Bt[(long)(K + kk) * ldbt + N + n] = __float2bfloat16_rn(w.x);
+}
+
+// Packed complex weight gradient from the real block gradient dB[n'][k']
+// (row stride ldb): g = dL/dRe W + i dL/dIm W.
+__global__ void k_ptc_wgrad(int cout, int cin, const float *__restrict__ dB, int ldb,
+                            double2 *__restrict__ gW) {
+    const int K = cin * 36, N = cout * 4;
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i >= (long)N * K) return;
+    const int n = (int)(i / K), kk = (int)(i - (long)n * K);
+    const int cp = n >> 2, sp = n & 3;
+    const int c = kk / 36, k = (kk % 36) >> 2, s = kk & 3;
+    const double gr = (double)dB[(long)n * ldb + kk] + dB[(long)(N + n) * ldb + K + kk];
+    const double gi = -(double)dB[(long)n * ldb + K + kk] + dB[(long)(N + n) * ldb + kk];
+    gW[((((long)cp * cin + c) * PTC_NK + k) * 4 + sp) * 4 + s] = make_double2(gr, gi);
+}
+
+// Adam on the real and imaginary parts of the weights.
+__global__ void k_ptc_adam(long n, float2 *W, const double2 *g, float2 *m, float2 *v, float lr,
+                           float b1, float b2, float eps, float c1, float c2) {
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i >= n) return;
+    const float gr = (float)g[i].x, gi = (float)g[i].y;
+    float2 mm = m[i], vv = v[i], w = W[i];
+    mm.x = b1 * mm.x + (1.f - b1) * gr;
+    mm.y = b1 * mm.y + (1.f - b1) * gi;
+    vv.x = b2 * vv.x + (1.f - b2) * gr * gr;
+    vv.y = b2 * vv.y + (1.f - b2) * gi * gi;
+    w.x -= lr * (mm.x / c1) / (sqrtf(vv.x / c2) + eps);
+    w.y -= lr * (mm.y / c1) / (sqrtf(vv.y / c2) + eps);
+    m[i] = mm;
+    v[i] = vv;
+    W[i] = w;
+}
+
 }  // namespace wd
 
 // =================================================================== host side
@@ -226,6 +370,18 @@ struct wd_ptc {
     double *partials_host = nullptr;
     int *err = nullptr;
     cudaStream_t stream = nullptr;
+    // training
+    bool train_ready = false;
+    int Rp[PTC_MAX_LAYERS + 1] = {};          // BF16 gradient row strides (multiple of 64)
+    float *dF[PTC_MAX_LAYERS + 1] = {};       // activation gradients, FP32
+    __nv_bfloat16 *dFb[PTC_MAX_LAYERS + 1] = {};
+    float *dA = nullptr;                      // gathered-operand gradient, FP32
+    __nv_bfloat16 *Bt[PTC_MAX_LAYERS] = {};   // transposed weight matrices
+    float *dB[PTC_MAX_LAYERS] = {};           // real block weight gradients
+    double2 *gW = nullptr;                    // packed complex gradient, all layers
+    float2 *adam_m = nullptr, *adam_v = nullptr;
+    long adam_t = 0;
+    cublasHandle_t blas = nullptr;
     std::vector<void *> allocs;
 };
 
@@ -305,6 +461,7 @@ void wd_ptc_destroy(wd_ptc *n) {
     if (n->stream) cudaStreamSynchronize(n->stream);
     for (void *p : n->allocs) cudaFree(p);
     if (n->partials_host) cudaFreeHost(n->partials_host);
+    if (n->blas) cublasDestroy(n->blas);
     if (n->stream) cudaStreamDestroy(n->stream);
     delete n;
 }
@@ -373,8 +530,105 @@ static int ptc_rebuild_b(wd_ptc *n) {
         const long cnt = (long)n->ch[l + 1] * 4 * n->ch[l] * 36;
         k_ptc_weights<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(n->ch[l + 1], n->ch[l], n->W[l],
                                                                    n->B[l], n->Kp[l]);
+        if (n->train_ready)
+            k_ptc_weights_t<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(
+                n->ch[l + 1], n->ch[l], n->W[l], n->Bt[l], n->Rp[l + 1]);
         PTC_CUDA(cudaGetLastError());
     }
+    return WD_OK;
+}
+
+// Training buffers, allocated on the first gradient request.
+static int ptc_train_setup(wd_ptc *n) {
+    if (n->train_ready) return WD_OK;
+    int kmax = 0;
+    long wtot = 0;
+    for (int l = 0; l <= n->nl; ++l) {
+        n->Rp[l] = (int)pad_to(n->ldF[l], TC_BK);
+        PTC_TRY(ptc_alloc(n, (void **)&n->dF[l], sizeof(float) * n->Mp * n->ldF[l]));
+        PTC_TRY(ptc_alloc(n, (void **)&n->dFb[l], sizeof(__nv_bfloat16) * n->Mp * n->Rp[l]));
+    }
+    for (int l = 0; l < n->nl; ++l) {
+        kmax = std::max(kmax, n->Kp[l]);
+        wtot += n->wcount[l];
+        PTC_TRY(ptc_alloc(n, (void **)&n->Bt[l], sizeof(__nv_bfloat16) * (long)n->Kp[l] * n->Rp[l + 1]));
+        PTC_TRY(ptc_alloc(n, (void **)&n->dB[l], sizeof(float) * (long)n->Np[l] * n->Kp[l]));
+    }
+    PTC_TRY(ptc_alloc(n, (void **)&n->dA, sizeof(float) * n->Mp * kmax));
+    PTC_TRY(ptc_alloc(n, (void **)&n->gW, sizeof(double2) * wtot));
+    PTC_TRY(ptc_alloc(n, (void **)&n->adam_m, sizeof(float2) * wtot));
+    PTC_TRY(ptc_alloc(n, (void **)&n->adam_v, sizeof(float2) * wtot));
+    if (cublasCreate(&n->blas) != CUBLAS_STATUS_SUCCESS)
+        return ptc_fail(WD_ERR_CUDA, "cublasCreate failed");
+    if (cublasSetStream(n->blas, n->stream) != CUBLAS_STATUS_SUCCESS)
+        return ptc_fail(WD_ERR_CUDA, "cublasSetStream failed");
+    n->train_ready = true;
+    return ptc_rebuild_b(n);
+}
+
+static double ptc_sum_partials(wd_ptc *n, int nb) {
+    double t = 0.0;
+    for (int i = 0; i < nb; ++i) t += n->partials_host[i];
+    return t;
+}
+
+// Loss of the samples and the gradient accumulated into dB[] (not yet folded).
+static int ptc_accumulate(wd_ptc *n, const double *r, const double *e, int ns, double *loss) {
+    const long V = n->g.V;
+    const long fs = V * 12;    // complex entries per field
+    for (int l = 0; l < n->nl; ++l)
+        PTC_CUDA(cudaMemsetAsync(n->dB[l], 0, sizeof(float) * (long)n->Np[l] * n->Kp[l], n->stream));
+    double L = 0.0;
+    const unsigned nbn = (unsigned)std::min<long>(4096, (fs + PTC_BLOCK - 1) / PTC_BLOCK);
+    for (int i = 0; i < ns; ++i) {
+        const double2 *ei = (const double2 *)e + i * fs;
+        k_norm2_c128<<<nbn, PTC_BLOCK, 0, n->stream>>>(fs, ei, n->partials);
+        PTC_CUDA(cudaMemcpyAsync(n->partials_host, n->partials, sizeof(double) * nbn,
+                                 cudaMemcpyDeviceToHost, n->stream));
+        PTC_CUDA(cudaStreamSynchronize(n->stream));
+        const double ne = ptc_sum_partials(n, nbn);
+        PTC_TRY(ptc_forward(n, r + i * fs * 2, 1.0));
+        const int L_ = n->nl;
+        const unsigned nbl = grid_for(3 * V);
+        if (nbl > 4096) return ptc_fail(WD_ERR_DIMS, "lattice too large for the loss reduction");
+        k_ptc_loss_grad<<<nbl, PTC_BLOCK, 0, n->stream>>>(V, n->F[L_], n->ldF[L_], ei, 1.0 / ne,
+                                                          n->dF[L_], n->dFb[L_], n->Rp[L_],
+                                                          n->partials);
+        PTC_CUDA(cudaGetLastError());
+        PTC_CUDA(cudaMemcpyAsync(n->partials_host, n->partials, sizeof(double) * nbl,
+                                 cudaMemcpyDeviceToHost, n->stream));
+        for (int l = L_ - 1; l >= 0; --l) {
+            // dB[l] += dF[l+1]^T A[l]   (cuBLAS, column-major view: dB^T = A^T dF)
+            const float one = 1.0f;
+            cublasStatus_t st = cublasGemmEx(
+                n->blas, CUBLAS_OP_N, CUBLAS_OP_T, n->Kp[l], n->Np[l], (int)n->Mp, &one, n->A[l],
+                CUDA_R_16BF, n->Kp[l], n->dFb[l + 1], CUDA_R_16BF, n->Rp[l + 1], &one, n->dB[l],
+                CUDA_R_32F, n->Kp[l], CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+            if (st != CUBLAS_STATUS_SUCCESS) return ptc_fail(WD_ERR_CUDA, "cublasGemmEx failed");
+            if (l == 0) break;
+            // dA = dF[l+1] B[l] on the tensor cores, then the adjoint transports
+            PTC_TRY(ptc_gemm(n, n->dFb[l + 1], n->Bt[l], n->dA, n->Mp, n->Kp[l], n->Rp[l + 1],
+                             n->Rp[l + 1], n->Rp[l + 1], n->Kp[l]));
+            k_ptc_scatter<<<grid_for(V * n->ch[l]), PTC_BLOCK, 0, n->stream>>>(
+                n->g, n->ch[l], n->dA, n->Kp[l], n->U, n->dF[l], n->ldF[l], n->dFb[l], n->Rp[l]);
+            PTC_CUDA(cudaGetLastError());
+        }
+        PTC_CUDA(cudaStreamSynchronize(n->stream));
+        L += ptc_sum_partials(n, nbl) / ne;
+    }
+    if (loss) *loss = L;
+    return ptc_check_err(n);
+}
+
+static int ptc_fold_grad(wd_ptc *n) {
+    long off = 0;
+    for (int l = 0; l < n->nl; ++l) {
+        const long cnt = (long)n->ch[l + 1] * 4 * n->ch[l] * 36;
+        k_ptc_wgrad<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(n->ch[l + 1], n->ch[l], n->dB[l],
+                                                                 n->Kp[l], n->gW + off);
+        off += n->wcount[l];
+    }
+    PTC_CUDA(cudaGetLastError());
     return WD_OK;
 }
 
@@ -419,6 +673,44 @@ int wd_ptc_apply(wd_ptc *n, double *y, const double *r) {
         n->g.V, n->F[n->nl], n->ldF[n->nl], (double2 *)y, 1.0);
     PTC_CUDA(cudaGetLastError());
     return ptc_check_err(n);
+}
+
+int wd_ptc_loss_grad(wd_ptc *n, const double *r, const double *e, int nsamples, double *loss,
+                     double *grad) {
+    if (!n || !r || !e || nsamples < 1) return ptc_fail(WD_ERR_ARG, "bad argument");
+    PTC_TRY(ptc_train_setup(n));
+    PTC_TRY(ptc_accumulate(n, r, e, nsamples, loss));
+    PTC_TRY(ptc_fold_grad(n));
+    if (grad) {
+        long tot = 0;
+        for (int l = 0; l < n->nl; ++l) tot += n->wcount[l];
+        PTC_CUDA(cudaMemcpyAsync(grad, n->gW, sizeof(double2) * tot, cudaMemcpyDeviceToDevice,
+                                 n->stream));
+    }
+    PTC_CUDA(cudaStreamSynchronize(n->stream));
+    return WD_OK;
+}
+
+int wd_ptc_train_step(wd_ptc *n, const double *r, const double *e, int nsamples, double lr,
+                      double *loss) {
+    if (!n || !r || !e || nsamples < 1 || !(lr > 0)) return ptc_fail(WD_ERR_ARG, "bad argument");
+    PTC_TRY(ptc_train_setup(n));
+    PTC_TRY(ptc_accumulate(n, r, e, nsamples, loss));
+    PTC_TRY(ptc_fold_grad(n));
+    const float b1 = 0.9f, b2 = 0.999f;
+    n->adam_t += 1;
+    const float c1 = 1.f - powf(b1, (float)n->adam_t), c2 = 1.f - powf(b2, (float)n->adam_t);
+    long off = 0;
+    for (int l = 0; l < n->nl; ++l) {
+        k_ptc_adam<<<grid_for(n->wcount[l]), PTC_BLOCK, 0, n->stream>>>(
+            n->wcount[l], n->W[l], n->gW + off, n->adam_m + off, n->adam_v + off, (float)lr, b1, b2,
+            1e-8f, c1, c2);
+        off += n->wcount[l];
+    }
+    PTC_CUDA(cudaGetLastError());
+    PTC_TRY(ptc_rebuild_b(n));
+    PTC_CUDA(cudaStreamSynchronize(n->stream));
+    return WD_OK;
 }
 
 // D = A * B^T through the tensor-core GEMM, for tests of the GEMM alone:

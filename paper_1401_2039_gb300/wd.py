@@ -401,6 +401,32 @@ class PtcNet:
                                         ctypes.c_void_p(r.data_ptr())))
         return y
 
+    def loss_grad(self, r: torch.Tensor, e: torch.Tensor):
+        """Loss sum_i |N(r_i) - e_i|^2 / |e_i|^2 over samples r, e [n, V, 3, 4] and its
+        packed gradient dL/dRe W + i dL/dIm W (complex128 [n_weights])."""
+        n = r.shape[0]
+        _dev(r, (n, self.V, 3, 4), "r")
+        _dev(e, (n, self.V, 3, 4), "e")
+        g = torch.empty(self.n_weights, dtype=torch.complex128, device="cuda")
+        loss = ctypes.c_double()
+        torch.cuda.synchronize()
+        self._chk(self.lib.wd_ptc_loss_grad(self.handle, ctypes.c_void_p(r.data_ptr()),
+                                            ctypes.c_void_p(e.data_ptr()), n, ctypes.byref(loss),
+                                            ctypes.c_void_p(g.data_ptr())))
+        return loss.value, g
+
+    def train_step(self, r: torch.Tensor, e: torch.Tensor, lr: float = 1e-3) -> float:
+        """One Adam step on the samples; returns the loss before the step."""
+        n = r.shape[0]
+        _dev(r, (n, self.V, 3, 4), "r")
+        _dev(e, (n, self.V, 3, 4), "e")
+        loss = ctypes.c_double()
+        torch.cuda.synchronize()
+        self._chk(self.lib.wd_ptc_train_step(self.handle, ctypes.c_void_p(r.data_ptr()),
+                                             ctypes.c_void_p(e.data_ptr()), n, float(lr),
+                                             ctypes.byref(loss)))
+        return loss.value
+
     def gemm(self, A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
         """D = A B^T on the tensor-core GEMM (bf16 in, fp32 out), for tests."""
         M, K = A.shape
@@ -431,6 +457,8 @@ def _setup_ptc_signatures(lib):
         "wd_ptc_weight_count": (l, [vp]),
         "wd_ptc_apply": (i, [vp, vp, vp]),
         "wd_tc_gemm_bf16": (i, [vp, vp, vp, vp, l, i, i]),
+        "wd_ptc_loss_grad": (i, [vp, vp, vp, i, ctypes.POINTER(d), vp]),
+        "wd_ptc_train_step": (i, [vp, vp, vp, i, d, ctypes.POINTER(d)]),
         "wd_ptc_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
