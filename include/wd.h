@@ -188,6 +188,9 @@ int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int
 /* Stream the handle queues its work on (a cudaStream_t). */
 void *wd_op_stream(wd_op *op);
 
+/* Number of sites of one parity, V/2 (0 for a null handle). */
+long wd_op_half_volume(const wd_op *op);
+
 /* Algorithmic (compulsory) bytes of one single-parity hopping-term launch in
  * the handle's storage precision: Vh * (24 in + 24 out + 8 links * recon)
  * reals. */
@@ -230,6 +233,57 @@ int wd_apply_eo_noalloc(double *out, const double *in, const double *U, const in
                         double kappa, const double phase[8], int parity, int dagger,
                         void *stream);
 const char *wd_noalloc_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner (not in the paper): a linear, gauge-equivariant
+ * parallel-transport convolution network (Lehner & Wettig, arXiv:2302.05419)
+ * that maps one spinor field to one through layers of channels[0..nlayers]
+ * (channels[0] = channels[nlayers] = 1):
+ *   out_c'(x) = sum_c sum_{k=0..8} W[c', c, k] (T_k in_c)(x),
+ * W[c', c, k] complex 4x4 spin matrices, T_0 = 1,
+ * T_{1+mu} psi(x) = U_mu(x) phi_mu psi(x+mu), T_{5+mu} psi(x) =
+ * U_mu(x-mu)^dag phi_mu^* psi(x-mu) (phases on hops that wrap).  The channel
+ * mixing runs on the tensor cores (BF16 operands, FP32 accumulation).
+ * Weights cross the boundary as one device complex128 vector, layers in
+ * order, each [C_out][C_in][9][4][4]; gradients use the same layout packed as
+ * dL/dRe W + i dL/dIm W.  Spinors are device canonical [V][3][4] complex128.
+ */
+typedef struct wd_ptc wd_ptc;
+int wd_ptc_create(wd_ptc **net, const int dims[4], const double phase[8], int nlayers,
+                  const int *channels);
+void wd_ptc_destroy(wd_ptc *net);
+int wd_ptc_set_gauge(wd_ptc *net, const double *U);       /* canonical [V][4][3][3] */
+long wd_ptc_weight_count(const wd_ptc *net);              /* complex weights in total */
+int wd_ptc_set_weights(wd_ptc *net, const double *W);
+int wd_ptc_get_weights(wd_ptc *net, double *W);
+int wd_ptc_apply(wd_ptc *net, double *y, const double *r);  /* y = N(r), synchronous */
+/* Loss L = sum_i ||N(r_i) - e_i||^2 / ||e_i||^2 over nsamples fields r, e
+ * ([nsamples][V][3][4]) and its gradient (grad: device, weight layout, or NULL). */
+int wd_ptc_loss_grad(wd_ptc *net, const double *r, const double *e, int nsamples,
+                     double *loss, double *grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on
+ * the same loss; *loss receives the loss before the step. */
+int wd_ptc_train_step(wd_ptc *net, const double *r, const double *e, int nsamples, double lr,
+                      double *loss);
+/* The network's tensor-core GEMM alone, D = A B^T (A [M][K], B [N][K] BF16,
+ * D [M][N] FP32, device; M % 128 == 0, N % 16 == 0, K % 64 == 0). */
+int wd_tc_gemm_bf16(wd_ptc *net, const void *A, const void *B, float *D, long M, int N, int K);
+const char *wd_ptc_last_error(void);
+
+/* Flexible GCR(nkrylov) on the full system D x = b (not in the paper), with
+ * the network as right preconditioner (net may be NULL: plain GCR).  w = D z
+ * uses op_lo (any storage precision); the residual is recomputed with op_hi
+ * (a WD_F64 operator on the same lattice) at every restart, and the solve
+ * stops when ||b - D x|| / ||b|| <= tol by that FP64 residual.  x, b: device
+ * canonical [V][3][4] complex128.  info->iters counts preconditioned
+ * directions, info->reliable_updates restarts.  The handle owns its basis
+ * (2 nkrylov + 3 fields); the operators and the network must outlive it. */
+typedef struct wd_fgcr wd_fgcr;
+int wd_fgcr_create(wd_fgcr **solver, wd_op *op_lo, wd_op *op_hi, wd_ptc *net, int nkrylov);
+void wd_fgcr_destroy(wd_fgcr *solver);
+int wd_fgcr_solve(wd_fgcr *solver, double *x, const double *b, double tol, int maxiter,
+                  wd_solve_info *info);
+const char *wd_fgcr_last_error(void);
 
 #ifdef __cplusplus
 }

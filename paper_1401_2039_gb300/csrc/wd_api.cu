@@ -223,6 +223,8 @@ const char *wd_last_error(void) { return g_last_error.c_str(); }
 
 void *wd_op_stream(wd_op *op) { return op ? (void *)op->stream : nullptr; }
 
+long wd_op_half_volume(const wd_op *op) { return op ? op->g.vh : 0; }
+
 double wd_dslash_bytes(const wd_op *op) {
     if (!op) return 0.0;
     return (double)op->g.vh * (48.0 + 8.0 * op->recon) * (double)prec_bytes(op->prec);

@@ -63,6 +63,7 @@ def load_library() -> ctypes.CDLL:
             "wd_field_store": (i, [vp, i, vp]),
             "wd_dslash_resident": (i, [vp, i, i, i]),
             "wd_op_stream": (vp, [vp]),
+            "wd_op_half_volume": (ctypes.c_long, [vp]),
             "wd_op_set_solver": (i, [vp, d, i]),
             "wd_op_set_residual_precision": (i, [vp, i]),
             "wd_dslash_tuning": (i, [vp, i, dp, i, ip, ip, ip]),
@@ -466,3 +467,53 @@ def _setup_ptc_signatures(lib):
         f.restype = res
         f.argtypes = args
     _ptc_sigs_done = True
+
+
+class Fgcr:
+    """Flexible GCR on the full system with an optional learned right
+    preconditioner (handle on a wd_fgcr)."""
+
+    def __init__(self, op_lo: WilsonDirac, op_hi: WilsonDirac, net: "PtcNet | None" = None,
+                 nkrylov: int = 16):
+        self.lib = load_library()
+        _setup_ptc_signatures(self.lib)
+        vp, i = ctypes.c_void_p, ctypes.c_int
+        for name, res, args in (("wd_fgcr_create", i, [ctypes.POINTER(vp), vp, vp, vp, i]),
+                                ("wd_fgcr_destroy", None, [vp]),
+                                ("wd_fgcr_solve", i, [vp, vp, vp, ctypes.c_double, i,
+                                                      ctypes.POINTER(SolveInfo)]),
+                                ("wd_fgcr_last_error", ctypes.c_char_p, [])):
+            f = getattr(self.lib, name)
+            f.restype = res
+            f.argtypes = args
+        self.ops = (op_lo, op_hi, net)     # keep them alive
+        self.V = op_lo.V
+        handle = ctypes.c_void_p()
+        rc = self.lib.wd_fgcr_create(ctypes.byref(handle), op_lo.handle, op_hi.handle,
+                                     net.handle if net is not None else None, int(nkrylov))
+        if rc != WD_OK:
+            raise WDError(rc, self.lib.wd_fgcr_last_error().decode())
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.wd_fgcr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b: torch.Tensor, tol: float = 1e-10, maxiter: int = 2000, check=True):
+        _dev(b, (self.V, 3, 4), "b")
+        x = torch.empty_like(b)
+        info = SolveInfo()
+        torch.cuda.synchronize()
+        rc = self.lib.wd_fgcr_solve(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                    ctypes.c_void_p(b.data_ptr()), float(tol), int(maxiter),
+                                    ctypes.byref(info))
+        if check and rc != WD_OK:
+            raise WDError(rc, self.lib.wd_fgcr_last_error().decode())
+        return SolveResult(x, rc, info.as_dict())
