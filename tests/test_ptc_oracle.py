@@ -110,3 +110,23 @@ def test_identity_init_is_identity_at_zero_scale(U):
     Ws = ptc.identity_init(1, scale=0.0)
     r = syn.gaussian_spinor(syn.volume(DIMS), 7)
     assert np.allclose(ptc.net_forward(r, Ws, U, DIMS, PHASE), r, atol=1e-15)
+
+
+def test_neumann_initialisation_is_the_degree_four_neumann_series(U):
+    """The training driver's starting weights make the 1-16-16-16-1 network
+    equal sum_{k<=4} (kappa H)^k (Horner's rule on two channels)."""
+    from paper_1401_2039_gb300.train_preconditioner import neumann_weights
+    kappa, ch = 0.12, (1, 16, 16, 16, 1)
+    flat = neumann_weights(ch, kappa, 7, scale=0.0)
+    Ws, off = [], 0
+    for cin, cout in zip(ch[:-1], ch[1:]):
+        n = cout * cin * 9 * 16
+        Ws.append(flat[off:off + n].reshape(cout, cin, 9, 4, 4))
+        off += n
+    r = syn.gaussian_spinor(syn.volume(DIMS), 1)
+    ref, t = r.copy(), r.copy()
+    for _ in range(4):
+        t = kappa * oracle.hop(t, U, DIMS, PHASE)
+        ref = ref + t
+    y = ptc.net_forward(r, Ws, U, DIMS, PHASE)
+    assert np.linalg.norm(y - ref) < 1e-13 * np.linalg.norm(ref)
