@@ -244,13 +244,15 @@ const char *wd_noalloc_last_error(void);
  * T_{1+mu} psi(x) = U_mu(x) phi_mu psi(x+mu), T_{5+mu} psi(x) =
  * U_mu(x-mu)^dag phi_mu^* psi(x-mu) (phases on hops that wrap).  The channel
  * mixing runs on the tensor cores (BF16 operands, FP32 accumulation).
+ * Every call is ordered after the work queued on the stream given at
+ * creation and completes before later work on it.
  * Weights cross the boundary as one device complex128 vector, layers in
  * order, each [C_out][C_in][9][4][4]; gradients use the same layout packed as
  * dL/dRe W + i dL/dIm W.  Spinors are device canonical [V][3][4] complex128.
  */
 typedef struct wd_ptc wd_ptc;
 int wd_ptc_create(wd_ptc **net, const int dims[4], const double phase[8], int nlayers,
-                  const int *channels);
+                  const int *channels, void *stream);   /* stream as for wd_op_create */
 void wd_ptc_destroy(wd_ptc *net);
 int wd_ptc_set_gauge(wd_ptc *net, const double *U);       /* canonical [V][4][3][3] */
 long wd_ptc_weight_count(const wd_ptc *net);              /* complex weights in total */

@@ -369,7 +369,9 @@ struct wd_ptc {
     double *partials = nullptr;
     double *partials_host = nullptr;
     int *err = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;            // work stream owned by the network
+    cudaStream_t user = nullptr;              // caller's stream (nullptr = legacy)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // training
     bool train_ready = false;
     int Rp[PTC_MAX_LAYERS + 1] = {};          // BF16 gradient row strides (multiple of 64)
@@ -384,6 +386,19 @@ struct wd_ptc {
     cublasHandle_t blas = nullptr;
     std::vector<void *> allocs;
 };
+
+// Work of a call is ordered after what the caller queued on its stream and
+// before what it queues later.
+static int ptc_fork(wd_ptc *n) {
+    PTC_CUDA(cudaEventRecord(n->ev_fork, n->user));
+    PTC_CUDA(cudaStreamWaitEvent(n->stream, n->ev_fork, 0));
+    return WD_OK;
+}
+static int ptc_join(wd_ptc *n) {
+    PTC_CUDA(cudaEventRecord(n->ev_join, n->stream));
+    PTC_CUDA(cudaStreamWaitEvent(n->user, n->ev_join, 0));
+    return WD_OK;
+}
 
 static int ptc_alloc(wd_ptc *n, void **p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -462,12 +477,14 @@ void wd_ptc_destroy(wd_ptc *n) {
     for (void *p : n->allocs) cudaFree(p);
     if (n->partials_host) cudaFreeHost(n->partials_host);
     if (n->blas) cublasDestroy(n->blas);
+    if (n->ev_fork) cudaEventDestroy(n->ev_fork);
+    if (n->ev_join) cudaEventDestroy(n->ev_join);
     if (n->stream) cudaStreamDestroy(n->stream);
     delete n;
 }
 
 int wd_ptc_create(wd_ptc **out, const int dims[4], const double phase[8], int nlayers,
-                  const int *channels) {
+                  const int *channels, void *stream) {
     if (!out || !dims || !phase || !channels) return ptc_fail(WD_ERR_ARG, "null argument");
     *out = nullptr;
     if (nlayers < 1 || nlayers > PTC_MAX_LAYERS) return ptc_fail(WD_ERR_ARG, "1..8 layers");
@@ -489,7 +506,10 @@ int wd_ptc_create(wd_ptc **out, const int dims[4], const double phase[8], int nl
     n->M = 3 * V;
     n->Mp = pad_to(n->M, TC_BM);
     auto fail_free = [&](int rc) { std::string m = g_ptc_error; wd_ptc_destroy(n); g_ptc_error = m; return rc; };
-    if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) != cudaSuccess)
+    n->user = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return fail_free(ptc_fail(WD_ERR_CUDA, "stream creation failed"));
     n->ldF[0] = 8;
     for (int l = 0; l < nlayers; ++l) {
@@ -518,11 +538,12 @@ int wd_ptc_create(wd_ptc **out, const int dims[4], const double phase[8], int nl
 
 int wd_ptc_set_gauge(wd_ptc *n, const double *U) {
     if (!n || !U) return ptc_fail(WD_ERR_ARG, "null argument");
+    PTC_TRY(ptc_fork(n));
     const long cnt = n->g.V * 36;
     k_c128_to_c64<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(cnt, (const double2 *)U, n->U);
     PTC_CUDA(cudaGetLastError());
     PTC_CUDA(cudaStreamSynchronize(n->stream));
-    return WD_OK;
+    return ptc_join(n);
 }
 
 static int ptc_rebuild_b(wd_ptc *n) {
@@ -641,6 +662,7 @@ long wd_ptc_weight_count(const wd_ptc *n) {
 
 int wd_ptc_set_weights(wd_ptc *n, const double *W) {
     if (!n || !W) return ptc_fail(WD_ERR_ARG, "null argument");
+    PTC_TRY(ptc_fork(n));
     long off = 0;
     for (int l = 0; l < n->nl; ++l) {
         k_c128_to_c64<<<grid_for(n->wcount[l]), PTC_BLOCK, 0, n->stream>>>(
@@ -650,11 +672,12 @@ int wd_ptc_set_weights(wd_ptc *n, const double *W) {
     PTC_CUDA(cudaGetLastError());
     PTC_TRY(ptc_rebuild_b(n));
     PTC_CUDA(cudaStreamSynchronize(n->stream));
-    return WD_OK;
+    return ptc_join(n);
 }
 
 int wd_ptc_get_weights(wd_ptc *n, double *W) {
     if (!n || !W) return ptc_fail(WD_ERR_ARG, "null argument");
+    PTC_TRY(ptc_fork(n));
     long off = 0;
     for (int l = 0; l < n->nl; ++l) {
         k_c64_to_c128<<<grid_for(n->wcount[l]), PTC_BLOCK, 0, n->stream>>>(
@@ -663,21 +686,24 @@ int wd_ptc_get_weights(wd_ptc *n, double *W) {
     }
     PTC_CUDA(cudaGetLastError());
     PTC_CUDA(cudaStreamSynchronize(n->stream));
-    return WD_OK;
+    return ptc_join(n);
 }
 
 int wd_ptc_apply(wd_ptc *n, double *y, const double *r) {
     if (!n || !y || !r) return ptc_fail(WD_ERR_ARG, "null argument");
+    PTC_TRY(ptc_fork(n));
     PTC_TRY(ptc_forward(n, r, 1.0));
     k_ptc_out<<<grid_for(3 * n->g.V), PTC_BLOCK, 0, n->stream>>>(
         n->g.V, n->F[n->nl], n->ldF[n->nl], (double2 *)y, 1.0);
     PTC_CUDA(cudaGetLastError());
-    return ptc_check_err(n);
+    PTC_TRY(ptc_check_err(n));
+    return ptc_join(n);
 }
 
 int wd_ptc_loss_grad(wd_ptc *n, const double *r, const double *e, int nsamples, double *loss,
                      double *grad) {
     if (!n || !r || !e || nsamples < 1) return ptc_fail(WD_ERR_ARG, "bad argument");
+    PTC_TRY(ptc_fork(n));
     PTC_TRY(ptc_train_setup(n));
     PTC_TRY(ptc_accumulate(n, r, e, nsamples, loss));
     PTC_TRY(ptc_fold_grad(n));
@@ -688,12 +714,13 @@ int wd_ptc_loss_grad(wd_ptc *n, const double *r, const double *e, int nsamples, 
                                  n->stream));
     }
     PTC_CUDA(cudaStreamSynchronize(n->stream));
-    return WD_OK;
+    return ptc_join(n);
 }
 
 int wd_ptc_train_step(wd_ptc *n, const double *r, const double *e, int nsamples, double lr,
                       double *loss) {
     if (!n || !r || !e || nsamples < 1 || !(lr > 0)) return ptc_fail(WD_ERR_ARG, "bad argument");
+    PTC_TRY(ptc_fork(n));
     PTC_TRY(ptc_train_setup(n));
     PTC_TRY(ptc_accumulate(n, r, e, nsamples, loss));
     PTC_TRY(ptc_fold_grad(n));
@@ -710,15 +737,17 @@ int wd_ptc_train_step(wd_ptc *n, const double *r, const double *e, int nsamples,
     PTC_CUDA(cudaGetLastError());
     PTC_TRY(ptc_rebuild_b(n));
     PTC_CUDA(cudaStreamSynchronize(n->stream));
-    return WD_OK;
+    return ptc_join(n);
 }
 
 // D = A * B^T through the tensor-core GEMM, for tests of the GEMM alone:
 // A [M x K], B [N x K] BF16 row-major (device), D [M x N] FP32.
 int wd_tc_gemm_bf16(wd_ptc *n, const void *A, const void *B, float *D, long M, int N, int K) {
     if (!n || !A || !B || !D) return ptc_fail(WD_ERR_ARG, "null argument");
+    PTC_TRY(ptc_fork(n));
     PTC_TRY(ptc_gemm(n, (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, D, M, N, K, K, K, N));
-    return ptc_check_err(n);
+    PTC_TRY(ptc_check_err(n));
+    return ptc_join(n);
 }
 
 }  // extern "C"

@@ -347,9 +347,11 @@ class PtcNet:
     right preconditioner.  Weights are one flat complex128 vector, layers in
     order, each [C_out, C_in, 9, 4, 4]."""
 
-    def __init__(self, dims, phase=(1, 1, 1, -1), channels=(1, 16, 16, 16, 1)):
+    def __init__(self, dims, phase=(1, 1, 1, -1), channels=(1, 16, 16, 16, 1),
+                 stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("PtcNet needs a CUDA device; there is no CPU fallback")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.lib = load_library()
         _setup_ptc_signatures(self.lib)
         self.dims = tuple(int(d) for d in dims)
@@ -360,7 +362,8 @@ class PtcNet:
         handle = ctypes.c_void_p()
         ch = (ctypes.c_int * len(self.channels))(*self.channels)
         rc = self.lib.wd_ptc_create(ctypes.byref(handle), (ctypes.c_int * 4)(*self.dims),
-                                    phases_array(phase), len(self.channels) - 1, ch)
+                                    phases_array(phase), len(self.channels) - 1, ch,
+                                    ctypes.c_void_p(self.stream.cuda_stream))
         if rc != WD_OK:
             raise WDError(rc, self.lib.wd_ptc_last_error().decode())
         self.handle = handle
@@ -450,7 +453,7 @@ def _setup_ptc_signatures(lib):
     vp, i, d, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
     sig = {
         "wd_ptc_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(d), i,
-                              ctypes.POINTER(i)]),
+                              ctypes.POINTER(i), vp]),
         "wd_ptc_destroy": (None, [vp]),
         "wd_ptc_set_gauge": (i, [vp, vp]),
         "wd_ptc_set_weights": (i, [vp, vp]),
