@@ -9,10 +9,16 @@
    mixed-precision even-odd CGNR solve to a 1e-11 FP64 true residual and x_n
    after n = 8, 16 or 32 CGNR iterations give e = x - x_n and r = b - D x_n
    (= D e, low-mode rich, the part of D^-1 that slows a solver down); with
-   --data gaussian r is the Gaussian itself and e = D^-1 r.
+   --data gaussian r is the Gaussian itself and e = D^-1 r; --data mixed
+   alternates the two kinds so that both ends of the spectrum are fitted.
 2. Training: the 1 -> 16 -> 16 -> 16 -> 1 parallel-transport network, weights
-   starting at the identity map plus small noise, Adam (lr 1e-3) on the loss
-   sum ||N(r) - e||^2 / ||e||^2 over minibatches, every step on the GPU.
+   starting at the degree-4 Neumann polynomial of D^-1 (or the identity map)
+   plus small noise, Adam on the loss sum ||N(r) - e||^2 / ||e||^2 over
+   minibatches, every step on the GPU.  After every epoch the weights are
+   scored by the directions flexible GCR needs with them on a held-out gauge
+   field (seed 21); the best scoring weights, the initial ones included, are
+   kept (a lower loss on the pairs does not by itself make a better
+   preconditioner).
 3. Evaluation on gauge fields the network never saw (16^3 x 32 with gauge seed
    11, and 32^3 x 64 with seed 12 when --eval-large): flexible GCR(16) with the
    network as right preconditioner against plain GCR(16) and the even-odd CGNR
@@ -96,11 +102,12 @@ def main():
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=1e-4)
+    ap.add_argument("--max-directions", type=int, default=600)
     ap.add_argument("--kappa", type=float, default=0.124)
     ap.add_argument("--out", default=".")
     ap.add_argument("--eval-large", action="store_true")
-    ap.add_argument("--data", choices=["residual", "gaussian"], default="residual")
+    ap.add_argument("--data", choices=["residual", "gaussian", "mixed"], default="mixed")
     ap.add_argument("--init", choices=["neumann", "identity"], default="neumann")
     args = ap.parse_args()
     channels = (1, 16, 16, 16, 1)
@@ -123,7 +130,7 @@ def main():
     for i in range(args.pairs):
         b = torch.from_numpy(syn.gaussian_spinor(V, 1000 + i)).cuda()
         x = solver.solve(b, tol=1e-11).x
-        if args.data == "gaussian":
+        if args.data == "gaussian" or (args.data == "mixed" and i % 2 == 0):
             r, e = b, x
         else:
             xn = solver.solve(b, tol=1e-11, maxiter=(8, 16, 32)[i % 3], check=False).x
@@ -133,6 +140,22 @@ def main():
         E[i] = e.to(torch.complex64)
     torch.cuda.synchronize()
     summary["data_seconds"] = time.perf_counter() - t0
+
+    # held-out field for model selection
+    Uv = torch.from_numpy(syn.su3_links(dims, eps=0.3, seed=21)).cuda()
+    v_lo = WilsonDirac(dims, args.kappa, ph, prec="f32")
+    v_hi = WilsonDirac(dims, args.kappa, ph, prec="f64")
+    v_lo.set_gauge(Uv)
+    v_hi.set_gauge(Uv)
+    v_net = PtcNet(dims, ph, channels)
+    v_net.set_gauge(Uv)
+    v_b = torch.from_numpy(syn.gaussian_spinor(V, 555)).cuda()
+    v_solver = Fgcr(v_lo, v_hi, v_net, nkrylov=16)
+
+    def validate(weights):
+        v_net.set_weights(weights)
+        res = v_solver.solve(v_b, tol=1e-10, maxiter=args.max_directions, check=False)
+        return res.info["iters"] if res.status == 0 else 10 ** 9
 
     # ---- 2. training
     net = PtcNet(dims, ph, channels)
@@ -144,6 +167,9 @@ def main():
     summary["init"] = args.init
     net.set_weights(W0)
     history = []
+    best_w = net.get_weights()
+    best_dirs = validate(best_w)
+    validation = [best_dirs]
     t0 = time.perf_counter()
     steps = 0
     g = torch.Generator(device="cpu").manual_seed(5)
@@ -157,12 +183,24 @@ def main():
             ep_loss += net.train_step(rb, eb, lr=args.lr)
             steps += 1
         history.append(ep_loss / args.pairs)
-        print(f"epoch {ep}: mean loss {history[-1]:.4f}", flush=True)
+        w_ep = net.get_weights()
+        dirs = validate(w_ep)
+        validation.append(dirs)
+        if dirs < best_dirs:
+            best_dirs, best_w = dirs, w_ep
+        print(f"epoch {ep}: mean loss {history[-1]:.4f}, validation directions {dirs}", flush=True)
     torch.cuda.synchronize()
     summary["train_seconds"] = time.perf_counter() - t0
     summary["train_steps"] = steps
     summary["loss_per_epoch"] = history
-    W = net.get_weights()
+    summary["validation_directions"] = validation     # [initial, after each epoch]
+    summary["kept"] = "initial" if best_dirs == validation[0] and validation.index(best_dirs) == 0 \
+        else f"epoch {validation.index(best_dirs) - 1}"
+    W = best_w
+    v_solver.close()
+    v_net.close()
+    v_lo.close()
+    v_hi.close()
     os.makedirs(args.out, exist_ok=True)
     torch.save({"channels": channels, "kappa": args.kappa, "weights": W.cpu()},
                os.path.join(args.out, "ptc_weights.pt"))
@@ -202,7 +240,8 @@ def main():
         for name, pre in (("fgcr_learned", enet), ("fgcr_neumann4_untrained", nnet),
                           ("gcr_plain", None)):
             fg = Fgcr(lo, hi, pre, nkrylov=16)
-            res, ms = timed(lambda: fg.solve(b, tol=1e-10, maxiter=4000, check=False))
+            res, ms = timed(lambda: fg.solve(b, tol=1e-10, maxiter=args.max_directions,
+                                             check=False))
             row[name] = {"directions": res.info["iters"], "restarts": res.info["reliable_updates"],
                          "ms": ms, "true_rel_resid": res.info["true_rel_resid"],
                          "status": res.status}
