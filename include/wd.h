@@ -88,6 +88,14 @@ int wd_apply(wd_op *op, double *out, const double *in, int dagger);
  * (Alg. "schur": D22 - D21 D11^-1 D12 for p = 1). */
 int wd_apply_eo(wd_op *op, double *out, const double *in, int parity, int dagger);
 
+/* out = Mhat_p in (dagger: Mhat_p^dag in) as wd_apply_eo, but evaluated in
+ * the handle's residual arithmetic -- the arithmetic of the reliable updates
+ * (native FP64, or double-float for mixed-precision handles, selected with
+ * wd_op_set_residual_precision) on the FP64-side 18-real copy of the links.
+ * Same layout, ownership and errors as wd_apply_eo.  Lets a caller check
+ * residuals, or the double-float arithmetic, against an FP64 reference. */
+int wd_apply_eo_residual(wd_op *op, double *out, const double *in, int parity, int dagger);
+
 /* out = P_p H P_q^t in (dagger: the same with H^dag): the hopping term from
  * parity q = 1 - p onto parity p, half-lattice canonical spinors. */
 int wd_dslash_eo(wd_op *op, double *out, const double *in, int out_parity, int dagger);

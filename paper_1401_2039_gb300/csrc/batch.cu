@@ -113,7 +113,7 @@ __device__ __forceinline__ void bt_finish(const BtArgs &a, const double *sacc) {
 // ------------------------------------------------------------------ hopping term
 template <typename S, typename R, int RECON, int MU, int DAG>
 __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], long h, int r,
-                                            R *acc) {
+                                            Acc<R> *acc) {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
     const long ss = P.g.stride * P.nrhs;
@@ -122,7 +122,7 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
         const long hn = neighbour<MU, +1>(P.g, h, c, wrap);
         R psi[24];
         Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
-        cx<R> hs[2][3], u[2][3];
+        cx<Acc<R>> hs[2][3], u[2][3];
         project<MU, SF>(psi, hs);
         R U[18];
         load_link<S, R, RECON>(P.gauge_out + MU * P.dir_bytes, P.g.stride, h, U);
@@ -135,7 +135,7 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
         const long hn = neighbour<MU, -1>(P.g, h, c, wrap);
         R psi[24];
         Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
-        cx<R> hs[2][3], u[2][3];
+        cx<Acc<R>> hs[2][3], u[2][3];
         project<MU, SB>(psi, hs);
         R U[18];
         load_link<S, R, RECON>(P.gauge_in + MU * P.dir_bytes, P.g.stride, hn, U);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_dslash_batch(const __grid_constant
             const int r = (int)((unsigned)item - hu * (unsigned)nr);
             int c[4];
             site_coords(P.g, h, a.parity, c);
-            R acc[24];
+            Acc<R> acc[24];
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
             bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
@@ -175,20 +175,21 @@ __global__ void __launch_bounds__(BT_BLOCK) k_dslash_batch(const __grid_constant
             bt_hop_pair<S, R, RECON, 3, DAG>(P, c, h, r, acc);
             const long ss = P.g.stride * nr;
             const R sc = (R)P.scale;
+            R o[24];
             if (XPAY) {
                 R xv[24];
                 Rec<S, 24>::template load<R, 0>(P.f[2], ss, item, xv);
 #pragma unroll
-                for (int k = 0; k < 24; ++k) acc[k] = xv[k] + sc * acc[k];
+                for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + sc * acc[k]);
             } else {
 #pragma unroll
-                for (int k = 0; k < 24; ++k) acc[k] *= sc;
+                for (int k = 0; k < 24; ++k) o[k] = settle(sc * acc[k]);
             }
-            Rec<S, 24>::store(P.f[0], ss, item, acc);
+            Rec<S, 24>::store(P.f[0], ss, item, o);
             if (NORM) {
                 R sq = 0;
 #pragma unroll
-                for (int k = 0; k < 24; ++k) sq += acc[k] * acc[k];
+                for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
                 v = (double)sq;
             }
         }

@@ -25,17 +25,22 @@ struct df64 {
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
+// The error-free transformations below spell every operation with the
+// round-to-nearest intrinsics: nvcc contracts a multiply feeding an add into
+// one FMA by default, and a sum s that is not fl(a + b) breaks their
+// exactness.
+
 // s + e = a + b exactly
 __device__ __forceinline__ df64 two_sum(float a, float b) {
-    const float s = a + b;
-    const float v = s - a;
-    const float e = (a - (s - v)) + (b - v);
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
     return df64(s, e);
 }
 // s + e = a + b exactly when |a| >= |b|
 __device__ __forceinline__ df64 quick_two_sum(float a, float b) {
-    const float s = a + b;
-    return df64(s, b - (s - a));
+    const float s = __fadd_rn(a, b);
+    return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
 __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
@@ -46,7 +51,7 @@ __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
 __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
-    const float p = a.hi * b.hi;
+    const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);       // exact error of the leading product
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
@@ -55,5 +60,49 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
 __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 __device__ __forceinline__ df64 &operator*=(df64 &a, df64 b) { return a = a * b; }
+
+// Lazily normalised double-float: the value s + e where s is the FP32 sum of
+// the leading parts and e collects, in plain FP32, the exact rounding error
+// of every leading addition (TwoSum), the exact error of every leading
+// product (one FMA) and the products with the trailing parts.  This is the
+// compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci.
+// Comput. 26, 2005): a sum of n products comes out as accurate as one
+// evaluated with twice the working precision, error <= gamma_n^2 sum |a_i b_i|
+// with gamma_n = n u / (1 - n u), u = 2^-24.  Only s forms a serial chain
+// (one FP32 add per term); everything else is independent work.
+struct dfl {
+    float s, e;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float s_, float e_) : s(s_), e(e_) {}
+    __host__ __device__ constexpr dfl(int v) : s((float)v), e(0.0f) {}
+    __host__ __device__ constexpr dfl(df64 a) : s(a.hi), e(a.lo) {}
+};
+
+template <int SGN>
+__device__ __forceinline__ dfl lazy_add(dfl a, dfl b) {
+    const float bs = SGN > 0 ? b.s : -b.s, be = SGN > 0 ? b.e : -b.e;
+    const float s = __fadd_rn(a.s, bs);
+    const float v = __fsub_rn(s, a.s);
+    const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, v)), __fsub_rn(bs, v));
+    return dfl(s, a.e + (t + be));
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) { return lazy_add<1>(a, b); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return lazy_add<-1>(a, b); }
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.s, -a.e); }
+__device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
+__device__ __forceinline__ dfl &operator-=(dfl &a, dfl b) { return a = a - b; }
+// a * b as (leading product, exact error of it + cross products with the
+// trailing parts); the trailing-times-trailing term is below 2^-48 |a b|.
+__device__ __forceinline__ dfl operator*(df64 a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.s);
+    float c = fmaf(a.hi, b.s, -p);
+    c = fmaf(a.hi, b.e, c);
+    c = fmaf(a.lo, b.s, c);
+    return dfl(p, c);
+}
+__device__ __forceinline__ dfl operator*(dfl a, df64 b) { return b * a; }
+// nearest normalised double-float (TwoSum of the two parts: s and e carry
+// no ordering once e has collected several terms)
+__device__ __forceinline__ df64 normalise(dfl a) { return two_sum(a.s, a.e); }
 
 }  // namespace wd

@@ -14,7 +14,11 @@
 //   4. applies the boundary phase if the hop wrapped,
 //   5. expands back to four spin rows and accumulates.
 // Gamma matrices: DeGrand-Rossi basis (gamma_5 = diag(1, 1, -1, -1)).
-// Arithmetic type R = double for FP64 storage, float otherwise.
+// Arithmetic type R = double for FP64 storage, float otherwise, df64
+// (double-float) for the residuals of the reliable updates.  Intermediates
+// (half spinors, transported half spinors, the accumulator) use Acc<R>: R
+// itself, except that df64 keeps them as lazily normalised pairs (dfl, the
+// compensated dot product of df64.cuh) and rounds once, before the store.
 #pragma once
 
 #include "wd_internal.cuh"
@@ -22,6 +26,14 @@
 namespace wd {
 
 template <typename R> struct cx { R re, im; };
+
+template <typename R> struct AccOf { using T = R; };
+template <> struct AccOf<df64> { using T = dfl; };
+template <typename R> using Acc = typename AccOf<R>::T;
+
+__device__ __forceinline__ float settle(float a) { return a; }
+__device__ __forceinline__ double settle(double a) { return a; }
+__device__ __forceinline__ df64 settle(dfl a) { return normalise(a); }
 
 template <typename R>
 __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
@@ -33,14 +45,14 @@ __device__ __forceinline__ cx<R> cmuli(cx<R> a) { return {-a.im, a.re}; }
 
 // Half spinor h[spin row k][colour] from the 24 reals of a site, projector
 // 1 + SGN * gamma_MU.  psi real index = 2 * (4 * colour + spin) + (0 re | 1 im).
-template <int MU, int SGN, typename R>
-__device__ __forceinline__ void project(const R *psi, cx<R> h[2][3]) {
+template <int MU, int SGN, typename R, typename A>
+__device__ __forceinline__ void project(const R *psi, cx<A> h[2][3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        cx<R> p0 = {psi[8 * c + 0], psi[8 * c + 1]};
-        cx<R> p1 = {psi[8 * c + 2], psi[8 * c + 3]};
-        cx<R> p2 = {psi[8 * c + 4], psi[8 * c + 5]};
-        cx<R> p3 = {psi[8 * c + 6], psi[8 * c + 7]};
+        cx<A> p0 = {psi[8 * c + 0], psi[8 * c + 1]};
+        cx<A> p1 = {psi[8 * c + 2], psi[8 * c + 3]};
+        cx<A> p2 = {psi[8 * c + 4], psi[8 * c + 5]};
+        cx<A> p3 = {psi[8 * c + 6], psi[8 * c + 7]};
         if (MU == 0) {          // gamma_x: rows (3, i) (2, i) (1, -i) (0, -i)
             h[0][c] = SGN > 0 ? cadd(p0, cmuli(p3)) : csub(p0, cmuli(p3));
             h[1][c] = SGN > 0 ? cadd(p1, cmuli(p2)) : csub(p1, cmuli(p2));
@@ -59,11 +71,11 @@ __device__ __forceinline__ void project(const R *psi, cx<R> h[2][3]) {
 
 // acc += (1 + SGN gamma_MU) expanded from the transported half spinor u:
 // rows 0, 1 are u itself, rows 2, 3 are fixed multiples of u rows.
-template <int MU, int SGN, typename R>
-__device__ __forceinline__ void accumulate(R *acc, const cx<R> u[2][3]) {
+template <int MU, int SGN, typename A>
+__device__ __forceinline__ void accumulate(A *acc, const cx<A> u[2][3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        cx<R> r2, r3;
+        cx<A> r2, r3;
         if (MU == 0) {          // r2 = -SGN i u1, r3 = -SGN i u0
             r2 = cmuli(u[1][c]); r3 = cmuli(u[0][c]);
             if (SGN > 0) { r2 = {-r2.re, -r2.im}; r3 = {-r3.re, -r3.im}; }
@@ -104,14 +116,14 @@ __device__ __forceinline__ void load_link(const void *base, long stride, long h,
 
 // u[k][a] = sum_b U[a][b] h[k][b], written as chains of single
 // multiply-adds so that every real product becomes one FMA.
-template <typename R>
-__device__ __forceinline__ void su3_mul(const R *U, const cx<R> h[2][3], cx<R> u[2][3]) {
+template <typename R, typename A>
+__device__ __forceinline__ void su3_mul(const R *U, const cx<A> h[2][3], cx<A> u[2][3]) {
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            R re = U[6 * a] * h[k][0].re;
-            R im = U[6 * a] * h[k][0].im;
+            A re = U[6 * a] * h[k][0].re;
+            A im = U[6 * a] * h[k][0].im;
             re -= U[6 * a + 1] * h[k][0].im;
             im += U[6 * a + 1] * h[k][0].re;
 #pragma unroll
@@ -127,14 +139,14 @@ __device__ __forceinline__ void su3_mul(const R *U, const cx<R> h[2][3], cx<R> u
 }
 
 // u[k][a] = sum_b conj(U[b][a]) h[k][b]
-template <typename R>
-__device__ __forceinline__ void su3_adj_mul(const R *U, const cx<R> h[2][3], cx<R> u[2][3]) {
+template <typename R, typename A>
+__device__ __forceinline__ void su3_adj_mul(const R *U, const cx<A> h[2][3], cx<A> u[2][3]) {
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            R re = U[2 * a] * h[k][0].re;
-            R im = U[2 * a] * h[k][0].im;
+            A re = U[2 * a] * h[k][0].re;
+            A im = U[2 * a] * h[k][0].im;
             re += U[2 * a + 1] * h[k][0].im;
             im -= U[2 * a + 1] * h[k][0].re;
 #pragma unroll
@@ -149,14 +161,14 @@ __device__ __forceinline__ void su3_adj_mul(const R *U, const cx<R> h[2][3], cx<
         }
 }
 
-template <typename R>
-__device__ __forceinline__ void phase_mul(cx<R> u[2][3], R pr, R pi) {
+template <typename R, typename A>
+__device__ __forceinline__ void phase_mul(cx<A> u[2][3], R pr, R pi) {
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const R re = u[k][a].re * pr - u[k][a].im * pi;
-            const R im = u[k][a].re * pi + u[k][a].im * pr;
+            const A re = u[k][a].re * pr - u[k][a].im * pi;
+            const A im = u[k][a].re * pi + u[k][a].im * pr;
             u[k][a] = {re, im};
         }
 }
@@ -194,7 +206,8 @@ __device__ __forceinline__ long neighbour(const Geom &g, long h, const int c[4],
 }
 
 template <typename S, typename R, int RECON, int MU, int DAG>
-__device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4], long h, R *acc) {
+__device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4], long h,
+                                         Acc<R> *acc) {
     constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
     constexpr int SB = -SF;
     // forward hop: U_mu(x) in(x + mu)
@@ -203,7 +216,7 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
         const long hn = neighbour<MU, +1>(a.g, h, c, wrap);
         R psi[24];
         Rec<S, 24>::template load<R, 0>(a.in, a.g.stride, hn, psi);
-        cx<R> hs[2][3], u[2][3];
+        cx<Acc<R>> hs[2][3], u[2][3];
         project<MU, SF>(psi, hs);
         R U[18];
         load_link<S, R, RECON>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, U);
@@ -217,7 +230,7 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
         const long hn = neighbour<MU, -1>(a.g, h, c, wrap);
         R psi[24];
         Rec<S, 24>::template load<R, 0>(a.in, a.g.stride, hn, psi);
-        cx<R> hs[2][3], u[2][3];
+        cx<Acc<R>> hs[2][3], u[2][3];
         project<MU, SB>(psi, hs);
         R U[18];
         load_link<S, R, RECON>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, U);
@@ -239,27 +252,28 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
         if (h < a.g.vh) {
             int c[4];
             site_coords(a.g, h, a.parity, c);
-            R acc[24];
+            Acc<R> acc[24];
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
             hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
             hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
             hop_pair<S, R, RECON, 2, DAG>(a, c, h, acc);
             hop_pair<S, R, RECON, 3, DAG>(a, c, h, acc);
+            R o[24];
             if (EPI == EPI_XPAY) {
                 R xv[24];
                 Rec<S, 24>::template load<R, 0>(a.x, a.g.stride, h, xv);
 #pragma unroll
-                for (int k = 0; k < 24; ++k) acc[k] = xv[k] + a.scale * acc[k];
+                for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + a.scale * acc[k]);
             } else {
 #pragma unroll
-                for (int k = 0; k < 24; ++k) acc[k] *= a.scale;
+                for (int k = 0; k < 24; ++k) o[k] = settle(a.scale * acc[k]);
             }
-            Rec<S, 24>::store(a.out, a.g.stride, h, acc);
+            Rec<S, 24>::store(a.out, a.g.stride, h, o);
             if (NORM) {
                 R sq = 0;
 #pragma unroll
-                for (int k = 0; k < 24; ++k) sq += acc[k] * acc[k];
+                for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
                 nrm += (double)sq;
             }
         }
@@ -275,6 +289,11 @@ struct DslashCfg { int block, minb, spt; };
 constexpr int N_DSLASH_CFG = 5;
 constexpr DslashCfg DSLASH_CFGS[N_DSLASH_CFG] = {
     {128, 1, 1}, {128, 8, 1}, {256, 1, 1}, {256, 4, 1}, {128, 1, 2}};
+// The double-float hopping term (one site per thread, a loop over the hops)
+// has its own table: its register appetite makes the minimum resident blocks,
+// i.e. the register cap, the parameter that matters.
+constexpr DslashCfg DSLASH_DF_CFGS[N_DSLASH_CFG] = {
+    {128, 3, 1}, {128, 1, 1}, {128, 2, 1}, {128, 4, 1}, {256, 2, 1}};
 
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int CFG>
 void launch_cfg(const DslashArgs<R> &a, cudaStream_t s) {

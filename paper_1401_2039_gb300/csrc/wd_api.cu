@@ -198,9 +198,10 @@ int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int
     if (!op || (hi != 0 && hi != 1)) return -1;
     const int k = op->cfg[hi];
     for (int i = 0; us && i < n && i < N_DSLASH_CFG; ++i) us[i] = op->tune_us[hi][i];
-    if (block) *block = DSLASH_CFGS[k].block;
-    if (min_blocks) *min_blocks = DSLASH_CFGS[k].minb;
-    if (sites_per_thread) *sites_per_thread = DSLASH_CFGS[k].spt;
+    const DslashCfg &C = (hi && op->hi_prec == WD_DF64) ? DSLASH_DF_CFGS[k] : DSLASH_CFGS[k];
+    if (block) *block = C.block;
+    if (min_blocks) *min_blocks = C.minb;
+    if (sites_per_thread) *sites_per_thread = C.spt;
     return k;
 }
 
@@ -370,6 +371,18 @@ int wd_apply_eo(wd_op *op, double *out, const double *in, int parity, int dagger
     WD_CUDA(launch_pack_half(op->prec, op->g, op->fa[0], in, op->stream));
     WD_TRY(schur(op, false, parity, dagger, op->fc[0], op->fa[0], op->ftmp, nullptr));
     WD_CUDA(launch_unpack_half(op->prec, op->g, out, op->fc[0], op->stream));
+    return join(op);
+}
+
+int wd_apply_eo_residual(wd_op *op, double *out, const double *in, int parity, int dagger) {
+    WD_TRY(check_op(op));
+    if (!out || !in) return fail(WD_ERR_ARG, "null spinor");
+    if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (dagger != 0 && dagger != 1) return fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    WD_TRY(fork(op));
+    WD_CUDA(launch_pack_half(op->hi_prec, op->g, op->xh, in, op->stream));
+    WD_TRY(schur(op, true, parity, dagger, op->axh, op->xh, op->th, nullptr));
+    WD_CUDA(launch_unpack_half(op->hi_prec, op->g, out, op->axh, op->stream));
     return join(op);
 }
 

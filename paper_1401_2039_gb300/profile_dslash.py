@@ -6,7 +6,9 @@ It builds the workload's operator, loads one Gaussian half spinor into both
 resident slots and launches the storage-precision hopping term N times,
 ping-ponging between the slots and alternating the output parity, as the
 Schur operator does.  Prints the mean launch time measured with CUDA events
-on the operator's work stream.
+on the operator's work stream.  With --residual it applies the Schur operator
+in the residual arithmetic of the reliable updates instead (two hopping-term
+launches in double-float or FP64 per application, plus layout conversion).
 """
 from __future__ import annotations
 
@@ -31,6 +33,8 @@ def main():
     ap.add_argument("--recon", type=int, default=None)
     ap.add_argument("--launches", type=int, default=5)
     ap.add_argument("--dagger", action="store_true")
+    ap.add_argument("--residual", choices=["df64", "f64"], default=None,
+                    help="apply Mhat in this residual arithmetic instead")
     args = ap.parse_args()
     w = syn.WORKLOADS[args.workload]
     prec = args.prec or w.prec
@@ -39,6 +43,22 @@ def main():
     half = torch.from_numpy(syn.gaussian_spinor(w.vh, w.source_seed)).cuda()
     op = WilsonDirac(w.dims, w.kappa, w.phase, prec=prec, recon=recon)
     op.set_gauge(U)
+    if args.residual:
+        op.set_residual_precision(args.residual)
+        out = torch.empty_like(half)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.launches):
+            op.apply_eo(half, 1, args.dagger, out=out, residual=True)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / max(1, args.launches)
+        print(f"{w.name} Mhat in {args.residual} arithmetic: {args.launches} applications, "
+              f"{us:.1f} us each")
+        op.close()
+        return
     op.field_load(0, half)
     op.field_load(1, half)
     ws = torch.cuda.ExternalStream(op.work_stream)

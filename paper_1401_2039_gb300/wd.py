@@ -56,6 +56,7 @@ def load_library() -> ctypes.CDLL:
             "wd_op_set_gauge": (i, [vp, vp]),
             "wd_apply": (i, [vp, vp, vp, i]),
             "wd_apply_eo": (i, [vp, vp, vp, i, i]),
+            "wd_apply_eo_residual": (i, [vp, vp, vp, i, i]),
             "wd_dslash_eo": (i, [vp, vp, vp, i, i]),
             "wd_solve_cg": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
             "wd_solve_cg_host": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
@@ -169,12 +170,15 @@ class WilsonDirac:
         return out
 
     def apply_eo(self, psi: torch.Tensor, parity: int = 1, dagger: bool = False,
-                 out=None) -> torch.Tensor:
+                 out=None, residual: bool = False) -> torch.Tensor:
+        """Mhat_p psi; residual=True evaluates it in the residual arithmetic
+        of the reliable updates (FP64 or double-float) instead of storage
+        precision."""
         _dev(psi, (self.Vh, 3, 4), "psi")
         out = torch.empty_like(psi) if out is None else _dev(out, (self.Vh, 3, 4), "out")
-        _check(self.lib.wd_apply_eo(self.handle, ctypes.c_void_p(out.data_ptr()),
-                                    ctypes.c_void_p(psi.data_ptr()), int(parity),
-                                    int(bool(dagger))))
+        fn = self.lib.wd_apply_eo_residual if residual else self.lib.wd_apply_eo
+        _check(fn(self.handle, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(psi.data_ptr()),
+                  int(parity), int(bool(dagger))))
         return out
 
     def dslash_eo(self, psi: torch.Tensor, out_parity: int, dagger: bool = False,

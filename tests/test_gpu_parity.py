@@ -242,6 +242,26 @@ def test_residual_precision_modes(prec, recon):
         assert rel(x, x_ref) < 1e-8, mode
 
 
+@pytest.mark.parametrize("dims", [(6, 6, 2, 4), (8, 4, 6, 10), (2, 2, 2, 2)])
+@pytest.mark.parametrize("mode", ["df64", "f64"])
+def test_residual_arithmetic_schur_operator(dims, mode):
+    """Mhat_p and its dagger in the arithmetic of the reliable updates agree
+    with the FP64 oracle to 1e-13: native FP64, and double-float (48-bit
+    significands, compensated sums rounded once per output)."""
+    U, psi = fields(dims)
+    kappa = 0.124
+    for phase in PHASES.values():
+        op = make_op(dims, kappa, phase, "f16", 12, U)
+        op.set_residual_precision(mode)
+        for parity in (0, 1):
+            src = syn.to_half(psi, dims, parity)
+            for dag in (False, True):
+                ref = oracle.apply_eo(src, U, dims, kappa, phase, parity, dag)
+                got = host(op.apply_eo(cuda(src), parity, dag, residual=True))
+                assert rel(got, ref) < 1e-13, (mode, parity, dag, rel(got, ref))
+        op.close()
+
+
 def test_f64_operator_rejects_double_float_residuals():
     from paper_1401_2039_gb300 import WDError
     dims = (4, 4, 4, 4)
