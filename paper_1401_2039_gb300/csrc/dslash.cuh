@@ -245,7 +245,9 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK, int MINB,
           int SPT>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
-    double nrm = 0.0;
+    double nrm[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) nrm[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
         const long h = (long)blockIdx.x * (BLOCK * SPT) + i * BLOCK + threadIdx.x;
@@ -274,17 +276,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
                 R sq = 0;
 #pragma unroll
                 for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-                nrm += (double)sq;
+                nrm[i] = (double)sq;
             }
         }
     }
-    if (NORM) block_reduce_finish<BLOCK>(nrm, a.red);
+    if (NORM) chunk_reduce_finish<BLOCK, SPT>(nrm, a.g.vh, a.red);
 }
 
 // Launch configurations the tuner chooses from: threads per block, the
 // minimum resident blocks per SM handed to the register allocator, and
-// output sites per thread.  Kernels that fuse a norm always use entry 0 so
-// that reductions add in one fixed order.
+// output sites per thread.  A fused norm adds in the same order under every
+// configuration (chunk_reduce_finish), so all variants use the tuned one.
 struct DslashCfg { int block, minb, spt; };
 constexpr int N_DSLASH_CFG = 5;
 constexpr DslashCfg DSLASH_CFGS[N_DSLASH_CFG] = {
@@ -303,14 +305,14 @@ void launch_cfg(const DslashArgs<R> &a, cudaStream_t s) {
     k_dslash<S, R, RECON, DAG, EPI, NORM, C.block, C.minb, C.spt><<<grid, C.block, 0, s>>>(a);
 }
 
-template <typename S, typename R, int RECON, int DAG, int EPI>
+template <typename S, typename R, int RECON, int DAG, int EPI, int NORM>
 void launch_any_cfg(int cfg, const DslashArgs<R> &a, cudaStream_t s) {
     switch (cfg) {
-    case 1: launch_cfg<S, R, RECON, DAG, EPI, 0, 1>(a, s); break;
-    case 2: launch_cfg<S, R, RECON, DAG, EPI, 0, 2>(a, s); break;
-    case 3: launch_cfg<S, R, RECON, DAG, EPI, 0, 3>(a, s); break;
-    case 4: launch_cfg<S, R, RECON, DAG, EPI, 0, 4>(a, s); break;
-    default: launch_cfg<S, R, RECON, DAG, EPI, 0, 0>(a, s); break;
+    case 1: launch_cfg<S, R, RECON, DAG, EPI, NORM, 1>(a, s); break;
+    case 2: launch_cfg<S, R, RECON, DAG, EPI, NORM, 2>(a, s); break;
+    case 3: launch_cfg<S, R, RECON, DAG, EPI, NORM, 3>(a, s); break;
+    case 4: launch_cfg<S, R, RECON, DAG, EPI, NORM, 4>(a, s); break;
+    default: launch_cfg<S, R, RECON, DAG, EPI, NORM, 0>(a, s); break;
     }
 }
 
@@ -331,15 +333,15 @@ cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
     if (L.red) a.red = *L.red;
     else a.red = Reduction{nullptr, nullptr, nullptr, FIN_NONE};
     const int cfg = L.cfg;
-    if (L.red) {   // fused norm: fixed configuration, fixed summation order
-        if (L.dagger) launch_cfg<S, R, RECON, 1, EPI_XPAY, 1, 0>(a, s);
-        else launch_cfg<S, R, RECON, 0, EPI_XPAY, 1, 0>(a, s);
+    if (L.red) {   // fused norm (after an xpay epilogue)
+        if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_XPAY, 1>(cfg, a, s);
+        else launch_any_cfg<S, R, RECON, 0, EPI_XPAY, 1>(cfg, a, s);
     } else if (L.epi == EPI_PLAIN) {
-        if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_PLAIN>(cfg, a, s);
-        else launch_any_cfg<S, R, RECON, 0, EPI_PLAIN>(cfg, a, s);
+        if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_PLAIN, 0>(cfg, a, s);
+        else launch_any_cfg<S, R, RECON, 0, EPI_PLAIN, 0>(cfg, a, s);
     } else {
-        if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_XPAY>(cfg, a, s);
-        else launch_any_cfg<S, R, RECON, 0, EPI_XPAY>(cfg, a, s);
+        if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_XPAY, 0>(cfg, a, s);
+        else launch_any_cfg<S, R, RECON, 0, EPI_XPAY, 0>(cfg, a, s);
     }
     return cudaGetLastError();
 }

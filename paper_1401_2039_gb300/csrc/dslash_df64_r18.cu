@@ -33,7 +33,7 @@ __device__ __forceinline__ cdf sel(bool first, cdf a, cdf b) { return first ? a 
 
 template <int DAG, int EPI, int NORM, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64> a) {
-    double nrm = 0.0;
+    double nrm[1] = {0.0};
     const long h = (long)blockIdx.x * BLOCK + threadIdx.x;
     if (h < a.g.vh) {
         int c[4];
@@ -132,10 +132,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64
             df64 sq = 0;
 #pragma unroll
             for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-            nrm = (double)sq;
+            nrm[0] = (double)sq;
         }
     }
-    if (NORM) block_reduce_finish<BLOCK>(nrm, a.red);
+    if (NORM) chunk_reduce_finish<BLOCK, 1>(nrm, a.g.vh, a.red);
 }
 
 template <int DAG, int EPI, int NORM, int CFG>
@@ -171,7 +171,7 @@ cudaError_t launch_dslash_df64_r18(const DslashLaunch &L, cudaStream_t s) {
     for (int i = 0; i < 8; ++i) a.ph[i] = df64(L.phase[i]);
     a.parity = L.out_parity;
     a.red = L.red ? *L.red : Reduction{nullptr, nullptr, nullptr, FIN_NONE};
-    if (L.red) {   // fused norm: fixed configuration, fixed summation order
+    if (L.red) {   // fused norm; the residuals never use it: one configuration
         if (L.dagger) launch_df<1, EPI_XPAY, 1, 0>(a, s);
         else launch_df<0, EPI_XPAY, 1, 0>(a, s);
     } else if (L.epi == EPI_PLAIN) {

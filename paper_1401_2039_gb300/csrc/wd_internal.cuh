@@ -419,6 +419,66 @@ __device__ __forceinline__ void block_reduce_finish(double v, const Reduction &r
     }
 }
 
+// Sum of one value per output site whose rounding does not depend on the
+// launch configuration: fixed 128-site chunks (four 32-site warp sums added
+// in order) give the partials, and the last block to arrive adds them over
+// 128 strided lanes in a fixed tree.  Site h of a block is base + i * BLOCK
+// + threadIdx.x for i < SPT, and blocks cover whole chunks, so the chunk and
+// warp of every site, and with them every rounding, are the same for any
+// (BLOCK, SPT).  Sites past the end contribute exact zeros.
+template <int BLOCK, int SPT>
+__device__ __forceinline__ void chunk_reduce_finish(const double (&v)[SPT], long n_sites,
+                                                    const Reduction &red) {
+    static_assert(BLOCK % 128 == 0, "blocks must cover whole 128-site chunks");
+    constexpr int W = BLOCK * SPT / 32;     // site warps per block
+    constexpr int C = W / 4;                // chunks per block
+    __shared__ double warp_sums[W];
+    __shared__ bool is_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+        double s = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) warp_sums[i * (BLOCK / 32) + wid] = s;
+    }
+    __syncthreads();
+    const long n_chunks = (n_sites + 127) / 128;
+    if (threadIdx.x < C) {
+        const long chunk = (long)blockIdx.x * C + threadIdx.x;
+        if (chunk < n_chunks) {
+            double s = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s += warp_sums[4 * threadIdx.x + j];
+            red.partials[chunk] = s;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int prev = atomicAdd(red.counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double s = 0;
+    if (threadIdx.x < 128)
+        for (long i = threadIdx.x; i < n_chunks; i += 128) s += __ldcg(&red.partials[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();   // the chunk sums above are read; reuse warp_sums
+    if (lane == 0 && wid < 4) warp_sums[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t += warp_sums[i];
+        apply_final(red.scalars, red.op, t);
+        *red.counter = 0u;
+    }
+}
+
 // ---------------------------------------------------------------- host side
 struct Field {          // one parity spinor field in the internal layout
     void *ptr = nullptr;

@@ -262,6 +262,27 @@ def test_residual_arithmetic_schur_operator(dims, mode):
         op.close()
 
 
+@pytest.mark.parametrize("prec,recon", [("f16", 12), ("f32", 18)])
+def test_solve_bitwise_identical_across_launch_configurations(monkeypatch, prec, recon):
+    """Fused norms add in one order under every launch configuration, so
+    the iterates and the solution are bitwise identical whichever
+    configuration the tuner picks (ragged last chunk: Vh = 1440)."""
+    dims = (8, 6, 6, 10)
+    U, _ = fields(dims)
+    b = syn.gaussian_spinor(syn.volume(dims), 3)
+    runs = []
+    for k in range(5):
+        monkeypatch.setenv("WD_DSLASH_CFG", str(k))
+        op = make_op(dims, 0.124, PHASES["apbc"], prec, recon, U)
+        assert op.dslash_tuning()["index"] == k
+        res = op.solve(cuda(b), tol=1e-10)
+        runs.append((host(res.x), res.info["iters"], res.info["reliable_updates"]))
+        op.close()
+    for x, it, ru in runs[1:]:
+        assert (it, ru) == runs[0][1:]
+        assert np.array_equal(x, runs[0][0])
+
+
 def test_f64_operator_rejects_double_float_residuals():
     from paper_1401_2039_gb300 import WDError
     dims = (4, 4, 4, 4)
