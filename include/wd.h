@@ -184,8 +184,11 @@ int wd_field_store(wd_op *op, int slot, double *half_out);
 int wd_dslash_resident(wd_op *op, int in_slot, int out_parity, int dagger);
 
 /* Launch configuration of the hopping term picked by the autotuner when the
- * gauge field was loaded (hi = 0: storage precision, hi = 1: the FP64
- * kernels of the reliable updates).  us (optional, n entries) receives the
+ * gauge field was loaded.  hi = 0: the storage-precision kernel; hi = 1: the
+ * residual-arithmetic (FP64 or double-float) kernel of the reliable updates;
+ * hi = 2: the storage-precision kernel with the xpay epilogue and fused norm
+ * that ends each Schur operator of the CGNR iteration (tuned on its own: its
+ * register demand differs).  us (optional, n entries) receives the
  * measured microseconds per launch of every candidate; block, min_blocks and
  * sites_per_thread (optional) describe the chosen one.  Returns its index,
  * or -1 for a null handle.  Setting WD_DSLASH_CFG=k in the environment

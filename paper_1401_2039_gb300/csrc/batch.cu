@@ -93,21 +93,17 @@ __device__ __forceinline__ void bt_finish(const BtArgs &a, const double *sacc) {
         a.partials[(long)blockIdx.x * BT_MAX_SLOTS + s] = sacc[s];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) last = arrive_last(a.counter, gridDim.x, blockIdx.x);
     __syncthreads();
     if (!last) return;
     __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int s = warp; s < a.nslots; s += BT_BLOCK / 32) {
-        double sum = 0.0;
-        for (unsigned b = lane; b < gridDim.x; b += 32)
-            sum += __ldcg(&a.partials[(long)b * BT_MAX_SLOTS + s]);
+        double sum = strided_sum<32>(a.partials + s, gridDim.x, lane, BT_MAX_SLOTS);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (lane == 0) apply_final(&a.scalars[s], a.fin, sum);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *a.counter = 0u;
 }
 
 // ------------------------------------------------------------------ hopping term
@@ -905,7 +901,7 @@ static int batch_create_impl(wd_batch *bt) {
         }
     }
     BT_TRY(bt_alloc(bt, (void **)&bt->partials, sizeof(double) * BT_GRID * BT_MAX_SLOTS));
-    BT_TRY(bt_alloc(bt, (void **)&bt->counter, sizeof(unsigned int) * 4));
+    BT_TRY(bt_alloc(bt, (void **)&bt->counter, sizeof(unsigned int) * ARRIVE_WORDS));
     BT_TRY(bt_alloc(bt, (void **)&bt->sc, sizeof(SolverScalars) * BT_MAX_SLOTS));
     BT_TRY(bt_alloc(bt, (void **)&bt->consts, sizeof(double) * 4 * BT_MAX_SLOTS));
     BT_CUDA(cudaMallocHost((void **)&bt->sc_host, sizeof(SolverScalars) * BT_MAX_SLOTS));

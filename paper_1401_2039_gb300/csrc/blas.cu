@@ -26,9 +26,29 @@ inline unsigned blas_grid(long n) {
     return (unsigned)b;
 }
 
+// partials: one per 32 output sites (warp_partials), or one per BLAS block
 int reduction_blocks(const Geom &g) {
-    long d = (g.vh + 127) / 128;
+    long d = (g.vh + 31) / 32;
     return (int)(d > BLAS_MAX_GRID ? d : BLAS_MAX_GRID);
+}
+
+constexpr int FINISH_BLOCK = 1024;
+
+__global__ void __launch_bounds__(FINISH_BLOCK) k_finish_partials(Reduction red, long n) {
+    __shared__ df64 warp_sums[FINISH_BLOCK / 32];
+    const df64 s = warp_sum(strided_sum<FINISH_BLOCK>(red.partials, n, threadIdx.x));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_sums[wid] = s;
+    __syncthreads();
+    if (wid == 0) {
+        const df64 t = warp_sum(warp_sums[lane]);
+        if (lane == 0) apply_final(red.scalars, red.op, (double)t);
+    }
+}
+
+cudaError_t launch_finish_partials(const Reduction &red, long n, cudaStream_t s) {
+    k_finish_partials<<<1, FINISH_BLOCK, 0, s>>>(red, n);
+    return cudaGetLastError();
 }
 
 // x += alpha p;  r -= alpha Ap;  ||r||^2  (alpha from the device scalars)

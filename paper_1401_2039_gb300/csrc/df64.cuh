@@ -16,7 +16,7 @@
 
 namespace wd {
 
-struct df64 {
+struct __align__(8) df64 {
     float hi, lo;
     df64() = default;
     __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}

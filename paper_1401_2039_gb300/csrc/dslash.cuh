@@ -245,9 +245,9 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK, int MINB,
           int SPT>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
-    double nrm[SPT];
+    df64 nrm[SPT];
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) nrm[i] = 0.0;
+    for (int i = 0; i < SPT; ++i) nrm[i] = df64(0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
         const long h = (long)blockIdx.x * (BLOCK * SPT) + i * BLOCK + threadIdx.x;
@@ -276,21 +276,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
                 R sq = 0;
 #pragma unroll
                 for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-                nrm[i] = (double)sq;
+                nrm[i] = to_df(sq);
             }
         }
     }
-    if (NORM) chunk_reduce_finish<BLOCK, SPT>(nrm, a.g.vh, a.red);
+    if (NORM) warp_partials<BLOCK, SPT>(nrm, a.g.vh, a.red.partials);
 }
 
 // Launch configurations the tuner chooses from: threads per block, the
 // minimum resident blocks per SM handed to the register allocator, and
 // output sites per thread.  A fused norm adds in the same order under every
-// configuration (chunk_reduce_finish), so all variants use the tuned one.
+// configuration (warp_partials), so every variant can take its own tuned one.
 struct DslashCfg { int block, minb, spt; };
 constexpr int N_DSLASH_CFG = 5;
 constexpr DslashCfg DSLASH_CFGS[N_DSLASH_CFG] = {
-    {128, 1, 1}, {128, 8, 1}, {256, 1, 1}, {256, 4, 1}, {128, 1, 2}};
+    {128, 1, 1}, {128, 8, 1}, {128, 6, 1}, {256, 4, 1}, {128, 1, 2}};
 // The double-float hopping term (one site per thread, a loop over the hops)
 // has its own table: its register appetite makes the minimum resident blocks,
 // i.e. the register cap, the parameter that matters.
@@ -333,9 +333,12 @@ cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
     if (L.red) a.red = *L.red;
     else a.red = Reduction{nullptr, nullptr, nullptr, FIN_NONE};
     const int cfg = L.cfg;
-    if (L.red) {   // fused norm (after an xpay epilogue)
+    if (L.red) {   // fused norm (after an xpay epilogue), then the fixed-order finish
         if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_XPAY, 1>(cfg, a, s);
         else launch_any_cfg<S, R, RECON, 0, EPI_XPAY, 1>(cfg, a, s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_finish_partials(*L.red, (L.g.vh + 31) / 32, s);
     } else if (L.epi == EPI_PLAIN) {
         if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_PLAIN, 0>(cfg, a, s);
         else launch_any_cfg<S, R, RECON, 0, EPI_PLAIN, 0>(cfg, a, s);

@@ -33,7 +33,7 @@ __device__ __forceinline__ cdf sel(bool first, cdf a, cdf b) { return first ? a 
 
 template <int DAG, int EPI, int NORM, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64> a) {
-    double nrm[1] = {0.0};
+    df64 nrm[1] = {df64(0.0f, 0.0f)};
     const long h = (long)blockIdx.x * BLOCK + threadIdx.x;
     if (h < a.g.vh) {
         int c[4];
@@ -132,10 +132,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64
             df64 sq = 0;
 #pragma unroll
             for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-            nrm[0] = (double)sq;
+            nrm[0] = sq;
         }
     }
-    if (NORM) chunk_reduce_finish<BLOCK, 1>(nrm, a.g.vh, a.red);
+    if (NORM) warp_partials<BLOCK, 1>(nrm, a.g.vh, a.red.partials);
 }
 
 template <int DAG, int EPI, int NORM, int CFG>
@@ -174,6 +174,9 @@ cudaError_t launch_dslash_df64_r18(const DslashLaunch &L, cudaStream_t s) {
     if (L.red) {   // fused norm; the residuals never use it: one configuration
         if (L.dagger) launch_df<1, EPI_XPAY, 1, 0>(a, s);
         else launch_df<0, EPI_XPAY, 1, 0>(a, s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_finish_partials(a.red, (L.g.vh + 31) / 32, s);
     } else if (L.epi == EPI_PLAIN) {
         if (L.dagger) launch_df_cfg<1, EPI_PLAIN>(L.cfg, a, s);
         else launch_df_cfg<0, EPI_PLAIN>(L.cfg, a, s);

@@ -43,7 +43,7 @@ struct wd_op {
     double *stage_x = nullptr, *stage_b = nullptr;
 
     // reductions
-    double *partials = nullptr;
+    wd::df64 *partials = nullptr;
     unsigned int *counter = nullptr;
     SolverScalars *sc = nullptr;      // device
     SolverScalars *sc_host = nullptr; // pinned mirror
@@ -55,9 +55,10 @@ struct wd_op {
     double ru_delta = RU_DELTA_DEFAULT;
     int stall_iters = STALL_ITERS_DEFAULT;
 
-    // tuned launch configuration of the hopping term: [0] storage precision, [1] FP64
-    int cfg[2] = {0, 0};
-    double tune_us[2][8] = {};
+    // tuned launch configuration of the hopping term: [0] storage precision,
+    // [1] residual arithmetic, [2] storage precision with xpay and fused norm
+    int cfg[3] = {0, 0, 0};
+    double tune_us[3][8] = {};
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;
 
     // CUDA graphs of 2^k CGNR iterations, per solved parity

@@ -102,7 +102,7 @@ static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, con
     L.scale = scale;
     L.epi = x ? EPI_XPAY : EPI_PLAIN;
     L.red = red;
-    L.cfg = op->cfg[hi ? 1 : 0];
+    L.cfg = hi ? op->cfg[1] : red ? op->cfg[2] : op->cfg[0];
     WD_CUDA(launch_dslash(L, hi ? op->hi_prec : op->prec, op->stream));
     return WD_OK;
 }
@@ -121,42 +121,49 @@ static int check_op(const wd_op *op) {
     return WD_OK;
 }
 
-// Autotuner: time every launch configuration of the plain hopping term on
+// Autotuner: time every launch configuration of one hopping-term variant on
 // this operator's lattice (two warm-up and five timed launches each, CUDA
-// events on the work stream) and keep the fastest.  WD_DSLASH_CFG=k forces
+// events on the work stream) and keep the fastest.  Variant 0: the plain
+// storage-precision hop; 1: the plain residual-arithmetic hop; 2: the
+// storage-precision hop with xpay epilogue and fused norm (the reduction
+// result is the same under every configuration).  WD_DSLASH_CFG=k forces
 // configuration k, WD_TUNE=0 keeps configuration 0.
-static int tune_dslash(wd_op *op, bool hi) {
-    const int slot = hi ? 1 : 0;
+static int tune_dslash(wd_op *op, int variant) {
     const char *force = getenv("WD_DSLASH_CFG");
     const char *tune = getenv("WD_TUNE");
     if (force) {
         int k = atoi(force);
-        op->cfg[slot] = (k >= 0 && k < N_DSLASH_CFG) ? k : 0;
+        op->cfg[variant] = (k >= 0 && k < N_DSLASH_CFG) ? k : 0;
         return WD_OK;
     }
     if (tune && tune[0] == '0') {
-        op->cfg[slot] = 0;
+        op->cfg[variant] = 0;
         return WD_OK;
     }
+    const bool hi = variant == 1;
     void *in = hi ? (void *)op->th : op->slot[0];
     void *out = hi ? (void *)op->axh : op->slot[1];
+    Reduction red = reduction(op, FIN_STORE0);
+    auto launch = [&](int parity) {
+        if (variant == 2)   // out = out - kappa^2 H in, |out|^2 -> scratch
+            return dslash(op, false, parity, 0, out, in, out, -op->kappa * op->kappa, &red);
+        return dslash(op, hi, parity, 0, out, in, nullptr, 1.0, nullptr);
+    };
     int best = 0;
     float best_ms = 1e30f;
     for (int k = 0; k < N_DSLASH_CFG; ++k) {
-        op->cfg[slot] = k;
-        for (int w = 0; w < 2; ++w)
-            WD_TRY(dslash(op, hi, w & 1, 0, out, in, nullptr, 1.0, nullptr));
+        op->cfg[variant] = k;
+        for (int w = 0; w < 2; ++w) WD_TRY(launch(w & 1));
         WD_CUDA(cudaEventRecord(op->ev_t0, op->stream));
-        for (int r = 0; r < 5; ++r)
-            WD_TRY(dslash(op, hi, r & 1, 0, out, in, nullptr, 1.0, nullptr));
+        for (int r = 0; r < 5; ++r) WD_TRY(launch(r & 1));
         WD_CUDA(cudaEventRecord(op->ev_t1, op->stream));
         WD_CUDA(cudaEventSynchronize(op->ev_t1));
         float ms = 0;
         WD_CUDA(cudaEventElapsedTime(&ms, op->ev_t0, op->ev_t1));
-        op->tune_us[slot][k] = ms * 1e3 / 5;
+        op->tune_us[variant][k] = ms * 1e3 / 5;
         if (ms < best_ms) { best_ms = ms; best = k; }
     }
-    op->cfg[slot] = best;
+    op->cfg[variant] = best;
     return WD_OK;
 }
 
@@ -189,16 +196,16 @@ int wd_op_set_residual_precision(wd_op *op, int mode) {
     }
     op->hi_prec = want;
     op->gauge_hi.prec = want;
-    if (op->gauge_loaded) WD_TRY(tune_dslash(op, true));
+    if (op->gauge_loaded) WD_TRY(tune_dslash(op, 1));
     return join(op);
 }
 
 int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,
                      int *sites_per_thread) {
-    if (!op || (hi != 0 && hi != 1)) return -1;
+    if (!op || hi < 0 || hi > 2) return -1;
     const int k = op->cfg[hi];
     for (int i = 0; us && i < n && i < N_DSLASH_CFG; ++i) us[i] = op->tune_us[hi][i];
-    const DslashCfg &C = (hi && op->hi_prec == WD_DF64) ? DSLASH_DF_CFGS[k] : DSLASH_CFGS[k];
+    const DslashCfg &C = (hi == 1 && op->hi_prec == WD_DF64) ? DSLASH_DF_CFGS[k] : DSLASH_CFGS[k];
     if (block) *block = C.block;
     if (min_blocks) *min_blocks = C.minb;
     if (sites_per_thread) *sites_per_thread = C.spt;
@@ -285,8 +292,8 @@ static int create_impl(wd_op *op) {
     WD_TRY(dev_alloc(op, (void **)&op->stage_x, canon));
     WD_TRY(dev_alloc(op, (void **)&op->stage_b, canon));
     // reductions
-    WD_TRY(dev_alloc(op, (void **)&op->partials, sizeof(double) * reduction_blocks(g)));
-    WD_TRY(dev_alloc(op, (void **)&op->counter, sizeof(unsigned int) * 4));
+    WD_TRY(dev_alloc(op, (void **)&op->partials, sizeof(df64) * reduction_blocks(g)));
+    WD_TRY(dev_alloc(op, (void **)&op->counter, sizeof(unsigned int) * ARRIVE_WORDS));
     WD_TRY(dev_alloc(op, (void **)&op->sc, sizeof(SolverScalars)));
     WD_TRY(dev_alloc(op, (void **)&op->dev_consts, sizeof(double) * 4));
     WD_CUDA(cudaMallocHost((void **)&op->sc_host, sizeof(SolverScalars)));
@@ -341,8 +348,9 @@ int wd_op_set_gauge(wd_op *op, const double *U) {
     WD_TRY(fork(op));
     WD_CUDA(launch_pack_gauge(op->gauge_lo, op->g, U, op->stream));
     if (!op->hi_shared) WD_CUDA(launch_pack_gauge(op->gauge_hi, op->g, U, op->stream));
-    WD_TRY(tune_dslash(op, false));
-    if (!op->hi_shared) WD_TRY(tune_dslash(op, true));
+    WD_TRY(tune_dslash(op, 0));
+    WD_TRY(tune_dslash(op, 2));
+    if (!op->hi_shared) WD_TRY(tune_dslash(op, 1));
     else op->cfg[1] = op->cfg[0];
     WD_TRY(join(op));
     op->gauge_loaded = true;

@@ -337,7 +337,7 @@ enum FinalOp {
 // Partial sums of one reduction: one double per block, plus the arrival
 // counter of the last-block-done pattern (reset by the last block).
 struct Reduction {
-    double *partials;
+    df64 *partials;          // per-block or per-warp partial sums
     unsigned int *counter;
     SolverScalars *scalars;
     int op;
@@ -379,103 +379,130 @@ __device__ __forceinline__ void apply_final(SolverScalars *s, int op, double sum
     }
 }
 
-// Block-wide sum of v (every thread of the block must call), then the
+// Reductions add in double-float arithmetic (df64.cuh) on the FP32 pipes.
+// GB300 runs FP64 at a small fraction of its FP32 rate; a final pass over
+// tens of thousands of partials in FP64 inside one block took 10-15 us, and
+// FP64 shuffle trees in every warp of a hopping-term kernel added more.
+// Double-float keeps about 48 significand bits, ample for the scalars of
+// the iteration, and every sum below has a fixed tree, so results are
+// reproducible bit for bit.
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ df64 ldcg(const df64 *p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return df64(v.x, v.y);
+}
+__device__ __forceinline__ df64 to_df(float v) { return df64(v, 0.0f); }
+__device__ __forceinline__ df64 to_df(double v) { return df64(v); }
+__device__ __forceinline__ df64 to_df(df64 v) { return v; }
+
+__device__ __forceinline__ df64 warp_sum(df64 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = v + df64(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    return v;
+}
+
+// Arrival counting for "the last block to finish adds the partials".  One
+// counter for thousands of blocks serialises their atomics in one L2 slice,
+// so the count runs in two levels: block b bumps group counter b mod
+// ARRIVE_GROUPS, each on its own 128-byte line; the block that completes a
+// group bumps the top counter; the block that completes the top counter is
+// the last one.  Counters are reset by the blocks that complete them, so
+// they read zero again when the kernel ends.  Call from one thread after a
+// __threadfence() that publishes the block's partials; the caller fences
+// again before reading the other blocks' partials.
+constexpr int ARRIVE_GROUPS = 64;
+constexpr int ARRIVE_STRIDE = 32;   // unsigned ints per 128-byte line
+constexpr int ARRIVE_WORDS = ARRIVE_STRIDE * (ARRIVE_GROUPS + 1);
+
+__device__ __forceinline__ bool arrive_last(unsigned int *counters, unsigned int nblocks,
+                                            unsigned int b) {
+    const unsigned int g = b % ARRIVE_GROUPS;
+    const unsigned int group_size = (nblocks - g + ARRIVE_GROUPS - 1) / ARRIVE_GROUPS;
+    unsigned int *gc = counters + ARRIVE_STRIDE * (g + 1);
+    if (atomicAdd(gc, 1u) != group_size - 1) return false;
+    *gc = 0u;
+    __threadfence();
+    const unsigned int groups = nblocks < ARRIVE_GROUPS ? nblocks : ARRIVE_GROUPS;
+    if (atomicAdd(counters, 1u) != groups - 1) return false;
+    *counters = 0u;
+    return true;
+}
+
+// sum_k p[(lane + k * LANES) * es] for k = 0, 1, ... while the index is
+// below n, in that order.  The loads go out sixteen at a time so that a
+// pass over thousands of partials is not a chain of dependent L2 round
+// trips; the additions keep their order (out-of-range terms are zeros).
+template <int LANES, typename T>
+__device__ __forceinline__ T strided_sum(const T *p, long n, long lane, long es = 1) {
+    constexpr int DEPTH = 16;
+    T s = T(0);
+    for (long base = lane; base < n; base += (long)LANES * DEPTH) {
+        T t[DEPTH];
+#pragma unroll
+        for (int j = 0; j < DEPTH; ++j) {
+            const long i = base + (long)j * LANES;
+            t[j] = i < n ? ldcg(&p[i * es]) : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < DEPTH; ++j) s = s + t[j];
+    }
+    return s;
+}
+
+// Block-wide sum of v (every thread of the block calls it), then the
 // deterministic grid-wide finish: the last block to arrive adds the
 // per-block partials in block order and applies the final operation.
-template <int BLOCK>
-__device__ __forceinline__ void block_reduce_finish(double v, const Reduction &red) {
-    __shared__ double warp_sums[BLOCK / 32];
+template <int BLOCK, typename T>
+__device__ __forceinline__ void block_reduce_finish(T v_in, const Reduction &red) {
+    __shared__ df64 warp_sums[BLOCK / 32];
     __shared__ bool is_last;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    df64 v = warp_sum(to_df(v_in));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) warp_sums[wid] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0;
+        df64 s = 0;
 #pragma unroll
-        for (int i = 0; i < BLOCK / 32; ++i) s += warp_sums[i];
+        for (int i = 0; i < BLOCK / 32; ++i) s = s + warp_sums[i];
         red.partials[blockIdx.x] = s;
         __threadfence();
-        unsigned int prev = atomicAdd(red.counter, 1u);
-        is_last = (prev == gridDim.x - 1);
+        is_last = arrive_last(red.counter, gridDim.x, blockIdx.x);
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    double s = 0;
-    for (unsigned int i = threadIdx.x; i < gridDim.x; i += BLOCK)
-        s += __ldcg(&red.partials[i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    df64 s = warp_sum(strided_sum<BLOCK>(red.partials, gridDim.x, threadIdx.x));
+    __syncthreads();   // every thread has read warp_sums above
     if (lane == 0) warp_sums[wid] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0;
+        df64 t = 0;
 #pragma unroll
-        for (int i = 0; i < BLOCK / 32; ++i) t += warp_sums[i];
-        apply_final(red.scalars, red.op, t);
-        *red.counter = 0u;
+        for (int i = 0; i < BLOCK / 32; ++i) t = t + warp_sums[i];
+        apply_final(red.scalars, red.op, (double)t);
     }
 }
 
 // Sum of one value per output site whose rounding does not depend on the
-// launch configuration: fixed 128-site chunks (four 32-site warp sums added
-// in order) give the partials, and the last block to arrive adds them over
-// 128 strided lanes in a fixed tree.  Site h of a block is base + i * BLOCK
-// + threadIdx.x for i < SPT, and blocks cover whole chunks, so the chunk and
-// warp of every site, and with them every rounding, are the same for any
-// (BLOCK, SPT).  Sites past the end contribute exact zeros.
+// launch configuration, in two kernels.  The producing kernel writes one
+// partial per 32-site warp -- site h = base + i * BLOCK + threadIdx.x, so
+// warp w of step i covers sites [32 k, 32 k + 32) with k = (base + i * BLOCK)
+// / 32 + w -- with no barrier, fence or atomic: a block's threads retire as
+// soon as their sites are stored.  The one-block kernel behind
+// launch_finish_partials then adds the ceil(n_sites / 32) partials in a
+// fixed order and applies the final operation.  Sites past the end
+// contribute zeros.
 template <int BLOCK, int SPT>
-__device__ __forceinline__ void chunk_reduce_finish(const double (&v)[SPT], long n_sites,
-                                                    const Reduction &red) {
-    static_assert(BLOCK % 128 == 0, "blocks must cover whole 128-site chunks");
-    constexpr int W = BLOCK * SPT / 32;     // site warps per block
-    constexpr int C = W / 4;                // chunks per block
-    __shared__ double warp_sums[W];
-    __shared__ bool is_last;
+__device__ __forceinline__ void warp_partials(const df64 (&v)[SPT], long n_sites,
+                                              df64 *partials) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long n_warps = (n_sites + 31) / 32;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
-        double s = v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) warp_sums[i * (BLOCK / 32) + wid] = s;
-    }
-    __syncthreads();
-    const long n_chunks = (n_sites + 127) / 128;
-    if (threadIdx.x < C) {
-        const long chunk = (long)blockIdx.x * C + threadIdx.x;
-        if (chunk < n_chunks) {
-            double s = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) s += warp_sums[4 * threadIdx.x + j];
-            red.partials[chunk] = s;
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int prev = atomicAdd(red.counter, 1u);
-        is_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    double s = 0;
-    if (threadIdx.x < 128)
-        for (long i = threadIdx.x; i < n_chunks; i += 128) s += __ldcg(&red.partials[i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __syncthreads();   // the chunk sums above are read; reuse warp_sums
-    if (lane == 0 && wid < 4) warp_sums[wid] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) t += warp_sums[i];
-        apply_final(red.scalars, red.op, t);
-        *red.counter = 0u;
+        const df64 s = warp_sum(v[i]);
+        const long k = ((long)blockIdx.x * BLOCK * SPT + (long)i * BLOCK) / 32 + wid;
+        if (lane == 0 && k < n_warps) partials[k] = s;
     }
 }
 
@@ -521,6 +548,8 @@ cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction
                          cudaStream_t s);
 cudaError_t launch_xmy_norm(int prec, const Geom &g, void *out, const void *x, const void *y,
                             const Reduction &red, cudaStream_t s);
+// Adds the n partials warp_partials wrote (fixed order) and applies red.op.
+cudaError_t launch_finish_partials(const Reduction &red, long n, cudaStream_t s);
 cudaError_t launch_xpay_hi(int prec, const Geom &g, void *out, const void *y, double a,
                            const void *x, cudaStream_t s);
 cudaError_t launch_f64_df64(void *buf, long n_reals, int to_df, cudaStream_t s);

@@ -224,11 +224,15 @@ class WilsonDirac:
         """Residual arithmetic of the reliable updates: "f64" or "df64" (double-float)."""
         _check(self.lib.wd_op_set_residual_precision(self.handle, {"f64": 0, "df64": 1}[mode]))
 
-    def dslash_tuning(self, hi: bool = False) -> dict:
-        """The autotuner's choice for the hopping term and its per-candidate timings (us)."""
+    def dslash_tuning(self, hi: bool = False, norm: bool = False) -> dict:
+        """The autotuner's choice for the hopping term and its per-candidate
+        timings (us): storage precision (default), residual arithmetic
+        (hi=True), or the storage-precision variant with xpay and fused norm
+        (norm=True)."""
         us = (ctypes.c_double * 8)()
         blk, mb, spt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        k = self.lib.wd_dslash_tuning(self.handle, int(bool(hi)), us, 8, ctypes.byref(blk),
+        variant = 2 if norm else int(bool(hi))
+        k = self.lib.wd_dslash_tuning(self.handle, variant, us, 8, ctypes.byref(blk),
                                       ctypes.byref(mb), ctypes.byref(spt))
         return {"index": k, "block": blk.value, "min_blocks": mb.value,
                 "sites_per_thread": spt.value, "us": [round(v, 2) for v in us[:5]]}
