@@ -151,7 +151,7 @@ def kernel_source_sha() -> str:
     import hashlib
     csrc = os.path.join(ROOT, "paper_1401_2039_gb300", "csrc")
     src = b"".join(open(os.path.join(csrc, f), "rb").read()
-                   for f in ("dslash.cuh", "wd_internal.cuh"))
+                   for f in ("dslash.cuh", "wd_internal.cuh", "df64.cuh"))
     return hashlib.sha256(src).hexdigest()[:16]
 
 

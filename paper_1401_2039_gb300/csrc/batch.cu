@@ -24,7 +24,9 @@
 #include <string>
 #include <vector>
 
-#include "dslash.cuh"
+#include <type_traits>
+
+#include "dslash_df.cuh"
 
 namespace wd {
 
@@ -54,7 +56,7 @@ struct BtArgs {
     int parity;              // output parity of hopping terms
     int fin;                 // final operation applied per slot
     int nslots;
-    double *partials;        // [grid][BT_MAX_SLOTS]
+    df64 *partials;          // [grid][BT_MAX_SLOTS]
     unsigned int *counter;
     SolverScalars *scalars;  // [nslots]
     const double *consts;    // per-slot constants, [4][BT_MAX_SLOTS]
@@ -69,25 +71,26 @@ __device__ __forceinline__ int bt_problem(const BtArgs &a, long t) {
 }
 
 // Per-tile sum of v over the items of each rhs (fixed order), added to the
-// block's slot accumulators.  Every thread of the block must call.
-__device__ __forceinline__ void bt_tile_sums(double v, const BtProb &P, long item0, double *tv,
-                                             double *sacc) {
+// block's slot accumulators.  Every thread of the block must call.  Sums are
+// double-float: the FP64 adder of GB300 is too slow for per-item work.
+__device__ __forceinline__ void bt_tile_sums(df64 v, const BtProb &P, long item0, df64 *tv,
+                                             df64 *sacc) {
     tv[threadIdx.x] = v;
     __syncthreads();
     const int nr = P.nrhs;
     if ((int)threadIdx.x < nr) {
         const int j = threadIdx.x;
         const int i0 = (int)(((long)j - item0 % nr + nr) % nr);
-        double s = 0.0;
-        for (int i = i0; i < BT_BLOCK; i += nr) s += tv[i];
-        sacc[P.slot0 + j] += s;
+        df64 s = 0;
+        for (int i = i0; i < BT_BLOCK; i += nr) s = s + tv[i];
+        sacc[P.slot0 + j] = sacc[P.slot0 + j] + s;
     }
     __syncthreads();
 }
 
 // Grid-wide finish: per-block slot partials, then the last block adds them
 // in block order (one warp per slot) and applies the final operation.
-__device__ __forceinline__ void bt_finish(const BtArgs &a, const double *sacc) {
+__device__ __forceinline__ void bt_finish(const BtArgs &a, const df64 *sacc) {
     __shared__ bool last;
     for (int s = threadIdx.x; s < a.nslots; s += BT_BLOCK)
         a.partials[(long)blockIdx.x * BT_MAX_SLOTS + s] = sacc[s];
@@ -99,10 +102,8 @@ __device__ __forceinline__ void bt_finish(const BtArgs &a, const double *sacc) {
     __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int s = warp; s < a.nslots; s += BT_BLOCK / 32) {
-        double sum = strided_sum<32>(a.partials + s, gridDim.x, lane, BT_MAX_SLOTS);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) apply_final(&a.scalars[s], a.fin, sum);
+        const df64 sum = warp_sum(strided_sum<32>(a.partials + s, gridDim.x, lane, BT_MAX_SLOTS));
+        if (lane == 0) apply_final(&a.scalars[s], a.fin, (double)sum);
     }
 }
 
@@ -142,19 +143,22 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
 }
 
 // f[0] = out, f[1] = in, f[2] = x:  out = scale * H in  or  x + scale * H in
+// Double-float instances run the hop loop of dslash_df.cuh (unrolled, their
+// code outgrows the instruction cache) under a 168-register cap.
 template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM>
-__global__ void __launch_bounds__(BT_BLOCK) k_dslash_batch(const __grid_constant__ BtArgs a) {
-    __shared__ double tv[BT_BLOCK];
-    __shared__ double sacc[BT_MAX_SLOTS];
+__global__ void __launch_bounds__(BT_BLOCK, std::is_same<S, df64>::value ? 3 : 1)
+    k_dslash_batch(const __grid_constant__ BtArgs a) {
+    __shared__ df64 tv[BT_BLOCK];
+    __shared__ df64 sacc[BT_MAX_SLOTS];
     if (NORM) {
-        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = 0.0;
+        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = df64(0.0f, 0.0f);
         __syncthreads();
     }
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long item0 = (t - P.tile0) * BT_BLOCK;
         const long item = item0 + threadIdx.x;
-        double v = 0.0;
+        df64 v = 0;
         if (item < P.nitems) {
             const int nr = P.nrhs;
             const unsigned hu = (unsigned)item / (unsigned)nr;   // items < 2^31
@@ -165,10 +169,15 @@ __global__ void __launch_bounds__(BT_BLOCK) k_dslash_batch(const __grid_constant
             Acc<R> acc[24];
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
-            bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
-            bt_hop_pair<S, R, RECON, 1, DAG>(P, c, h, r, acc);
-            bt_hop_pair<S, R, RECON, 2, DAG>(P, c, h, r, acc);
-            bt_hop_pair<S, R, RECON, 3, DAG>(P, c, h, r, acc);
+            if constexpr (std::is_same<S, df64>::value) {
+                df_hops<DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                             P.g.stride * nr, nr, r, h, c, acc);
+            } else {
+                bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
+                bt_hop_pair<S, R, RECON, 1, DAG>(P, c, h, r, acc);
+                bt_hop_pair<S, R, RECON, 2, DAG>(P, c, h, r, acc);
+                bt_hop_pair<S, R, RECON, 3, DAG>(P, c, h, r, acc);
+            }
             const long ss = P.g.stride * nr;
             const R sc = (R)P.scale;
             R o[24];
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_dslash_batch(const __grid_constant
                 R sq = 0;
 #pragma unroll
                 for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-                v = (double)sq;
+                v = to_df(sq);
             }
         }
         if (NORM) bt_tile_sums(v, P, item0, tv, sacc);
@@ -202,18 +211,18 @@ enum BtOp { BT_XR = 0, BT_P = 1, BT_NORM = 2, BT_RESCALE = 3 };
 template <typename S, typename R, int OP>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtArgs a) {
     using C = Chunk16<S, R>;
-    __shared__ double tv[BT_BLOCK];
-    __shared__ double sacc[BT_MAX_SLOTS];
+    __shared__ df64 tv[BT_BLOCK];
+    __shared__ df64 sacc[BT_MAX_SLOTS];
     constexpr bool RED = OP == BT_XR || OP == BT_NORM;
     if (RED) {
-        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = 0.0;
+        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = df64(0.0f, 0.0f);
         __syncthreads();
     }
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long item0 = (t - P.tile0) * BT_BLOCK;
         const long i = item0 + threadIdx.x;
-        double v = 0.0;
+        df64 v = 0;
         if (i < P.nitems) {
             SolverScalars *s = &a.scalars[P.slot0 + (int)((unsigned)i % (unsigned)P.nrhs)];
             if (OP == BT_XR) {          // f = {x, r, p, Ap}: x += a p, r -= a Ap, |r|^2
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtA
                 }
                 C::store(P.f[0], i, xv);
                 C::store(P.f[1], i, rv);
-                v = (double)sq;
+                v = to_df(sq);
             } else if (OP == BT_P) {    // f = {p, z}: p = z + b p
                 const R be = (R)s->beta;
                 R pv[C::K], zv[C::K];
@@ -244,8 +253,10 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtA
             } else if (OP == BT_NORM) { // f = {v}
                 R vv[C::K];
                 C::load(P.f[0], i, vv);
+                R sq = 0;
 #pragma unroll
-                for (int k = 0; k < C::K; ++k) v += (double)vv[k] * (double)vv[k];
+                for (int k = 0; k < C::K; ++k) sq += vv[k] * vv[k];
+                v = to_df(sq);
             } else {                    // f = {p}: p *= ratio[slot]
                 const int slot = P.slot0 + (int)((unsigned)i % (unsigned)P.nrhs);
                 const R ratio = (R)a.consts[2 * BT_MAX_SLOTS + slot];
@@ -269,17 +280,17 @@ enum BtOp64 { BT64_XMY = 0, BT64_XPAY = 1 };
 template <typename H, int OP>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_hi(const __grid_constant__ BtArgs a) {
     using C = Chunk16<H, H>;
-    __shared__ double tv[BT_BLOCK];
-    __shared__ double sacc[BT_MAX_SLOTS];
+    __shared__ df64 tv[BT_BLOCK];
+    __shared__ df64 sacc[BT_MAX_SLOTS];
     if (OP == BT64_XMY) {
-        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = 0.0;
+        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = df64(0.0f, 0.0f);
         __syncthreads();
     }
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long item0 = (t - P.tile0) * BT_BLOCK;
         const long i = item0 + threadIdx.x;
-        double v = 0.0;
+        df64 v = 0;
         if (i < P.nitems) {
             H xv[C::K], yv[C::K], d[C::K];
             C::load(P.f[1], i, xv);
@@ -292,7 +303,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_hi(const __grid_constant__ BtAr
                 sq += d[k] * d[k];
             }
             C::store(P.f[0], i, d);
-            v = (double)sq;
+            v = to_df(sq);
         }
         if (OP == BT64_XMY) bt_tile_sums(v, P, item0, tv, sacc);
     }
@@ -302,29 +313,38 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_hi(const __grid_constant__ BtAr
 // Conversions over (site, rhs) items, with per-slot constants:
 //   CONV: f = {out (SO), in (SI)}: out = consts[0][slot] * in
 //   FOLD: f = {x_hi (H), x_lo (SI)}: x_hi += consts[1][slot] * x_lo; x_lo = 0
+template <typename H, typename T> __device__ __forceinline__ H widen(T v) { return H(v); }
+template <> __device__ __forceinline__ df64 widen<df64, float>(float v) { return df64(v, 0.0f); }
+
 template <typename SO, typename SI, int FOLD, typename H = double>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_conv(const __grid_constant__ BtArgs a) {
+    // intermediate: FP32 unless an FP64 field takes part (GB300's FP64
+    // adder is too slow for per-element work); double-float fields convert
+    // to and from FP32 on the FP32 pipes
+    constexpr bool F64 = std::is_same<SI, double>::value ||
+                         (FOLD ? std::is_same<H, double>::value : std::is_same<SO, double>::value);
+    using T = std::conditional_t<F64, double, float>;
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long i = (t - P.tile0) * BT_BLOCK + threadIdx.x;
         if (i >= P.nitems) continue;
         const int slot = P.slot0 + (int)((unsigned)i % (unsigned)P.nrhs);
         const long ss = P.g.stride * P.nrhs;
-        double v[24];
-        Rec<SI, 24>::template load_coherent<double>(P.f[1], ss, i, v);
-        if (FOLD) {
+        T v[24];
+        Rec<SI, 24>::template load_coherent<T>(P.f[1], ss, i, v);
+        if constexpr (FOLD != 0) {
             H hi[24];
             Rec<H, 24>::template load_coherent<H>(P.f[0], ss, i, hi);
             const H is = H(a.consts[BT_MAX_SLOTS + slot]);
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
-                hi[k] += is * H(v[k]);
-                v[k] = 0.0;
+                hi[k] += is * widen<H>(v[k]);
+                v[k] = T(0);
             }
             Rec<H, 24>::store(P.f[0], ss, i, hi);
             Rec<SI, 24>::store(P.f[1], ss, i, v);
         } else {
-            const double sc = a.consts[slot];
+            const T sc = (T)a.consts[slot];
 #pragma unroll
             for (int k = 0; k < 24; ++k) v[k] *= sc;
             Rec<SO, 24>::store(P.f[0], ss, i, v);
@@ -446,7 +466,7 @@ struct wd_batch {
     cudaStream_t user = nullptr, stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     BtFields fl[BT_MAX_PROB];
-    double *partials = nullptr;
+    df64 *partials = nullptr;
     unsigned int *counter = nullptr;
     SolverScalars *sc = nullptr, *sc_host = nullptr;
     double *consts = nullptr, *consts_host = nullptr;
@@ -900,7 +920,7 @@ static int batch_create_impl(wd_batch *bt) {
             BT_TRY(bt_alloc(bt, &bt->fl[p].f[f], is_lo ? lo : hi));
         }
     }
-    BT_TRY(bt_alloc(bt, (void **)&bt->partials, sizeof(double) * BT_GRID * BT_MAX_SLOTS));
+    BT_TRY(bt_alloc(bt, (void **)&bt->partials, sizeof(df64) * BT_GRID * BT_MAX_SLOTS));
     BT_TRY(bt_alloc(bt, (void **)&bt->counter, sizeof(unsigned int) * ARRIVE_WORDS));
     BT_TRY(bt_alloc(bt, (void **)&bt->sc, sizeof(SolverScalars) * BT_MAX_SLOTS));
     BT_TRY(bt_alloc(bt, (void **)&bt->consts, sizeof(double) * 4 * BT_MAX_SLOTS));

@@ -51,13 +51,22 @@ cudaError_t launch_finish_partials(const Reduction &red, long n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Per-thread accumulator of a norm: FP64 kernels keep FP64; FP32 arithmetic
+// accumulates its per-chunk sums in double-float (the FP64 adder of GB300 is
+// slow enough that one DADD per 16-byte chunk showed in the update kernel).
+template <typename R> struct ThreadAccOf { using T = df64; };
+template <> struct ThreadAccOf<double> { using T = double; };
+template <typename R> using ThreadAcc = typename ThreadAccOf<R>::T;
+template <typename R> __device__ __forceinline__ ThreadAcc<R> thread_term(R s) { return to_df(s); }
+template <> __device__ __forceinline__ double thread_term<double>(double s) { return s; }
+
 // x += alpha p;  r -= alpha Ap;  ||r||^2  (alpha from the device scalars)
 template <typename S, typename R>
 __global__ void __launch_bounds__(BLAS_BLOCK)
 k_cg_update_xr(long n, void *x, void *r, const void *p, const void *Ap, Reduction red) {
     using C = Chunk<S, R>;
     const R alpha = (R)red.scalars->alpha;
-    double acc = 0.0;
+    ThreadAcc<R> acc = 0;
     for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
          i += (long)gridDim.x * BLAS_BLOCK) {
         R xv[C::K], rv[C::K], pv[C::K], av[C::K];
@@ -74,7 +83,7 @@ k_cg_update_xr(long n, void *x, void *r, const void *p, const void *Ap, Reductio
         }
         C::store(x, i, xv);
         C::store(r, i, rv);
-        acc += (double)s;
+        acc = acc + thread_term<R>(s);
     }
     block_reduce_finish<BLAS_BLOCK>(acc, red);
 }
@@ -189,7 +198,7 @@ __global__ void k_f64_df64(long n, void *buf, int to_df) {
          i += (long)gridDim.x * BLAS_BLOCK) {
         if (to_df) {
             const double d = reinterpret_cast<double *>(buf)[i];
-            const df64 v(d);
+            const df64 v = split_double(d);
             reinterpret_cast<float2 *>(buf)[i] = make_float2(v.hi, v.lo);
         } else {
             const float2 f = reinterpret_cast<float2 *>(buf)[i];
@@ -201,13 +210,15 @@ __global__ void k_f64_df64(long n, void *buf, int to_df) {
 template <typename S, typename R>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_norm2(long n, const void *v, Reduction red) {
     using C = Chunk<S, R>;
-    double acc = 0.0;
+    ThreadAcc<R> acc = 0;
     for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
          i += (long)gridDim.x * BLAS_BLOCK) {
         R a[C::K];
         C::load(v, i, a);
+        R s = 0;
 #pragma unroll
-        for (int k = 0; k < C::K; ++k) acc += (double)a[k] * (double)a[k];
+        for (int k = 0; k < C::K; ++k) s += a[k] * a[k];
+        acc = acc + thread_term<R>(s);
     }
     block_reduce_finish<BLAS_BLOCK>(acc, red);
 }

@@ -16,14 +16,54 @@
 
 namespace wd {
 
+struct df64;
+__device__ df64 split_double(double d);
+
 struct __align__(8) df64 {
     float hi, lo;
     df64() = default;
     __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ constexpr df64(int v) : hi((float)v), lo(0.0f) {}
-    __host__ __device__ df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ df64(double d);
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
+
+// hi = d rounded to FP32, lo = (d - hi) rounded to FP32.  On the device the
+// split is done on the bit pattern: GB300's FP64 adder runs at a small
+// fraction of the FP32 rate (a DADD per element made the canonical-to-
+// double-float conversion three times slower than a copy), while integer
+// operations and the narrowing conversion do not touch it.  Exact halfway
+// cases of hi round away from zero instead of to even.  Zeros, values below
+// 2^-74 or from 2^127 in magnitude, infinities and NaNs take the FP64 route.
+__device__ __forceinline__ df64 split_double(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((u >> 52) & 0x7FF) - 1023;
+    if (e < -74 || e > 126) {
+        if ((u << 1) == 0) return df64(__double2float_rn(d), 0.0f);   // +-0
+        const float h = __double2float_rn(d);
+        return df64(h, __double2float_rn(d - (double)h));
+    }
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    unsigned int hb = ((unsigned int)(u >> 32) & 0x80000000u) |
+                      ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29);
+    int r = (int)(m & 0x1FFFFFFFu);          // the 29 bits below hi's last
+    if (r >= (1 << 28)) {                    // round hi up, remainder negative
+        hb += 1u;
+        r -= (1 << 29);
+    }
+    float lo = __int2float_rn(r) * __int_as_float((e - 52 + 127) << 23);
+    if (u >> 63) lo = -lo;
+    return df64(__uint_as_float(hb), lo);
+}
+
+__host__ __device__ inline df64::df64(double d) {
+#ifdef __CUDA_ARCH__
+    *this = split_double(d);
+#else
+    hi = (float)d;
+    lo = (float)(d - (double)(float)d);
+#endif
+}
 
 // The error-free transformations below spell every operation with the
 // round-to-nearest intrinsics: nvcc contracts a multiply feeding an add into

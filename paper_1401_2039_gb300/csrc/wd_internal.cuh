@@ -188,9 +188,9 @@ template <> struct Words<df64, double> {
     __device__ static void pack(const double *r, uint32_t *w, int n) {
 #pragma unroll
         for (int i = 0; i < n; ++i) {
-            const float h = __double2float_rn(r[i]);
-            w[2 * i] = __float_as_uint(h);
-            w[2 * i + 1] = __float_as_uint(__double2float_rn(r[i] - (double)h));
+            const df64 v = split_double(r[i]);
+            w[2 * i] = __float_as_uint(v.hi);
+            w[2 * i + 1] = __float_as_uint(v.lo);
         }
     }
 };
