@@ -57,6 +57,19 @@ def _load():
         lib.oracle_solve.argtypes = [dp, dp, dp, ip, ctypes.c_double, dp, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_int, ip]
         lib.oracle_solve.restype = ctypes.c_int
+        d = ctypes.c_double
+        lib.oracle_twist.argtypes = [dp, dp, ctypes.c_long, d, d, ctypes.c_int]
+        lib.oracle_twist.restype = ctypes.c_int
+        lib.oracle_apply_tm.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int]
+        lib.oracle_apply_eo_tm.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int, ctypes.c_int]
+        lib.oracle_schur_prepare_tm.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int]
+        lib.oracle_schur_reconstruct_tm.argtypes = [dp, dp, dp, dp, ip, d, d, dp, ctypes.c_int]
+        lib.oracle_cgnr_tm.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int, d, ctypes.c_int,
+                                       ip, dp]
+        lib.oracle_cgnr_tm.restype = ctypes.c_int
+        lib.oracle_solve_tm.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int, d, ctypes.c_int,
+                                        ip]
+        lib.oracle_solve_tm.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -190,8 +203,9 @@ def solve(b_full, U, dims, kappa, phase, parity=1, tol=1e-12, maxiter=10000):
     return x, it.value, rc == 0
 
 
-def dense_matrix(U, dims, kappa, phase, dagger=False) -> np.ndarray:
-    """D as a dense (12V x 12V) matrix, built column by column from ``apply``.
+def dense_matrix(U, dims, kappa, phase, dagger=False, mu=None) -> np.ndarray:
+    """D as a dense (12V x 12V) matrix, built column by column from ``apply``
+    (``apply_tm`` with the twisted mass mu when given).
     Row/column index = lex * 12 + colour * 4 + spin.  Small lattices only."""
     n = 12 * _vol(dims)
     if n > 12 * 4 ** 4:
@@ -201,5 +215,82 @@ def dense_matrix(U, dims, kappa, phase, dagger=False) -> np.ndarray:
     for j in range(n):
         e[:] = 0
         e[j] = 1
-        M[:, j] = apply(e.reshape(-1, 3, 4), U, dims, kappa, phase, dagger).reshape(n)
+        v = e.reshape(-1, 3, 4)
+        col = (apply(v, U, dims, kappa, phase, dagger) if mu is None
+               else apply_tm(v, U, dims, kappa, mu, phase, dagger))
+        M[:, j] = col.reshape(n)
     return M
+
+
+# ---------------------------------------------------------------- twisted mass
+# Fig. "dirac" with mu != 0: D = I + 2 i kappa mu gamma_5 - kappa H, whose
+# diagonal parity blocks A = I + 2 i kappa mu gamma_5 enter Alg. "schur".
+
+def twist(psi, kappa, mu, inverse=False) -> np.ndarray:
+    """A psi (or A^-1 psi) site by site, A = I + 2 i kappa mu gamma_5."""
+    psi = _c128(psi)
+    out = np.empty_like(psi)
+    rc = _load().oracle_twist(_dp(out), _dp(psi), psi.size // 12, float(kappa), float(mu),
+                              int(bool(inverse)))
+    if rc != 0:
+        raise RuntimeError("gamma_5 of the oracle's basis is not diagonal")
+    return out
+
+
+def apply_tm(psi, U, dims, kappa, mu, phase, dagger=False) -> np.ndarray:
+    """D psi = A psi - kappa H psi (dagger: A(-mu) psi - kappa H^dag psi)."""
+    psi, U = _c128(psi), _c128(U)
+    out = np.empty_like(psi)
+    _load().oracle_apply_tm(_dp(out), _dp(psi), _dp(U), _dims(dims), float(kappa), float(mu),
+                            _dp(_phase(phase)), int(bool(dagger)))
+    return out
+
+
+def apply_eo_tm(psi_half, U, dims, kappa, mu, phase, parity=1, dagger=False) -> np.ndarray:
+    """Mhat_p = A - kappa^2 P_p H P_q^t A^-1 P_q H P_p^t (dagger: H^dag, -mu)."""
+    psi_half, U = _c128(psi_half), _c128(U)
+    out = np.empty_like(psi_half)
+    _load().oracle_apply_eo_tm(_dp(out), _dp(psi_half), _dp(U), _dims(dims), float(kappa),
+                               float(mu), _dp(_phase(phase)), int(parity), int(bool(dagger)))
+    return out
+
+
+def schur_prepare_tm(b_full, U, dims, kappa, mu, phase, parity=1) -> np.ndarray:
+    """bhat_p = b_p + kappa P_p H P_q^t A^-1 b_q."""
+    b_full, U = _c128(b_full), _c128(U)
+    out = np.empty((_vol(dims) // 2, 3, 4), dtype=np.complex128)
+    _load().oracle_schur_prepare_tm(_dp(out), _dp(b_full), _dp(U), _dims(dims), float(kappa),
+                                    float(mu), _dp(_phase(phase)), int(parity))
+    return out
+
+
+def schur_reconstruct_tm(x_half, b_full, U, dims, kappa, mu, phase, parity=1) -> np.ndarray:
+    """Full solution from x_p: x_q = A^-1 (b_q + kappa P_q H P_p^t x_p)."""
+    x_half, b_full, U = _c128(x_half), _c128(b_full), _c128(U)
+    out = np.empty_like(b_full)
+    _load().oracle_schur_reconstruct_tm(_dp(out), _dp(x_half), _dp(b_full), _dp(U), _dims(dims),
+                                        float(kappa), float(mu), _dp(_phase(phase)), int(parity))
+    return out
+
+
+def cgnr_tm(b_half, U, dims, kappa, mu, phase, parity=1, tol=1e-12, maxiter=10000):
+    """Alg. CGNR on the twisted-mass Mhat_p.  Returns (x, iterations, converged, history)."""
+    b_half, U = _c128(b_half), _c128(U)
+    x = np.empty_like(b_half)
+    it = ctypes.c_int(0)
+    hist = np.zeros(maxiter + 1, dtype=np.float64)
+    rc = _load().oracle_cgnr_tm(_dp(x), _dp(b_half), _dp(U), _dims(dims), float(kappa), float(mu),
+                                _dp(_phase(phase)), int(parity), float(tol), int(maxiter),
+                                ctypes.byref(it), _dp(hist))
+    return x, it.value, rc == 0, hist[: it.value + 1].copy()
+
+
+def solve_tm(b_full, U, dims, kappa, mu, phase, parity=1, tol=1e-12, maxiter=10000):
+    """x = D^-1 b with the twisted mass ("CGNR schur").  Returns (x, iterations, converged)."""
+    b_full, U = _c128(b_full), _c128(U)
+    x = np.empty_like(b_full)
+    it = ctypes.c_int(0)
+    rc = _load().oracle_solve_tm(_dp(x), _dp(b_full), _dp(U), _dims(dims), float(kappa), float(mu),
+                                 _dp(_phase(phase)), int(parity), float(tol), int(maxiter),
+                                 ctypes.byref(it))
+    return x, it.value, rc == 0

@@ -9,7 +9,9 @@
  * What it computes (Barthou et al., "Automated Code Generation for Lattice
  * QCD and beyond", arXiv:1401.2039):
  *
- *   D = I - kappa * H                         (Fig. "dirac", with mu = 0)
+ *   D = I - kappa * H                         (Fig. "dirac", with mu = 0;
+ *                                              the twisted mass mu != 0 is
+ *                                              in the *_tm functions below)
  *   (H psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x)       phi_mu(x)  psi(x+mu)
  *                        + (1 + gamma_mu) U_mu(x-mu)^dag phi_mu*(x) psi(x-mu) ]
  *
@@ -369,6 +371,174 @@ int oracle_solve(double *x_full, const double *b_full, const double *U, const in
     int rc = oracle_cgnr((double *)xp, (double *)bhat, U, dims, kappa, phase, parity,
                          rel, maxiter, iters_out, NULL);
     oracle_schur_reconstruct(x_full, (double *)xp, b_full, U, dims, kappa, phase, parity);
+    free(bhat); free(xp);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Twisted mass (Fig. "dirac" with mu != 0):
+ *   D = I + 2 i kappa mu (I_L (x) I_C (x) gamma_5) - kappa H.
+ * The diagonal blocks D_ee = D_oo = A := I + 2 i kappa mu gamma_5 act on the
+ * spin index of each site alone.  Fig. "id" states that gamma_5 is diagonal,
+ * so A is diagonal and A^-1 has the reciprocal diagonal entries; this code
+ * checks the diagonality of its own gamma_5 (the product of the four gamma
+ * matrices) instead of assuming a basis.  Because gamma_5 is hermitian,
+ * D^dag = I - 2 i kappa mu gamma_5 - kappa H^dag: the adjoint flips mu.
+ *
+ * out = A in (inverse = 0) or A^-1 in (inverse = 1) on n sites.
+ * Returns 0, or -1 if gamma_5 is not diagonal.                            */
+int oracle_twist(double *out_, const double *in_, long n, double kappa, double mu, int inverse) {
+    cplx g5[4][4];
+    gamma_matrix(4, g5);
+    cplx d[4];
+    for (int s = 0; s < 4; ++s) {
+        for (int t = 0; t < 4; ++t)
+            if (t != s && cabs(g5[s][t]) != 0.0) return -1;
+        const cplx a = 1.0 + 2.0 * I * kappa * mu * g5[s][s];   /* A_ss */
+        d[s] = inverse ? 1.0 / a : a;
+    }
+    cplx *out = (cplx *)out_;
+    const cplx *in = (const cplx *)in_;
+    for (long site = 0; site < n; ++site)
+        for (int c = 0; c < 3; ++c)
+            for (int s = 0; s < 4; ++s)
+                out[site * 12 + 4 * c + s] = d[s] * in[site * 12 + 4 * c + s];
+    return 0;
+}
+
+/* out = D in with the twisted mass (dagger: D^dag in = A(-mu) in - kappa H^dag in). */
+void oracle_apply_tm(double *out_, const double *in_, const double *U, const int *dims,
+                     double kappa, double mu, const double *phase, int dagger) {
+    geom g = make_geom(dims);
+    cplx *out = (cplx *)out_;
+    cplx *h = (cplx *)malloc(sizeof(cplx) * 12 * g.vol);
+    cplx *a = (cplx *)malloc(sizeof(cplx) * 12 * g.vol);
+    oracle_hop((double *)h, in_, U, dims, phase, dagger);
+    oracle_twist((double *)a, in_, g.vol, kappa, dagger ? -mu : mu, 0);
+    for (long i = 0; i < 12 * g.vol; ++i) out[i] = a[i] - kappa * h[i];
+    free(h); free(a);
+}
+
+/* Schur operator with the twisted mass on parity p (q = 1 - p):
+ *   Mhat_p = D_pp - D_pq D_qq^-1 D_qp = A - kappa^2 P_p H P_q^t A^-1 P_q H P_p^t
+ * dagger: the same with H^dag and -mu.                                    */
+void oracle_apply_eo_tm(double *out_, const double *in_, const double *U, const int *dims,
+                        double kappa, double mu, const double *phase, int parity, int dagger) {
+    geom g = make_geom(dims);
+    long vh = g.vol / 2;
+    int q = 1 - parity;
+    double m = dagger ? -mu : mu;
+    cplx *t = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *ti = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *u = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *ax = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    oracle_hop_eo((double *)t, in_, U, dims, phase, q, dagger);       /* D_qp-part: H_qp x */
+    oracle_twist((double *)ti, (double *)t, vh, kappa, m, 1);         /* A^-1 H_qp x       */
+    oracle_hop_eo((double *)u, (double *)ti, U, dims, phase, parity, dagger);
+    oracle_twist((double *)ax, in_, vh, kappa, m, 0);                 /* A x               */
+    cplx *out = (cplx *)out_;
+    for (long i = 0; i < 12 * vh; ++i) out[i] = ax[i] - kappa * kappa * u[i];
+    free(t); free(ti); free(u); free(ax);
+}
+
+/* Alg. "schur" with the twisted mass:
+ *   bhat_p = b_p - D_pq D_qq^-1 b_q = b_p + kappa P_p H P_q^t A^-1 b_q
+ *   x_q = D_qq^-1 (b_q - D_qp x_p) = A^-1 (b_q + kappa P_q H P_p^t x_p).    */
+void oracle_schur_prepare_tm(double *bhat_, const double *b_full, const double *U,
+                             const int *dims, double kappa, double mu, const double *phase,
+                             int parity) {
+    geom g = make_geom(dims);
+    long vh = g.vol / 2;
+    int q = 1 - parity;
+    cplx *bq = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *bqi = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *bp = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *hb = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    project_half(&g, bq, (const cplx *)b_full, q);
+    project_half(&g, bp, (const cplx *)b_full, parity);
+    oracle_twist((double *)bqi, (double *)bq, vh, kappa, mu, 1);
+    oracle_hop_eo((double *)hb, (double *)bqi, U, dims, phase, parity, 0);
+    cplx *bhat = (cplx *)bhat_;
+    for (long i = 0; i < 12 * vh; ++i) bhat[i] = bp[i] + kappa * hb[i];
+    free(bq); free(bqi); free(bp); free(hb);
+}
+
+void oracle_schur_reconstruct_tm(double *x_full, const double *x_p, const double *b_full,
+                                 const double *U, const int *dims, double kappa, double mu,
+                                 const double *phase, int parity) {
+    geom g = make_geom(dims);
+    long vh = g.vol / 2;
+    int q = 1 - parity;
+    cplx *bq = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *hx = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *v = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *xq = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    project_half(&g, bq, (const cplx *)b_full, q);
+    oracle_hop_eo((double *)hx, x_p, U, dims, phase, q, 0);
+    for (long i = 0; i < 12 * vh; ++i) v[i] = bq[i] + kappa * hx[i];
+    oracle_twist((double *)xq, (double *)v, vh, kappa, mu, 1);
+    cplx *x = (cplx *)x_full;
+    cplx *a = (cplx *)malloc(sizeof(cplx) * 12 * g.vol);
+    embed_half(&g, x, (const cplx *)x_p, parity);
+    embed_half(&g, a, xq, q);
+    for (long i = 0; i < 12 * g.vol; ++i) x[i] += a[i];
+    free(bq); free(hx); free(v); free(xq); free(a);
+}
+
+/* Alg. "CGNR" on the twisted-mass Schur operator (the same loop as
+ * oracle_cgnr, with Mhat_p of oracle_apply_eo_tm).                          */
+int oracle_cgnr_tm(double *x_, const double *b_, const double *U, const int *dims,
+                   double kappa, double mu, const double *phase, int parity, double tol,
+                   int maxiter, int *iters_out, double *resid) {
+    geom g = make_geom(dims);
+    long n = 12 * (g.vol / 2);
+    cplx *x = (cplx *)x_;
+    const cplx *b = (const cplx *)b_;
+    cplx *r = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *z = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *p = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *Ap = (cplx *)malloc(sizeof(cplx) * n);
+    memcpy(r, b, sizeof(cplx) * n);
+    oracle_apply_eo_tm((double *)z, (double *)r, U, dims, kappa, mu, phase, parity, 1);
+    memcpy(p, z, sizeof(cplx) * n);
+    memset(x, 0, sizeof(cplx) * n);
+    double nz = norm2(z, n);
+    double nr = norm2(r, n);
+    double eps = tol * tol * norm2(b, n);
+    int k = 0;
+    if (resid) resid[0] = sqrt(nr);
+    while (nr > eps && k < maxiter) {
+        oracle_apply_eo_tm((double *)Ap, (double *)p, U, dims, kappa, mu, phase, parity, 0);
+        double alpha = nz / norm2(Ap, n);
+        for (long i = 0; i < n; ++i) x[i] += alpha * p[i];
+        for (long i = 0; i < n; ++i) r[i] -= alpha * Ap[i];
+        oracle_apply_eo_tm((double *)z, (double *)r, U, dims, kappa, mu, phase, parity, 1);
+        double nz1 = norm2(z, n);
+        for (long i = 0; i < n; ++i) p[i] = z[i] + (nz1 / nz) * p[i];
+        nz = nz1;
+        nr = norm2(r, n);
+        ++k;
+        if (resid) resid[k] = sqrt(nr);
+    }
+    if (iters_out) *iters_out = k;
+    free(r); free(z); free(p); free(Ap);
+    return nr > eps ? 1 : 0;
+}
+
+int oracle_solve_tm(double *x_full, const double *b_full, const double *U, const int *dims,
+                    double kappa, double mu, const double *phase, int parity, double tol,
+                    int maxiter, int *iters_out) {
+    geom g = make_geom(dims);
+    long vh = g.vol / 2;
+    cplx *bhat = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *xp = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    oracle_schur_prepare_tm((double *)bhat, b_full, U, dims, kappa, mu, phase, parity);
+    double nb = sqrt(norm2((const cplx *)b_full, 12 * g.vol));
+    double nbh = sqrt(norm2(bhat, 12 * vh));
+    double rel = nbh > 0 ? tol * nb / nbh : tol;
+    int rc = oracle_cgnr_tm((double *)xp, (double *)bhat, U, dims, kappa, mu, phase, parity,
+                            rel, maxiter, iters_out, NULL);
+    oracle_schur_reconstruct_tm(x_full, (double *)xp, b_full, U, dims, kappa, mu, phase, parity);
     free(bhat); free(xp);
     return rc;
 }

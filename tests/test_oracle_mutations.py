@@ -26,11 +26,19 @@ MUTANTS = [
      "xq[i] = 2 * kappa * bq[i] + kappa * hx[i];"),
     ("CGNR beta inverted", "double beta = nz1 / nz;", "double beta = nz / nz1;"),
     ("gamma_x sign slip", "g[0][3] = I;  g[1][2] = I;", "g[0][3] = -I;  g[1][2] = I;"),
+    ("twisted mass without its factor 2", "const cplx a = 1.0 + 2.0 * I * kappa * mu * g5[s][s];",
+     "const cplx a = 1.0 + I * kappa * mu * g5[s][s];"),
+    ("adjoint keeps the sign of mu", "double m = dagger ? -mu : mu;", "double m = mu;"),
+    ("A instead of A^-1 in the reconstruction",
+     "oracle_twist((double *)xq, (double *)v, vh, kappa, mu, 1);",
+     "oracle_twist((double *)xq, (double *)v, vh, kappa, mu, 0);"),
 ]
 
 FAST_PINS = ("test_gamma_basis_clifford or test_free_field_plane_waves or "
              "test_gamma5_hermiticity or test_gauge_covariance or "
-             "test_schur_blocks_dense or test_cgnr_schur_solve_matches_lu")
+             "test_schur_blocks_dense or test_cgnr_schur_solve_matches_lu or "
+             "test_twisted_free_field or test_twisted_adjoint_flips_mu or "
+             "test_twisted_solve_matches_lu")
 
 
 @pytest.mark.parametrize("desc,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])

@@ -278,3 +278,117 @@ def test_recursive_residual_tracks_true_residual(oracle_lib):
         assert iters == it and not ok
         r_true = bh - oracle_lib.apply_eo(x, U, dims, kappa, phase, par)
         assert abs(np.linalg.norm(r_true) - hist[-1]) < 1e-12 * hist[0]
+
+
+# ---------------------------------------------------------------------------
+# Twisted mass (Fig. dirac with mu != 0): D = 1 + 2 i kappa mu gamma5 - kappa H.
+@pytest.mark.parametrize("mu", [0.05, -0.3])
+def test_twisted_free_field(oracle_lib, mu):
+    """Unit links, plane waves: D acts on the spin index as
+    (1 - 2 kappa sum cos p) + 2 i kappa mu gamma5 + 2 i kappa sum gamma_mu sin p_mu,
+    whose eigenvalues are m +- i sqrt((2 kappa mu)^2 + sum (2 kappa sin p)^2)
+    (gamma5 anticommutes with every gamma_mu and all square to one)."""
+    dims, kappa = (4, 2, 4, 6), 0.11
+    theta = (0.0, 0.0, 0.0, np.pi)
+    U = syn.unit_links(dims)
+    phase = np.exp(1j * np.asarray(theta))
+    X = syn.coords(dims)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        n = [rng.integers(0, L) for L in dims]
+        p = np.array([(2 * np.pi * n[m] + theta[m]) / dims[m] for m in range(4)])
+        wave = np.exp(1j * (X @ p))
+        m0 = 1 - 2 * kappa * np.cos(p).sum()
+        M_exact = m0 * np.eye(4) + 2j * kappa * mu * G5 + 2j * kappa * sum(
+            GAMMA_DR[k] * np.sin(p[k]) for k in range(4))
+        M = np.zeros((4, 4), dtype=complex)
+        for s0 in range(4):
+            psi = np.zeros((len(wave), 3, 4), dtype=complex)
+            psi[:, 1, s0] = wave
+            out = oracle_lib.apply_tm(psi, U, dims, kappa, mu, phase)
+            col = out[:, 1, :] / wave[:, None]
+            assert np.abs(col - col[0]).max() < 1e-13
+            M[:, s0] = col[0]
+        assert np.abs(M - M_exact).max() < 1e-13
+        ev = np.linalg.eigvals(M)
+        ev = ev[np.argsort(ev.imag)]
+        w = np.sqrt((2 * kappa * mu) ** 2 + ((2 * kappa * np.sin(p)) ** 2).sum())
+        ref = np.array([m0 - 1j * w] * 2 + [m0 + 1j * w] * 2)
+        assert np.abs(ev - ref).max() < 1e-7
+
+
+def test_twisted_adjoint_flips_mu(oracle_lib):
+    """D(mu)^dag = gamma5 D(-mu) gamma5 (gamma5 hermitian and diagonal,
+    gamma5 H gamma5 = H^dag), for D and for the Schur operator."""
+    dims, kappa, mu = (4, 4, 2, 4), 0.12, 0.2
+    phase = np.exp(1j * np.array([0.4, 0.0, -0.7, np.pi]))
+    U = syn.su3_links(dims, eps=0.3, seed=5)
+    V = syn.volume(dims)
+    phi, psi = syn.gaussian_spinor(V, 8), syn.gaussian_spinor(V, 9)
+    Dpsi = oracle_lib.apply_tm(psi, U, dims, kappa, mu, phase)
+    Ddphi = oracle_lib.apply_tm(phi, U, dims, kappa, mu, phase, dagger=True)
+    assert abs(inner(phi, Dpsi) - inner(Ddphi, psi)) < 1e-12 * abs(inner(phi, Dpsi))
+    assert relerr(Ddphi, g5(oracle_lib.apply_tm(g5(phi), U, dims, kappa, -mu, phase))) < 1e-14
+    # the twist is not invisible to the adjoint: D(mu)^dag != gamma5 D(mu) gamma5
+    assert relerr(Ddphi, g5(oracle_lib.apply_tm(g5(phi), U, dims, kappa, mu, phase))) > 1e-2
+    for par in (0, 1):
+        ph, ps = syn.to_half(phi, dims, par), syn.to_half(psi, dims, par)
+        Mps = oracle_lib.apply_eo_tm(ps, U, dims, kappa, mu, phase, par)
+        Mdph = oracle_lib.apply_eo_tm(ph, U, dims, kappa, mu, phase, par, dagger=True)
+        assert abs(inner(ph, Mps) - inner(Mdph, ps)) < 1e-12 * abs(inner(ph, Mps))
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 2, 2)])
+def test_twisted_schur_blocks_dense(oracle_lib, dims):
+    """Dense D(mu): the diagonal parity blocks are 1 + 2 i kappa mu gamma5 on
+    every site, and Mhat_p = D_pp - D_pq D_qq^-1 D_qp (Alg. schur)."""
+    kappa, mu = 0.12, 0.15
+    phase = syn.workloads.APBC_T
+    U = syn.su3_links(dims, eps=0.3, seed=21)
+    D = oracle_lib.dense_matrix(U, dims, kappa, phase, mu=mu)
+    ie, io = _parity_perm(dims)
+    n = len(ie)
+    A = np.kron(np.eye(n // 12), np.kron(np.eye(3), np.eye(4) + 2j * kappa * mu * G5))
+    assert np.abs(D[np.ix_(ie, ie)] - A).max() < 1e-15
+    assert np.abs(D[np.ix_(io, io)] - A).max() < 1e-15
+    for par, (ip, iq) in ((0, (ie, io)), (1, (io, ie))):
+        ref = D[np.ix_(ip, ip)] - D[np.ix_(ip, iq)] @ np.linalg.solve(D[np.ix_(iq, iq)],
+                                                                         D[np.ix_(iq, ip)])
+        Mhat = np.empty((n, n), dtype=complex)
+        e = np.zeros(n, dtype=complex)
+        for j in range(n):
+            e[:] = 0
+            e[j] = 1
+            Mhat[:, j] = oracle_lib.apply_eo_tm(e.reshape(-1, 3, 4), U, dims, kappa, mu, phase,
+                                                par).ravel()
+        assert np.abs(Mhat - ref).max() < 1e-14
+    Dd = oracle_lib.dense_matrix(U, dims, kappa, phase, dagger=True, mu=mu)
+    assert np.abs(Dd - D.conj().T).max() < 1e-15
+
+
+@pytest.mark.parametrize("dims,parity", [((2, 2, 2, 2), 1), ((4, 4, 4, 4), 0)])
+def test_twisted_solve_matches_lu(oracle_lib, dims, parity):
+    """Schur prepare, CGNR and reconstruction with the twisted mass give the
+    dense LU solution of D(mu) x = b."""
+    kappa, mu = 0.124, 0.1
+    phase = syn.workloads.APBC_T
+    U = syn.su3_links(dims, eps=0.3, seed=1)
+    b = syn.gaussian_spinor(syn.volume(dims), 2)
+    D = oracle_lib.dense_matrix(U, dims, kappa, phase, mu=mu)
+    x, iters, ok = oracle_lib.solve_tm(b, U, dims, kappa, mu, phase, parity=parity, tol=1e-13)
+    assert ok and iters > 0
+    assert np.linalg.norm(b.ravel() - D @ x.ravel()) <= 1.01e-13 * np.linalg.norm(b)
+    x_lu = np.linalg.solve(D, b.ravel())
+    assert relerr(x.ravel(), x_lu) < 10 * np.linalg.cond(D) * 1e-13
+
+
+def test_twisted_mass_zero_is_the_wilson_operator(oracle_lib):
+    dims, kappa = (4, 4, 2, 4), 0.12
+    phase = syn.workloads.APBC_T
+    U = syn.su3_links(dims, seed=3)
+    psi = syn.gaussian_spinor(syn.volume(dims), 1)
+    assert relerr(oracle_lib.apply_tm(psi, U, dims, kappa, 0.0, phase),
+                  oracle_lib.apply(psi, U, dims, kappa, phase)) < 1e-15
+    h = syn.to_half(psi, dims, 1)
+    assert relerr(oracle_lib.apply_eo_tm(h, U, dims, kappa, 0.0, phase, 1),
+                  oracle_lib.apply_eo(h, U, dims, kappa, phase, 1)) < 1e-15
