@@ -142,6 +142,21 @@ int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters);
  * use FP64 (mode 1 is rejected).  Not in the paper. */
 int wd_op_set_residual_precision(wd_op *op, int mode);
 
+/* Twisted mass (Fig. "dirac": D = 1 + 2 i kappa mu gamma5 - kappa H; the
+ * handle starts with mu = 0, the Wilson operator).  With mu != 0 every
+ * operator call of the handle includes the term: wd_apply applies D (the
+ * adjoint flips the sign of mu), wd_apply_eo and wd_apply_eo_residual apply
+ * Mhat_p = A - kappa^2 H_pq A^-1 H_qp with A = 1 + 2 i kappa mu gamma5 (the
+ * diagonal block D11 of Alg. "schur", inverted site by site), and
+ * wd_solve_cg solves D x = b through bhat_p = b_p + kappa H_pq A^-1 b_q and
+ * x_q = A^-1 (b_q + kappa H_qp x_p).  wd_dslash_eo stays the bare hopping
+ * term; wd_apply_eo_noalloc and batches (wd_batch_*) have no twisted mass
+ * (a batch over a twisted handle returns WD_ERR_ARG).  mu must be finite
+ * (WD_ERR_ARG otherwise). */
+int wd_op_set_twisted_mass(wd_op *op, double mu);
+/* The handle's mu (0 for a null handle). */
+double wd_op_twisted_mass(const wd_op *op);
+
 /* The same solve with x and b in HOST memory (pageable or pinned); the
  * host<->device copies go through buffers the handle owns. */
 int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,

@@ -940,6 +940,8 @@ int wd_batch_create(wd_batch **out, wd_op *const *ops, const int *nrhs, int nops
         if (!ops[p] || !ops[p]->gauge_loaded)
             return bt_fail(WD_ERR_STATE, "every operator needs its gauge field loaded");
         if (nrhs[p] < 1) return bt_fail(WD_ERR_ARG, "nrhs must be >= 1");
+        if (ops[p]->mu != 0.0)
+            return bt_fail(WD_ERR_ARG, "batches have no twisted mass (mu must be 0)");
         if (ops[p]->prec != ops[0]->prec || ops[p]->recon != ops[0]->recon ||
             ops[p]->hi_prec != ops[0]->hi_prec)
             return bt_fail(WD_ERR_ARG,
@@ -989,6 +991,9 @@ int wd_batch_dslash(wd_batch *bt, double *const *out, const double *const *in, i
     if (!bt || !out || !in) return bt_fail(WD_ERR_ARG, "null argument to wd_batch_dslash");
     if (out_parity != 0 && out_parity != 1) return bt_fail(WD_ERR_ARG, "parity must be 0 or 1");
     if (dagger != 0 && dagger != 1) return bt_fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    for (int p = 0; p < bt->nprob; ++p)
+        if (bt->ops[p]->mu != 0.0)
+            return bt_fail(WD_ERR_ARG, "batches have no twisted mass (mu must be 0)");
     BT_TRY(bt_fork(bt));
     for (int p = 0; p < bt->nprob; ++p) {
         const wd_op *op = bt->ops[p];
@@ -1028,6 +1033,9 @@ int wd_batch_solve(wd_batch *bt, double *const *x, const double *const *b, doubl
     if (!bt || !x || !b) return bt_fail(WD_ERR_ARG, "null argument to wd_batch_solve");
     if (parity != 0 && parity != 1) return bt_fail(WD_ERR_ARG, "parity must be 0 or 1");
     if (!(tol > 0) || maxiter < 0) return bt_fail(WD_ERR_ARG, "tol must be > 0, maxiter >= 0");
+    for (int p = 0; p < bt->nprob; ++p)
+        if (bt->ops[p]->mu != 0.0)
+            return bt_fail(WD_ERR_ARG, "batches have no twisted mass (mu must be 0)");
     if (info) memset(info, 0, sizeof(wd_solve_info) * bt->nslots);
     BT_TRY(bt_fork(bt));
     const int rc = bt_solve_impl(bt, x, b, tol, maxiter, parity, info);

@@ -361,6 +361,36 @@ cudaError_t launch_xpay_hi(int prec, const Geom &g, void *out, const void *y, do
     return cudaGetLastError();
 }
 
+// out = c (1 + i t gamma5) in over 16-byte chunks of an FP64 or double-float
+// field: chunk i holds the complex component j = i / stride of its site, j =
+// 4 colour + spin, and gamma5 = diag(1, 1, -1, -1) on the spin.
+template <typename H>
+__global__ void __launch_bounds__(BLAS_BLOCK)
+k_twist_hi(long n, long stride, void *out, const void *in, H t, H c) {
+    using C = Chunk16<H, H>;
+    for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
+         i += (long)gridDim.x * BLAS_BLOCK) {
+        H v[C::K];
+        C::load(in, i, v);
+        const int spin = (int)((i / stride) & 3);
+        const H ts = spin < 2 ? t : -t;
+        const H re = v[0], im = v[1];
+        v[0] = c * (re - ts * im);
+        v[1] = c * (im + ts * re);
+        C::store(out, i, v);
+    }
+}
+
+cudaError_t launch_twist_hi(int prec, const Geom &g, void *out, const void *in, double t, double c,
+                            cudaStream_t s) {
+    const long n = spinor_chunks(WD_F64, g);
+    if (prec == WD_DF64)
+        k_twist_hi<df64><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, g.stride, out, in, df64(t), df64(c));
+    else
+        k_twist_hi<double><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, g.stride, out, in, t, c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_f64_df64(void *buf, long n_reals, int to_df, cudaStream_t s) {
     k_f64_df64<<<blas_grid(n_reals), BLAS_BLOCK, 0, s>>>(n_reals, buf, to_df);
     return cudaGetLastError();

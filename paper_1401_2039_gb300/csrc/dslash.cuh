@@ -185,7 +185,24 @@ template <typename R> struct DslashArgs {
     R ph[8];
     int parity;              // output parity
     Reduction red;
+    R twist;                 // twisted mass factor t (twist_on != 0)
+    int twist_on;
 };
+
+// v <- (1 + i t gamma5) v on one site's 24 reals.  gamma5 = diag(1, 1, -1, -1)
+// in the DeGrand-Rossi basis: spins 0 and 1 take 1 + i t, spins 2 and 3 1 - i t.
+template <typename R>
+__device__ __forceinline__ void twist_site(R *v, R t) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const R ts = s < 2 ? t : -t;
+            const R re = v[8 * c + 2 * s], im = v[8 * c + 2 * s + 1];
+            v[8 * c + 2 * s] = re - ts * im;
+            v[8 * c + 2 * s + 1] = im + ts * re;
+        }
+}
 
 // Half-lattice index of the neighbour x +- mu of site h (coordinates c),
 // from offsets: h = ((t*Lz + z)*Ly + y)*(Lx/2) + x/2.
@@ -265,11 +282,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
             if (EPI == EPI_XPAY) {
                 R xv[24];
                 Rec<S, 24>::template load<R, 0>(a.x, a.g.stride, h, xv);
+                if (a.twist_on) twist_site(xv, a.twist);
 #pragma unroll
                 for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + a.scale * acc[k]);
             } else {
 #pragma unroll
                 for (int k = 0; k < 24; ++k) o[k] = settle(a.scale * acc[k]);
+                if (a.twist_on) twist_site(o, -a.twist);
             }
             Rec<S, 24>::store(a.out, a.g.stride, h, o);
             if (NORM) {
@@ -332,6 +351,8 @@ cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
     a.parity = L.out_parity;
     if (L.red) a.red = *L.red;
     else a.red = Reduction{nullptr, nullptr, nullptr, FIN_NONE};
+    a.twist = (R)L.twist;
+    a.twist_on = L.twist != 0.0;
     const int cfg = L.cfg;
     if (L.red) {   // fused norm (after an xpay epilogue), then the fixed-order finish
         if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_XPAY, 1>(cfg, a, s);

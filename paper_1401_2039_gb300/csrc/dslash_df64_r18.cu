@@ -22,11 +22,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64
         if (EPI == EPI_XPAY) {
             df64 xv[24];
             Rec<df64, 24>::template load<df64, 0>(a.x, a.g.stride, h, xv);
+            if (a.twist_on) twist_site(xv, a.twist);
 #pragma unroll
             for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + a.scale * acc[k]);
         } else {
 #pragma unroll
             for (int k = 0; k < 24; ++k) o[k] = settle(a.scale * acc[k]);
+            if (a.twist_on) twist_site(o, -a.twist);
         }
         Rec<df64, 24>::store(a.out, a.g.stride, h, o);
         if (NORM) {
@@ -72,6 +74,8 @@ cudaError_t launch_dslash_df64_r18(const DslashLaunch &L, cudaStream_t s) {
     for (int i = 0; i < 8; ++i) a.ph[i] = df64(L.phase[i]);
     a.parity = L.out_parity;
     a.red = L.red ? *L.red : Reduction{nullptr, nullptr, nullptr, FIN_NONE};
+    a.twist = df64(L.twist);
+    a.twist_on = L.twist != 0.0;
     if (L.red) {   // fused norm; the residuals never use it: one configuration
         if (L.dagger) launch_df<1, EPI_XPAY, 1, 0>(a, s);
         else launch_df<0, EPI_XPAY, 1, 0>(a, s);

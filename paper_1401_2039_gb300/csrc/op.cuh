@@ -53,6 +53,10 @@ struct wd_op {
     // solver parameters (FP32 inner iterations stay accurate over a deeper
     // residual drop than FP16/BF16 ones)
     double ru_delta = RU_DELTA_DEFAULT;
+    // twisted mass mu of D = 1 + 2 i kappa mu gamma5 - kappa H (0: Wilson)
+    double mu = 0.0;
+    // t = 2 kappa mu of A = 1 + i t gamma5; the adjoint flips its sign
+    double twist(int dagger) const { return (dagger ? -2.0 : 2.0) * kappa * mu; }
     int stall_iters = STALL_ITERS_DEFAULT;
 
     // tuned launch configuration of the hopping term: [0] storage precision,

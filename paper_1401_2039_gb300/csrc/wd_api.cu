@@ -87,9 +87,10 @@ static Reduction reduction(wd_op *op, int fin) {
     return Reduction{op->partials, op->counter, op->sc, fin};
 }
 
-// out = scale * H_{p,q} in  (PLAIN) or  x + scale * H_{p,q} in  (XPAY), optional norm
+// out = scale * H_{p,q} in  (PLAIN) or  x + scale * H_{p,q} in  (XPAY), optional norm.
+// twist t != 0: out = scale (1 - i t gamma5) H in  or  (1 + i t gamma5) x + scale H in.
 static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, const void *in,
-                  const void *x, double scale, const Reduction *red) {
+                  const void *x, double scale, const Reduction *red, double twist = 0.0) {
     DslashLaunch L;
     L.g = op->g;
     L.gauge = hi ? &op->gauge_hi : &op->gauge_lo;
@@ -103,15 +104,19 @@ static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, con
     L.epi = x ? EPI_XPAY : EPI_PLAIN;
     L.red = red;
     L.cfg = hi ? op->cfg[1] : red ? op->cfg[2] : op->cfg[0];
+    L.twist = twist;
     WD_CUDA(launch_dslash(L, hi ? op->hi_prec : op->prec, op->stream));
     return WD_OK;
 }
 
-// out_p = in_p - kappa^2 H_pq H_qp in_p  (Mhat_p, or Mhat_p^dag with H^dag)
+// out_p = A in_p - kappa^2 H_pq A^-1 H_qp in_p  (Mhat_p, Alg. "schur"), with
+// A = 1 + i t gamma5, t = 2 kappa mu (A = 1 for the Wilson operator), so that
+// A^-1 = (1 - i t gamma5) / (1 + t^2).  Mhat_p^dag: H^dag and -t.
 static int schur(wd_op *op, bool hi, int p, int dagger, void *out, const void *in, void *tmp,
                  const Reduction *red) {
-    WD_TRY(dslash(op, hi, 1 - p, dagger, tmp, in, nullptr, 1.0, nullptr));
-    WD_TRY(dslash(op, hi, p, dagger, out, tmp, in, -op->kappa * op->kappa, red));
+    const double t = op->twist(dagger);
+    WD_TRY(dslash(op, hi, 1 - p, dagger, tmp, in, nullptr, 1.0 / (1.0 + t * t), nullptr, t));
+    WD_TRY(dslash(op, hi, p, dagger, out, tmp, in, -op->kappa * op->kappa, red, t));
     return WD_OK;
 }
 
@@ -199,6 +204,24 @@ int wd_op_set_residual_precision(wd_op *op, int mode) {
     if (op->gauge_loaded) WD_TRY(tune_dslash(op, 1));
     return join(op);
 }
+
+int wd_op_set_twisted_mass(wd_op *op, double mu) {
+    if (!op) return fail(WD_ERR_ARG, "null operator handle");
+    if (!std::isfinite(mu)) return fail(WD_ERR_ARG, "mu must be finite");
+    if (mu == op->mu) return WD_OK;
+    // the cached iteration graphs carry the old twist in their kernel arguments
+    WD_CUDA(cudaStreamSynchronize(op->stream));
+    for (auto &row : op->graphs)
+        for (auto &ge : row)
+            if (ge) {
+                cudaGraphExecDestroy(ge);
+                ge = nullptr;
+            }
+    op->mu = mu;
+    return WD_OK;
+}
+
+double wd_op_twisted_mass(const wd_op *op) { return op ? op->mu : 0.0; }
 
 int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,
                      int *sites_per_thread) {
@@ -363,9 +386,9 @@ int wd_apply(wd_op *op, double *out, const double *in, int dagger) {
     if (dagger != 0 && dagger != 1) return fail(WD_ERR_ARG, "dagger must be 0 or 1");
     WD_TRY(fork(op));
     WD_CUDA(launch_pack_full(op->prec, op->g, op->fa[0], op->fa[1], in, op->stream));
-    for (int p = 0; p < 2; ++p)   // out_p = in_p - kappa H_pq in_q
+    for (int p = 0; p < 2; ++p)   // out_p = A in_p - kappa H_pq in_q
         WD_TRY(dslash(op, false, p, dagger, op->fc[p], op->fa[1 - p], op->fa[p], -op->kappa,
-                      nullptr));
+                      nullptr, op->twist(dagger)));
     WD_CUDA(launch_unpack_full(op->prec, op->g, out, op->fc[0], op->fc[1], op->stream));
     return join(op);
 }
@@ -542,13 +565,23 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
     const double n_real = 24.0 * (double)g.vh;
     const bool mixed = op->prec != WD_F64;
 
-    // Alg. schur: split b and the initial guess by parity, bhat_p = b_p + kappa H_pq b_q
+    // Alg. schur: split b and the initial guess by parity,
+    // bhat_p = b_p + kappa H_pq A^-1 b_q  (A = 1 + i t gamma5, t = 2 kappa mu)
     WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));
     {
         double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
         WD_CUDA(launch_pack_full(op->hi_prec, g, xe, xo, x, op->stream));
     }
-    WD_TRY(dslash(op, true, st.p, 0, op->bh, op->hb[st.q], op->hb[st.p], op->kappa, nullptr));
+    const double tw = op->twist(0);
+    const double inv_norm = 1.0 / (1.0 + tw * tw);
+    if (tw != 0.0) {   // A^-1 b_q = (1 - i t gamma5) b_q / (1 + t^2)
+        WD_CUDA(launch_twist_hi(op->hi_prec, g, op->axh, op->hb[st.q], -tw, inv_norm, op->stream));
+        WD_TRY(dslash(op, true, st.p, 0, op->bh, op->axh, op->hb[st.p], op->kappa, nullptr));
+        st.launches += 1;
+        st.bytes += 2 * field_b(op, WD_F64);
+    } else {
+        WD_TRY(dslash(op, true, st.p, 0, op->bh, op->hb[st.q], op->hb[st.p], op->kappa, nullptr));
+    }
     Reduction r1 = reduction(op, FIN_STORE1), r0 = reduction(op, FIN_STORE0),
               r2 = reduction(op, FIN_STORE2), r3 = reduction(op, FIN_STORE3);
     WD_CUDA(launch_norm2(op->hi_prec, g, op->hb[st.q], r1, op->stream));
@@ -683,27 +716,47 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
         }
     }
 
-    // reconstruction x_q = b_q + kappa H_qp x_p, then the true residual of the
-    // full system: r_p = b_p - (x_p - kappa H_pq x_q), r_q = b_q - (x_q - kappa
-    // H_qp x_p).  H_qp x_p is the one the last residual-arithmetic refresh
-    // left in th when x_p has not changed since (the same kernel on the same
-    // input gives the same bits, so recomputing it would check nothing).
+    // reconstruction x_q = A^-1 (b_q + kappa H_qp x_p), then the true residual
+    // of the full system: r_p = b_p - (A x_p - kappa H_pq x_q), r_q = b_q -
+    // (A x_q - kappa H_qp x_p).  When x_p has not changed since the last
+    // residual-arithmetic refresh, that refresh's first hop is still in th:
+    // th = A^-1 H_qp x_p (the same kernel on the same input gives the same
+    // bits, so recomputing it would check nothing).  Then
+    // x_q = A^-1 b_q + kappa th and A x_q - kappa H_qp x_p = A (x_q - kappa th).
     const bool reuse = st.th_valid;
     if (reuse) {
-        WD_CUDA(launch_xpay_hi(op->hi_prec, g, op->xq, op->hb[st.q], op->kappa, op->th, op->stream));
+        const void *bq = op->hb[st.q];
+        if (tw != 0.0) {
+            WD_CUDA(launch_twist_hi(op->hi_prec, g, op->xq, op->hb[st.q], -tw, inv_norm,
+                                    op->stream));
+            bq = op->xq;
+            st.launches += 1;
+            st.bytes += 2 * field_b(op, WD_F64);
+        }
+        WD_CUDA(launch_xpay_hi(op->hi_prec, g, op->xq, bq, op->kappa, op->th, op->stream));
         st.bytes += 3 * field_b(op, WD_F64);
     } else {
         WD_TRY(dslash(op, true, st.q, 0, op->xq, op->xh, op->hb[st.q], op->kappa, nullptr));
         st.dslash_hi += 1;
         st.bytes += dslash_b(op, true, true);
+        if (tw != 0.0) {
+            WD_CUDA(launch_twist_hi(op->hi_prec, g, op->xq, op->xq, -tw, inv_norm, op->stream));
+            st.launches += 1;
+            st.bytes += 2 * field_b(op, WD_F64);
+        }
     }
-    WD_TRY(dslash(op, true, st.p, 0, op->axh, op->xq, op->xh, -op->kappa, nullptr));
+    WD_TRY(dslash(op, true, st.p, 0, op->axh, op->xq, op->xh, -op->kappa, nullptr, tw));
     WD_CUDA(launch_xmy_norm(op->hi_prec, g, op->rh, op->hb[st.p], op->axh, r0, op->stream));
     if (reuse) {
         WD_CUDA(launch_xpay_hi(op->hi_prec, g, op->axh, op->xq, -op->kappa, op->th, op->stream));
         st.bytes += 3 * field_b(op, WD_F64);
+        if (tw != 0.0) {
+            WD_CUDA(launch_twist_hi(op->hi_prec, g, op->axh, op->axh, tw, 1.0, op->stream));
+            st.launches += 1;
+            st.bytes += 2 * field_b(op, WD_F64);
+        }
     } else {
-        WD_TRY(dslash(op, true, st.q, 0, op->axh, op->xh, op->xq, -op->kappa, nullptr));
+        WD_TRY(dslash(op, true, st.q, 0, op->axh, op->xh, op->xq, -op->kappa, nullptr, tw));
         st.dslash_hi += 1;
         st.bytes += dslash_b(op, true, true);
     }

@@ -534,6 +534,9 @@ struct DslashLaunch {
     int epi;
     const Reduction *red;  // optional ||out||^2
     int cfg = 0;           // launch configuration (tuned per operator)
+    // twisted mass: t != 0 makes the xpay epilogue out = (1 + i t gamma5) x +
+    // scale H in, and the plain one out = scale (1 - i t gamma5) H in
+    double twist = 0.0;
 };
 
 // dslash.cu
@@ -548,6 +551,10 @@ cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction
                          cudaStream_t s);
 cudaError_t launch_xmy_norm(int prec, const Geom &g, void *out, const void *x, const void *y,
                             const Reduction &red, cudaStream_t s);
+// out = c (1 + i t gamma5) in on a residual-precision (FP64 or double-float)
+// half-lattice field, site by site (in place allowed).
+cudaError_t launch_twist_hi(int prec, const Geom &g, void *out, const void *in, double t, double c,
+                            cudaStream_t s);
 // Adds the n partials warp_partials wrote (fixed order) and applies red.op.
 cudaError_t launch_finish_partials(const Reduction &red, long n, cudaStream_t s);
 cudaError_t launch_xpay_hi(int prec, const Geom &g, void *out, const void *y, double a,

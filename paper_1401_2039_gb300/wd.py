@@ -57,6 +57,8 @@ def load_library() -> ctypes.CDLL:
             "wd_apply": (i, [vp, vp, vp, i]),
             "wd_apply_eo": (i, [vp, vp, vp, i, i]),
             "wd_apply_eo_residual": (i, [vp, vp, vp, i, i]),
+            "wd_op_set_twisted_mass": (i, [vp, ctypes.c_double]),
+            "wd_op_twisted_mass": (ctypes.c_double, [vp]),
             "wd_dslash_eo": (i, [vp, vp, vp, i, i]),
             "wd_solve_cg": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
             "wd_solve_cg_host": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
@@ -219,6 +221,15 @@ class WilsonDirac:
     def set_solver(self, ru_delta: float = 0.1, stall_iters: int = 200):
         """Reliable-update threshold and stagnation restart of the mixed-precision solve."""
         _check(self.lib.wd_op_set_solver(self.handle, float(ru_delta), int(stall_iters)))
+
+    def set_twisted_mass(self, mu: float):
+        """D = 1 + 2 i kappa mu gamma5 - kappa H (Fig. dirac); mu = 0 is the
+        Wilson operator.  Applies to apply, apply_eo and solve."""
+        _check(self.lib.wd_op_set_twisted_mass(self.handle, float(mu)))
+
+    @property
+    def mu(self) -> float:
+        return float(self.lib.wd_op_twisted_mass(self.handle))
 
     def set_residual_precision(self, mode: str = "df64"):
         """Residual arithmetic of the reliable updates: "f64" or "df64" (double-float)."""
