@@ -16,6 +16,7 @@ Printed as one JSON line:
   fp64_cg_ms    the same solve with plain FP64 even-odd CGNR on the same GPU
   e2e           the solve through wd_solve_cg_host: b and x in pinned host
                 memory, host<->device copies inside the timed region
+  twisted_mass  the same comparison with a twisted mass mu (Fig. dirac)
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
 
 Multi-GPU (torchrun): independent replicas, one per GPU, each with its own
@@ -43,6 +44,8 @@ import synthetic as syn  # noqa: E402
 
 METRIC = "Dslash GB/s vs HBM peak; time to 1e-10 residual, chosen vs plain FP64 CG"
 DEFAULT_WORKLOAD = "wilson_32x32x32x64_f16r12"
+# twisted mass of the twisted-mass comparison (2 kappa mu = 0.0124 at kappa 0.124)
+TWISTED_MU = 0.05
 
 
 def parse_args():
@@ -58,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched multi-source / uneven-lattice measurement")
+    ap.add_argument("--no-twisted", action="store_true",
+                    help="skip the twisted-mass solve comparison (reported as null)")
     return ap.parse_args()
 
 
@@ -363,6 +368,7 @@ def main():
     # ---- plain FP64 even-odd CGNR on the same GPU, same problem
     fp64_ms = None
     fp64_iters = None
+    tm_fp64 = None
     if not args.no_fp64_cg:
         op64 = WilsonDirac(w.dims, w.kappa, w.phase, prec="f64", recon=18, stream=stream)
         op64.set_gauge(torch.from_numpy(U_np).cuda())
@@ -376,6 +382,15 @@ def main():
         torch.cuda.synchronize()
         fp64_ms = f0.elapsed_time(f1)
         fp64_iters = r64.info["iters"]
+        if rank == 0 and not args.no_twisted:   # the same comparison with a twisted mass
+            op64.set_twisted_mass(TWISTED_MU)
+            op64.solve(b, tol=w.tol, maxiter=40000)
+            torch.cuda.synchronize()
+            f0.record(stream)
+            r64 = op64.solve(b, tol=w.tol, maxiter=40000)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            tm_fp64 = (f0.elapsed_time(f1), r64.info["iters"])
         op64.close()
 
     # ---- end to end through the host-memory entry point
@@ -392,6 +407,28 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = e_bytes / e2e_s / 1e9
     spinor_bytes = w.volume * 12 * 16
+
+    # ---- twisted mass (Fig. dirac, 2 i kappa mu gamma5): the chosen solver on
+    # the same problem with mu != 0, against plain FP64 CGNR with the same mu
+    twisted = None
+    if rank == 0 and not args.no_twisted:
+        op.set_twisted_mass(TWISTED_MU)
+        solve()
+        torch.cuda.synchronize()
+        t0e = torch.cuda.Event(enable_timing=True)
+        t1e = torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        rt = solve()
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        op.set_twisted_mass(0.0)
+        tm_ms = t0e.elapsed_time(t1e)
+        twisted = {"mu": TWISTED_MU, "ms": tm_ms, "iters": rt.info["iters"],
+                   "reliable_updates": rt.info["reliable_updates"],
+                   "true_rel_resid": rt.info["true_rel_resid"],
+                   "fp64_cg_ms": tm_fp64[0] if tm_fp64 else None,
+                   "fp64_cg_iters": tm_fp64[1] if tm_fp64 else None,
+                   "speedup_vs_fp64_cg": (tm_fp64[0] / tm_ms) if tm_fp64 else None}
 
     # ---- batched solves (the multi-source and uneven-lattice workloads)
     batch = None
@@ -433,6 +470,7 @@ def main():
             "clocks": clocks.summary(),
             "residual_arithmetic": "double-float (2 x FP32)" if w.prec != "f64" else "f64",
             "batch": batch,
+            "twisted_mass": twisted,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
