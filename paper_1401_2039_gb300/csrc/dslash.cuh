@@ -21,6 +21,8 @@
 // compensated dot product of df64.cuh) and rounds once, before the store.
 #pragma once
 
+#include <type_traits>
+
 #include "wd_internal.cuh"
 
 namespace wd {
@@ -257,6 +259,184 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
     }
 }
 
+// ---------------------------------------------------------------- FP16 storage
+// With FP16 storage the generic hop spends about a sixth of its instructions
+// converting halves to FP32 (one conversion per stored element).  This
+// variant keeps spinors and links in their packed half2 words (one complex
+// number each, real part in the low half): the spin projection adds half2
+// words in FP16 arithmetic, and every product of the SU(3) multiply is a
+// mixed-precision FMA, f16 x f16 -> f32 (PTX fma.rn.f32.f16), accumulating in
+// FP32.  The product of two halves is exact in FP32, so the one new rounding
+// is the FP16 projection sum (relative 2^-11, the size of the storage
+// rounding).  The twelve-real links rebuild row 2 = conj(row0 x row1) with the
+// same mixed FMAs and round it to FP16, as an 18-real FP16 link would store it.
+#define WD_MIXED_FMA(NAME, SA, SB)                                                           \
+    __device__ __forceinline__ float NAME(uint32_t a, uint32_t b, float c) {                 \
+        float d;                                                                             \
+        asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"                                             \
+            "mov.b32 {a0, a1}, %1;\n\tmov.b32 {b0, b1}, %2;\n\t"                             \
+            "fma.rn.f32.f16 %0, " SA ", " SB ", %3;\n\t}"                                    \
+            : "=f"(d) : "r"(a), "r"(b), "f"(c));                                             \
+        return d;                                                                            \
+    }
+// mf_XY(a, b, c) = a.X * b.Y + c with X, Y in {l = real, h = imaginary}
+WD_MIXED_FMA(mf_ll, "a0", "b0")
+WD_MIXED_FMA(mf_lh, "a0", "b1")
+WD_MIXED_FMA(mf_hl, "a1", "b0")
+WD_MIXED_FMA(mf_hh, "a1", "b1")
+#undef WD_MIXED_FMA
+
+__device__ __forceinline__ uint32_t h2_neg(uint32_t a) { return a ^ 0x80008000u; }
+__device__ __forceinline__ __half2 as_h2(uint32_t a) { return *reinterpret_cast<__half2 *>(&a); }
+__device__ __forceinline__ uint32_t as_u32(__half2 a) { return *reinterpret_cast<uint32_t *>(&a); }
+
+// p + F q on half2 complex words, F = +1, -1, +i, -i (codes 0..3)
+template <int F>
+__device__ __forceinline__ uint32_t h2_comb(uint32_t p, uint32_t q) {
+    if (F == 0) return as_u32(__hadd2(as_h2(p), as_h2(q)));
+    if (F == 1) return as_u32(__hsub2(as_h2(p), as_h2(q)));
+    // i q = (-q.im, q.re), -i q = (q.im, -q.re): swap the halves, then one FMA
+    const __half2 sq = __lowhigh2highlow(as_h2(q));
+    const __half2 sg = F == 2 ? __floats2half2_rn(-1.0f, 1.0f) : __floats2half2_rn(1.0f, -1.0f);
+    return as_u32(__hfma2(sq, sg, as_h2(p)));
+}
+
+// half spinor h[k][colour] (half2 words) of the site's 12 words (word 4 c + s)
+template <int MU, int SGN>
+__device__ __forceinline__ void project_h2(const uint32_t *p, uint32_t h[2][3]) {
+    constexpr int PI = SGN > 0 ? 2 : 3, MI = SGN > 0 ? 3 : 2;   // SGN i, -SGN i
+    constexpr int P1 = SGN > 0 ? 0 : 1, M1 = SGN > 0 ? 1 : 0;   // SGN, -SGN
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const uint32_t p0 = p[4 * c], p1 = p[4 * c + 1], p2 = p[4 * c + 2], p3 = p[4 * c + 3];
+        if (MU == 0) {
+            h[0][c] = h2_comb<PI>(p0, p3);
+            h[1][c] = h2_comb<PI>(p1, p2);
+        } else if (MU == 1) {
+            h[0][c] = h2_comb<M1>(p0, p3);
+            h[1][c] = h2_comb<P1>(p1, p2);
+        } else if (MU == 2) {
+            h[0][c] = h2_comb<PI>(p0, p2);
+            h[1][c] = h2_comb<MI>(p1, p3);
+        } else {
+            h[0][c] = h2_comb<P1>(p0, p2);
+            h[1][c] = h2_comb<P1>(p1, p3);
+        }
+    }
+}
+
+// link as 9 half2 words (row-major); 12-real records rebuild row 2
+template <int RECON>
+__device__ __forceinline__ void load_link_h2(const char *base, long stride, long site,
+                                             uint32_t U[9]) {
+    Rec<__half, RECON>::template load_words<1>(base, stride, site, U);
+    if (RECON == 12) {
+        // row2_j = conj(row0_k row1_l - row0_l row1_k), (j, k, l) cyclic
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = (j + 1) % 3, l = (j + 2) % 3;
+            const uint32_t x = U[k], y = U[3 + l], z = U[l], w = U[3 + k];
+            const uint32_t yn = h2_neg(y), wn = h2_neg(w);
+            float re = mf_ll(x, y, 0.0f);
+            re = mf_hh(x, yn, re);
+            re = mf_ll(z, wn, re);
+            re = mf_hh(z, w, re);
+            float im = mf_lh(x, yn, 0.0f);
+            im = mf_hl(x, yn, im);
+            im = mf_lh(z, w, im);
+            im = mf_hl(z, w, im);
+            U[6 + j] = as_u32(__floats2half2_rn(re, im));
+        }
+    }
+}
+
+// u[k][a] = sum_b U[a][b] h[k][b]
+__device__ __forceinline__ void su3_mul_h2(const uint32_t U[9], const uint32_t h[2][3],
+                                           cx<float> u[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint32_t hn[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) hn[b] = h2_neg(h[k][b]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float re = mf_ll(U[3 * a], h[k][0], 0.0f);
+            float im = mf_lh(U[3 * a], h[k][0], 0.0f);
+            re = mf_hh(U[3 * a], hn[0], re);
+            im = mf_hl(U[3 * a], h[k][0], im);
+#pragma unroll
+            for (int b = 1; b < 3; ++b) {
+                re = mf_ll(U[3 * a + b], h[k][b], re);
+                re = mf_hh(U[3 * a + b], hn[b], re);
+                im = mf_lh(U[3 * a + b], h[k][b], im);
+                im = mf_hl(U[3 * a + b], h[k][b], im);
+            }
+            u[k][a] = {re, im};
+        }
+    }
+}
+
+// u[k][a] = sum_b conj(U[b][a]) h[k][b]
+__device__ __forceinline__ void su3_adj_mul_h2(const uint32_t U[9], const uint32_t h[2][3],
+                                               cx<float> u[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint32_t hn[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) hn[b] = h2_neg(h[k][b]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float re = mf_ll(U[a], h[k][0], 0.0f);
+            float im = mf_lh(U[a], h[k][0], 0.0f);
+            re = mf_hh(U[a], h[k][0], re);
+            im = mf_hl(U[a], hn[0], im);
+#pragma unroll
+            for (int b = 1; b < 3; ++b) {
+                re = mf_ll(U[3 * b + a], h[k][b], re);
+                re = mf_hh(U[3 * b + a], h[k][b], re);
+                im = mf_lh(U[3 * b + a], h[k][b], im);
+                im = mf_hl(U[3 * b + a], hn[b], im);
+            }
+            u[k][a] = {re, im};
+        }
+    }
+}
+
+template <int RECON, int MU, int DAG>
+__device__ __forceinline__ void hop_pair_h2(const DslashArgs<float> &a, const int c[4], long h,
+                                            float *acc) {
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    {
+        bool wrap;
+        const long hn = neighbour<MU, +1>(a.g, h, c, wrap);
+        uint32_t p[12];
+        Rec<__half, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, p);
+        uint32_t hs[2][3];
+        project_h2<MU, SF>(p, hs);
+        uint32_t U[9];
+        load_link_h2<RECON>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, U);
+        cx<float> u[2][3];
+        su3_mul_h2(U, hs, u);
+        if (wrap) phase_mul(u, a.ph[2 * MU], a.ph[2 * MU + 1]);
+        accumulate<MU, SF>(acc, u);
+    }
+    {
+        bool wrap;
+        const long hn = neighbour<MU, -1>(a.g, h, c, wrap);
+        uint32_t p[12];
+        Rec<__half, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, p);
+        uint32_t hs[2][3];
+        project_h2<MU, SB>(p, hs);
+        uint32_t U[9];
+        load_link_h2<RECON>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, U);
+        cx<float> u[2][3];
+        su3_adj_mul_h2(U, hs, u);
+        if (wrap) phase_mul(u, a.ph[2 * MU], -a.ph[2 * MU + 1]);
+        accumulate<MU, SB>(acc, u);
+    }
+}
+
 // One output site per (thread, i < SPT): site h = block base + i * BLOCK +
 // thread, so each of a warp's loads stays one contiguous request.
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK, int MINB,
@@ -274,10 +454,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
             Acc<R> acc[24];
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
-            hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
-            hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
-            hop_pair<S, R, RECON, 2, DAG>(a, c, h, acc);
-            hop_pair<S, R, RECON, 3, DAG>(a, c, h, acc);
+            if constexpr (std::is_same<S, __half>::value) {
+                hop_pair_h2<RECON, 0, DAG>(a, c, h, acc);
+                hop_pair_h2<RECON, 1, DAG>(a, c, h, acc);
+                hop_pair_h2<RECON, 2, DAG>(a, c, h, acc);
+                hop_pair_h2<RECON, 3, DAG>(a, c, h, acc);
+            } else {
+                hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
+                hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
+                hop_pair<S, R, RECON, 2, DAG>(a, c, h, acc);
+                hop_pair<S, R, RECON, 3, DAG>(a, c, h, acc);
+            }
             R o[24];
             if (EPI == EPI_XPAY) {
                 R xv[24];
