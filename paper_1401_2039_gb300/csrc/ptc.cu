@@ -8,8 +8,10 @@
 // T_{5+mu} psi(x) = U_mu(x-mu)^dag phi^* psi(x-mu) (phases on wrapping hops).
 //
 // GB300 mapping.  Rows m = (site x, colour a), M = 3V.  A layer is
-//   1. gather   A[m][(part, c, k, s)] = Re/Im (T_k in_c)(x)[a][s]  (BF16,
-//      K = 2 * C_in * 36 columns, padded to a multiple of 64),
+//   1. gather   A[m][(part, k, c, s)] = Re/Im (T_k in_c)(x)[a][s]  (BF16,
+//      K = 2 * C_in * 36 columns, padded to a multiple of 64; the channel
+//      index inside the transport index, so that the threads of a warp,
+//      consecutive channels of a site, store consecutive 8-byte chunks),
 //   2. GEMM     F_out[m][(part', c', s')] = sum A[m][.] B[(part', c', s')][.]
 //      on the tensor cores (tcgen05, FP32 accumulation), with the complex
 //      weights laid out as the real block matrix [[Wr, -Wi], [Wi, Wr]],
@@ -86,6 +88,25 @@ __device__ __forceinline__ long ptc_neighbour(const PtcGeom &g, const int c[4], 
     return lex_of(g, n);
 }
 
+// the four spins of channel c in an activation row: Re and Im as float4
+__device__ __forceinline__ void load_spins(const float *row, int cin, int c, float2 v[4]) {
+    const float4 re = *reinterpret_cast<const float4 *>(row + c * 4);
+    const float4 im = *reinterpret_cast<const float4 *>(row + 4 * cin + c * 4);
+    v[0] = make_float2(re.x, im.x);
+    v[1] = make_float2(re.y, im.y);
+    v[2] = make_float2(re.z, im.z);
+    v[3] = make_float2(re.w, im.w);
+}
+
+// four BF16 values as one 8-byte store
+__device__ __forceinline__ void store_bf16x4(__nv_bfloat16 *p, float a, float b, float c, float d) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    uint2 w;
+    w.x = *reinterpret_cast<const uint32_t *>(&lo);
+    w.y = *reinterpret_cast<const uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(p) = w;
+}
+
 // Gather: one thread per (site x, input channel c).  F_in row stride ldf holds
 // [Re (c, s)][Im (c, s)] blocks of 4*C_in values; A row stride lda.
 __global__ void __launch_bounds__(PTC_BLOCK)
@@ -101,22 +122,14 @@ k_ptc_gather(PtcGeom g, int cin, const float *__restrict__ F, int ldf,
     for (int k = 0; k < PTC_NK; ++k) {
         float2 v[3][4];
         if (k == 0) {
-            for (int a = 0; a < 3; ++a)
-                for (int s = 0; s < 4; ++s) {
-                    const float *row = F + (x * 3 + a) * (long)ldf;
-                    v[a][s] = make_float2(row[c * 4 + s], row[4 * cin + c * 4 + s]);
-                }
+            for (int a = 0; a < 3; ++a) load_spins(F + (x * 3 + a) * (long)ldf, cin, c, v[a]);
         } else {
             const int mu = (k - 1) & 3;
             const bool fwd = k <= 4;
             bool wrap;
             const long xn = ptc_neighbour(g, co, mu, fwd ? 1 : -1, wrap);
             float2 p[3][4];
-            for (int b = 0; b < 3; ++b)
-                for (int s = 0; s < 4; ++s) {
-                    const float *row = F + (xn * 3 + b) * (long)ldf;
-                    p[b][s] = make_float2(row[c * 4 + s], row[4 * cin + c * 4 + s]);
-                }
+            for (int b = 0; b < 3; ++b) load_spins(F + (xn * 3 + b) * (long)ldf, cin, c, p[b]);
             const float2 *Ul = U + ((fwd ? x : xn) * 4 + mu) * 9;
             float pr = 1.f, pi = 0.f;
             if (wrap) { pr = g.ph[2 * mu]; pi = fwd ? g.ph[2 * mu + 1] : -g.ph[2 * mu + 1]; }
@@ -134,16 +147,14 @@ k_ptc_gather(PtcGeom g, int cin, const float *__restrict__ F, int ldf,
                 }
         }
         for (int a = 0; a < 3; ++a) {
-            __nv_bfloat16 *row = A + (x * 3 + a) * (long)lda + (c * PTC_NK + k) * 4;
-            for (int s = 0; s < 4; ++s) {
-                row[s] = __float2bfloat16_rn(v[a][s].x);
-                row[K + s] = __float2bfloat16_rn(v[a][s].y);
-            }
+            __nv_bfloat16 *row = A + (x * 3 + a) * (long)lda + (k * cin + c) * 4;
+            store_bf16x4(row, v[a][0].x, v[a][1].x, v[a][2].x, v[a][3].x);
+            store_bf16x4(row + K, v[a][0].y, v[a][1].y, v[a][2].y, v[a][3].y);
         }
     }
 }
 
-// Real block form of the complex weights: B[(p', c', s')][(p, c, k, s)], row
+// Real block form of the complex weights: B[(p', c', s')][(p, k, c, s)], row
 // stride ldb, from W (complex64 as float2) [cout][cin][9][4][4].
 __global__ void k_ptc_weights(int cout, int cin, const float2 *__restrict__ W,
                               __nv_bfloat16 *__restrict__ B, int ldb) {
@@ -152,7 +163,7 @@ __global__ void k_ptc_weights(int cout, int cin, const float2 *__restrict__ W,
     if (i >= (long)N * K) return;
     const int n = (int)(i / K), kk = (int)(i - (long)n * K);
     const int cp = n >> 2, sp = n & 3;
-    const int c = kk / 36, k = (kk % 36) >> 2, s = kk & 3;
+    const int k = kk / (4 * cin), c = (kk >> 2) % cin, s = kk & 3;   // kk = (k cin + c) 4 + s
     const float2 w = W[((((long)cp * cin + c) * PTC_NK + k) * 4 + sp) * 4 + s];
     B[(long)n * ldb + kk] = __float2bfloat16_rn(w.x);              // Re out <- Re in:  Wr
     B[(long)n * ldb + K + kk] = __float2bfloat16_rn(-w.y);         // Re out <- Im in: -Wi
@@ -222,7 +233,7 @@ __global__ void k_ptc_loss_grad(long V, const float *__restrict__ F, int ld,
 
 // Adjoint of the gather: dF_c(x) = sum_k (T_k^dag dA_{c,k})(x) with
 // T_{1+mu}^dag = T_{5+mu} and T_{5+mu}^dag = T_{1+mu}; dA rows (y, a) hold
-// [Re (c, k, s)][Im (c, k, s)].  One thread per (site x, channel c).
+// [Re (k, c, s)][Im (k, c, s)].  One thread per (site x, channel c).
 __global__ void __launch_bounds__(PTC_BLOCK)
 k_ptc_scatter(PtcGeom g, int cin, const float *__restrict__ dA, int lda,
               const float2 *__restrict__ U, float *__restrict__ dF, int ldf,
@@ -237,7 +248,7 @@ k_ptc_scatter(PtcGeom g, int cin, const float *__restrict__ dA, int lda,
     float2 acc[3][4];
     for (int a = 0; a < 3; ++a)
         for (int s = 0; s < 4; ++s) {
-            const float *row = dA + (x * 3 + a) * (long)lda + (c * PTC_NK) * 4;
+            const float *row = dA + (x * 3 + a) * (long)lda + c * 4;
             acc[a][s] = make_float2(row[s], row[K + s]);
         }
     for (int k = 1; k < PTC_NK; ++k) {
@@ -252,7 +263,7 @@ k_ptc_scatter(PtcGeom g, int cin, const float *__restrict__ dA, int lda,
         float2 p[3][4];
         for (int b = 0; b < 3; ++b)
             for (int s = 0; s < 4; ++s) {
-                const float *row = dA + (xn * 3 + b) * (long)lda + (c * PTC_NK + k) * 4;
+                const float *row = dA + (xn * 3 + b) * (long)lda + (k * cin + c) * 4;
                 p[b][s] = make_float2(row[s], row[K + s]);
             }
         for (int a = 0; a < 3; ++a)
@@ -280,7 +291,7 @@ k_ptc_scatter(PtcGeom g, int cin, const float *__restrict__ dA, int lda,
     }
 }
 
-// Transposed real block weights Bt[(p, c, k, s)][(p', c', s')], row stride ldbt.
+// Transposed real block weights Bt[(p, k, c, s)][(p', c', s')], row stride ldbt.
 __global__ void k_ptc_weights_t(int cout, int cin, const float2 *__restrict__ W,
                                 __nv_bfloat16 *__restrict__ Bt, int ldbt) {
     const int K = cin * 36, N = cout * 4;
@@ -288,7 +299,7 @@ __global__ void k_ptc_weights_t(int cout, int cin, const float2 *__restrict__ W,
     if (i >= (long)N * K) return;
     const int n = (int)(i / K), kk = (int)(i - (long)n * K);
     const int cp = n >> 2, sp = n & 3;
-    const int c = kk / 36, k = (kk % 36) >> 2, s = kk & 3;
+    const int k = kk / (4 * cin), c = (kk >> 2) % cin, s = kk & 3;   // kk = (k cin + c) 4 + s
     const float2 w = W[((((long)cp * cin + c) * PTC_NK + k) * 4 + sp) * 4 + s];
     Bt[(long)kk * ldbt + n] = __float2bfloat16_rn(w.x);
     Bt[(long)(K + kk) * ldbt + n] = __float2bfloat16_rn(-w.y);
@@ -305,7 +316,7 @@ __global__ void k_ptc_wgrad(int cout, int cin, const float *__restrict__ dB, int
     if (i >= (long)N * K) return;
     const int n = (int)(i / K), kk = (int)(i - (long)n * K);
     const int cp = n >> 2, sp = n & 3;
-    const int c = kk / 36, k = (kk % 36) >> 2, s = kk & 3;
+    const int k = kk / (4 * cin), c = (kk >> 2) % cin, s = kk & 3;   // kk = (k cin + c) 4 + s
     const double gr = (double)dB[(long)n * ldb + kk] + dB[(long)(N + n) * ldb + K + kk];
     const double gi = -(double)dB[(long)n * ldb + K + kk] + dB[(long)(N + n) * ldb + kk];
     gW[((((long)cp * cin + c) * PTC_NK + k) * 4 + sp) * 4 + s] = make_double2(gr, gi);
