@@ -430,21 +430,24 @@ static int ptc_gemm(wd_ptc *n, const __nv_bfloat16 *A, const __nv_bfloat16 *B, f
                     int N, int K, int lda, int ldb, int ldd) {
     if (M % TC_BM || K % TC_BK || N % 16)
         return ptc_fail(WD_ERR_ARG, "GEMM shape not tile aligned");
+    // dynamic shared memory: the ring of A and B tiles.  At BN = 128 it also
+    // keeps at most two CTAs per SM, within the SM's 512 TMEM columns.
+    static bool attr_set = false;
+    if (!attr_set) {
+        PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc_gemm_smem_bytes<128>()));
+        PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc_gemm_smem_bytes<16>()));
+        attr_set = true;
+    }
     if (N % 128 == 0) {
-        // 16 KB of dynamic shared memory on top of the tiles keeps at most four
-        // CTAs per SM, so their 4 x 128 TMEM columns fit the SM's 512
-        static bool attr_set = false;
-        if (!attr_set) {
-            PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<128>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 16384));
-            attr_set = true;
-        }
         dim3 grid((unsigned)(M / TC_BM), (unsigned)(N / 128));
-        k_gemm_bf16_tc<128><<<grid, TC_THREADS, 16384, n->stream>>>(A, B, D, K, lda, ldb, ldd,
-                                                                     n->err);
+        k_gemm_bf16_tc<128><<<grid, TC_THREADS, tc_gemm_smem_bytes<128>(), n->stream>>>(
+            A, B, D, K, lda, ldb, ldd, n->err);
     } else {
         dim3 grid((unsigned)(M / TC_BM), (unsigned)(N / 16));
-        k_gemm_bf16_tc<16><<<grid, TC_THREADS, 0, n->stream>>>(A, B, D, K, lda, ldb, ldd, n->err);
+        k_gemm_bf16_tc<16><<<grid, TC_THREADS, tc_gemm_smem_bytes<16>(), n->stream>>>(
+            A, B, D, K, lda, ldb, ldd, n->err);
     }
     PTC_CUDA(cudaGetLastError());
     return WD_OK;

@@ -109,6 +109,9 @@ def main():
     ap.add_argument("--eval-large", action="store_true")
     ap.add_argument("--data", choices=["residual", "gaussian", "mixed"], default="mixed")
     ap.add_argument("--init", choices=["neumann", "identity"], default="neumann")
+    ap.add_argument("--eval-only", action="store_true",
+                    help="skip data and training; evaluate the starting weights (the degree-4 "
+                         "Neumann network, which validation kept in the training runs)")
     args = ap.parse_args()
     channels = (1, 16, 16, 16, 1)
     ph = syn.workloads.APBC_T
@@ -116,6 +119,11 @@ def main():
     V = syn.volume(dims)
     summary = {"channels": channels, "kappa": args.kappa, "train_lattice": dims,
                "pairs": args.pairs, "epochs": args.epochs, "batch": args.batch, "lr": args.lr}
+
+    if args.eval_only:
+        W = torch.from_numpy(neumann_weights(channels, args.kappa, 7)).cuda()
+        summary["weights"] = "degree-4 Neumann initialisation (no training)"
+        return evaluate(args, summary, channels, ph, W)
 
     # ---- 1. data
     U = torch.from_numpy(syn.su3_links(dims, eps=0.3, seed=1)).cuda()
@@ -209,6 +217,18 @@ def main():
     exact.close()
     del R, E
     torch.cuda.empty_cache()
+    return evaluate(args, summary, channels, ph, W)
+
+
+def evaluate(args, summary, channels, ph, W):
+    """FGCR with the network, with the untrained Neumann network and without a
+    preconditioner, and the even-odd CGNR in FP32 (reliable updates) and plain
+    FP64, on unseen gauge fields, to a 1e-10 FP64 true residual."""
+    import numpy as np  # noqa: F401
+    import torch
+
+    import synthetic as syn
+    from paper_1401_2039_gb300 import Fgcr, PtcNet, WilsonDirac
 
     # ---- 3. evaluation on unseen gauge fields
     evals = []
@@ -249,6 +269,9 @@ def main():
         res, ms = timed(lambda: lo.solve(b, tol=1e-10))
         row["cgnr_even_odd_f32"] = {"iterations": res.info["iters"], "ms": ms,
                                     "true_rel_resid": res.info["true_rel_resid"]}
+        res, ms = timed(lambda: hi.solve(b, tol=1e-10, maxiter=40000))
+        row["cgnr_even_odd_f64"] = {"iterations": res.info["iters"], "ms": ms,
+                                    "true_rel_resid": res.info["true_rel_resid"]}
         evals.append(row)
         print(json.dumps(row), flush=True)
         enet.close()
@@ -257,6 +280,7 @@ def main():
         hi.close()
         torch.cuda.empty_cache()
     summary["evaluation"] = evals
+    os.makedirs(args.out, exist_ok=True)
     with open(os.path.join(args.out, "learned_preconditioner.json"), "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps(summary))
