@@ -172,6 +172,16 @@ __global__ void __launch_bounds__(BT_BLOCK, std::is_same<S, df64>::value ? 3 : 1
             if constexpr (std::is_same<S, df64>::value) {
                 df_hops<DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
                              P.g.stride * nr, nr, r, h, c, acc);
+            } else if constexpr (std::is_same<S, __half>::value) {
+                const long ss = P.g.stride * nr;
+                hop_pair_h2<RECON, 0, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
+                hop_pair_h2<RECON, 1, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
+                hop_pair_h2<RECON, 2, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
+                hop_pair_h2<RECON, 3, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
             } else {
                 bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
                 bt_hop_pair<S, R, RECON, 1, DAG>(P, c, h, r, acc);

@@ -402,39 +402,52 @@ __device__ __forceinline__ void su3_adj_mul_h2(const uint32_t U[9], const uint32
     }
 }
 
-template <int RECON, int MU, int DAG>
-__device__ __forceinline__ void hop_pair_h2(const DslashArgs<float> &a, const int c[4], long h,
-                                            float *acc) {
+// acc += the forward and backward hops in direction MU.  The input field
+// holds nrhs right-hand sides with the rhs index innermost (site s, rhs r at
+// record s * nrhs + r of plane stride in_stride); ph: the boundary phases.
+template <int RECON, int MU, int DAG, typename PH>
+__device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out,
+                                            const char *gauge_in, size_t dir_bytes, const PH *ph,
+                                            const void *in, long in_stride, int nrhs, int r,
+                                            const int c[4], long h, float *acc) {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
+    const float pr = (float)ph[2 * MU], pi = (float)ph[2 * MU + 1];
     {
         bool wrap;
-        const long hn = neighbour<MU, +1>(a.g, h, c, wrap);
+        const long hn = neighbour<MU, +1>(g, h, c, wrap);
         uint32_t p[12];
-        Rec<__half, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, p);
+        Rec<__half, 24>::template load_words<0>((const char *)in, in_stride, hn * nrhs + r, p);
         uint32_t hs[2][3];
         project_h2<MU, SF>(p, hs);
         uint32_t U[9];
-        load_link_h2<RECON>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, U);
+        load_link_h2<RECON>(gauge_out + MU * dir_bytes, g.stride, h, U);
         cx<float> u[2][3];
         su3_mul_h2(U, hs, u);
-        if (wrap) phase_mul(u, a.ph[2 * MU], a.ph[2 * MU + 1]);
+        if (wrap) phase_mul(u, pr, pi);
         accumulate<MU, SF>(acc, u);
     }
     {
         bool wrap;
-        const long hn = neighbour<MU, -1>(a.g, h, c, wrap);
+        const long hn = neighbour<MU, -1>(g, h, c, wrap);
         uint32_t p[12];
-        Rec<__half, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, p);
+        Rec<__half, 24>::template load_words<0>((const char *)in, in_stride, hn * nrhs + r, p);
         uint32_t hs[2][3];
         project_h2<MU, SB>(p, hs);
         uint32_t U[9];
-        load_link_h2<RECON>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, U);
+        load_link_h2<RECON>(gauge_in + MU * dir_bytes, g.stride, hn, U);
         cx<float> u[2][3];
         su3_adj_mul_h2(U, hs, u);
-        if (wrap) phase_mul(u, a.ph[2 * MU], -a.ph[2 * MU + 1]);
+        if (wrap) phase_mul(u, pr, -pi);
         accumulate<MU, SB>(acc, u);
     }
+}
+
+template <int RECON, int MU, int DAG>
+__device__ __forceinline__ void hop_pair_h2(const DslashArgs<float> &a, const int c[4], long h,
+                                            float *acc) {
+    hop_pair_h2<RECON, MU, DAG>(a.g, a.gauge_out, a.gauge_in, a.dir_bytes, a.ph, a.in, a.g.stride,
+                                1, 0, c, h, acc);
 }
 
 // One output site per (thread, i < SPT): site h = block base + i * BLOCK +
