@@ -647,7 +647,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
                 WD_TRY(read_scalars(op));
                 iters = op->sc_host->iter;
                 st.dslash_lo += 4.0 * n;
-                st.launches += 6.0 * n;
+                st.launches += 8.0 * n;   // 4 hops, 2 norm finishes, 2 vector updates
                 st.bytes += per_iter_bytes * n;
             }
             const SolverScalars &h = *op->sc_host;
