@@ -17,6 +17,9 @@ Printed as one JSON line:
   e2e           the solve through wd_solve_cg_host: b and x in pinned host
                 memory, host<->device copies inside the timed region
   twisted_mass  the same comparison with a twisted mass mu (Fig. dirac)
+  dslash_sweep  the hopping term alone for every storage precision and link
+                compression on the same lattice
+  small_config  16^3 x 32, FP32 with reliable updates against plain FP64 CG
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
 
 Multi-GPU (torchrun): independent replicas, one per GPU, each with its own
@@ -63,6 +66,8 @@ def parse_args():
                     help="skip the batched multi-source / uneven-lattice measurement")
     ap.add_argument("--no-twisted", action="store_true",
                     help="skip the twisted-mass solve comparison (reported as null)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the hopping-term precision sweep and the 16^3 x 32 comparison")
     return ap.parse_args()
 
 
@@ -228,14 +233,75 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def dslash_sweep(dims, U_np, launches: int = 50):
+    """Hopping term alone at every storage precision and link compression
+    (autotuned, back-to-back launches between two resident half spinors,
+    CUDA events on the handle's work stream): us per launch, algorithmic
+    GB/s and GFLOP/s (1320 flop/site)."""
+    import torch
+    from paper_1401_2039_gb300 import WilsonDirac
+    U = torch.from_numpy(U_np).cuda()
+    vh = int(np.prod(dims)) // 2
+    half = torch.from_numpy(syn.gaussian_spinor(vh, 3)).cuda()
+    out = {}
+    for prec in ("f64", "f32", "f16", "bf16"):
+        for recon in (18, 12):
+            op = WilsonDirac(dims, 0.124, syn.workloads.APBC_T, prec=prec, recon=recon)
+            op.set_gauge(U)
+            op.field_load(0, half)
+            op.field_load(1, half)
+            ws = torch.cuda.ExternalStream(op.work_stream)
+            for i in range(6):
+                op.dslash_resident(i & 1, 1 - (i & 1))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ws)
+            for i in range(launches):
+                op.dslash_resident(i & 1, 1 - (i & 1))
+            e1.record(ws)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / launches
+            out[f"{prec}_r{recon}"] = {"us": us, "gbs": op.dslash_bytes / (us * 1e-6) / 1e9,
+                                       "gflops": 1320.0 * vh / (us * 1e-6) / 1e9}
+            op.close()
+    return out
+
+
+def small_config_comparison():
+    """16^3 x 32, FP32 hopping term with reliable updates (double-float
+    residuals) against plain FP64 even-odd CGNR, both to a 1e-10 true residual
+    (the lattice fits in L2, so this is an L2-resident comparison)."""
+    import torch
+    from paper_1401_2039_gb300 import WilsonDirac
+    w = syn.WORKLOADS["wilson_16x16x16x32_f32"]
+    U = torch.from_numpy(syn.su3_links(w.dims, eps=w.eps, seed=w.gauge_seed)).cuda()
+    b = torch.from_numpy(syn.gaussian_spinor(w.volume, w.source_seed)).cuda()
+    row = {"workload": w.name}
+    for name, prec in (("chosen", w.prec), ("fp64_cg", "f64")):
+        op = WilsonDirac(w.dims, w.kappa, w.phase, prec=prec, recon=18)
+        op.set_gauge(U)
+        op.solve(b, tol=w.tol, maxiter=40000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = op.solve(b, tol=w.tol, maxiter=40000)
+        torch.cuda.synchronize()
+        row[name] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": r.info["iters"],
+                     "true_rel_resid": r.info["true_rel_resid"]}
+        op.close()
+    row["speedup_vs_fp64_cg"] = row["fp64_cg"]["ms"] / row["chosen"]["ms"]
+    return row
+
+
 def batch_measurement(prec: str, recon: int):
     """Batched solves against the same systems solved one at a time:
     12 point sources (every spin and colour) on 24^3 x 48, and 4 Gaussian
-    sources on each of 8^4, 12^3 x 24, 16^3 x 32 in one persistent batch."""
+    sources on each of 8^4, 12^3 x 24, 16^3 x 32 in one persistent batch
+    (storage precision prec, recon-real links)."""
     import torch
     from paper_1401_2039_gb300 import WilsonBatch, WilsonDirac
     ph = syn.workloads.APBC_T
-    out = {}
+    out = {"storage": prec, "link_reals": recon}
 
     def timed(fn, reps=2):
         fn()
@@ -432,8 +498,15 @@ def main():
 
     # ---- batched solves (the multi-source and uneven-lattice workloads)
     batch = None
-    if rank == 0 and not args.no_batch and w.prec in ("f32", "f16"):
-        batch = batch_measurement(w.prec, w.recon)
+    if rank == 0 and not args.no_batch:
+        # the batched configuration: FP32 inner iterations, FP64-class residuals
+        batch = batch_measurement("f32", 18)
+
+    # ---- hopping-term sweep over storage precisions, and the small configuration
+    sweep = small = None
+    if rank == 0 and not args.no_sweep:
+        sweep = dslash_sweep(w.dims, U_np)
+        small = small_config_comparison()
 
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
@@ -462,7 +535,9 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"k_dslash<{w.prec},{w.recon}> (plain hop)",
                          "launch_us": dslash_us, "peak_kind": peak_kind,
-                         "bytes_per_launch": op.dslash_bytes},
+                         "bytes_per_launch": op.dslash_bytes,
+                         "frac_of_nominal_8000": achieved / 8000.0,
+                         "traffic_over_algorithmic": (traffic / op.dslash_bytes) if traffic else None},
             "dslash_gflops": 1320.0 * w.vh / (dslash_us * 1e-6) / 1e9,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 2 * spinor_bytes,
                     "d2h_bytes_per_step": spinor_bytes, "ms_per_step": e2e_s / n_e2e * 1e3},
@@ -471,6 +546,8 @@ def main():
             "residual_arithmetic": "double-float (2 x FP32)" if w.prec != "f64" else "f64",
             "batch": batch,
             "twisted_mass": twisted,
+            "dslash_sweep_32x32x32x64": sweep,
+            "small_config": small,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -70,20 +70,45 @@ __device__ __forceinline__ int bt_problem(const BtArgs &a, long t) {
     return pi;
 }
 
-// Per-tile sum of v over the items of each rhs (fixed order), added to the
-// block's slot accumulators.  Every thread of the block must call.  Sums are
-// double-float: the FP64 adder of GB300 is too slow for per-item work.
-__device__ __forceinline__ void bt_tile_sums(df64 v, const BtProb &P, long item0, df64 *tv,
-                                             df64 *sacc) {
-    tv[threadIdx.x] = v;
-    __syncthreads();
+// Per-rhs sums of the items of a tile, without block barriers.  Each warp
+// stages its 32 values (items item0 + 32 w + lane; the item's rhs is item %
+// nrhs) in its own shared-memory row; lane j then adds the values of rhs j in
+// lane order and accumulates them into the warp's slot row wacc[w][slot].
+// bt_block_sums later adds the warps' rows in warp order, so every sum has a
+// fixed order.  Values are double-float (the FP64 adder of GB300 is too slow
+// for per-item work).
+constexpr int BT_WARPS = BT_BLOCK / 32;
+
+__device__ __forceinline__ void bt_warp_sums(df64 v, const BtProb &P, long item0, df64 *wv,
+                                             df64 (*wacc)[BT_MAX_SLOTS]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    wv[threadIdx.x] = v;
+    __syncwarp();
     const int nr = P.nrhs;
-    if ((int)threadIdx.x < nr) {
-        const int j = threadIdx.x;
-        const int i0 = (int)(((long)j - item0 % nr + nr) % nr);
+    const long iw = item0 + 32 * w;
+    const int base = (int)(iw % nr);
+    for (int j = lane; j < nr; j += 32) {
         df64 s = 0;
-        for (int i = i0; i < BT_BLOCK; i += nr) s = s + tv[i];
-        sacc[P.slot0 + j] = sacc[P.slot0 + j] + s;
+        for (int l = (j - base + nr) % nr; l < 32; l += nr) s = s + wv[32 * w + l];
+        wacc[w][P.slot0 + j] = wacc[w][P.slot0 + j] + s;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void bt_zero_sums(df64 (*wacc)[BT_MAX_SLOTS]) {
+    for (int i = threadIdx.x; i < BT_WARPS * BT_MAX_SLOTS; i += BT_BLOCK)
+        wacc[i / BT_MAX_SLOTS][i % BT_MAX_SLOTS] = df64(0.0f, 0.0f);
+    __syncthreads();
+}
+
+// the block's slot sums: the warps' rows added in warp order
+__device__ __forceinline__ void bt_block_sums(df64 (*wacc)[BT_MAX_SLOTS], df64 *sacc, int nslots) {
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < nslots; sl += BT_BLOCK) {
+        df64 t = wacc[0][sl];
+#pragma unroll
+        for (int w = 1; w < BT_WARPS; ++w) t = t + wacc[w][sl];
+        sacc[sl] = t;
     }
     __syncthreads();
 }
@@ -148,12 +173,10 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
 template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM>
 __global__ void __launch_bounds__(BT_BLOCK, std::is_same<S, df64>::value ? 3 : 1)
     k_dslash_batch(const __grid_constant__ BtArgs a) {
-    __shared__ df64 tv[BT_BLOCK];
+    __shared__ df64 wv[BT_BLOCK];
+    __shared__ df64 wacc[BT_WARPS][BT_MAX_SLOTS];
     __shared__ df64 sacc[BT_MAX_SLOTS];
-    if (NORM) {
-        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = df64(0.0f, 0.0f);
-        __syncthreads();
-    }
+    if (NORM) bt_zero_sums(wacc);
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long item0 = (t - P.tile0) * BT_BLOCK;
@@ -208,9 +231,12 @@ __global__ void __launch_bounds__(BT_BLOCK, std::is_same<S, df64>::value ? 3 : 1
                 v = to_df(sq);
             }
         }
-        if (NORM) bt_tile_sums(v, P, item0, tv, sacc);
+        if (NORM) bt_warp_sums(v, P, item0, wv, wacc);
     }
-    if (NORM) bt_finish(a, sacc);
+    if (NORM) {
+        bt_block_sums(wacc, sacc, a.nslots);
+        bt_finish(a, sacc);
+    }
 }
 
 // ------------------------------------------------------------------ vector kernels
@@ -221,13 +247,11 @@ enum BtOp { BT_XR = 0, BT_P = 1, BT_NORM = 2, BT_RESCALE = 3 };
 template <typename S, typename R, int OP>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtArgs a) {
     using C = Chunk16<S, R>;
-    __shared__ df64 tv[BT_BLOCK];
+    __shared__ df64 wv[BT_BLOCK];
+    __shared__ df64 wacc[BT_WARPS][BT_MAX_SLOTS];
     __shared__ df64 sacc[BT_MAX_SLOTS];
     constexpr bool RED = OP == BT_XR || OP == BT_NORM;
-    if (RED) {
-        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = df64(0.0f, 0.0f);
-        __syncthreads();
-    }
+    if (RED) bt_zero_sums(wacc);
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long item0 = (t - P.tile0) * BT_BLOCK;
@@ -277,9 +301,12 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtA
                 C::store(P.f[0], i, pv);
             }
         }
-        if (RED) bt_tile_sums(v, P, item0, tv, sacc);
+        if (RED) bt_warp_sums(v, P, item0, wv, wacc);
     }
-    if (RED) bt_finish(a, sacc);
+    if (RED) {
+        bt_block_sums(wacc, sacc, a.nslots);
+        bt_finish(a, sacc);
+    }
 }
 
 // High-precision (FP64 or double-float) kernels over 16-byte chunks:
@@ -290,12 +317,10 @@ enum BtOp64 { BT64_XMY = 0, BT64_XPAY = 1 };
 template <typename H, int OP>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_hi(const __grid_constant__ BtArgs a) {
     using C = Chunk16<H, H>;
-    __shared__ df64 tv[BT_BLOCK];
+    __shared__ df64 wv[BT_BLOCK];
+    __shared__ df64 wacc[BT_WARPS][BT_MAX_SLOTS];
     __shared__ df64 sacc[BT_MAX_SLOTS];
-    if (OP == BT64_XMY) {
-        for (int i = threadIdx.x; i < BT_MAX_SLOTS; i += BT_BLOCK) sacc[i] = df64(0.0f, 0.0f);
-        __syncthreads();
-    }
+    if (OP == BT64_XMY) bt_zero_sums(wacc);
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long item0 = (t - P.tile0) * BT_BLOCK;
@@ -315,9 +340,12 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_hi(const __grid_constant__ BtAr
             C::store(P.f[0], i, d);
             v = to_df(sq);
         }
-        if (OP == BT64_XMY) bt_tile_sums(v, P, item0, tv, sacc);
+        if (OP == BT64_XMY) bt_warp_sums(v, P, item0, wv, wacc);
     }
-    if (OP == BT64_XMY) bt_finish(a, sacc);
+    if (OP == BT64_XMY) {
+        bt_block_sums(wacc, sacc, a.nslots);
+        bt_finish(a, sacc);
+    }
 }
 
 // Conversions over (site, rhs) items, with per-slot constants:
@@ -371,24 +399,42 @@ __global__ void k_bt_rescale_nz(SolverScalars *sc, const double *consts, int nsl
     }
 }
 
+// item i of an [nrhs][V] enumeration: rhs r, lexicographic site lex and the
+// site's parity.  32-bit arithmetic (volumes stay below 2^31) except for the
+// rhs division of items past 2^32.
+__device__ __forceinline__ void bt_item_site(const Geom &g, long i, long V, int &r, long &lex,
+                                             int &par) {
+    if (i < (1L << 32)) {
+        const unsigned iu = (unsigned)i, Vu = (unsigned)V;
+        r = (int)(iu / Vu);
+        lex = (long)(iu - (unsigned)r * Vu);
+    } else {
+        r = (int)(i / V);
+        lex = i - (long)r * V;
+    }
+    unsigned q = (unsigned)lex;
+    unsigned s = q / (unsigned)g.L[0];
+    par = (int)(q - s * (unsigned)g.L[0]);
+    q = s / (unsigned)g.L[1];
+    par += (int)(s - q * (unsigned)g.L[1]);
+    s = q / (unsigned)g.L[2];
+    par += (int)(q - s * (unsigned)g.L[2]) + (int)s;
+    par &= 1;
+}
+
 // Canonical [nrhs][V][3][4] complex128 <-> batched FP64 parity fields.
 template <typename H>
 __global__ void k_bt_pack_full(Geom g, int nrhs, void *even, void *odd, const double *src) {
     const long i = (long)blockIdx.x * BT_BLOCK + threadIdx.x;
     const long V = 2 * g.vh;
     if (i >= V * nrhs) return;
-    const int r = (int)(i / V);
-    const long lex = i - (long)r * V;
-    long q = lex;
-    const int x = (int)(q % g.L[0]); q /= g.L[0];
-    const int y = (int)(q % g.L[1]); q /= g.L[1];
-    const int z = (int)(q % g.L[2]);
-    const int t = (int)(q / g.L[2]);
+    int r, par;
+    long lex;
+    bt_item_site(g, i, V, r, lex, par);
     double v[24];
     const double2 *s2 = (const double2 *)(src + i * 24);
     for (int k = 0; k < 12; ++k) { v[2 * k] = s2[k].x; v[2 * k + 1] = s2[k].y; }
-    Rec<H, 24>::store(((x + y + z + t) & 1) ? odd : even, g.stride * nrhs,
-                      (lex >> 1) * nrhs + r, v);
+    Rec<H, 24>::store(par ? odd : even, g.stride * nrhs, (lex >> 1) * nrhs + r, v);
 }
 
 template <typename H>
@@ -397,16 +443,12 @@ __global__ void k_bt_unpack_full(Geom g, int nrhs, double *dst, const void *even
     const long i = (long)blockIdx.x * BT_BLOCK + threadIdx.x;
     const long V = 2 * g.vh;
     if (i >= V * nrhs) return;
-    const int r = (int)(i / V);
-    const long lex = i - (long)r * V;
-    long q = lex;
-    const int x = (int)(q % g.L[0]); q /= g.L[0];
-    const int y = (int)(q % g.L[1]); q /= g.L[1];
-    const int z = (int)(q % g.L[2]);
-    const int t = (int)(q / g.L[2]);
+    int r, par;
+    long lex;
+    bt_item_site(g, i, V, r, lex, par);
     double v[24];
-    Rec<H, 24>::template load_coherent<double>(((x + y + z + t) & 1) ? odd : even,
-                                               g.stride * nrhs, (lex >> 1) * nrhs + r, v);
+    Rec<H, 24>::template load_coherent<double>(par ? odd : even, g.stride * nrhs,
+                                               (lex >> 1) * nrhs + r, v);
     double2 *d2 = (double2 *)(dst + i * 24);
     for (int k = 0; k < 12; ++k) d2[k] = make_double2(v[2 * k], v[2 * k + 1]);
 }

@@ -44,13 +44,17 @@ __global__ void k_unpack_half(Geom g, double *dst, const void *src) {
     store_canonical(dst, h, v, 24);
 }
 
+// parity of lexicographic site lex (32-bit arithmetic: volumes stay below 2^31;
+// 64-bit division costs tens of instructions per site)
 __device__ __forceinline__ int lex_parity(const Geom &g, long lex) {
-    long r = lex;
-    int x = (int)(r % g.L[0]); r /= g.L[0];
-    int y = (int)(r % g.L[1]); r /= g.L[1];
-    int z = (int)(r % g.L[2]);
-    int t = (int)(r / g.L[2]);
-    return (x + y + z + t) & 1;
+    unsigned r = (unsigned)lex;
+    unsigned q = r / (unsigned)g.L[0];
+    int par = (int)(r - q * (unsigned)g.L[0]);
+    r = q / (unsigned)g.L[1];
+    par += (int)(q - r * (unsigned)g.L[1]);
+    q = r / (unsigned)g.L[2];
+    par += (int)(r - q * (unsigned)g.L[2]) + (int)q;
+    return par & 1;
 }
 
 template <typename S>
