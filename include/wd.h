@@ -127,7 +127,7 @@ int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, int maxiter,
 /* Reliable-update parameters of the mixed-precision solve (ignored for
  * WD_F64): the FP64 residual is recomputed whenever the iterated residual
  * has fallen by ru_delta (0 < ru_delta < 1; default 0.01 for WD_F32, 0.1
- * for WD_F16/WD_BF16) since the last
+ * for WD_F16, 0.3 for WD_BF16) since the last
  * recomputation, and the Krylov direction restarts when the iterated residual
  * has not improved for stall_iters iterations (default 200). */
 int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters);
