@@ -87,6 +87,16 @@ def test_null_handles_are_rejected(lib):
     lib.wd_last_error.restype = ctypes.c_char_p
     assert b"null" in lib.wd_last_error()
     lib.wd_op_destroy(None)   # no-op
+    lib.wd_apply_eo_residual.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int]
+    assert lib.wd_apply_eo_residual(None, None, None, 1, 0) == 1
+    lib.wd_op_set_twisted_mass.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    assert lib.wd_op_set_twisted_mass(None, 0.1) == 1
+    lib.wd_op_twisted_mass.argtypes = [ctypes.c_void_p]
+    lib.wd_op_twisted_mass.restype = ctypes.c_double
+    assert lib.wd_op_twisted_mass(None) == 0.0
+    lib.wd_dslash_tuning.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.wd_dslash_tuning(None, 0, None, 0, None, None, None) == -1
 
 
 def test_product_path_has_no_cpu_fallback():
