@@ -20,7 +20,8 @@ Printed as one JSON line:
   dslash_sweep  the hopping term alone for every storage precision and link
                 compression on the same lattice
   small_config  16^3 x 32, FP32 with reliable updates against plain FP64 CG
-  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample; it also
+                recomputes the FP64 true residual of the timed solve's solution
 
 Multi-GPU (torchrun): independent replicas, one per GPU, each with its own
 source (there is no data exchange on this path); value sums the ranks' bytes
@@ -184,9 +185,15 @@ def fp64_schur_bytes(vh: int) -> float:
     return 8.0 * vh * ((48 + 144) + (48 + 144 + 24))
 
 
-def cpu_baseline(w, U, b, seconds_target=15.0):
-    """Time the FP64 oracle's Schur operator on the host cores (bounded sample)."""
+def cpu_baseline(w, U, b, x=None, seconds_target=15.0):
+    """Time the FP64 oracle's Schur operator on the host cores (bounded sample),
+    and, given the timed solve's solution x, let the oracle recompute its FP64
+    true residual ||b - D x|| / ||b||."""
     import oracle
+    check = None
+    if x is not None:
+        r = b - oracle.apply(x, U, w.dims, w.kappa, w.phase)
+        check = float(np.linalg.norm(r) / np.linalg.norm(b))
     half = syn.to_half(b, w.dims, 1)
     t0 = time.perf_counter()
     n = 0
@@ -198,6 +205,7 @@ def cpu_baseline(w, U, b, seconds_target=15.0):
             break
     return {"value": fp64_schur_bytes(w.vh) * n / el / 1e9, "unit": "GB/s",
             "cores": oracle.num_threads(), "kind": "oracle",
+            "oracle_true_rel_resid_of_timed_solve": check,
             "sample": f"{n} FP64 Schur-operator applications (2 hops each) of the oracle on "
                       f"{'x'.join(map(str, w.dims))}, {el:.1f} s; bytes counted as the FP64 "
                       f"compulsory traffic"}
@@ -398,7 +406,8 @@ def main():
         e0.record(stream)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            infos.append(solve().info)
+            last = solve()
+            infos.append(last.info)
         e1.record(stream)
         torch.cuda.synchronize()
         host_s = time.perf_counter() - t0
@@ -511,7 +520,7 @@ def main():
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, U_np, b_np)
+        cpu = cpu_baseline(w, U_np, b_np, last.x.cpu().numpy())
 
     if rank == 0:
         ms = elapsed_ms / args.steps
