@@ -29,7 +29,7 @@ from .build import build_oracle, library_path
 __all__ = [
     "gamma", "hop", "hop_sites", "apply", "apply_eo", "hop_eo", "schur_prepare",
     "schur_reconstruct", "cgnr", "solve", "dense_matrix", "num_threads",
-    "build_oracle",
+    "build_oracle", "CR_METHODS", "cr", "solve_cr",
 ]
 
 _lib = None
@@ -70,6 +70,12 @@ def _load():
         lib.oracle_solve_tm.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int, d, ctypes.c_int,
                                         ip]
         lib.oracle_solve_tm.restype = ctypes.c_int
+        lib.oracle_cr.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int, ctypes.c_int, d,
+                                  ctypes.c_int, ip, dp]
+        lib.oracle_cr.restype = ctypes.c_int
+        lib.oracle_solve_cr.argtypes = [dp, dp, dp, ip, d, d, dp, ctypes.c_int, ctypes.c_int, d,
+                                        ctypes.c_int, ip]
+        lib.oracle_solve_cr.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -294,3 +300,42 @@ def solve_tm(b_full, U, dims, kappa, mu, phase, parity=1, tol=1e-12, maxiter=100
                                  _dp(_phase(phase)), int(parity), float(tol), int(maxiter),
                                  ctypes.byref(it))
     return x, it.value, rc == 0
+
+
+# ------------------------------------------------------- conjugate residual
+# Sec. 5 compares CRNE, MCR1 and MCR2 with CGNR on the Schur system without
+# defining them; wilson_oracle.c states the textbook readings (CR of Saad,
+# Alg. 6.20, on A A^dag and on gamma_5 A).
+
+CR_METHODS = {"crne": 1, "mcr1": 2, "mcr2": 3}
+
+
+def cr(b_half, U, dims, kappa, phase, method, mu=0.0, parity=1, tol=1e-12, maxiter=10000):
+    """CRNE / MCR1 / MCR2 on Mhat_p (twisted mass mu, CRNE only: MCR needs
+    gamma5-hermiticity).  Returns (x, iterations, status, ||r_k|| history);
+    status 0 converged, 1 maxiter, 2 breakdown."""
+    b_half, U = _c128(b_half), _c128(U)
+    x = np.empty_like(b_half)
+    it = ctypes.c_int(0)
+    hist = np.zeros(maxiter + 1, dtype=np.float64)
+    rc = _load().oracle_cr(_dp(x), _dp(b_half), _dp(U), _dims(dims), float(kappa), float(mu),
+                           _dp(_phase(phase)), int(parity), CR_METHODS[method], float(tol),
+                           int(maxiter), ctypes.byref(it), _dp(hist))
+    if rc < 0:
+        raise ValueError("oracle_cr: unknown method, MCR with mu != 0 or non-diagonal gamma_5")
+    return x, it.value, rc, hist[: it.value + 1].copy()
+
+
+def solve_cr(b_full, U, dims, kappa, phase, method, mu=0.0, parity=1, tol=1e-12, maxiter=10000):
+    """x = D^-1 b with Alg. "schur" around CRNE / MCR1 / MCR2.
+    Returns (x, iterations, status)."""
+    b_full, U = _c128(b_full), _c128(U)
+    x = np.empty_like(b_full)
+    it = ctypes.c_int(0)
+    rc = _load().oracle_solve_cr(_dp(x), _dp(b_full), _dp(U), _dims(dims), float(kappa),
+                                 float(mu), _dp(_phase(phase)), int(parity), CR_METHODS[method],
+                                 float(tol), int(maxiter), ctypes.byref(it))
+    if rc < 0:
+        raise ValueError("oracle_solve_cr: unknown method, MCR with mu != 0 or non-diagonal "
+                         "gamma_5")
+    return x, it.value, rc

@@ -543,6 +543,155 @@ int oracle_solve_tm(double *x_full, const double *b_full, const double *U, const
     return rc;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Conjugate-residual solvers on the Schur system.  Sec. 5 (Fig. "algosxp")
+ * compares CRNE, MCR1 and MCR2 with CGNR, all on the Schur-reduced system,
+ * without defining them; these are the textbook readings.
+ *
+ * CR (Saad, "Iterative Methods for Sparse Linear Systems", 2nd ed., Alg.
+ * 6.20) solves B y = c for a Hermitian B and minimises ||c - B y|| over the
+ * Krylov space K_k(B, c):
+ *   r = c, p = r, Bp = B p
+ *   alpha = (r|B r) / (Bp|Bp),  y += alpha p,  r -= alpha Bp
+ *   beta = (r'|B r') / (r|B r),  p = r' + beta p,  Bp = B r' + beta Bp
+ *
+ *   CRNE (method 1): B = A A^dag (Hermitian positive definite), c = b, and
+ *                    x = A^dag y at the end.
+ *   MCR1 (method 2): B = gamma_5 A, c = gamma_5 b.  gamma_5 A is Hermitian
+ *                    because A^dag = gamma_5 A gamma_5 (Fig. "id"), and
+ *                    indefinite.  Bp is formed by an application of B every
+ *                    iteration.  With a twisted mass gamma_5 A(mu) gamma_5 =
+ *                    A(-mu)^dag, so MCR is defined for mu = 0 only.
+ *   MCR2 (method 3): as MCR1, with Bp from the recurrence above: one
+ *                    application of A per iteration instead of two.
+ * A = Mhat_p with the twisted mass (mu = 0: the Wilson operator).  The CR
+ * residual r = c - B y has the norm of the Schur residual b - A x in every
+ * case (gamma_5 is unitary).  (r|B r) is real for a Hermitian B; its
+ * rounding-level imaginary part is dropped.
+ */
+typedef struct {
+    const double *U, *phase;
+    const int *dims;
+    double kappa, mu;
+    int parity, method;
+    long n;
+    cplx *tmp;
+    double g5[4];
+} cr_ctx;
+
+static void cr_gamma5(const cr_ctx *c, cplx *v) {
+    for (long i = 0; i < c->n; ++i) v[i] *= c->g5[i % 4];
+}
+
+/* out = B in */
+static void cr_apply_B(const cr_ctx *c, cplx *out, const cplx *in) {
+    if (c->method == 1) {
+        oracle_apply_eo_tm((double *)c->tmp, (const double *)in, c->U, c->dims, c->kappa, c->mu,
+                           c->phase, c->parity, 1);
+        oracle_apply_eo_tm((double *)out, (const double *)c->tmp, c->U, c->dims, c->kappa, c->mu,
+                           c->phase, c->parity, 0);
+    } else {
+        oracle_apply_eo_tm((double *)out, (const double *)in, c->U, c->dims, c->kappa, c->mu,
+                           c->phase, c->parity, 0);
+        cr_gamma5(c, out);
+    }
+}
+
+static cplx dot(const cplx *a, const cplx *b, long n) {
+    cplx s = 0;
+    for (long i = 0; i < n; ++i) s += conj(a[i]) * b[i];
+    return s;
+}
+
+/* The CR loop above with A = Mhat_p, on half-lattice vectors.
+ * Stops when ||r|| <= tol * ||b|| or after maxiter iterations; resid
+ * (optional, length maxiter + 1) receives ||r_k||.  Returns 0 when
+ * converged, 1 at maxiter, 2 on a breakdown ((r|B r) or (Bp|Bp) zero),
+ * -1 for an unknown method, MCR with mu != 0 or a non-diagonal gamma_5.   */
+int oracle_cr(double *x_, const double *b_, const double *U, const int *dims, double kappa,
+              double mu, const double *phase, int parity, int method, double tol, int maxiter,
+              int *iters_out, double *resid) {
+    if (method < 1 || method > 3 || (method != 1 && mu != 0.0)) return -1;
+    geom g = make_geom(dims);
+    cr_ctx c = {U, phase, dims, kappa, mu, parity, method, 12 * (g.vol / 2), NULL, {0}};
+    cplx g5m[4][4];
+    gamma_matrix(4, g5m);
+    for (int s = 0; s < 4; ++s) {
+        for (int t = 0; t < 4; ++t)
+            if (t != s && cabs(g5m[s][t]) != 0.0) return -1;
+        c.g5[s] = creal(g5m[s][s]);
+    }
+    const long n = c.n;
+    const cplx *b = (const cplx *)b_;
+    cplx *y = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *r = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *p = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *Br = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *Bp = (cplx *)malloc(sizeof(cplx) * n);
+    c.tmp = (cplx *)malloc(sizeof(cplx) * n);
+
+    memset(y, 0, sizeof(cplx) * n);                      /* y = 0           */
+    memcpy(r, b, sizeof(cplx) * n);                      /* r = c           */
+    if (method != 1) cr_gamma5(&c, r);
+    memcpy(p, r, sizeof(cplx) * n);                      /* p = r           */
+    cr_apply_B(&c, Br, r);                               /* B r             */
+    memcpy(Bp, Br, sizeof(cplx) * n);                    /* B p = B r       */
+    double rBr = creal(dot(r, Br, n));
+    double nr = norm2(r, n);
+    const double eps = tol * tol * norm2(b, n);
+    int k = 0, rc = 1;
+    if (resid) resid[0] = sqrt(nr);
+    while (nr > eps && k < maxiter) {
+        const double nBp = norm2(Bp, n);
+        if (rBr == 0.0 || nBp == 0.0) { rc = 2; break; }
+        const double alpha = rBr / nBp;
+        for (long i = 0; i < n; ++i) y[i] += alpha * p[i];
+        for (long i = 0; i < n; ++i) r[i] -= alpha * Bp[i];
+        cr_apply_B(&c, Br, r);
+        const double rBr1 = creal(dot(r, Br, n));
+        const double beta = rBr1 / rBr;
+        for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        if (method == 2)
+            cr_apply_B(&c, Bp, p);
+        else
+            for (long i = 0; i < n; ++i) Bp[i] = Br[i] + beta * Bp[i];
+        rBr = rBr1;
+        nr = norm2(r, n);
+        ++k;
+        if (resid) resid[k] = sqrt(nr);
+    }
+    if (nr <= eps) rc = 0;
+    if (method == 1)                                     /* x = A^dag y     */
+        oracle_apply_eo_tm(x_, (const double *)y, U, dims, kappa, mu, phase, parity, 1);
+    else
+        memcpy(x_, y, sizeof(cplx) * n);
+    if (iters_out) *iters_out = k;
+    free(y); free(r); free(p); free(Br); free(Bp); free(c.tmp);
+    return rc;
+}
+
+/* x = D^-1 b with Alg. "schur" around oracle_cr (tol relative to ||b||, as
+ * in oracle_solve).                                                        */
+int oracle_solve_cr(double *x_full, const double *b_full, const double *U, const int *dims,
+                    double kappa, double mu, const double *phase, int parity, int method,
+                    double tol, int maxiter, int *iters_out) {
+    geom g = make_geom(dims);
+    long vh = g.vol / 2;
+    cplx *bhat = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    cplx *xp = (cplx *)malloc(sizeof(cplx) * 12 * vh);
+    oracle_schur_prepare_tm((double *)bhat, b_full, U, dims, kappa, mu, phase, parity);
+    double nb = sqrt(norm2((const cplx *)b_full, 12 * g.vol));
+    double nbh = sqrt(norm2(bhat, 12 * vh));
+    double rel = nbh > 0 ? tol * nb / nbh : tol;
+    int rc = oracle_cr((double *)xp, (double *)bhat, U, dims, kappa, mu, phase, parity, method,
+                       rel, maxiter, iters_out, NULL);
+    if (rc >= 0)
+        oracle_schur_reconstruct_tm(x_full, (double *)xp, b_full, U, dims, kappa, mu, phase,
+                                    parity);
+    free(bhat); free(xp);
+    return rc;
+}
+
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */
 #ifdef _OPENMP
 #include <omp.h>

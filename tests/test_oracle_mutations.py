@@ -34,15 +34,33 @@ MUTANTS = [
      "oracle_twist((double *)xq, (double *)v, vh, kappa, mu, 0);"),
 ]
 
+# The conjugate-residual solvers sit on top of the operator that the pins
+# above already hold; their mutants are run against the solver pins alone (a
+# subset of the full set, so rejection by it implies rejection by all).
+CR_MUTANTS = [
+    ("MCR without gamma5 on the right-hand side", "if (method != 1) cr_gamma5(&c, r);",
+     "if (method == 0) cr_gamma5(&c, r);"),
+    ("CR step length from (r|r)", "const double alpha = rBr / nBp;",
+     "const double alpha = nr / nBp;"),
+    ("CR beta inverted", "const double beta = rBr1 / rBr;", "const double beta = rBr / rBr1;"),
+    ("CRNE returns y instead of A^dag y", "if (method == 1)                                     /*",
+     "if (method == 0)                                     /*"),
+    ("CR recurrence for B p drops beta", "Bp[i] = Br[i] + beta * Bp[i];", "Bp[i] = Br[i] + Bp[i];"),
+]
+
 FAST_PINS = ("test_gamma_basis_clifford or test_free_field_plane_waves or "
              "test_gamma5_hermiticity or test_gauge_covariance or "
              "test_schur_blocks_dense or test_cgnr_schur_solve_matches_lu or "
              "test_twisted_free_field or test_twisted_adjoint_flips_mu or "
              "test_twisted_solve_matches_lu")
+CR_PINS = ("test_cr_iterates_minimise_over_krylov_space or test_cr_solves_match_lu or "
+           "test_cr_special_cases")
 
 
-@pytest.mark.parametrize("desc,orig,planted", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_reject_mutant(tmp_path, desc, orig, planted):
+@pytest.mark.parametrize("desc,orig,planted,pins",
+                         [m + (FAST_PINS,) for m in MUTANTS] + [m + (CR_PINS,) for m in CR_MUTANTS],
+                         ids=[m[0] for m in MUTANTS + CR_MUTANTS])
+def test_pins_reject_mutant(tmp_path, desc, orig, planted, pins):
     src = open(SRC).read()
     assert src.count(orig) == 1, f"mutation anchor not found: {orig}"
     mut = tmp_path / "mut.c"
@@ -52,6 +70,6 @@ def test_pins_reject_mutant(tmp_path, desc, orig, planted):
                     str(lib), "-lm"], check=True)
     env = dict(os.environ, WD_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", FAST_PINS],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", pins],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1 and "1 failed" in r.stdout, (desc, r.stdout[-2000:])

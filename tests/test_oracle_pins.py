@@ -392,3 +392,111 @@ def test_twisted_mass_zero_is_the_wilson_operator(oracle_lib):
     h = syn.to_half(psi, dims, 1)
     assert relerr(oracle_lib.apply_eo_tm(h, U, dims, kappa, 0.0, phase, 1),
                   oracle_lib.apply_eo(h, U, dims, kappa, phase, 1)) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Conjugate-residual solvers.  Sec. 5 compares CRNE, MCR1 and MCR2 with CGNR
+# on the Schur system without defining them; the oracle takes the textbook
+# readings (CR on A A^dag, and CR on the Hermitian gamma5 A with B p formed by
+# the operator or by recurrence).  CR minimises the residual over its Krylov
+# space, so its k-th iterate is fixed by dense linear algebra alone.
+def _dense_schur(oracle_lib, U, dims, kappa, phase, mu, parity):
+    D = oracle_lib.dense_matrix(U, dims, kappa, phase, mu=mu)
+    ie, io = _parity_perm(dims)
+    ip, iq = (ie, io) if parity == 0 else (io, ie)
+    return D[np.ix_(ip, ip)] - D[np.ix_(ip, iq)] @ np.linalg.solve(D[np.ix_(iq, iq)],
+                                                                     D[np.ix_(iq, ip)])
+
+
+def _krylov_minimiser(A, B, c, b, k):
+    """argmin ||b - A x|| over x in K_k(B, c): an orthonormal basis of the
+    Krylov space (Gram-Schmidt, applied twice) and a dense least-squares solve."""
+    Q = np.zeros((len(c), k), dtype=complex)
+    v = c / np.linalg.norm(c)
+    for j in range(k):
+        for _ in range(2):
+            v = v - Q[:, :j] @ (Q[:, :j].conj().T @ v)
+        Q[:, j] = v / np.linalg.norm(v)
+        v = B @ Q[:, j]
+    coef = np.linalg.lstsq(A @ Q, b, rcond=None)[0]
+    return Q @ coef
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.1])
+def test_cr_iterates_minimise_over_krylov_space(oracle_lib, mu):
+    """CRNE's k-th iterate minimises ||b - A x|| over K_k(A^dag A, A^dag b);
+    MCR1's and MCR2's over K_k(gamma5 A, gamma5 b) (mu = 0 only: gamma5 A is
+    Hermitian for the Wilson operator alone)."""
+    dims, kappa, parity = (4, 4, 2, 4), 0.124, 1
+    phase = syn.workloads.APBC_T
+    U = syn.su3_links(dims, eps=0.3, seed=4)
+    b = syn.to_half(syn.gaussian_spinor(syn.volume(dims), 6), dims, parity)
+    A = _dense_schur(oracle_lib, U, dims, kappa, phase, mu, parity)
+    bv = b.ravel()
+    G = np.kron(np.eye(len(bv) // 4), G5)
+    spaces = {"crne": (A.conj().T @ A, A.conj().T @ bv), "mcr1": (G @ A, G @ bv),
+              "mcr2": (G @ A, G @ bv)}
+    for method, (B, c) in spaces.items():
+        if method != "crne" and mu != 0.0:
+            assert np.abs(G @ A - (G @ A).conj().T).max() > 1e-3   # not Hermitian
+            with pytest.raises(ValueError):
+                oracle_lib.cr(b, U, dims, kappa, phase, method, mu=mu, parity=parity)
+            continue
+        assert method == "crne" or np.abs(B - B.conj().T).max() < 1e-14
+        for k in (1, 2, 4, 7):
+            x, iters, status, _ = oracle_lib.cr(b, U, dims, kappa, phase, method, mu=mu,
+                                                parity=parity, tol=1e-30, maxiter=k)
+            assert iters == k and status == 1
+            ref = _krylov_minimiser(A, B, c, bv, k)
+            assert relerr(x.ravel(), ref) < 1e-9, (method, k, relerr(x.ravel(), ref))
+
+
+@pytest.mark.parametrize("dims,parity", [((2, 2, 2, 2), 1), ((4, 4, 2, 4), 0)])
+def test_cr_solves_match_lu(oracle_lib, dims, parity):
+    """Schur prepare, CRNE / MCR1 / MCR2 and reconstruction give the dense LU
+    solution of D x = b, with and without the twisted mass."""
+    kappa = 0.124
+    phase = syn.workloads.APBC_T
+    U = syn.su3_links(dims, eps=0.3, seed=1)
+    b = syn.gaussian_spinor(syn.volume(dims), 2)
+    for mu in (0.0, 0.1):
+        D = oracle_lib.dense_matrix(U, dims, kappa, phase, mu=mu)
+        x_lu = np.linalg.solve(D, b.ravel())
+        for method in ("crne", "mcr1", "mcr2") if mu == 0.0 else ("crne",):
+            x, iters, status = oracle_lib.solve_cr(b, U, dims, kappa, phase, method, mu=mu,
+                                                   parity=parity, tol=1e-13, maxiter=2000)
+            assert status == 0 and iters > 0, (method, mu, status)
+            assert np.linalg.norm(b.ravel() - D @ x.ravel()) <= 1.01e-13 * np.linalg.norm(b)
+            assert relerr(x.ravel(), x_lu) < 10 * np.linalg.cond(D) * 1e-13
+
+
+def test_cr_special_cases(oracle_lib):
+    """kappa = 0 (A = 1): CRNE takes one iteration; MCR (B = gamma5, eigenvalues
+    +-1) exactly two; both end at x = b.  The CR residual never grows
+    (residual minimisation over nested spaces).  CRNE and CGNR minimise the
+    same residual over the same space, so their iterates agree; MCR1 and MCR2
+    differ only in how B p is formed."""
+    dims, parity = (4, 4, 2, 4), 1
+    phase = syn.workloads.APBC_T
+    U = syn.su3_links(dims, eps=0.3, seed=2)
+    b = syn.to_half(syn.gaussian_spinor(syn.volume(dims), 3), dims, parity)
+    for method in ("crne", "mcr1", "mcr2"):
+        # MCR's second step divides by its first coefficient (gamma5 b | b) / ||b||^2,
+        # of order 1/sqrt(n): the exact two-step answer carries ~1e-14 rounding
+        x, iters, status, _ = oracle_lib.cr(b, U, dims, 0.0, phase, method, parity=parity,
+                                            tol=1e-12, maxiter=10)
+        assert status == 0 and iters == (1 if method == "crne" else 2) and relerr(x, b) < 1e-12
+        _, _, status, hist = oracle_lib.cr(b, U, dims, 0.124, phase, method, parity=parity,
+                                           tol=1e-12, maxiter=500)
+        assert status == 0 and np.all(np.diff(hist) <= 1e-14 * hist[0])
+    for k in (3, 10, 25):
+        xc, _, _, _ = oracle_lib.cgnr(b, U, dims, 0.124, phase, parity=parity, tol=1e-30,
+                                      maxiter=k)
+        xr, _, _, _ = oracle_lib.cr(b, U, dims, 0.124, phase, "crne", parity=parity, tol=1e-30,
+                                    maxiter=k)
+        assert relerr(xr, xc) < 1e-11
+        x1, _, _, _ = oracle_lib.cr(b, U, dims, 0.124, phase, "mcr1", parity=parity, tol=1e-30,
+                                    maxiter=k)
+        x2, _, _, _ = oracle_lib.cr(b, U, dims, 0.124, phase, "mcr2", parity=parity, tol=1e-30,
+                                    maxiter=k)
+        assert relerr(x2, x1) < 1e-11
