@@ -20,6 +20,9 @@ Printed as one JSON line:
   dslash_sweep  the hopping term alone for every storage precision and link
                 compression on the same lattice
   small_config  16^3 x 32, FP32 with reliable updates against plain FP64 CG
+  solver_comparison  the solvers of Sec. 5 (CGNR, CRNE, MCR1, MCR2) in FP64 on
+                the paper's 24^3 x 48 lattice: iterations, time per iteration,
+                time to the 1e-10 residual
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample; it also
                 recomputes the FP64 true residual of the timed solve's solution
 
@@ -69,6 +72,8 @@ def parse_args():
                     help="skip the twisted-mass solve comparison (reported as null)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the hopping-term precision sweep and the 16^3 x 32 comparison")
+    ap.add_argument("--no-solvers", action="store_true",
+                    help="skip the CGNR / CRNE / MCR1 / MCR2 comparison on 24^3 x 48")
     return ap.parse_args()
 
 
@@ -273,6 +278,27 @@ def dslash_sweep(dims, U_np, launches: int = 50):
             out[f"{prec}_r{recon}"] = {"us": us, "gbs": op.dslash_bytes / (us * 1e-6) / 1e9,
                                        "gflops": 1320.0 * vh / (us * 1e-6) / 1e9}
             op.close()
+    return out
+
+
+def oracle_solver_sample(workload, iterations=2):
+    """The FP64 oracle's CGNR / CRNE / MCR1 / MCR2 on the host cores, a
+    bounded sample: the first iterations from x = 0 on the same Schur system."""
+    import oracle
+    w = syn.WORKLOADS[workload]
+    U = syn.su3_links(w.dims, eps=w.eps, seed=w.gauge_seed)
+    b = syn.gaussian_spinor(w.volume, w.source_seed)
+    bhat = oracle.schur_prepare(b, U, w.dims, w.kappa, w.phase, 1)
+    out = {"sample": f"{iterations} iterations from x = 0 on {w.name}",
+           "cores": oracle.num_threads()}
+    for m in ("cgnr", "crne", "mcr1", "mcr2"):
+        t0 = time.perf_counter()
+        if m == "cgnr":
+            oracle.cgnr(bhat, U, w.dims, w.kappa, w.phase, 1, tol=1e-30, maxiter=iterations)
+        else:
+            oracle.cr(bhat, U, w.dims, w.kappa, w.phase, m, parity=1, tol=1e-30,
+                      maxiter=iterations)
+        out[m] = {"ms_per_iteration": (time.perf_counter() - t0) * 1e3 / iterations}
     return out
 
 
@@ -517,6 +543,14 @@ def main():
         sweep = dslash_sweep(w.dims, U_np)
         small = small_config_comparison()
 
+    # ---- the solver comparison of Sec. 5 on the paper's 24^3 x 48 lattice
+    solvers = None
+    if rank == 0 and not args.no_solvers:
+        from paper_1401_2039_gb300.compare_solvers import compare
+        solvers = compare("wilson_24x24x24x48_f32", reps=1)
+        if world == 1 and not args.no_cpu_baseline:
+            solvers["oracle"] = oracle_solver_sample("wilson_24x24x24x48_f32")
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -557,6 +591,7 @@ def main():
             "twisted_mass": twisted,
             "dslash_sweep_32x32x32x64": sweep,
             "small_config": small,
+            "solver_comparison": solvers,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -313,6 +313,46 @@ int wd_fgcr_solve(wd_fgcr *solver, double *x, const double *b, double tol, int m
                   wd_solve_info *info);
 const char *wd_fgcr_last_error(void);
 
+/* The other solvers of the paper's solver comparison (Sec. 5, Fig.
+ * "algosxp": CGNR, CRNE, MCR1, MCR2 on the Schur system), which the paper
+ * names without defining; textbook readings:
+ *   WD_KRYLOV_CGNR  Alg. "CGNR" (as wd_solve_cg with WD_F64, host-driven)
+ *   WD_KRYLOV_CRNE  conjugate residual (Saad, Iterative Methods for Sparse
+ *                   Linear Systems, Alg. 6.20) on Mhat Mhat^dag y = bhat,
+ *                   x = Mhat^dag y; two operator applications per iteration
+ *   WD_KRYLOV_MCR1  conjugate residual on the Hermitian indefinite
+ *                   gamma5 Mhat x = gamma5 bhat, B p formed by the operator
+ *                   (two applications per iteration)
+ *   WD_KRYLOV_MCR2  the same with B p updated by recurrence (one application)
+ * MCR relies on gamma5-hermiticity (Mhat^dag = gamma5 Mhat gamma5), which a
+ * twisted mass breaks: a solve with mu != 0 returns WD_ERR_ARG for MCR1/2.
+ *
+ * wd_krylov_create: op must be a WD_F64 operator (the methods run in FP64);
+ * the handle owns 9 half-lattice FP64 fields and keeps a pointer to op,
+ * which must outlive it.  wd_krylov_solve: the same arguments and layout as
+ * wd_solve_cg (x, b device canonical [V][3][4] complex128; the parity-p part
+ * of x on entry is the initial guess), the same Schur preparation and
+ * reconstruction (with the twisted mass of op), and x is accepted only on
+ * the FP64 true residual ||b - D x|| / ||b|| <= tol; when the recursive
+ * residual met the target but the true one does not, the method restarts
+ * from x.  info->iters counts iterations, info->reliable_updates true-
+ * residual checks, info->dslash_hi hopping terms.  Returns WD_OK,
+ * WD_ERR_NOT_CONVERGED, WD_ERR_BREAKDOWN ((r|B r) or |B p| zero, or a
+ * non-finite residual), WD_ERR_ARG or WD_ERR_STATE (no gauge field);
+ * blocks until done. */
+typedef enum {
+    WD_KRYLOV_CGNR = 0,
+    WD_KRYLOV_CRNE = 1,
+    WD_KRYLOV_MCR1 = 2,
+    WD_KRYLOV_MCR2 = 3
+} wd_krylov_method;
+typedef struct wd_krylov wd_krylov;
+int wd_krylov_create(wd_krylov **solver, wd_op *op, int method);
+void wd_krylov_destroy(wd_krylov *solver);
+int wd_krylov_solve(wd_krylov *solver, double *x, const double *b, double tol, int maxiter,
+                    int parity, wd_solve_info *info);
+const char *wd_krylov_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

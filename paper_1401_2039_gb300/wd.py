@@ -539,3 +539,57 @@ class Fgcr:
         if check and rc != WD_OK:
             raise WDError(rc, self.lib.wd_fgcr_last_error().decode())
         return SolveResult(x, rc, info.as_dict())
+
+
+KRYLOV_METHODS = {"cgnr": 0, "crne": 1, "mcr1": 2, "mcr2": 3}
+
+
+class Krylov:
+    """CGNR, CRNE, MCR1 or MCR2 on the Schur system of a WD_F64 operator
+    (the solvers of the paper's solver comparison; handle on a wd_krylov)."""
+
+    def __init__(self, op: WilsonDirac, method: str):
+        if method not in KRYLOV_METHODS:
+            raise ValueError(f"method must be one of {sorted(KRYLOV_METHODS)}, got {method!r}")
+        self.lib = load_library()
+        vp, i = ctypes.c_void_p, ctypes.c_int
+        for name, res, args in (("wd_krylov_create", i, [ctypes.POINTER(vp), vp, i]),
+                                ("wd_krylov_destroy", None, [vp]),
+                                ("wd_krylov_solve", i, [vp, vp, vp, ctypes.c_double, i, i,
+                                                        ctypes.POINTER(SolveInfo)]),
+                                ("wd_krylov_last_error", ctypes.c_char_p, [])):
+            f = getattr(self.lib, name)
+            f.restype = res
+            f.argtypes = args
+        self.op = op                      # keep it alive
+        self.method = method
+        self.V = op.V
+        handle = ctypes.c_void_p()
+        rc = self.lib.wd_krylov_create(ctypes.byref(handle), op.handle, KRYLOV_METHODS[method])
+        if rc != WD_OK:
+            raise WDError(rc, self.lib.wd_krylov_last_error().decode())
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.wd_krylov_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b: torch.Tensor, tol: float = 1e-10, maxiter: int = 20000, parity: int = 1,
+              x0: torch.Tensor | None = None, check: bool = True) -> SolveResult:
+        _dev(b, (self.V, 3, 4), "b")
+        x = torch.zeros_like(b) if x0 is None else _dev(x0, (self.V, 3, 4), "x0").clone()
+        info = SolveInfo()
+        torch.cuda.synchronize()
+        rc = self.lib.wd_krylov_solve(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(b.data_ptr()), float(tol), int(maxiter),
+                                      int(parity), ctypes.byref(info))
+        if check and rc != WD_OK:
+            raise WDError(rc, self.lib.wd_krylov_last_error().decode())
+        return SolveResult(x, rc, info.as_dict())

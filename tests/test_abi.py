@@ -97,6 +97,16 @@ def test_null_handles_are_rejected(lib):
     lib.wd_dslash_tuning.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.wd_dslash_tuning(None, 0, None, 0, None, None, None) == -1
+    lib.wd_krylov_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    assert lib.wd_krylov_create(None, None, 1) == 1
+    h = ctypes.c_void_p()
+    assert lib.wd_krylov_create(ctypes.byref(h), None, 1) == 1 and not h.value
+    lib.wd_krylov_solve.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                            ctypes.c_int, ctypes.c_void_p]
+    assert lib.wd_krylov_solve(None, None, None, 1e-10, 100, 1, None) == 1
+    lib.wd_krylov_last_error.restype = ctypes.c_char_p
+    assert b"null" in lib.wd_krylov_last_error()
+    lib.wd_krylov_destroy(None)   # no-op
 
 
 def test_product_path_has_no_cpu_fallback():
