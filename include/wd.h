@@ -188,6 +188,13 @@ int wd_batch_dslash_resident(wd_batch *bt, int out_parity, int dagger);
 int wd_batch_solve(wd_batch *bt, double *const *x, const double *const *b, double tol,
                    int maxiter, int parity, wd_solve_info *info);
 const char *wd_batch_last_error(void);
+/* One-call form of the batched solve: wd_batch_create, wd_batch_solve and
+ * wd_batch_destroy in one (the same arguments, order and errors; the error
+ * text is in wd_batch_last_error).  It allocates and frees the batch's
+ * fields on every call; repeated solves should keep a wd_batch instead. */
+int wd_solve_cg_multi(wd_op *const *ops, int nops, double *const *x, const double *const *b,
+                      const int *nrhs, double tol, int maxiter, int parity,
+                      wd_solve_info *info);
 
 /* Resident fields for timing the hopping term alone: slot 0 and 1 are two
  * half-lattice spinors the handle owns, in its internal layout and storage

@@ -1099,4 +1099,17 @@ int wd_batch_solve(wd_batch *bt, double *const *x, const double *const *b, doubl
     return rc != WD_OK ? rc : rj;
 }
 
+int wd_solve_cg_multi(wd_op *const *ops, int nops, double *const *x, const double *const *b,
+                      const int *nrhs, double tol, int maxiter, int parity,
+                      wd_solve_info *info) {
+    wd_batch *bt = nullptr;
+    const int rc = wd_batch_create(&bt, ops, nrhs, nops);
+    if (rc != WD_OK) return rc;
+    const int rs = wd_batch_solve(bt, x, b, tol, maxiter, parity, info);
+    const std::string err = g_bt_error;
+    wd_batch_destroy(bt);
+    g_bt_error = err;
+    return rs;
+}
+
 }  // extern "C"

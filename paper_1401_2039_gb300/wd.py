@@ -265,6 +265,33 @@ class WilsonDirac:
                                            int(bool(dagger))))
 
 
+def solve_cg_multi(ops, nrhs, bs, tol: float = 1e-10, maxiter: int = 20000, parity: int = 1,
+                   x0s=None, check: bool = True):
+    """One-call batched solve (wd_solve_cg_multi): bs[k] is [nrhs_k, V_k, 3, 4]
+    for operator ops[k].  Returns (xs, status, infos) like WilsonBatch.solve."""
+    lib = load_library()
+    _setup_batch_signatures(lib)
+    if len(ops) != len(nrhs) or len(bs) != len(ops):
+        raise ValueError("one nrhs and one right-hand-side tensor per operator")
+    nrhs = [int(n) for n in nrhs]
+    shapes = [(n, op.V, 3, 4) for n, op in zip(nrhs, ops)]
+    for t, shp in zip(bs, shapes):
+        _dev(t, shp, "b")
+    xs = [torch.zeros(sh, dtype=torch.complex128, device="cuda") for sh in shapes] \
+        if x0s is None else [x.clone() for x in x0s]
+    for t, shp in zip(xs, shapes):
+        _dev(t, shp, "x0")
+    vpa = ctypes.c_void_p * len(ops)
+    infos = (SolveInfo * sum(nrhs))()
+    rc = lib.wd_solve_cg_multi(vpa(*[op.handle for op in ops]), len(ops),
+                               vpa(*[x.data_ptr() for x in xs]), vpa(*[b.data_ptr() for b in bs]),
+                               (ctypes.c_int * len(ops))(*nrhs), float(tol), int(maxiter),
+                               int(parity), infos)
+    if check and rc != WD_OK:
+        raise WDError(rc, lib.wd_batch_last_error().decode())
+    return xs, rc, [i.as_dict() for i in infos]
+
+
 class WilsonBatch:
     """Lockstep batch of systems: several operators (lattices of any size, same
     storage precision) with nrhs right-hand sides each (handle on a wd_batch)."""
@@ -353,6 +380,8 @@ def _setup_batch_signatures(lib):
         "wd_batch_dslash_resident": (i, [vp, i, i]),
         "wd_batch_solve": (i, [vp, pp, pp, d, i, i, ctypes.POINTER(SolveInfo)]),
         "wd_batch_last_error": (ctypes.c_char_p, []),
+        "wd_solve_cg_multi": (i, [pp, i, pp, pp, ctypes.POINTER(i), d, i, i,
+                                  ctypes.POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

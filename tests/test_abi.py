@@ -107,6 +107,10 @@ def test_null_handles_are_rejected(lib):
     lib.wd_krylov_last_error.restype = ctypes.c_char_p
     assert b"null" in lib.wd_krylov_last_error()
     lib.wd_krylov_destroy(None)   # no-op
+    lib.wd_solve_cg_multi.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    assert lib.wd_solve_cg_multi(None, 1, None, None, None, 1e-10, 100, 1, None) == 1
 
 
 def test_product_path_has_no_cpu_fallback():

@@ -106,3 +106,25 @@ def test_batch_rejects_mixed_precisions():
     b.set_gauge(U)
     with pytest.raises(WDError):
         WilsonBatch([a, b], [1, 1])
+
+
+def test_one_call_multi_solve_equals_the_batch_handle():
+    """wd_solve_cg_multi (create, solve, destroy in one call) gives bitwise the
+    batch handle's solutions and meets the oracle's FP64 true residual."""
+    from paper_1401_2039_gb300 import WDError, solve_cg_multi
+    bt, ops, Us = make("f32", 18)
+    bs = [torch.from_numpy(np.stack([syn.gaussian_spinor(syn.volume(dims), 300 + 3 * k + r)
+                                     for r in range(n)])).cuda()
+          for k, (dims, n, _) in enumerate(PROBLEMS)]
+    xs_h, rc_h, _ = bt.solve(bs, tol=1e-10)
+    xs, rc, infos = solve_cg_multi(ops, [n for _, n, _ in PROBLEMS], bs, tol=1e-10)
+    assert rc == rc_h == 0 and len(infos) == sum(n for _, n, _ in PROBLEMS)
+    for k, (dims, n, kappa) in enumerate(PROBLEMS):
+        assert torch.equal(xs[k], xs_h[k])
+        x, b = xs[k].cpu().numpy(), bs[k].cpu().numpy()
+        for r in range(n):
+            rt = np.linalg.norm(b[r] - oracle.apply(x[r], Us[k], dims, kappa, APBC))
+            assert rt <= 1.05e-10 * np.linalg.norm(b[r])
+    ops[0].set_twisted_mass(0.1)   # batches have no twisted mass: an argument error
+    with pytest.raises(WDError):
+        solve_cg_multi(ops, [n for _, n, _ in PROBLEMS], bs, tol=1e-10)
