@@ -15,7 +15,9 @@ canonical layout:
 
 Parity: every function here is pinned by ``tests/test_oracle_*.py``
 (free-field closed form, gamma5-hermiticity, gauge covariance, Schur
-identity, dense LU, kappa = 0); none is "parity unpinned".
+identity, dense LU, kappa = 0; the conjugate-residual solvers by the dense
+least-squares minimiser over their Krylov spaces); none is "parity
+unpinned".
 """
 from __future__ import annotations
 
