@@ -1,7 +1,7 @@
 // Flexible GCR on the full Wilson-Dirac system D x = b, with an optional
 // right preconditioner (the learned PTC network).  Not in the paper; the
-// plain even-odd CGNR of wd_solve_cg stays the fallback and the judge of its
-// error.
+// plain even-odd CGNR of wd_solve_cg stays the fallback and the reference
+// for its error.
 //
 // Restarted FGCR(m): from the residual r,
 //   z_j = N(r)  (or z_j = r without a network),  w_j = D z_j,
