@@ -129,3 +129,31 @@ def test_product_package_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.lower(), f
+
+
+def _header_enum(name):
+    """{enumerator: value} of the typedef enum `name` in include/wd.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "wd.h")).read(), flags=re.S)
+    m = re.search(r"typedef enum\s*\{([^}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    return {k: int(v) for k, v in re.findall(r"(WD_[A-Z0-9_]+)\s*=\s*(-?\d+)", m.group(1))}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's integer constants are the header's enums (a mismatch
+    would send the wrong precision, method or status across the ABI)."""
+    from paper_1401_2039_gb300 import wd
+    prec = _header_enum("wd_prec")
+    assert {k: prec["WD_" + k.upper()] for k in wd.PRECISIONS} == wd.PRECISIONS
+    methods = _header_enum("wd_krylov_method")
+    assert {k: methods["WD_KRYLOV_" + k.upper()] for k in wd.KRYLOV_METHODS} == wd.KRYLOV_METHODS
+    assert len(methods) == len(wd.KRYLOV_METHODS)
+    status = _header_enum("wd_status")
+    for name, value in status.items():
+        assert getattr(wd, name) == value, name
+
+
+def test_solve_cg_multi_checks_lengths_before_any_call():
+    from paper_1401_2039_gb300 import solve_cg_multi
+    with pytest.raises(ValueError):
+        solve_cg_multi([object()], [1, 2], [None])
