@@ -190,6 +190,56 @@ def fp64_schur_bytes(vh: int) -> float:
     return 8.0 * vh * ((48 + 144) + (48 + 144 + 24))
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
+    implementer and part numbers), with the architecture."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = (t.strip() for t in line.split(":", 1))
+                    fields.setdefault(k, v)
+    except OSError:
+        pass
+    if "model name" in fields:
+        name = fields["model name"]
+    elif "CPU part" in fields:
+        name = f"implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    else:
+        name = platform.processor() or "unknown"
+    return f"{name} ({platform.machine()})"
+
+
+def oracle_timing():
+    """The oracle's own figures: its CGNR solve (Schur preparation, CGNR,
+    reconstruction) to 1e-10 on the 4^4 and 16^3 x 32 workloads on all host
+    cores, and its Schur operator on 16^3 x 32 on one core and on all."""
+    import oracle
+    cores = oracle.num_threads()
+    out = {"cpu_model": cpu_model(), "nproc": os.cpu_count(), "cores": cores, "solves": {}}
+    for name in ("wilson_4x4x4x4_f64", "wilson_16x16x16x32_f32"):
+        w = syn.WORKLOADS[name]
+        U = syn.su3_links(w.dims, eps=w.eps, seed=w.gauge_seed)
+        b = syn.gaussian_spinor(w.volume, w.source_seed)
+        t0 = time.perf_counter()
+        _, iters, ok = oracle.solve(b, U, w.dims, w.kappa, w.phase, tol=w.tol)
+        out["solves"][name] = {"ms": (time.perf_counter() - t0) * 1e3, "iters": iters,
+                               "converged": bool(ok)}
+    half = syn.to_half(b, w.dims, 1)
+    apply_gbs = {}
+    for n_threads in (1, cores):
+        oracle.set_num_threads(n_threads)
+        oracle.apply_eo(half, U, w.dims, w.kappa, w.phase, 1)
+        t0 = time.perf_counter()
+        oracle.apply_eo(half, U, w.dims, w.kappa, w.phase, 1)
+        apply_gbs[f"threads_{n_threads}"] = fp64_schur_bytes(w.vh) / (time.perf_counter() - t0) / 1e9
+    oracle.set_num_threads(cores)
+    out["apply_eo_gbs_16x16x16x32"] = apply_gbs
+    return out
+
+
 def cpu_baseline(w, U, b, x=None, seconds_target=15.0):
     """Time the FP64 oracle's Schur operator on the host cores (bounded sample),
     and, given the timed solve's solution x, let the oracle recompute its FP64
@@ -211,6 +261,7 @@ def cpu_baseline(w, U, b, x=None, seconds_target=15.0):
     return {"value": fp64_schur_bytes(w.vh) * n / el / 1e9, "unit": "GB/s",
             "cores": oracle.num_threads(), "kind": "oracle",
             "oracle_true_rel_resid_of_timed_solve": check,
+            "oracle_timing": oracle_timing(),
             "sample": f"{n} FP64 Schur-operator applications (2 hops each) of the oracle on "
                       f"{'x'.join(map(str, w.dims))}, {el:.1f} s; bytes counted as the FP64 "
                       f"compulsory traffic"}

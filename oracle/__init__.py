@@ -30,7 +30,7 @@ from .build import build_oracle, library_path
 
 __all__ = [
     "gamma", "hop", "hop_sites", "apply", "apply_eo", "hop_eo", "schur_prepare",
-    "schur_reconstruct", "cgnr", "solve", "dense_matrix", "num_threads",
+    "schur_reconstruct", "cgnr", "solve", "dense_matrix", "num_threads", "set_num_threads",
     "build_oracle", "CR_METHODS", "cr", "solve_cr",
 ]
 
@@ -79,6 +79,7 @@ def _load():
                                         ctypes.c_int, ip]
         lib.oracle_solve_cr.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -109,6 +110,11 @@ def _vol(dims) -> int:
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the oracle's loops (for timing it on fewer cores)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def gamma(mu: int) -> np.ndarray:

@@ -692,10 +692,13 @@ int oracle_solve_cr(double *x_full, const double *b_full, const double *U, const
     return rc;
 }
 
-/* Number of OpenMP threads the oracle uses (1 without OpenMP). */
+/* Number of OpenMP threads the oracle uses (1 without OpenMP), and a setter
+ * for timing it on fewer cores. */
 #ifdef _OPENMP
 #include <omp.h>
 int oracle_num_threads(void) { return omp_get_max_threads(); }
+void oracle_set_num_threads(int n) { if (n > 0) omp_set_num_threads(n); }
 #else
 int oracle_num_threads(void) { return 1; }
+void oracle_set_num_threads(int n) { (void)n; }
 #endif
