@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 def test_combine_ranks_two_gloo_ranks():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of a process with threads
         out = m.dict()
         mp.start_processes(_worker, args=(world, port, out), nprocs=world, join=True,
                            start_method="spawn")
