@@ -500,3 +500,19 @@ def test_cr_special_cases(oracle_lib):
         x2, _, _, _ = oracle_lib.cr(b, U, dims, 0.124, phase, "mcr2", parity=parity, tol=1e-30,
                                     maxiter=k)
         assert relerr(x2, x1) < 1e-11
+
+
+def test_cr_operators_hermitian_forms(oracle_lib):
+    """The two Hermitian forms the CR readings rely on, from the dense D: gamma5
+    Mhat is Hermitian and indefinite (eigenvalues of both signs: MCR is CR on
+    an indefinite matrix), Mhat Mhat^dag is Hermitian positive definite (CRNE)."""
+    dims, kappa = (4, 4, 2, 2), 0.124
+    U = syn.su3_links(dims, eps=0.3, seed=9)
+    A = _dense_schur(oracle_lib, U, dims, kappa, syn.workloads.APBC_T, 0.0, 1)
+    G = np.kron(np.eye(A.shape[0] // 4), G5)
+    B = G @ A
+    assert np.abs(B - B.conj().T).max() < 1e-14
+    ev = np.linalg.eigvalsh(B)
+    assert ev.min() < -0.1 and ev.max() > 0.1
+    N = A @ A.conj().T
+    assert np.linalg.eigvalsh(N).min() > 0.0
