@@ -243,7 +243,8 @@ const char *wd_last_error(void);
  * allocates.  This entry point needs no handle and allocates nothing: it
  * reads the caller's canonical FP64 arrays directly and keeps its one
  * intermediate field in a fixed device array inside libwd (12,582,912
- * bytes, held on every GPU that loads the library until the process exits).
+ * bytes, held on every GPU where this entry point has been called, from the
+ * first call until the process exits).
  *
  *   out     device, [V/2][3][4] complex128, parity `parity`; must not overlap in
  *   in      device, [V/2][3][4] complex128, parity `parity`
@@ -256,9 +257,11 @@ const char *wd_last_error(void);
  * WD_ERR_DIMS, nothing queued).  Every call shares the one device array,
  * which keeps the last call's contents; calls that overlap on the GPU
  * (different streams or host threads) race on it and must be serialised by
- * the caller.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture begins.  Errors are described by
+ * the caller.  The first call on each device loads the entry point's kernels
+ * there and looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture
+ * begins.  Extents whose product exceeds the maximum are rejected before
+ * any arithmetic can overflow.  Errors are described by
  * wd_noalloc_last_error().
  */
 #define WD_NOALLOC_MAX_VH 65536

@@ -10,8 +10,8 @@
 // other parity, in a fixed file-scope device array.
 //
 // That array, g_noalloc_tmp, holds WD_NOALLOC_MAX_VH half-lattice sites of
-// 12 complex doubles (12,582,912 bytes).  Every GPU that loads libwd holds
-// it until the process exits.  In host code its name is only a host-side
+// 12 complex doubles (12,582,912 bytes).  It is placed on a GPU when this
+// entry point is first called there and stays until the process exits.  In host code its name is only a host-side
 // stand-in, so the host takes its device address with cudaGetSymbolAddress
 // once per device (with that device current) and passes that address to the
 // kernels.  All calls share the array and it keeps the last call's
@@ -59,12 +59,14 @@ k_hop_canonical(Geom g, int parity, const double2 *__restrict__ in,
             if (n[mu] < 0) { n[mu] = g.L[mu] - 1; wrap = true; }
             const long nlex = (((long)n[3] * g.L[2] + n[2]) * g.L[1] + n[1]) * g.L[0] + n[0];
             double psi[24], L18[18];
+#pragma unroll
             for (int i = 0; i < 12; ++i) {
                 double2 v = in[(nlex >> 1) * 12 + i];
                 psi[2 * i] = v.x;
                 psi[2 * i + 1] = v.y;
             }
             const double2 *link = U + ((dir == 0 ? lex : nlex) * 4 + mu) * 9;
+#pragma unroll
             for (int i = 0; i < 9; ++i) {
                 double2 v = link[i];
                 L18[2 * i] = v.x;
@@ -89,6 +91,7 @@ k_hop_canonical(Geom g, int parity, const double2 *__restrict__ in,
 #undef WD_HOP
         }
     }
+#pragma unroll
     for (int i = 0; i < 12; ++i) {
         double2 r = {scale * acc[2 * i], scale * acc[2 * i + 1]};
         if (XPAY) {
@@ -123,17 +126,19 @@ extern "C" int wd_apply_eo_noalloc(double *out, const double *in, const double *
         return noalloc_fail(WD_ERR_ARG, "null argument to wd_apply_eo_noalloc");
     if (parity != 0 && parity != 1) return noalloc_fail(WD_ERR_ARG, "parity must be 0 or 1");
     if (dagger != 0 && dagger != 1) return noalloc_fail(WD_ERR_ARG, "dagger must be 0 or 1");
+    // The volume is checked after every factor: each extent is at most
+    // 2^31 and the running product at most 2 * WD_NOALLOC_MAX_VH before a
+    // multiplication, so the product cannot wrap around.
     long V = 1;
     for (int m = 0; m < 4; ++m) {
         if (dims[m] < 2 || dims[m] % 2)
             return noalloc_fail(WD_ERR_DIMS, "every lattice extent must be even and >= 2");
         V *= dims[m];
+        if (V / 2 > WD_NOALLOC_MAX_VH)
+            return noalloc_fail(WD_ERR_DIMS,
+                                "half-lattice volume exceeds the no-allocation maximum of " +
+                                    std::to_string((long)WD_NOALLOC_MAX_VH) + " sites");
     }
-    if (V / 2 > WD_NOALLOC_MAX_VH)
-        return noalloc_fail(WD_ERR_DIMS,
-                            "half-lattice volume " + std::to_string(V / 2) +
-                                " exceeds the no-allocation maximum of " +
-                                std::to_string((long)WD_NOALLOC_MAX_VH) + " sites");
     // device address of the scratch array, looked up once per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -144,6 +149,19 @@ extern "C" int wd_apply_eo_noalloc(double *out, const double *in, const double *
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
         if (!g_noalloc_addr[dev]) {
+            // Load all four kernels on this device now, so that no later call
+            // (with the other dagger flag) triggers a lazy module load.
+            cudaFuncAttributes fa;
+            const void *kernels[4] = {(const void *)k_hop_canonical<0, 0>,
+                                      (const void *)k_hop_canonical<0, 1>,
+                                      (const void *)k_hop_canonical<1, 0>,
+                                      (const void *)k_hop_canonical<1, 1>};
+            for (const void *k : kernels) {
+                e = cudaFuncGetAttributes(&fa, k);
+                if (e != cudaSuccess)
+                    return noalloc_fail(WD_ERR_CUDA, std::string("cudaFuncGetAttributes: ") +
+                                                         cudaGetErrorString(e));
+            }
             e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_tmp);
             if (e != cudaSuccess) {
                 g_noalloc_addr[dev] = nullptr;

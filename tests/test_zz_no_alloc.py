@@ -50,6 +50,20 @@ def test_noalloc_rejects_lattices_above_its_maximum():
     assert rc == 1
 
 
+@pytest.mark.parametrize("dims", [(65536, 65536, 65536, 65536),   # product wraps to 0
+                                  (2, 2, 2**30, 2**30),           # product wraps in 64 bits
+                                  (1 << 17, 2, 2, 2)])             # one extent alone too large
+def test_noalloc_rejects_extents_whose_product_overflows(dims):
+    """A volume that would wrap around in 64-bit arithmetic is rejected
+    with WD_ERR_DIMS before any kernel is queued (no GPU needed)."""
+    lib = _lib()
+    dummy = ctypes.c_void_p(16)
+    rc = lib.wd_apply_eo_noalloc(dummy, dummy, dummy, (ctypes.c_int * 4)(*dims), KAPPA,
+                                 _phase8(), 1, 0, None)
+    assert rc == 2
+    assert b"exceeds the no-allocation maximum" in lib.wd_noalloc_last_error()
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("dims", [(6, 6, 2, 4), (16, 16, 16, 32)])   # the latter: V/2 = maximum
 def test_noalloc_matches_apply_eo_on_consecutive_calls(dims):
