@@ -26,7 +26,9 @@ g_W[c', c, k] = sum_x g_out,c'(x) (T_k in_c)(x)^dag  (summed over colour).
 
 Parity pins (tests/test_ptc_oracle.py): adjointness of the transports, a layer
 with Wilson weights equals the C oracle's D, gauge equivariance of the whole
-net, central finite differences of the gradients.
+net, central finite differences of the gradients; the sampled-site forward
+(net_forward_sites, for full-size checks) equals the full-field one at every
+site and reproduces a backward transport written out by hand.
 """
 from __future__ import annotations
 
@@ -138,3 +140,83 @@ def identity_init(seed: int, scale: float = 0.01, layers=LAYERS):
         W[0, 0, 0] += np.eye(4)
         Ws.append(W)
     return Ws
+
+
+# ----------------------------------------------------------------- sampled sites
+def _coords_of(lex, dims):
+    """Coordinates (x, y, z, t) of lexicographic site indices, [n, 4]."""
+    L = [int(d) for d in dims]
+    lex = np.asarray(lex, dtype=np.int64)
+    x = lex % L[0]
+    r = lex // L[0]
+    y = r % L[1]
+    r //= L[1]
+    z = r % L[2]
+    t = r // L[2]
+    return np.stack([x, y, z, t], axis=1)
+
+
+def _lex_of(c, dims):
+    L = [int(d) for d in dims]
+    return ((c[:, 3] * L[2] + c[:, 2]) * L[1] + c[:, 1]) * L[0] + c[:, 0]
+
+
+def _stencil(sites, dims):
+    """For each site: its 9 stencil sites (itself, x + mu, x - mu) and the
+    wrap flags of the 8 hops, as [n, 9] indices and [n, 9] bools."""
+    c = _coords_of(sites, dims)
+    nb = [np.asarray(sites, dtype=np.int64)]
+    wr = [np.zeros(len(sites), dtype=bool)]
+    for fwd in (True, False):
+        for mu in range(4):
+            L = int(dims[mu])
+            d = c.copy()
+            d[:, mu] += 1 if fwd else -1
+            wrap = (d[:, mu] == L) | (d[:, mu] < 0)
+            d[:, mu] %= L
+            nb.append(_lex_of(d, dims))
+            wr.append(wrap)
+    return np.stack(nb, axis=1), np.stack(wr, axis=1)
+
+
+def layer_forward_sites(inp, in_sites, W, U, dims, phase, out_sites):
+    """One layer at out_sites only.  inp [C_in, len(in_sites), 3, 4] holds the
+    layer input on in_sites (sorted), which must contain every stencil site
+    of out_sites.  Transport k = 1 + mu (forward) and 5 + mu (backward) as
+    in transport(); returns [C_out, len(out_sites), 3, 4]."""
+    nb, wr = _stencil(out_sites, dims)
+    pos = np.searchsorted(in_sites, nb)
+    assert np.all(in_sites[pos] == nb), "input does not cover the stencil"
+    out = np.zeros((W.shape[0], len(out_sites), 3, 4), dtype=np.complex128)
+    for k in range(NK):
+        v = inp[:, pos[:, k]]                                   # [C_in, n, 3, 4]
+        if k > 0:
+            mu = (k - 1) % 4
+            if k <= 4:      # U_mu(x) phi psi(x + mu)
+                link = U[out_sites, mu]
+                ph = complex(phase[mu])
+            else:           # U_mu(x - mu)^dag phi^* psi(x - mu)
+                link = np.conj(np.swapaxes(U[nb[:, k], mu], 1, 2))
+                ph = np.conj(complex(phase[mu]))
+            w = np.where(wr[:, k], ph, 1.0)
+            v = np.einsum("nab,cnbs->cnas", link, v) * w[None, :, None, None]
+        out += np.einsum("dcst,cnat->dnas", W[:, :, k], v)
+    return out
+
+
+def net_forward_sites(r, Ws, U, dims, phase, sites):
+    """N(r) at the given sites only, for checks of full-size fields: the
+    layers are evaluated backwards-expanded on the receptive field of the
+    sites (each layer widens it by one stencil), so the cost grows with the
+    number of sites, not with the volume.  Same result as
+    net_forward(r, ...)[sites]."""
+    need = [np.unique(np.asarray(sites, dtype=np.int64))]
+    for _ in Ws:
+        need.append(np.unique(_stencil(need[-1], dims)[0].ravel()))
+    need = need[::-1]                      # need[l]: sites of the layer-l input
+    x = np.asarray(r)[need[0]][None]
+    for l, W in enumerate(Ws):
+        x = layer_forward_sites(x, need[l], W, U, dims, phase, need[l + 1])
+    out = x[0]
+    order = np.searchsorted(need[-1], np.asarray(sites, dtype=np.int64))
+    return out[order]

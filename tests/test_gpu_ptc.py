@@ -1,6 +1,7 @@
 """The learned preconditioner on the GPU: the tensor-core GEMM against an
 FP32 matrix product of the same BF16 operands, and the network forward pass
-against the FP64 oracle (BF16 operands: norm-wise 3e-2)."""
+against the FP64 oracle (BF16 operands: norm-wise 3e-2), on small lattices
+in full and on the 16^3 x 32 production shape at sampled sites."""
 import numpy as np
 import pytest
 import torch
@@ -11,6 +12,9 @@ import synthetic as syn
 pytestmark = pytest.mark.gpu
 
 APBC = syn.workloads.APBC_T
+# per-site bound of the BF16 network output (four layers of BF16 operands,
+# each rounding at 2^-8 relative; measured on GB300 and set with a margin)
+PTC_SITE_TOL = 8e-2
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 64), (256, 128, 128), (1024, 128, 1152), (384, 16, 64)])
@@ -92,3 +96,72 @@ def test_ptc_training_reduces_the_loss():
     for _ in range(60):
         last = net.train_step(R, E, lr=3e-3)
     assert last < 0.5 * first, (first, last)
+
+
+# ------------------------------------------------------------- production shape
+PROD_DIMS = (16, 16, 16, 32)          # M = 3 V = 393,216 GEMM rows, 3,072 row tiles
+
+
+def _prod_sites(n_random=128, seed=7):
+    rng = np.random.default_rng(seed)
+    V = syn.volume(PROD_DIMS)
+    X = syn.coords(PROD_DIMS)
+    edge = np.nonzero(((X == 0) | (X == np.array(PROD_DIMS) - 1)).any(axis=1))[0]
+    pick = rng.choice(V, size=n_random, replace=False)
+    last = np.array([V - 1, V - 2, V - 3 * 128])          # the last GEMM row tiles
+    return np.unique(np.concatenate([pick, rng.choice(edge, 32, replace=False), last]))
+
+
+def test_ptc_forward_at_production_shape_on_sampled_sites():
+    """The full 1-16-16-16-1 network on 16^3 x 32 (every GEMM tile, the
+    gather's full-size indexing) against the oracle evaluated on the
+    receptive fields of sampled sites: norm-wise 3e-2 and per site."""
+    from paper_1401_2039_gb300 import PtcNet
+    from parity import check
+    U = syn.su3_links(PROD_DIMS, eps=0.3, seed=2)
+    Ws = optc.identity_init(3, scale=0.5)
+    net = PtcNet(PROD_DIMS, APBC, optc.LAYERS)
+    net.set_gauge(torch.from_numpy(U).cuda())
+    net.set_weights(torch.from_numpy(_to_flat(Ws)).cuda())
+    r = syn.gaussian_spinor(syn.volume(PROD_DIMS), 5)
+    y = net.apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    sites = _prod_sites()
+    ref = optc.net_forward_sites(r, Ws, U, PROD_DIMS, APBC, sites)
+    check(y[sites], ref, norm_tol=3e-2, site_tol=PTC_SITE_TOL)
+    net.close()
+
+
+def test_ptc_gradient_at_production_shape_by_exact_central_difference():
+    """The network is linear in each layer's weights, so the loss is a
+    quadratic function of them and (L(W + d) - L(W - d)) / 2 equals the
+    directional derivative <grad, d> exactly for a perturbation d of one
+    layer.  Checks the backward pass (tensor-core and weight-gradient GEMMs,
+    adjoint transports) over every tile of the 16^3 x 32 shape, layer by
+    layer; both sides run on the GPU, so only BF16 rounding separates them."""
+    from paper_1401_2039_gb300 import PtcNet
+    U = syn.su3_links(PROD_DIMS, eps=0.3, seed=2)
+    Ws = optc.identity_init(4, scale=0.5)
+    V = syn.volume(PROD_DIMS)
+    net = PtcNet(PROD_DIMS, APBC, optc.LAYERS)
+    net.set_gauge(torch.from_numpy(U).cuda())
+    w0 = _to_flat(Ws)
+    net.set_weights(torch.from_numpy(w0).cuda())
+    r = torch.from_numpy(syn.gaussian_spinor(V, 21)[None]).cuda()
+    e = torch.from_numpy(syn.gaussian_spinor(V, 22)[None]).cuda()
+    _, g = net.loss_grad(r, e)
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(8)
+    off = 0
+    for W in Ws:
+        n = W.size
+        d = np.zeros_like(w0)
+        d[off:off + n] = 0.3 * np.abs(W).mean() * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+        net.set_weights(torch.from_numpy(w0 + d).cuda())
+        lp, _ = net.loss_grad(r, e)
+        net.set_weights(torch.from_numpy(w0 - d).cuda())
+        lm, _ = net.loss_grad(r, e)
+        fd = (lp - lm) / 2
+        an = float(np.real(np.vdot(g, d)))
+        assert abs(fd - an) < 3e-2 * abs(fd) + 1e-3 * (lp + lm) / 2, (off, fd, an, lp, lm)
+        off += n
+    net.close()

@@ -5,8 +5,8 @@ The twist enters the hopping-term epilogues: the xpay epilogue multiplies
 x by A = 1 + i t gamma5 and the plain one multiplies by A^-1 (t = 2 kappa mu,
 -t for adjoints), so the full operator, the Schur operator A - kappa^2 H A^-1
 H (storage precision and residual arithmetic) and the solve with its Schur
-preparation and reconstruction are checked.  Norm-wise tolerances as for the
-Wilson operator: FP64 1e-13, FP32 1e-6, FP16/BF16 2e-2; solves by the oracle's
+preparation and reconstruction are checked.  Tolerances as for the Wilson
+operator, norm-wise and per site (tests/parity.py); solves by the oracle's
 FP64 true residual.
 """
 import numpy as np
@@ -15,10 +15,10 @@ import torch
 
 import oracle
 import synthetic as syn
+from parity import check
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-2, "bf16": 2e-2}
 PHASE = tuple(np.exp(1j * np.array([0.3, 0.0, -0.9, np.pi])))
 
 
@@ -57,14 +57,14 @@ def test_twisted_operators(dims, prec, recon):
     for dag in (False, True):
         got = host(op.apply(cuda(psi), dagger=dag))
         ref = oracle.apply_tm(psi, U, dims, kappa, mu, PHASE, dag)
-        assert rel(got, ref) < TOL[prec], ("apply", dag, rel(got, ref))
+        check(got, ref, prec, what=("apply", dag))
         for parity in (0, 1):
             half = syn.to_half(psi, dims, parity)
             ref = oracle.apply_eo_tm(half, U, dims, kappa, mu, PHASE, parity, dag)
             got = host(op.apply_eo(cuda(half), parity, dag))
-            assert rel(got, ref) < TOL[prec], ("apply_eo", parity, dag, rel(got, ref))
+            check(got, ref, prec, what=("apply_eo", parity, dag))
             got = host(op.apply_eo(cuda(half), parity, dag, residual=True))
-            assert rel(got, ref) < 1e-13, ("residual arithmetic", parity, dag, rel(got, ref))
+            check(got, ref, "f64", what=("residual arithmetic", parity, dag))
     op.close()
 
 
@@ -75,7 +75,7 @@ def test_twisted_hop_stays_bare():
     half = syn.to_half(syn.gaussian_spinor(syn.volume(dims), 5), dims, 0)
     op = make_op(dims, 0.12, PHASE, "f64", 18, U, 0.3)
     got = host(op.dslash_eo(cuda(half), 1))
-    assert rel(got, oracle.hop_eo(half, U, dims, PHASE, 1)) < 1e-13
+    check(got, oracle.hop_eo(half, U, dims, PHASE, 1), "f64")
     op.close()
 
 

@@ -130,3 +130,37 @@ def test_neumann_initialisation_is_the_degree_four_neumann_series(U):
         ref = ref + t
     y = ptc.net_forward(r, Ws, U, DIMS, PHASE)
     assert np.linalg.norm(y - ref) < 1e-13 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 2, 4), (2, 2, 2, 2), (6, 4, 2, 4)])
+def test_sampled_site_forward_equals_the_full_field_forward(dims):
+    """net_forward_sites (receptive field of the samples only) against the
+    pinned full-field forward, at every site and at a scattered subset that
+    includes wrapping boundaries; Wilson-weight layers tie it to the C
+    oracle's D through test_wilson_weights_reproduce_the_dirac_operator."""
+    U = syn.su3_links(dims, eps=0.3, seed=32)
+    Ws = ptc.identity_init(5, scale=0.7)
+    V = syn.volume(dims)
+    r = syn.gaussian_spinor(V, 9)
+    full = ptc.net_forward(r, Ws, U, dims, PHASE)
+    every = ptc.net_forward_sites(r, Ws, U, dims, PHASE, np.arange(V))
+    assert np.abs(every - full).max() < 1e-12 * np.abs(full).max()
+    some = np.array([V - 1, 0, 7, V // 2 + 1, 3])        # unsorted, with boundaries
+    got = ptc.net_forward_sites(r, Ws, U, dims, PHASE, some)
+    assert np.abs(got - full[some]).max() < 1e-12 * np.abs(full).max()
+
+
+def test_sampled_site_layer_uses_the_backward_link_of_the_neighbour():
+    """A single backward-transport layer at one site is U_mu(x - mu)^dag
+    phi^* psi(x - mu), written out here for t = 0 (wraps, phase -1)."""
+    dims = (4, 4, 4, 4)
+    U = syn.su3_links(dims, eps=0.3, seed=33)
+    V = syn.volume(dims)
+    r = syn.gaussian_spinor(V, 10)
+    W = np.zeros((1, 1, ptc.NK, 4, 4), dtype=complex)
+    W[0, 0, 8] = np.eye(4)                                 # T_{5+3}: backward in t
+    x = 5                                                  # t = 0
+    nbr = x + 3 * 64                                       # t = 3, same x, y, z
+    want = -np.einsum("ba,bs->as", np.conj(U[nbr, 3]), r[nbr])
+    got = ptc.net_forward_sites(r, [W], U, dims, syn.workloads.APBC_T, np.array([x]))[0]
+    assert np.abs(got - want).max() < 1e-13
