@@ -17,6 +17,8 @@ Printed as one JSON line:
   e2e           the solve through wd_solve_cg_host: b and x in pinned host
                 memory, host<->device copies inside the timed region
   twisted_mass  the same comparison with a twisted mass mu (Fig. dirac)
+  recovery      defect correction (inner tolerances 0.1 ... 1e-3) against the
+                reliable updates of the timed solve, same problem
   dslash_sweep  the hopping term alone for every storage precision and link
                 compression on the same lattice
   small_config  16^3 x 32, FP32 with reliable updates against plain FP64 CG
@@ -70,6 +72,8 @@ def parse_args():
                     help="skip the batched multi-source / uneven-lattice measurement")
     ap.add_argument("--no-twisted", action="store_true",
                     help="skip the twisted-mass solve comparison (reported as null)")
+    ap.add_argument("--no-recovery", action="store_true",
+                    help="skip the defect-correction solves (reported as null)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the hopping-term precision sweep and the 16^3 x 32 comparison")
     ap.add_argument("--no-solvers", action="store_true",
@@ -431,6 +435,10 @@ def batch_measurement(prec: str, recon: int):
 
 
 # ----------------------------------------------------------------------------- our arm
+def ms_of(elapsed_ms: float, args) -> float:
+    return elapsed_ms / args.steps
+
+
 def main():
     args = parse_args()
     w = syn.WORKLOADS[args.workload]
@@ -590,6 +598,30 @@ def main():
                    "fp64_cg_iters": tm_fp64[1] if tm_fp64 else None,
                    "speedup_vs_fp64_cg": (tm_fp64[0] / tm_ms) if tm_fp64 else None}
 
+    # ---- accuracy recovery: defect correction against the reliable updates
+    # of the timed solve, on the same problem (one timed solve per setting)
+    recovery = None
+    if rank == 0 and not args.no_recovery:
+        recovery = {"reliable_updates": {"ms": ms_of(elapsed_ms, args),
+                                         "iters": infos[-1]["iters"],
+                                         "outer_steps": infos[-1]["reliable_updates"]},
+                    "defect_correction": []}
+        for inner in (0.1, 0.03, 0.01, 1e-3):
+            op.set_recovery("defect", inner)
+            solve()
+            torch.cuda.synchronize()
+            r0e = torch.cuda.Event(enable_timing=True)
+            r1e = torch.cuda.Event(enable_timing=True)
+            r0e.record(stream)
+            rd = solve()
+            r1e.record(stream)
+            torch.cuda.synchronize()
+            recovery["defect_correction"].append(
+                {"inner_tol": inner, "ms": r0e.elapsed_time(r1e), "iters": rd.info["iters"],
+                 "outer_steps": rd.info["reliable_updates"],
+                 "true_rel_resid": rd.info["true_rel_resid"]})
+        op.set_recovery("reliable")
+
     # ---- batched solves (the multi-source and uneven-lattice workloads)
     batch = None
     if rank == 0 and not args.no_batch:
@@ -648,6 +680,7 @@ def main():
             "residual_arithmetic": "double-float (2 x FP32)" if w.prec != "f64" else "f64",
             "batch": batch,
             "twisted_mass": twisted,
+            "recovery": recovery,
             "dslash_sweep_32x32x32x64": sweep,
             "small_config": small,
             "solver_comparison": solvers,

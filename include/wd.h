@@ -132,6 +132,28 @@ int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, int maxiter,
  * has not improved for stall_iters iterations (default 200). */
 int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters);
 
+/* How the mixed-precision solve recovers FP64 accuracy (ignored for WD_F64;
+ * not in the paper, which runs CGNR in one precision):
+ *   WD_RECOVER_RELIABLE (default)  reliable updates (Clark et al. 2010): when
+ *       the iterated residual has fallen by ru_delta (wd_op_set_solver) the
+ *       inner solution is folded into the FP64 one, the residual is
+ *       recomputed in the residual arithmetic and the inner CGNR goes on with
+ *       its Krylov direction rescaled to the new residual;
+ *   WD_RECOVER_DEFECT  defect correction (iterative refinement): each outer
+ *       step computes r = bhat - Mhat x in the residual arithmetic, solves
+ *       Mhat e = r with an inner CGNR (Alg. "CGNR") in the storage precision
+ *       started from e = 0 in a fresh Krylov space until its iterated
+ *       residual has fallen by inner_tol (0 < inner_tol < 1, default 0.1),
+ *       and adds e to the FP64 x.
+ * Both stop on the same FP64 true residual; wd_solve_info.reliable_updates
+ * counts the residual recomputations (outer steps) of either.
+ * WD_ERR_ARG for another mode or an inner_tol outside (0, 1). */
+typedef enum { WD_RECOVER_RELIABLE = 0, WD_RECOVER_DEFECT = 1 } wd_recovery;
+int wd_op_set_recovery(wd_op *op, int mode, double inner_tol);
+/* The handle's recovery mode (-1 for a null handle) and, if inner_tol is not
+ * NULL, its defect-correction inner tolerance. */
+int wd_op_recovery(const wd_op *op, double *inner_tol);
+
 /* Arithmetic of the residual recomputations of the reliable updates, of the
  * Schur preparation and reconstruction and of the final true residual for
  * WD_F32/WD_F16/WD_BF16 operators: mode 0 = native FP64, mode 1 (default) =

@@ -13,6 +13,8 @@
 constexpr double RU_DELTA_DEFAULT = 0.1;
 constexpr int STALL_ITERS_DEFAULT = 200;
 constexpr int MAX_BATCH_LOG2 = 5;  // graph batches of 1, 2, ..., 32 iterations
+// Defect correction: each inner solve reduces its residual by this factor.
+constexpr double DC_DELTA_DEFAULT = 0.1;
 
 struct wd_op {
     using Geom = wd::Geom;
@@ -58,6 +60,12 @@ struct wd_op {
     // t = 2 kappa mu of A = 1 + i t gamma5; the adjoint flips its sign
     double twist(int dagger) const { return (dagger ? -2.0 : 2.0) * kappa * mu; }
     int stall_iters = STALL_ITERS_DEFAULT;
+    // accuracy recovery of the mixed-precision solve: WD_RECOVER_RELIABLE
+    // (reliable updates, the Krylov direction kept across refreshes) or
+    // WD_RECOVER_DEFECT (defect correction: every refresh restarts the inner
+    // solve on the new residual), and the inner tolerance of the latter
+    int recovery = WD_RECOVER_RELIABLE;
+    double dc_delta = DC_DELTA_DEFAULT;
 
     // tuned launch configuration of the hopping term: [0] storage precision,
     // [1] residual arithmetic, [2] storage precision with xpay and fused norm

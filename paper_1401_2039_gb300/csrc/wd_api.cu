@@ -184,6 +184,23 @@ int wd_op_set_solver(wd_op *op, double ru_delta, int stall_iters) {
     return WD_OK;
 }
 
+int wd_op_set_recovery(wd_op *op, int mode, double inner_tol) {
+    if (!op) return fail(WD_ERR_ARG, "null operator handle");
+    if (mode != WD_RECOVER_RELIABLE && mode != WD_RECOVER_DEFECT)
+        return fail(WD_ERR_ARG, "mode must be WD_RECOVER_RELIABLE or WD_RECOVER_DEFECT");
+    if (mode == WD_RECOVER_DEFECT && !(inner_tol > 0.0 && inner_tol < 1.0))
+        return fail(WD_ERR_ARG, "inner_tol must lie in (0, 1)");
+    op->recovery = mode;
+    if (mode == WD_RECOVER_DEFECT) op->dc_delta = inner_tol;
+    return WD_OK;
+}
+
+int wd_op_recovery(const wd_op *op, double *inner_tol) {
+    if (!op) return -1;
+    if (inner_tol) *inner_tol = op->dc_delta;
+    return op->recovery;
+}
+
 int wd_op_set_residual_precision(wd_op *op, int mode) {
     if (!op) return fail(WD_ERR_ARG, "null operator handle");
     if (mode != 0 && mode != 1) return fail(WD_ERR_ARG, "mode must be 0 (FP64) or 1 (double-float)");
@@ -657,7 +674,11 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
             const double r_lo = std::sqrt(h.nr);
             if (r_lo < best_lo) { best_lo = r_lo; best_it = iters; }
             const bool want_conv = r_lo <= st.target * st.scale;
-            const bool want_ru = mixed && r_lo < op->ru_delta * r_max_lo;
+            // reliable update: the iterated residual fell by ru_delta; defect
+            // correction: the inner solve reached its tolerance
+            const bool defect = mixed && op->recovery == WD_RECOVER_DEFECT;
+            const double delta = defect ? op->dc_delta : op->ru_delta;
+            const bool want_ru = mixed && r_lo < delta * r_max_lo;
             const bool stalled = mixed && iters - best_it >= op->stall_iters;
             const bool out_of_iters = iters >= maxiter;
             if (want_conv || want_ru || stalled || out_of_iters) {
@@ -679,13 +700,16 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
                 WD_TRY(set_consts(op, new_scale, 1.0 / new_scale, ratio));
                 WD_CUDA(launch_convert_scaled(op->prec, op->rl, op->hi_prec, op->rh, g,
                                               op->dev_consts, 0, op->stream));
-                if (stalled) {
-                    // restart: p = 0 and nz = +inf make the next direction z itself
+                if (stalled || defect) {
+                    // restart: p = 0 and nz = +inf make the next direction z itself.
+                    // Defect correction restarts at every outer step: the inner
+                    // CGNR solves Mhat e = r_hi from e = 0 (x_lo was folded
+                    // into x_hi and cleared) in a fresh Krylov space.
                     WD_CUDA(cudaMemsetAsync(op->pl, 0, op->lo_field_bytes(), op->stream));
                     op->host_consts[3] = INFINITY;
                     WD_CUDA(cudaMemcpyAsync(&op->sc->nz, &op->host_consts[3], sizeof(double),
                                             cudaMemcpyHostToDevice, op->stream));
-                    st.restarts += 1;
+                    st.restarts += stalled ? 1 : 0;
                 } else if (ratio != 1.0) {
                     WD_CUDA(launch_rescale_lo(op->prec, g, op->pl, op->sc, op->dev_consts + 2,
                                               op->stream));
@@ -709,7 +733,10 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
             if (di > 0 && lognr < last_lognr) {
                 const double rate = (lognr - last_lognr) / di;   // < 0
                 double thr = 2 * std::log(st.target * st.scale);
-                if (mixed) thr = std::max(thr, 2 * std::log(op->ru_delta * r_max_lo));
+                if (mixed) {
+                    const double d = op->recovery == WD_RECOVER_DEFECT ? op->dc_delta : op->ru_delta;
+                    thr = std::max(thr, 2 * std::log(d * r_max_lo));
+                }
                 next = (int)std::ceil((thr - lognr) / rate);
             }
             last_lognr = lognr;

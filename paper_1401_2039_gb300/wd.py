@@ -20,6 +20,7 @@ from . import build as _build
 WD_OK, WD_ERR_ARG, WD_ERR_DIMS, WD_ERR_CUDA, WD_ERR_NOMEM = 0, 1, 2, 3, 4
 WD_ERR_NOT_CONVERGED, WD_ERR_BREAKDOWN, WD_ERR_TIMEOUT, WD_ERR_STATE = 5, 6, 7, 8
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+RECOVERY = {"reliable": 0, "defect": 1}
 
 
 class WDError(RuntimeError):
@@ -68,6 +69,8 @@ def load_library() -> ctypes.CDLL:
             "wd_op_stream": (vp, [vp]),
             "wd_op_half_volume": (ctypes.c_long, [vp]),
             "wd_op_set_solver": (i, [vp, d, i]),
+            "wd_op_set_recovery": (i, [vp, i, d]),
+            "wd_op_recovery": (i, [vp, dp]),
             "wd_op_set_residual_precision": (i, [vp, i]),
             "wd_dslash_tuning": (i, [vp, i, dp, i, ip, ip, ip]),
             "wd_dslash_bytes": (d, [vp]),
@@ -221,6 +224,18 @@ class WilsonDirac:
     def set_solver(self, ru_delta: float = 0.1, stall_iters: int = 200):
         """Reliable-update threshold and stagnation restart of the mixed-precision solve."""
         _check(self.lib.wd_op_set_solver(self.handle, float(ru_delta), int(stall_iters)))
+
+    def set_recovery(self, mode: str = "reliable", inner_tol: float = 0.1):
+        """Accuracy recovery of the mixed-precision solve: "reliable" (reliable
+        updates, the default) or "defect" (defect correction with inner CGNR
+        solves that each reduce the residual by inner_tol)."""
+        _check(self.lib.wd_op_set_recovery(self.handle, RECOVERY[mode], float(inner_tol)))
+
+    @property
+    def recovery(self) -> tuple:
+        tol = ctypes.c_double()
+        k = self.lib.wd_op_recovery(self.handle, ctypes.byref(tol))
+        return ({v: n for n, v in RECOVERY.items()}[k], tol.value)
 
     def set_twisted_mass(self, mu: float):
         """D = 1 + 2 i kappa mu gamma5 - kappa H (Fig. dirac); mu = 0 is the

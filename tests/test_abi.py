@@ -148,6 +148,9 @@ def test_binding_constants_match_the_header():
     methods = _header_enum("wd_krylov_method")
     assert {k: methods["WD_KRYLOV_" + k.upper()] for k in wd.KRYLOV_METHODS} == wd.KRYLOV_METHODS
     assert len(methods) == len(wd.KRYLOV_METHODS)
+    rec = _header_enum("wd_recovery")
+    assert {k: rec["WD_RECOVER_" + k.upper()] for k in wd.RECOVERY} == wd.RECOVERY
+    assert len(rec) == len(wd.RECOVERY)
     status = _header_enum("wd_status")
     for name, value in status.items():
         assert getattr(wd, name) == value, name
@@ -157,3 +160,13 @@ def test_solve_cg_multi_checks_lengths_before_any_call():
     from paper_1401_2039_gb300 import solve_cg_multi
     with pytest.raises(ValueError):
         solve_cg_multi([object()], [1, 2], [None])
+
+
+def test_recovery_mode_arguments_are_checked(lib):
+    """wd_op_set_recovery rejects a null handle, unknown modes and inner
+    tolerances outside (0, 1) before any GPU work."""
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.wd_op_set_recovery.argtypes = [vp, i, d]
+    lib.wd_op_recovery.argtypes = [vp, ctypes.POINTER(d)]
+    assert lib.wd_op_set_recovery(None, 1, 0.1) == 1
+    assert lib.wd_op_recovery(None, None) == -1

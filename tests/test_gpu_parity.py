@@ -157,6 +157,40 @@ def test_solve_matches_oracle(prec, dims, kappa, recon):
         assert res.info["reliable_updates"] >= 2
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("inner_tol", [0.1, 1e-3])
+@pytest.mark.parametrize("dims,recon", [((8, 8, 8, 8), 12), ((6, 6, 2, 4), 18)])
+def test_defect_correction_solve_matches_oracle(prec, inner_tol, dims, recon):
+    """Defect correction (outer residual in the residual arithmetic, inner
+    storage-precision CGNR restarted on every new residual): the oracle's
+    FP64 true residual and its solution, as for reliable updates."""
+    U, _ = fields(dims)
+    kappa, phase = 0.124, PHASES["apbc"]
+    b = syn.gaussian_spinor(syn.volume(dims), 2)
+    op = make_op(dims, kappa, phase, prec, recon, U)
+    op.set_recovery("defect", inner_tol)
+    assert op.recovery == ("defect", inner_tol)
+    res = op.solve(cuda(b), tol=1e-10, maxiter=5000, parity=1)
+    x = host(res.x)
+    r_true = np.linalg.norm(b - oracle.apply(x, U, dims, kappa, phase)) / np.linalg.norm(b)
+    assert r_true <= 1.05e-10, (r_true, res.info)
+    assert abs(res.info["true_rel_resid"] - r_true) <= 1e-3 * r_true + 1e-15
+    x_ref, _, ok = oracle.solve(b, U, dims, kappa, phase, parity=1, tol=1e-13)
+    assert ok and rel(x, x_ref) < 1e-8
+    # several outer steps, none of them a stagnation restart
+    assert res.info["reliable_updates"] >= 2 and res.info["restarts"] == 0
+
+
+def test_recovery_mode_rejects_bad_arguments():
+    from paper_1401_2039_gb300.wd import WDError
+    U, _ = fields((4, 4, 4, 4))
+    op = make_op((4, 4, 4, 4), 0.12, PHASES["apbc"], "f16", 12, U)
+    for mode, tol in (("defect", 0.0), ("defect", 1.0), ("defect", float("nan"))):
+        with pytest.raises(WDError):
+            op.set_recovery(mode, tol)
+    assert op.recovery[0] == "reliable"
+
+
 def test_solve_even_parity_and_initial_guess():
     dims, kappa = (6, 6, 2, 4), 0.124
     U, _ = fields(dims)

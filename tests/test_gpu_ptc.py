@@ -12,9 +12,10 @@ import synthetic as syn
 pytestmark = pytest.mark.gpu
 
 APBC = syn.workloads.APBC_T
-# per-site bound of the BF16 network output (four layers of BF16 operands,
-# each rounding at 2^-8 relative; measured on GB300 and set with a margin)
-PTC_SITE_TOL = 8e-2
+# per-site bound of the BF16 network output: 8 u with u = 2^-8 the BF16 unit
+# roundoff (measured on GB300 at 16^3 x 32: at most 1.05e-2 per site,
+# 5.3e-3 norm-wise)
+PTC_SITE_TOL = 3e-2
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 64), (256, 128, 128), (1024, 128, 1152), (384, 16, 64)])
