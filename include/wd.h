@@ -328,6 +328,18 @@ int wd_ptc_train_step(wd_ptc *net, const double *r, const double *e, int nsample
 /* The network's tensor-core GEMM alone, D = A B^T (A [M][K], B [N][K] BF16,
  * D [M][N] FP32, device; M % 128 == 0, N % 16 == 0, K % 64 == 0). */
 int wd_tc_gemm_bf16(wd_ptc *net, const void *A, const void *B, float *D, long M, int N, int K);
+/* The transposed tensor-core GEMM of the weight gradient alone, D = A^T B
+ * (A [R][M], B [R][N] BF16 row-major, D [M][N] FP32, device; the reduction
+ * over the R rows is split over CTAs and summed in a fixed order;
+ * R % 64 == 0, M % 128 == 0, N % 16 == 0). */
+int wd_tc_gemm_bf16_tn(wd_ptc *net, const void *A, const void *B, float *D, long R, int M, int N);
+/* Bounded waits of the network's tensor-core GEMMs: every wait of a GEMM on
+ * its MMAs polls at most `polls` times (default 2^26) before the kernel gives
+ * up, lets the MMAs it issued drain, frees its tensor memory and the call
+ * returns WD_ERR_TIMEOUT.  withhold_mma = 1 (for tests of that path) makes
+ * the GEMMs issue no MMA at all, so that their first wait runs out with
+ * nothing in flight.  WD_ERR_ARG for polls = 0 or withhold_mma not 0/1. */
+int wd_ptc_set_wait_limit(wd_ptc *net, unsigned polls, int withhold_mma);
 const char *wd_ptc_last_error(void);
 
 /* Flexible GCR(nkrylov) on the full system D x = b (not in the paper), with

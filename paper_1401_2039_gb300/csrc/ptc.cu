@@ -16,13 +16,15 @@
 //      on the tensor cores (tcgen05, FP32 accumulation), with the complex
 //      weights laid out as the real block matrix [[Wr, -Wi], [Wi, Wr]],
 // and the FP32 output rows F[m] = (Re in_c'(x)[a][s'], then Im) are directly
-// the input rows of the next layer's gather.
+// the input rows of the next layer's gather.  Training runs the same GEMM
+// for the input gradient, dA = dF_out B, and its transposed form for the
+// weight gradient, dB^T = A^T dF_out (a reduction over the 3V rows, split
+// over CTAs and summed in a fixed order): every product of the network, in
+// inference and training, is a tcgen05 kernel of this library.
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
-
-#include <cublas_v2.h>
 
 #include "tc_gemm.cuh"
 #include "wd_internal.cuh"
@@ -183,9 +185,12 @@ __global__ void k_c64_to_c128(long n, const float2 *in, double2 *out) {
 
 // |v|^2 of a canonical complex128 field, one block-level partial per block
 // (deterministic final sum on the host side of the launch helper).
+// blockIdx.y selects the field (fields n entries apart), partials [y][x].
 __global__ void k_norm2_c128(long n, const double2 *v, double *partials) {
     __shared__ double ws[PTC_BLOCK / 32];
     double s = 0.0;
+    v += (long)blockIdx.y * n;
+    partials += (long)blockIdx.y * gridDim.x;
     for (long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x; i < n; i += (long)gridDim.x * PTC_BLOCK)
         s += v[i].x * v[i].x + v[i].y * v[i].y;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -203,9 +208,11 @@ __global__ void k_norm2_c128(long n, const double2 *v, double *partials) {
 // Loss gradient at the network output: G = 2 (y - e) / |e|^2 in the activation
 // layout (FP32, and a BF16 copy with row stride ldb), |y - e|^2 per block.
 __global__ void k_ptc_loss_grad(long V, const float *__restrict__ F, int ld,
-                                const double2 *__restrict__ e, double inv_ne, float *__restrict__ G,
-                                __nv_bfloat16 *__restrict__ Gb, int ldb, double *partials) {
+                                const double2 *__restrict__ e, const double *__restrict__ inv_ne_p,
+                                float *__restrict__ G, __nv_bfloat16 *__restrict__ Gb, int ldb,
+                                double *partials) {
     __shared__ double ws[PTC_BLOCK / 32];
+    const double inv_ne = *inv_ne_p;
     const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;   // (x, a)
     double d2 = 0.0;
     if (i < 3 * V) {
@@ -227,7 +234,7 @@ __global__ void k_ptc_loss_grad(long V, const float *__restrict__ F, int ld,
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < PTC_BLOCK / 32; ++w) t += ws[w];
-        partials[blockIdx.x] = t;
+        partials[blockIdx.x] = t * inv_ne;
     }
 }
 
@@ -307,9 +314,9 @@ __global__ void k_ptc_weights_t(int cout, int cin, const float2 *__restrict__ W,
     Bt[(long)(K + kk) * ldbt + N + n] = __float2bfloat16_rn(w.x);
 }
 
-// Packed complex weight gradient from the real block gradient dB[n'][k']
-// (row stride ldb): g = dL/dRe W + i dL/dIm W.
-__global__ void k_ptc_wgrad(int cout, int cin, const float *__restrict__ dB, int ldb,
+// Packed complex weight gradient from the transposed real block gradient
+// dBt[k'][n'] (row stride ldbt): g = dL/dRe W + i dL/dIm W.
+__global__ void k_ptc_wgrad(int cout, int cin, const float *__restrict__ dBt, int ldbt,
                             double2 *__restrict__ gW) {
     const int K = cin * 36, N = cout * 4;
     const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
@@ -317,9 +324,46 @@ __global__ void k_ptc_wgrad(int cout, int cin, const float *__restrict__ dB, int
     const int n = (int)(i / K), kk = (int)(i - (long)n * K);
     const int cp = n >> 2, sp = n & 3;
     const int k = kk / (4 * cin), c = (kk >> 2) % cin, s = kk & 3;   // kk = (k cin + c) 4 + s
-    const double gr = (double)dB[(long)n * ldb + kk] + dB[(long)(N + n) * ldb + K + kk];
-    const double gi = -(double)dB[(long)n * ldb + K + kk] + dB[(long)(N + n) * ldb + kk];
+    const double gr = (double)dBt[(long)kk * ldbt + n] + dBt[(long)(K + kk) * ldbt + N + n];
+    const double gi = -(double)dBt[(long)(K + kk) * ldbt + n] + dBt[(long)kk * ldbt + N + n];
     gW[((((long)cp * cin + c) * PTC_NK + k) * 4 + sp) * 4 + s] = make_double2(gr, gi);
+}
+
+// dBt += sum over the splits of the weight-gradient GEMM's partial products,
+// in split order (the sum does not depend on how the splits were scheduled).
+__global__ void k_ptc_sum_splits(long n, int splits, const float *__restrict__ part,
+                                 float *__restrict__ dBt) {
+    const long i = (long)blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i >= n) return;
+    float t = dBt[i];
+    for (int s = 0; s < splits; ++s) t += part[(long)s * n + i];
+    dBt[i] = t;
+}
+
+// out = the sum of n partials in a fixed order (one block: strided per-thread
+// sums, then a fixed tree).
+__global__ void k_ptc_sum_loss(long n, const double *__restrict__ partials, double *out) {
+    __shared__ double ws[PTC_BLOCK];
+    double t = 0.0;
+    for (long i = threadIdx.x; i < n; i += PTC_BLOCK) t += partials[i];
+    ws[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = PTC_BLOCK / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) ws[threadIdx.x] += ws[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = ws[0];
+}
+
+// inv_ne[i] = 1 / |e_i|^2 from per-block partials of the squared norms of
+// nsamples fields (one block per (sample, chunk)), summed in block order.
+__global__ void k_ptc_inv_norms(int nsamples, int chunks, const double *__restrict__ partials,
+                                double *__restrict__ inv_ne) {
+    const int i = blockIdx.x * PTC_BLOCK + threadIdx.x;
+    if (i >= nsamples) return;
+    double t = 0.0;
+    for (int c = 0; c < chunks; ++c) t += partials[(long)i * chunks + c];
+    inv_ne[i] = 1.0 / t;
 }
 
 // Adam on the real and imaginary parts of the weights.
@@ -390,11 +434,20 @@ struct wd_ptc {
     __nv_bfloat16 *dFb[PTC_MAX_LAYERS + 1] = {};
     float *dA = nullptr;                      // gathered-operand gradient, FP32
     __nv_bfloat16 *Bt[PTC_MAX_LAYERS] = {};   // transposed weight matrices
-    float *dB[PTC_MAX_LAYERS] = {};           // real block weight gradients
+    float *dBt[PTC_MAX_LAYERS] = {};          // real block weight gradients, [Kp][Np]
+    float *wsplit = nullptr;                  // partial products of the weight-gradient splits
+    long wsplit_elems = 0;
+    double *inv_ne = nullptr;                 // 1 / |e_i|^2 of the samples of a call
+    double *loss_dev = nullptr;               // per-sample losses of a call
+    int inv_ne_cap = 0;
+    double *norm_partials = nullptr;          // per-block partial norms, [sample][chunk]
     double2 *gW = nullptr;                    // packed complex gradient, all layers
     float2 *adam_m = nullptr, *adam_v = nullptr;
     long adam_t = 0;
-    cublasHandle_t blas = nullptr;
+    // bounded waits of the tensor-core GEMMs: polls per wait, and a test hook
+    // that makes the GEMMs issue no MMA (their waits then run out)
+    unsigned spin_limit = TC_SPIN_LIMIT;
+    int withhold = 0;
     std::vector<void *> allocs;
 };
 
@@ -425,30 +478,102 @@ static int ptc_alloc(wd_ptc *n, void **p, size_t bytes) {
 
 static unsigned grid_for(long n) { return (unsigned)std::max<long>(1, (n + PTC_BLOCK - 1) / PTC_BLOCK); }
 
+// dynamic shared memory of the GEMM kernels: the ring of A and B tiles.  At
+// BN = 128 it also keeps at most two CTAs per SM, within the SM's 512 TMEM
+// columns.  Set once per process (and device ordinal 0..63).
+static int ptc_gemm_attrs() {
+    static bool done[64] = {};
+    int dev = 0;
+    PTC_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && done[dev]) return WD_OK;
+    PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<128, TC_NT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tc_gemm_smem_bytes<128>()));
+    PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<16, TC_NT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tc_gemm_smem_bytes<16>()));
+    PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<128, TC_TN>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TC_TN_SMEM_BYTES));
+    PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<16, TC_TN>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, TC_TN_SMEM_BYTES));
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return WD_OK;
+}
+
+static TcArgs tc_args(wd_ptc *n, const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D,
+                      int lda, int ldb, int ldd, long k_total) {
+    TcArgs a{};
+    a.A = A;
+    a.B = B;
+    a.D = D;
+    a.lda = lda;
+    a.ldb = ldb;
+    a.ldd = ldd;
+    a.k_total = k_total;
+    a.k_split = k_total;
+    a.d_split = 0;
+    a.err = n->err;
+    a.spin_limit = n->spin_limit;
+    a.withhold = n->withhold;
+    return a;
+}
+
 // D = A * B^T on the tensor cores; N must be a multiple of 16 (tiles of 128 when possible).
 static int ptc_gemm(wd_ptc *n, const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D, long M,
                     int N, int K, int lda, int ldb, int ldd) {
     if (M % TC_BM || K % TC_BK || N % 16)
         return ptc_fail(WD_ERR_ARG, "GEMM shape not tile aligned");
-    // dynamic shared memory: the ring of A and B tiles.  At BN = 128 it also
-    // keeps at most two CTAs per SM, within the SM's 512 TMEM columns.
-    static bool attr_set = false;
-    if (!attr_set) {
-        PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tc_gemm_smem_bytes<128>()));
-        PTC_CUDA(cudaFuncSetAttribute(k_gemm_bf16_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tc_gemm_smem_bytes<16>()));
-        attr_set = true;
-    }
+    PTC_TRY(ptc_gemm_attrs());
+    const TcArgs a = tc_args(n, A, B, D, lda, ldb, ldd, K);
     if (N % 128 == 0) {
         dim3 grid((unsigned)(M / TC_BM), (unsigned)(N / 128));
-        k_gemm_bf16_tc<128><<<grid, TC_THREADS, tc_gemm_smem_bytes<128>(), n->stream>>>(
-            A, B, D, K, lda, ldb, ldd, n->err);
+        k_gemm_bf16_tc<128, TC_NT><<<grid, TC_THREADS, tc_gemm_smem_bytes<128>(), n->stream>>>(a);
     } else {
         dim3 grid((unsigned)(M / TC_BM), (unsigned)(N / 16));
-        k_gemm_bf16_tc<16><<<grid, TC_THREADS, tc_gemm_smem_bytes<16>(), n->stream>>>(
-            A, B, D, K, lda, ldb, ldd, n->err);
+        k_gemm_bf16_tc<16, TC_NT><<<grid, TC_THREADS, tc_gemm_smem_bytes<16>(), n->stream>>>(a);
     }
+    PTC_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+// Splits of the reduction of the transposed GEMM: enough CTAs to fill the
+// GPU's SMs about once (at least one 64-row step per split).
+static int tn_splits(long tiles, long R, int sms) {
+    long s = std::max<long>(1, (sms + tiles - 1) / tiles);
+    s = std::min<long>(s, std::max<long>(1, R / TC_BK));
+    return (int)std::min<long>(s, 64);
+}
+
+// D += A^T B on the tensor cores: A [R][M], B [R][N] row-major (a reduction
+// over the R rows), D [M][N] row stride ldd.  The rows are split over CTAs;
+// each split writes a partial product into n->wsplit and k_ptc_sum_splits
+// adds them to D in split order.  M % 128 == 0, N % 16 == 0, R % 64 == 0.
+static int ptc_gemm_tn(wd_ptc *n, const __nv_bfloat16 *A, const __nv_bfloat16 *B, float *D,
+                       long R, int M, int N, int lda, int ldb, int ldd) {
+    if (M % TC_BM || R % TC_BK || N % 16 || ldd != N)
+        return ptc_fail(WD_ERR_ARG, "transposed GEMM shape not tile aligned");
+    PTC_TRY(ptc_gemm_attrs());
+    int dev = 0, sms = 148;
+    PTC_CUDA(cudaGetDevice(&dev));
+    PTC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int bn = N % 128 == 0 ? 128 : 16;
+    const long tiles = (long)(M / TC_BM) * (N / bn);
+    const int splits = tn_splits(tiles, R, sms);
+    const long elems = (long)M * N;
+    if ((long)splits * elems > n->wsplit_elems) {   // grows (stream-ordered) to the largest product
+        PTC_CUDA(cudaStreamSynchronize(n->stream));
+        PTC_TRY(ptc_alloc(n, (void **)&n->wsplit, sizeof(float) * splits * elems));
+        n->wsplit_elems = (long)splits * elems;
+    }
+    TcArgs a = tc_args(n, A, B, n->wsplit, lda, ldb, N, R);
+    a.k_split = (R / splits + TC_BK - 1) / TC_BK * TC_BK;
+    a.d_split = elems;
+    const int used = (int)((R + a.k_split - 1) / a.k_split);   // splits with rows
+    dim3 grid((unsigned)(M / TC_BM), (unsigned)(N / bn), (unsigned)used);
+    if (bn == 128)
+        k_gemm_bf16_tc<128, TC_TN><<<grid, TC_THREADS, TC_TN_SMEM_BYTES, n->stream>>>(a);
+    else
+        k_gemm_bf16_tc<16, TC_TN><<<grid, TC_THREADS, TC_TN_SMEM_BYTES, n->stream>>>(a);
+    PTC_CUDA(cudaGetLastError());
+    k_ptc_sum_splits<<<grid_for(elems), PTC_BLOCK, 0, n->stream>>>(elems, used, n->wsplit, D);
     PTC_CUDA(cudaGetLastError());
     return WD_OK;
 }
@@ -459,7 +584,10 @@ static int ptc_check_err(wd_ptc *n) {
     PTC_CUDA(cudaStreamSynchronize(n->stream));
     if (h) {
         PTC_CUDA(cudaMemsetAsync(n->err, 0, sizeof(int), n->stream));
-        return ptc_fail(WD_ERR_TIMEOUT, "tensor-core GEMM gave up waiting for its MMAs");
+        PTC_CUDA(cudaStreamSynchronize(n->stream));
+        return ptc_fail(WD_ERR_TIMEOUT, h == 2 ? "tensor-core GEMM gave up waiting for its MMAs "
+                                                 "and for their drain"
+                                               : "tensor-core GEMM gave up waiting for its MMAs");
     }
     return WD_OK;
 }
@@ -490,7 +618,6 @@ void wd_ptc_destroy(wd_ptc *n) {
     if (n->stream) cudaStreamSynchronize(n->stream);
     for (void *p : n->allocs) cudaFree(p);
     if (n->partials_host) cudaFreeHost(n->partials_host);
-    if (n->blas) cublasDestroy(n->blas);
     if (n->ev_fork) cudaEventDestroy(n->ev_fork);
     if (n->ev_join) cudaEventDestroy(n->ev_join);
     if (n->stream) cudaStreamDestroy(n->stream);
@@ -527,7 +654,9 @@ int wd_ptc_create(wd_ptc **out, const int dims[4], const double phase[8], int nl
         return fail_free(ptc_fail(WD_ERR_CUDA, "stream creation failed"));
     n->ldF[0] = 8;
     for (int l = 0; l < nlayers; ++l) {
-        n->Kp[l] = (int)pad_to(2L * channels[l] * 36, TC_BK);
+        // a multiple of 128: the weight-gradient GEMM takes these columns as
+        // its 128-row output tiles
+        n->Kp[l] = (int)pad_to(2L * channels[l] * 36, TC_BM);
         n->Np[l] = (int)pad_to(2L * channels[l + 1] * 4, 16);
         n->ldF[l + 1] = n->Np[l];
         n->wcount[l] = (long)channels[l + 1] * channels[l] * PTC_NK * 16;
@@ -583,63 +712,71 @@ static int ptc_train_setup(wd_ptc *n) {
         PTC_TRY(ptc_alloc(n, (void **)&n->dF[l], sizeof(float) * n->Mp * n->ldF[l]));
         PTC_TRY(ptc_alloc(n, (void **)&n->dFb[l], sizeof(__nv_bfloat16) * n->Mp * n->Rp[l]));
     }
+    long wmax = 0;
     for (int l = 0; l < n->nl; ++l) {
         kmax = std::max(kmax, n->Kp[l]);
         wtot += n->wcount[l];
+        wmax = std::max(wmax, (long)n->Kp[l] * n->Np[l]);
         PTC_TRY(ptc_alloc(n, (void **)&n->Bt[l], sizeof(__nv_bfloat16) * (long)n->Kp[l] * n->Rp[l + 1]));
-        PTC_TRY(ptc_alloc(n, (void **)&n->dB[l], sizeof(float) * (long)n->Np[l] * n->Kp[l]));
+        PTC_TRY(ptc_alloc(n, (void **)&n->dBt[l], sizeof(float) * (long)n->Kp[l] * n->Np[l]));
     }
     PTC_TRY(ptc_alloc(n, (void **)&n->dA, sizeof(float) * n->Mp * kmax));
     PTC_TRY(ptc_alloc(n, (void **)&n->gW, sizeof(double2) * wtot));
     PTC_TRY(ptc_alloc(n, (void **)&n->adam_m, sizeof(float2) * wtot));
     PTC_TRY(ptc_alloc(n, (void **)&n->adam_v, sizeof(float2) * wtot));
-    if (cublasCreate(&n->blas) != CUBLAS_STATUS_SUCCESS)
-        return ptc_fail(WD_ERR_CUDA, "cublasCreate failed");
-    if (cublasSetStream(n->blas, n->stream) != CUBLAS_STATUS_SUCCESS)
-        return ptc_fail(WD_ERR_CUDA, "cublasSetStream failed");
+    n->wsplit_elems = 64 * wmax;   // at most 64 splits (tn_splits)
+    PTC_TRY(ptc_alloc(n, (void **)&n->wsplit, sizeof(float) * n->wsplit_elems));
+    (void)kmax;
     n->train_ready = true;
     return ptc_rebuild_b(n);
 }
 
-static double ptc_sum_partials(wd_ptc *n, int nb) {
-    double t = 0.0;
-    for (int i = 0; i < nb; ++i) t += n->partials_host[i];
-    return t;
+// 1 / |e_i|^2 of nsamples fields on the device (no host round trip).
+static int ptc_inv_norms(wd_ptc *n, const double *e, int ns) {
+    constexpr int CHUNKS = 256;
+    if (ns > n->inv_ne_cap) {
+        const int cap = std::max(ns, 64);
+        PTC_TRY(ptc_alloc(n, (void **)&n->inv_ne, sizeof(double) * cap));
+        PTC_TRY(ptc_alloc(n, (void **)&n->loss_dev, sizeof(double) * cap));
+        PTC_TRY(ptc_alloc(n, (void **)&n->norm_partials, sizeof(double) * cap * CHUNKS));
+        n->inv_ne_cap = cap;
+    }
+    const long fs = n->g.V * 12;
+    k_norm2_c128<<<dim3(CHUNKS, (unsigned)ns), PTC_BLOCK, 0, n->stream>>>(fs, (const double2 *)e,
+                                                                          n->norm_partials);
+    k_ptc_inv_norms<<<grid_for(ns), PTC_BLOCK, 0, n->stream>>>(ns, CHUNKS, n->norm_partials,
+                                                               n->inv_ne);
+    PTC_CUDA(cudaGetLastError());
+    return WD_OK;
 }
 
-// Loss of the samples and the gradient accumulated into dB[] (not yet folded).
+// Loss of the samples and the gradient accumulated into dBt[] (not yet
+// folded).  The samples run back to back on the work stream: the 1/|e_i|^2
+// factors stay on the device, each sample's loss is summed on the device
+// in a fixed order, and the host reads the per-sample losses and adds them,
+// in order, after one synchronisation at the end.
 static int ptc_accumulate(wd_ptc *n, const double *r, const double *e, int ns, double *loss) {
     const long V = n->g.V;
     const long fs = V * 12;    // complex entries per field
+    const int L_ = n->nl;
+    const unsigned nbl = grid_for(3 * V);
+    if (nbl > 4096) return ptc_fail(WD_ERR_DIMS, "lattice too large for the loss reduction");
+    if (ns > 4096) return ptc_fail(WD_ERR_ARG, "at most 4096 samples per call");
     for (int l = 0; l < n->nl; ++l)
-        PTC_CUDA(cudaMemsetAsync(n->dB[l], 0, sizeof(float) * (long)n->Np[l] * n->Kp[l], n->stream));
-    double L = 0.0;
-    const unsigned nbn = (unsigned)std::min<long>(4096, (fs + PTC_BLOCK - 1) / PTC_BLOCK);
+        PTC_CUDA(cudaMemsetAsync(n->dBt[l], 0, sizeof(float) * (long)n->Np[l] * n->Kp[l], n->stream));
+    PTC_TRY(ptc_inv_norms(n, e, ns));
     for (int i = 0; i < ns; ++i) {
         const double2 *ei = (const double2 *)e + i * fs;
-        k_norm2_c128<<<nbn, PTC_BLOCK, 0, n->stream>>>(fs, ei, n->partials);
-        PTC_CUDA(cudaMemcpyAsync(n->partials_host, n->partials, sizeof(double) * nbn,
-                                 cudaMemcpyDeviceToHost, n->stream));
-        PTC_CUDA(cudaStreamSynchronize(n->stream));
-        const double ne = ptc_sum_partials(n, nbn);
         PTC_TRY(ptc_forward(n, r + i * fs * 2, 1.0));
-        const int L_ = n->nl;
-        const unsigned nbl = grid_for(3 * V);
-        if (nbl > 4096) return ptc_fail(WD_ERR_DIMS, "lattice too large for the loss reduction");
-        k_ptc_loss_grad<<<nbl, PTC_BLOCK, 0, n->stream>>>(V, n->F[L_], n->ldF[L_], ei, 1.0 / ne,
+        k_ptc_loss_grad<<<nbl, PTC_BLOCK, 0, n->stream>>>(V, n->F[L_], n->ldF[L_], ei, n->inv_ne + i,
                                                           n->dF[L_], n->dFb[L_], n->Rp[L_],
                                                           n->partials);
+        k_ptc_sum_loss<<<1, PTC_BLOCK, 0, n->stream>>>(nbl, n->partials, n->loss_dev + i);
         PTC_CUDA(cudaGetLastError());
-        PTC_CUDA(cudaMemcpyAsync(n->partials_host, n->partials, sizeof(double) * nbl,
-                                 cudaMemcpyDeviceToHost, n->stream));
         for (int l = L_ - 1; l >= 0; --l) {
-            // dB[l] += dF[l+1]^T A[l]   (cuBLAS, column-major view: dB^T = A^T dF)
-            const float one = 1.0f;
-            cublasStatus_t st = cublasGemmEx(
-                n->blas, CUBLAS_OP_N, CUBLAS_OP_T, n->Kp[l], n->Np[l], (int)n->Mp, &one, n->A[l],
-                CUDA_R_16BF, n->Kp[l], n->dFb[l + 1], CUDA_R_16BF, n->Rp[l + 1], &one, n->dB[l],
-                CUDA_R_32F, n->Kp[l], CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-            if (st != CUBLAS_STATUS_SUCCESS) return ptc_fail(WD_ERR_CUDA, "cublasGemmEx failed");
+            // dB[l]^T += A[l]^T dF[l+1] on the tensor cores (split reduction over the rows)
+            PTC_TRY(ptc_gemm_tn(n, n->A[l], n->dFb[l + 1], n->dBt[l], n->Mp, n->Kp[l], n->Np[l],
+                                n->Kp[l], n->Rp[l + 1], n->Np[l]));
             if (l == 0) break;
             // dA = dF[l+1] B[l] on the tensor cores, then the adjoint transports
             PTC_TRY(ptc_gemm(n, n->dFb[l + 1], n->Bt[l], n->dA, n->Mp, n->Kp[l], n->Rp[l + 1],
@@ -648,9 +785,12 @@ static int ptc_accumulate(wd_ptc *n, const double *r, const double *e, int ns, d
                 n->g, n->ch[l], n->dA, n->Kp[l], n->U, n->dF[l], n->ldF[l], n->dFb[l], n->Rp[l]);
             PTC_CUDA(cudaGetLastError());
         }
-        PTC_CUDA(cudaStreamSynchronize(n->stream));
-        L += ptc_sum_partials(n, nbl) / ne;
     }
+    PTC_CUDA(cudaMemcpyAsync(n->partials_host, n->loss_dev, sizeof(double) * ns,
+                             cudaMemcpyDeviceToHost, n->stream));
+    PTC_CUDA(cudaStreamSynchronize(n->stream));
+    double L = 0.0;
+    for (int i = 0; i < ns; ++i) L += n->partials_host[i];
     if (loss) *loss = L;
     return ptc_check_err(n);
 }
@@ -659,8 +799,8 @@ static int ptc_fold_grad(wd_ptc *n) {
     long off = 0;
     for (int l = 0; l < n->nl; ++l) {
         const long cnt = (long)n->ch[l + 1] * 4 * n->ch[l] * 36;
-        k_ptc_wgrad<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(n->ch[l + 1], n->ch[l], n->dB[l],
-                                                                 n->Kp[l], n->gW + off);
+        k_ptc_wgrad<<<grid_for(cnt), PTC_BLOCK, 0, n->stream>>>(n->ch[l + 1], n->ch[l], n->dBt[l],
+                                                                 n->Np[l], n->gW + off);
         off += n->wcount[l];
     }
     PTC_CUDA(cudaGetLastError());
@@ -751,6 +891,27 @@ int wd_ptc_train_step(wd_ptc *n, const double *r, const double *e, int nsamples,
     PTC_CUDA(cudaGetLastError());
     PTC_TRY(ptc_rebuild_b(n));
     PTC_CUDA(cudaStreamSynchronize(n->stream));
+    return ptc_join(n);
+}
+
+// Bounded waits of the tensor-core GEMMs (see tc_gemm.cuh).
+int wd_ptc_set_wait_limit(wd_ptc *n, unsigned polls, int withhold_mma) {
+    if (!n || polls == 0 || (withhold_mma != 0 && withhold_mma != 1))
+        return ptc_fail(WD_ERR_ARG, "bad argument");
+    n->spin_limit = polls;
+    n->withhold = withhold_mma;
+    return WD_OK;
+}
+
+// D = A^T B through the transposed (weight-gradient) GEMM, for tests of
+// the GEMM alone: A [R x M], B [R x N] BF16 row-major (device), D [M x N] FP32.
+int wd_tc_gemm_bf16_tn(wd_ptc *n, const void *A, const void *B, float *D, long R, int M, int N) {
+    if (!n || !A || !B || !D) return ptc_fail(WD_ERR_ARG, "null argument");
+    if (R <= 0 || M <= 0 || N <= 0) return ptc_fail(WD_ERR_ARG, "empty product");
+    PTC_TRY(ptc_fork(n));
+    PTC_CUDA(cudaMemsetAsync(D, 0, sizeof(float) * M * (long)N, n->stream));
+    PTC_TRY(ptc_gemm_tn(n, (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)B, D, R, M, N, M, N, N));
+    PTC_TRY(ptc_check_err(n));
     return ptc_join(n);
 }
 

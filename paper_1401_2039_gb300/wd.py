@@ -494,6 +494,21 @@ class PtcNet:
                                              ctypes.byref(loss)))
         return loss.value
 
+    def gemm_tn(self, A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+        """D = A^T B on the transposed (weight-gradient) tensor-core GEMM, for tests."""
+        R, M = A.shape
+        N = B.shape[1]
+        D = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        self._chk(self.lib.wd_tc_gemm_bf16_tn(self.handle, ctypes.c_void_p(A.data_ptr()),
+                                              ctypes.c_void_p(B.data_ptr()),
+                                              ctypes.c_void_p(D.data_ptr()), R, M, N))
+        return D
+
+    def set_wait_limit(self, polls: int = 1 << 26, withhold_mma: bool = False):
+        """Polls per bounded GEMM wait; withhold_mma (tests) makes the GEMMs issue no MMA."""
+        self._chk(self.lib.wd_ptc_set_wait_limit(self.handle, int(polls), int(withhold_mma)))
+
     def gemm(self, A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
         """D = A B^T on the tensor-core GEMM (bf16 in, fp32 out), for tests."""
         M, K = A.shape
@@ -524,6 +539,8 @@ def _setup_ptc_signatures(lib):
         "wd_ptc_weight_count": (l, [vp]),
         "wd_ptc_apply": (i, [vp, vp, vp]),
         "wd_tc_gemm_bf16": (i, [vp, vp, vp, vp, l, i, i]),
+        "wd_tc_gemm_bf16_tn": (i, [vp, vp, vp, vp, l, i, i]),
+        "wd_ptc_set_wait_limit": (i, [vp, ctypes.c_uint, i]),
         "wd_ptc_loss_grad": (i, [vp, vp, vp, i, ctypes.POINTER(d), vp]),
         "wd_ptc_train_step": (i, [vp, vp, vp, i, d, ctypes.POINTER(d)]),
         "wd_ptc_last_error": (ctypes.c_char_p, []),

@@ -31,6 +31,49 @@ def test_tensor_core_gemm(M, N, K):
     assert err < 1e-5, err
 
 
+@pytest.mark.parametrize("R,M,N", [(64, 128, 16), (256, 128, 128), (6400, 384, 128),
+                                   (4096, 1152, 128), (192, 256, 16)])
+def test_tensor_core_gemm_transposed(R, M, N):
+    """The weight-gradient GEMM D = A^T B (MN-major operand tiles, reduction
+    split over CTAs and summed in a fixed order) against an FP32 product of
+    the same BF16 operands; the result is the same bits on a second call."""
+    from paper_1401_2039_gb300 import PtcNet
+    net = PtcNet((4, 4, 4, 4), APBC, (1, 2, 1))
+    g = torch.Generator(device="cuda").manual_seed(R + M + N)
+    A = torch.randn(R, M, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(R, N, device="cuda", generator=g).to(torch.bfloat16)
+    D = net.gemm_tn(A, B)
+    ref = A.float().T @ B.float()
+    err = ((D - ref).norm() / ref.norm()).item()
+    assert err < 1e-5, err
+    assert torch.equal(net.gemm_tn(A, B), D)
+    net.close()
+
+
+def test_gemm_bounded_wait_runs_out_and_the_gpu_stays_usable():
+    """The test hook makes the GEMM issue no MMA, so its first mbarrier wait
+    (limited to 2000 polls) runs out with nothing in flight: the call
+    returns WD_ERR_TIMEOUT, TMEM is freed, and the next GEMM on the same
+    handle, with the default limit, is correct."""
+    from paper_1401_2039_gb300 import PtcNet
+    from paper_1401_2039_gb300.wd import WD_ERR_TIMEOUT, WDError
+    net = PtcNet((4, 4, 4, 4), APBC, (1, 2, 1))
+    A = torch.randn(512, 256, device="cuda").to(torch.bfloat16)
+    B = torch.randn(128, 256, device="cuda").to(torch.bfloat16)
+    net.set_wait_limit(2000, withhold_mma=True)
+    for fn in (lambda: net.gemm(A, B), lambda: net.gemm_tn(A, A[:, :128].contiguous())):
+        with pytest.raises(WDError) as exc:
+            fn()
+        assert exc.value.status == WD_ERR_TIMEOUT
+    net.set_wait_limit()
+    D = net.gemm(A, B)
+    ref = A.float() @ B.float().T
+    assert ((D - ref).norm() / ref.norm()).item() < 1e-5
+    with pytest.raises(WDError):
+        net.set_wait_limit(0)
+    net.close()
+
+
 def _to_flat(Ws):
     return np.concatenate([W.ravel() for W in Ws])
 
