@@ -20,224 +20,16 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include <type_traits>
 
-#include "dslash_df.cuh"
+#include "batch_internal.cuh"
 
 namespace wd {
-
-constexpr int BT_BLOCK = 128;
-constexpr int BT_MAX_PROB = 8;
-constexpr int BT_MAX_SLOTS = 64;
-constexpr int BT_GRID = 152 * 8;
-
-struct BtProb {
-    Geom g;                  // stride = plane stride of one right-hand side
-    const char *gauge_out;   // links of the output parity
-    const char *gauge_in;    // links of the input parity
-    size_t dir_bytes;
-    void *f[4];              // fields of this launch (meaning set by the kernel)
-    double scale;            // per-problem coefficient
-    double ph[8];            // boundary phases
-    int nrhs;
-    int slot0;               // first solver slot of the problem
-    long tile0;              // first tile of the problem
-    long nitems;             // work items of the problem
-};
-
-struct BtArgs {
-    BtProb p[BT_MAX_PROB];
-    int nprob;
-    long ntiles;
-    int parity;              // output parity of hopping terms
-    int fin;                 // final operation applied per slot
-    int nslots;
-    df64 *partials;          // [grid][BT_MAX_SLOTS]
-    unsigned int *counter;
-    SolverScalars *scalars;  // [nslots]
-    const double *consts;    // per-slot constants, [4][BT_MAX_SLOTS]
-};
-
-__device__ __forceinline__ int bt_problem(const BtArgs &a, long t) {
-    int pi = 0;
-#pragma unroll 1
-    for (int k = 1; k < a.nprob; ++k)
-        if (t >= a.p[k].tile0) pi = k;
-    return pi;
-}
-
-// Per-rhs sums of the items of a tile, without block barriers.  Each warp
-// stages its 32 values (items item0 + 32 w + lane; the item's rhs is item %
-// nrhs) in its own shared-memory row; lane j then adds the values of rhs j in
-// lane order and accumulates them into the warp's slot row wacc[w][slot].
-// bt_block_sums later adds the warps' rows in warp order, so every sum has a
-// fixed order.  Values are double-float (the FP64 adder of GB300 is too slow
-// for per-item work).
-constexpr int BT_WARPS = BT_BLOCK / 32;
-
-__device__ __forceinline__ void bt_warp_sums(df64 v, const BtProb &P, long item0, df64 *wv,
-                                             df64 (*wacc)[BT_MAX_SLOTS]) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    wv[threadIdx.x] = v;
-    __syncwarp();
-    const int nr = P.nrhs;
-    const long iw = item0 + 32 * w;
-    const int base = (int)(iw % nr);
-    for (int j = lane; j < nr; j += 32) {
-        df64 s = 0;
-        for (int l = (j - base + nr) % nr; l < 32; l += nr) s = s + wv[32 * w + l];
-        wacc[w][P.slot0 + j] = wacc[w][P.slot0 + j] + s;
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ void bt_zero_sums(df64 (*wacc)[BT_MAX_SLOTS]) {
-    for (int i = threadIdx.x; i < BT_WARPS * BT_MAX_SLOTS; i += BT_BLOCK)
-        wacc[i / BT_MAX_SLOTS][i % BT_MAX_SLOTS] = df64(0.0f, 0.0f);
-    __syncthreads();
-}
-
-// the block's slot sums: the warps' rows added in warp order
-__device__ __forceinline__ void bt_block_sums(df64 (*wacc)[BT_MAX_SLOTS], df64 *sacc, int nslots) {
-    __syncthreads();
-    for (int sl = threadIdx.x; sl < nslots; sl += BT_BLOCK) {
-        df64 t = wacc[0][sl];
-#pragma unroll
-        for (int w = 1; w < BT_WARPS; ++w) t = t + wacc[w][sl];
-        sacc[sl] = t;
-    }
-    __syncthreads();
-}
-
-// Grid-wide finish: per-block slot partials, then the last block adds them
-// in block order (one warp per slot) and applies the final operation.
-__device__ __forceinline__ void bt_finish(const BtArgs &a, const df64 *sacc) {
-    __shared__ bool last;
-    for (int s = threadIdx.x; s < a.nslots; s += BT_BLOCK)
-        a.partials[(long)blockIdx.x * BT_MAX_SLOTS + s] = sacc[s];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = arrive_last(a.counter, gridDim.x, blockIdx.x);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int s = warp; s < a.nslots; s += BT_BLOCK / 32) {
-        const df64 sum = warp_sum(strided_sum<32>(a.partials + s, gridDim.x, lane, BT_MAX_SLOTS));
-        if (lane == 0) apply_final(&a.scalars[s], a.fin, (double)sum);
-    }
-}
-
-// ------------------------------------------------------------------ hopping term
-template <typename S, typename R, int RECON, int MU, int DAG>
-__device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], long h, int r,
-                                            Acc<R> *acc) {
-    constexpr int SF = DAG ? +1 : -1;
-    constexpr int SB = -SF;
-    const long ss = P.g.stride * P.nrhs;
-    {
-        bool wrap;
-        const long hn = neighbour<MU, +1>(P.g, h, c, wrap);
-        R psi[24];
-        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
-        cx<Acc<R>> hs[2][3], u[2][3];
-        project<MU, SF>(psi, hs);
-        R U[18];
-        load_link<S, R, RECON>(P.gauge_out + MU * P.dir_bytes, P.g.stride, h, U);
-        su3_mul(U, hs, u);
-        if (wrap) phase_mul(u, (R)P.ph[2 * MU], (R)P.ph[2 * MU + 1]);
-        accumulate<MU, SF>(acc, u);
-    }
-    {
-        bool wrap;
-        const long hn = neighbour<MU, -1>(P.g, h, c, wrap);
-        R psi[24];
-        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
-        cx<Acc<R>> hs[2][3], u[2][3];
-        project<MU, SB>(psi, hs);
-        R U[18];
-        load_link<S, R, RECON>(P.gauge_in + MU * P.dir_bytes, P.g.stride, hn, U);
-        su3_adj_mul(U, hs, u);
-        if (wrap) phase_mul(u, (R)P.ph[2 * MU], -(R)P.ph[2 * MU + 1]);
-        accumulate<MU, SB>(acc, u);
-    }
-}
-
-// f[0] = out, f[1] = in, f[2] = x:  out = scale * H in  or  x + scale * H in
-// Double-float instances run the hop loop of dslash_df.cuh (unrolled, their
-// code outgrows the instruction cache) under a 168-register cap.
-template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM>
-__global__ void __launch_bounds__(BT_BLOCK, std::is_same<S, df64>::value ? 3 : 1)
-    k_dslash_batch(const __grid_constant__ BtArgs a) {
-    __shared__ df64 wv[BT_BLOCK];
-    __shared__ df64 wacc[BT_WARPS][BT_MAX_SLOTS];
-    __shared__ df64 sacc[BT_MAX_SLOTS];
-    if (NORM) bt_zero_sums(wacc);
-    for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const BtProb &P = a.p[bt_problem(a, t)];
-        const long item0 = (t - P.tile0) * BT_BLOCK;
-        const long item = item0 + threadIdx.x;
-        df64 v = 0;
-        if (item < P.nitems) {
-            const int nr = P.nrhs;
-            const unsigned hu = (unsigned)item / (unsigned)nr;   // items < 2^31
-            const long h = hu;
-            const int r = (int)((unsigned)item - hu * (unsigned)nr);
-            int c[4];
-            site_coords(P.g, h, a.parity, c);
-            Acc<R> acc[24];
-#pragma unroll
-            for (int k = 0; k < 24; ++k) acc[k] = 0;
-            if constexpr (std::is_same<S, df64>::value) {
-                df_hops<DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                             P.g.stride * nr, nr, r, h, c, acc);
-            } else if constexpr (std::is_same<S, __half>::value) {
-                const long ss = P.g.stride * nr;
-                hop_pair_h2<RECON, 0, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
-                hop_pair_h2<RECON, 1, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
-                hop_pair_h2<RECON, 2, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
-                hop_pair_h2<RECON, 3, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
-            } else {
-                bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
-                bt_hop_pair<S, R, RECON, 1, DAG>(P, c, h, r, acc);
-                bt_hop_pair<S, R, RECON, 2, DAG>(P, c, h, r, acc);
-                bt_hop_pair<S, R, RECON, 3, DAG>(P, c, h, r, acc);
-            }
-            const long ss = P.g.stride * nr;
-            const R sc = (R)P.scale;
-            R o[24];
-            if (XPAY) {
-                R xv[24];
-                Rec<S, 24>::template load<R, 0>(P.f[2], ss, item, xv);
-#pragma unroll
-                for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + sc * acc[k]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 24; ++k) o[k] = settle(sc * acc[k]);
-            }
-            Rec<S, 24>::store(P.f[0], ss, item, o);
-            if (NORM) {
-                R sq = 0;
-#pragma unroll
-                for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-                v = to_df(sq);
-            }
-        }
-        if (NORM) bt_warp_sums(v, P, item0, wv, wacc);
-    }
-    if (NORM) {
-        bt_block_sums(wacc, sacc, a.nslots);
-        bt_finish(a, sacc);
-    }
-}
 
 // ------------------------------------------------------------------ vector kernels
 // Element-wise kernels walk 16-byte chunks; chunk i of a problem belongs to
@@ -523,6 +315,13 @@ struct wd_batch {
     SolverScalars *sc = nullptr, *sc_host = nullptr;
     double *consts = nullptr, *consts_host = nullptr;
     cudaGraphExec_t graphs[2][MAX_BATCH_LOG2 + 1] = {};
+    long max_grid = 0;          // blocks the partials buffer holds (SMs x 32)
+    unsigned vec_grid = 0;      // persistent grid of the element-wise kernels (SMs x 8)
+    // autotuned configuration (BT_CFGS) of the storage-precision hop per
+    // variant (BTV_PLAIN, BTV_XPAY_NORM), with every candidate's time and grid
+    int cfg[2] = {0, 0};
+    double tune_us[2][N_BT_CFG] = {};
+    unsigned tune_grid[2][N_BT_CFG] = {};
     std::vector<void *> allocs;
 };
 
@@ -562,7 +361,7 @@ double scale_of(const wd_op *op, int mode) {
 
 // Arguments of one batched launch: tile table, fields, per-problem scale.
 BtArgs make_args(wd_batch *bt, int kind, int fin, std::initializer_list<int> fields,
-                 int scale_mode, bool hi, int out_parity) {
+                 int scale_mode, bool hi, int out_parity, int tile_items = BT_BLOCK) {
     BtArgs a;
     memset(&a, 0, sizeof(a));
     a.nprob = bt->nprob;
@@ -583,7 +382,7 @@ BtArgs make_args(wd_batch *bt, int kind, int fin, std::initializer_list<int> fie
         P.slot0 = bt->slot0[p];
         P.tile0 = tile;
         P.nitems = items_of(bt, p, kind);
-        tile += (P.nitems + BT_BLOCK - 1) / BT_BLOCK;
+        tile += (P.nitems + tile_items - 1) / tile_items;
     }
     a.ntiles = tile;
     a.parity = out_parity;
@@ -593,46 +392,53 @@ BtArgs make_args(wd_batch *bt, int kind, int fin, std::initializer_list<int> fie
     a.counter = bt->counter;
     a.scalars = bt->sc;
     a.consts = bt->consts;
+    a.max_grid = bt->max_grid;
     return a;
 }
 
-unsigned grid_of(const BtArgs &a) {
-    return (unsigned)std::max<long>(1, std::min<long>(a.ntiles, BT_GRID));
+// grid of the element-wise kernels: persistent over SMs x 8 blocks of 128
+unsigned grid_of(const wd_batch *bt, const BtArgs &a) {
+    return (unsigned)std::max<long>(1, std::min<long>(a.ntiles, bt->vec_grid));
 }
 
-template <typename S, typename R, int RECON>
-void launch_hop_t(const BtArgs &a, int dagger, bool xpay, bool norm, cudaStream_t s) {
-    const unsigned gr = grid_of(a);
-#define BT_H(D, X, N) k_dslash_batch<S, R, RECON, D, X, N><<<gr, BT_BLOCK, 0, s>>>(a)
-    if (dagger) {
-        if (!xpay) BT_H(1, 0, 0); else if (!norm) BT_H(1, 1, 0); else BT_H(1, 1, 1);
-    } else {
-        if (!xpay) BT_H(0, 0, 0); else if (!norm) BT_H(0, 1, 0); else BT_H(0, 1, 1);
+int bt_hop_block(int prec, int cfg) {
+    return (prec == WD_F32 || prec == WD_F16) ? BT_CFGS[cfg].block : 128;
+}
+
+cudaError_t bt_launch_hop(int prec, int recon, int dagger, int variant, int cfg, const BtArgs &a,
+                          cudaStream_t s, unsigned *grid_out = nullptr) {
+    const bool r12 = recon == 12;
+    switch (prec) {
+    case WD_DF64:
+        return r12 ? cudaErrorInvalidValue
+                   : bt_launch_hop_df64_r18(dagger, variant, cfg, a, s, grid_out);
+    case WD_F64:
+        return r12 ? bt_launch_hop_f64_r12(dagger, variant, cfg, a, s, grid_out)
+                   : bt_launch_hop_f64_r18(dagger, variant, cfg, a, s, grid_out);
+    case WD_F32:
+        return r12 ? bt_launch_hop_f32_r12(dagger, variant, cfg, a, s, grid_out)
+                   : bt_launch_hop_f32_r18(dagger, variant, cfg, a, s, grid_out);
+    case WD_F16:
+        return r12 ? bt_launch_hop_f16_r12(dagger, variant, cfg, a, s, grid_out)
+                   : bt_launch_hop_f16_r18(dagger, variant, cfg, a, s, grid_out);
+    default: return cudaErrorInvalidValue;
     }
-#undef BT_H
 }
 
-// out = scale * H_{p,q} in  or  x + scale * H_{p,q} in, for every system
+// out = scale * H_{p,q} in  or  x + scale * H_{p,q} in, for every system, in
+// the variant's tuned configuration (cfg_override >= 0: that one)
 int bt_hop(wd_batch *bt, bool hi, int out_parity, int dagger, int out, int in, int x,
-           int scale_mode, int fin) {
-    BtArgs a = x >= 0 ? make_args(bt, IT_SITES, fin, {out, in, x}, scale_mode, hi, out_parity)
-                      : make_args(bt, IT_SITES, fin, {out, in}, scale_mode, hi, out_parity);
+           int scale_mode, int fin, int cfg_override = -1, unsigned *grid_out = nullptr) {
     const bool xpay = x >= 0, norm = fin != FIN_NONE;
+    const int variant = !xpay ? BTV_PLAIN : norm ? BTV_XPAY_NORM : BTV_XPAY;
     const int prec = hi ? bt->hi_prec : bt->prec;
     const int recon = hi ? 18 : bt->recon;
-    if (prec == WD_DF64) {
-        launch_hop_t<df64, df64, 18>(a, dagger, xpay, norm, bt->stream);
-    } else if (prec == WD_F64) {
-        if (recon == 12) launch_hop_t<double, double, 12>(a, dagger, xpay, norm, bt->stream);
-        else launch_hop_t<double, double, 18>(a, dagger, xpay, norm, bt->stream);
-    } else if (prec == WD_F32) {
-        if (recon == 12) launch_hop_t<float, float, 12>(a, dagger, xpay, norm, bt->stream);
-        else launch_hop_t<float, float, 18>(a, dagger, xpay, norm, bt->stream);
-    } else {
-        if (recon == 12) launch_hop_t<__half, float, 12>(a, dagger, xpay, norm, bt->stream);
-        else launch_hop_t<__half, float, 18>(a, dagger, xpay, norm, bt->stream);
-    }
-    BT_CUDA(cudaGetLastError());
+    const int cfg = cfg_override >= 0 ? cfg_override
+                                      : (variant == BTV_XPAY ? 0 : bt->cfg[variant]);
+    const int tile = variant == BTV_XPAY ? 128 : bt_hop_block(prec, cfg);
+    BtArgs a = xpay ? make_args(bt, IT_SITES, fin, {out, in, x}, scale_mode, hi, out_parity, tile)
+                    : make_args(bt, IT_SITES, fin, {out, in}, scale_mode, hi, out_parity, tile);
+    BT_CUDA(bt_launch_hop(prec, recon, dagger, variant, cfg, a, bt->stream, grid_out));
     return WD_OK;
 }
 
@@ -646,7 +452,7 @@ template <int OP>
 int bt_vec(wd_batch *bt, bool hi, int fin, std::initializer_list<int> fields) {
     BtArgs a = make_args(bt, hi ? IT_HI_CHUNKS : IT_LO_CHUNKS, fin, fields, SC_ONE, false, 0);
     const int prec = hi ? bt->hi_prec : bt->prec;
-    const unsigned gr = grid_of(a);
+    const unsigned gr = grid_of(bt, a);
     if (prec == WD_DF64) k_bt_vec<df64, df64, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
     else if (prec == WD_F64) k_bt_vec<double, double, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
     else if (prec == WD_F32) k_bt_vec<float, float, OP><<<gr, BT_BLOCK, 0, bt->stream>>>(a);
@@ -658,8 +464,8 @@ int bt_vec(wd_batch *bt, bool hi, int fin, std::initializer_list<int> fields) {
 template <int OP>
 int bt_f64(wd_batch *bt, int fin, std::initializer_list<int> fields, int scale_mode) {
     BtArgs a = make_args(bt, IT_HI_D2, fin, fields, scale_mode, false, 0);
-    if (bt->hi_prec == WD_DF64) k_bt_hi<df64, OP><<<grid_of(a), BT_BLOCK, 0, bt->stream>>>(a);
-    else k_bt_hi<double, OP><<<grid_of(a), BT_BLOCK, 0, bt->stream>>>(a);
+    if (bt->hi_prec == WD_DF64) k_bt_hi<df64, OP><<<grid_of(bt, a), BT_BLOCK, 0, bt->stream>>>(a);
+    else k_bt_hi<double, OP><<<grid_of(bt, a), BT_BLOCK, 0, bt->stream>>>(a);
     BT_CUDA(cudaGetLastError());
     return WD_OK;
 }
@@ -667,7 +473,7 @@ int bt_f64(wd_batch *bt, int fin, std::initializer_list<int> fields, int scale_m
 // lo <- consts[0] * hi  (FOLD = 0)   or   hi += consts[1] * lo, lo = 0  (FOLD = 1)
 int bt_conv(wd_batch *bt, bool fold, int dst, int src) {
     BtArgs a = make_args(bt, IT_SITES, FIN_NONE, {dst, src}, SC_ONE, false, 0);
-    const unsigned gr = grid_of(a);
+    const unsigned gr = grid_of(bt, a);
     cudaStream_t s = bt->stream;
     const bool df = bt->hi_prec == WD_DF64;
     if (fold) {
@@ -959,6 +765,58 @@ void wd_batch_destroy(wd_batch *bt) {
     delete bt;
 }
 
+// Autotuner of the storage-precision batched hop: every configuration of
+// BT_CFGS (threads per block, register cap; grid = the kernel's resident
+// capacity) is timed on this batch's own lattices and right-hand sides, the
+// plain hop and the norm-fused xpay hop of the Schur operator separately
+// (two warm-up and five timed launches on the resident fields, CUDA events
+// on the batch stream), and the fastest kept.  The per-system norms add in
+// an order fixed by the configuration (tile size and grid), so solves with
+// the same configuration repeat bit for bit.  WD_BATCH_CFG=k forces
+// configuration k, WD_TUNE=0 keeps configuration 0.
+static int bt_tune(wd_batch *bt) {
+    if (bt->prec != WD_F32 && bt->prec != WD_F16) return WD_OK;
+    const char *force = getenv("WD_BATCH_CFG");
+    const char *tune = getenv("WD_TUNE");
+    if (force || (tune && tune[0] == '0')) {
+        const int k = force ? atoi(force) : 0;
+        bt->cfg[0] = bt->cfg[1] = (k >= 0 && k < N_BT_CFG) ? k : 0;
+        return WD_OK;
+    }
+    cudaEvent_t e0, e1;
+    BT_CUDA(cudaEventCreate(&e0));
+    BT_CUDA(cudaEventCreate(&e1));
+    int rc = WD_OK;
+    for (int v = 0; v < 2 && rc == WD_OK; ++v) {
+        float best = 1e30f;
+        for (int k = 0; k < N_BT_CFG && rc == WD_OK; ++k) {
+            auto launch = [&](int par) {
+                return v == BTV_PLAIN
+                           ? bt_hop(bt, false, par, 0, F_IO1, F_IO0, -1, SC_ONE, FIN_NONE, k,
+                                    &bt->tune_grid[v][k])
+                           : bt_hop(bt, false, par, 0, F_IO1, F_IO0, F_IO1, SC_MKAPPA2, FIN_STORE0,
+                                    k, &bt->tune_grid[v][k]);
+            };
+            for (int w = 0; w < 2 && rc == WD_OK; ++w) rc = launch(w & 1);
+            if (rc != WD_OK) break;
+            if (cudaEventRecord(e0, bt->stream) != cudaSuccess) { rc = bt_fail(WD_ERR_CUDA, "event"); break; }
+            for (int r = 0; r < 5 && rc == WD_OK; ++r) rc = launch(r & 1);
+            if (rc != WD_OK) break;
+            float ms = 0;
+            if (cudaEventRecord(e1, bt->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = bt_fail(WD_ERR_CUDA, "event timing of the batch autotuner");
+                break;
+            }
+            bt->tune_us[v][k] = ms * 1e3 / 5;
+            if (ms < best) { best = ms; bt->cfg[v] = k; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 static int batch_create_impl(wd_batch *bt) {
     BT_CUDA(cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking));
     BT_CUDA(cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming));
@@ -972,14 +830,19 @@ static int batch_create_impl(wd_batch *bt) {
             BT_TRY(bt_alloc(bt, &bt->fl[p].f[f], is_lo ? lo : hi));
         }
     }
-    BT_TRY(bt_alloc(bt, (void **)&bt->partials, sizeof(df64) * BT_GRID * BT_MAX_SLOTS));
+    int dev = 0, sms = 1;
+    BT_CUDA(cudaGetDevice(&dev));
+    BT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    bt->max_grid = (long)sms * BT_BLOCKS_PER_SM_MAX;
+    bt->vec_grid = (unsigned)sms * 8;
+    BT_TRY(bt_alloc(bt, (void **)&bt->partials, sizeof(df64) * bt->max_grid * BT_MAX_SLOTS));
     BT_TRY(bt_alloc(bt, (void **)&bt->counter, sizeof(unsigned int) * ARRIVE_WORDS));
     BT_TRY(bt_alloc(bt, (void **)&bt->sc, sizeof(SolverScalars) * BT_MAX_SLOTS));
     BT_TRY(bt_alloc(bt, (void **)&bt->consts, sizeof(double) * 4 * BT_MAX_SLOTS));
     BT_CUDA(cudaMallocHost((void **)&bt->sc_host, sizeof(SolverScalars) * BT_MAX_SLOTS));
     BT_CUDA(cudaMallocHost((void **)&bt->consts_host, sizeof(double) * 4 * BT_MAX_SLOTS));
     BT_CUDA(cudaDeviceSynchronize());
-    return WD_OK;
+    return bt_tune(bt);
 }
 
 int wd_batch_create(wd_batch **out, wd_op *const *ops, const int *nrhs, int nops) {
@@ -1070,6 +933,17 @@ int wd_batch_dslash(wd_batch *bt, double *const *out, const double *const *in, i
     }
     BT_CUDA(cudaGetLastError());
     return bt_join(bt);
+}
+
+int wd_batch_tuning(const wd_batch *bt, int variant, double *us, int n, int *block,
+                    int *min_blocks, int *grid) {
+    if (!bt || variant < 0 || variant > 1) return -1;
+    const int k = bt->cfg[variant];
+    for (int i = 0; us && i < n && i < N_BT_CFG; ++i) us[i] = bt->tune_us[variant][i];
+    if (block) *block = BT_CFGS[k].block;
+    if (min_blocks) *min_blocks = BT_CFGS[k].minb;
+    if (grid) *grid = (int)bt->tune_grid[variant][k];
+    return k;
 }
 
 int wd_batch_dslash_resident(wd_batch *bt, int out_parity, int dagger) {

@@ -1,0 +1,10 @@
+// Batched hopping term, FP16 storage, 18-real links: every launch configuration the
+// batch autotuner chooses from (own translation unit for a parallel build).
+#include "batch_internal.cuh"
+
+namespace wd {
+cudaError_t bt_launch_hop_f16_r18(int dagger, int variant, int cfg, const BtArgs &a, cudaStream_t s,
+                   unsigned *grid_out) {
+    return bt_launch_lo<__half, float, 18>(dagger, variant, cfg, a, s, grid_out);
+}
+}  // namespace wd

@@ -1,0 +1,329 @@
+// Internal declarations of the batched solver (batch.cu) shared with the
+// translation units that instantiate its hopping-term kernels
+// (batch_hop_*.cu): problem table, deterministic per-system reductions and
+// the batched hopping term.
+//
+#pragma once
+
+#include <type_traits>
+
+#include "dslash_df.cuh"
+
+namespace wd {
+
+constexpr int BT_BLOCK = 128;       // block (and tile) size of the element-wise kernels
+constexpr int BT_WARPS = BT_BLOCK / 32;
+constexpr int BT_MAX_PROB = 8;
+constexpr int BT_MAX_SLOTS = 64;
+constexpr int BT_BLOCKS_PER_SM_MAX = 32;   // per-block partials are sized for this grid
+
+struct BtProb {
+    Geom g;                  // stride = plane stride of one right-hand side
+    const char *gauge_out;   // links of the output parity
+    const char *gauge_in;    // links of the input parity
+    size_t dir_bytes;
+    void *f[4];              // fields of this launch (meaning set by the kernel)
+    double scale;            // per-problem coefficient
+    double ph[8];            // boundary phases
+    int nrhs;
+    int slot0;               // first solver slot of the problem
+    long tile0;              // first tile of the problem
+    long nitems;             // work items of the problem
+};
+
+struct BtArgs {
+    BtProb p[BT_MAX_PROB];
+    int nprob;
+    long ntiles;
+    int parity;              // output parity of hopping terms
+    int fin;                 // final operation applied per slot
+    int nslots;
+    df64 *partials;          // [grid][BT_MAX_SLOTS]
+    unsigned int *counter;
+    SolverScalars *scalars;  // [nslots]
+    const double *consts;    // per-slot constants, [4][BT_MAX_SLOTS]
+    long max_grid;           // blocks the partials buffer holds
+};
+
+__device__ __forceinline__ int bt_problem(const BtArgs &a, long t) {
+    int pi = 0;
+#pragma unroll 1
+    for (int k = 1; k < a.nprob; ++k)
+        if (t >= a.p[k].tile0) pi = k;
+    return pi;
+}
+
+// Per-rhs sums of the items of a tile, without block barriers.  Each warp
+// stages its 32 values (items item0 + 32 w + lane; the item's rhs is item %
+// nrhs) in its own shared-memory row; lane j then adds the values of rhs j in
+// lane order and accumulates them into the warp's slot row wacc[w][slot].
+// bt_block_sums later adds the warps' rows in warp order, so every sum has a
+// fixed order.  Values are double-float (the FP64 adder of GB300 is too slow
+// for per-item work).
+template <int BLOCK = BT_BLOCK>
+__device__ __forceinline__ void bt_warp_sums(df64 v, const BtProb &P, long item0, df64 *wv,
+                                             df64 (*wacc)[BT_MAX_SLOTS]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    wv[threadIdx.x] = v;
+    __syncwarp();
+    const int nr = P.nrhs;
+    const long iw = item0 + 32 * w;
+    const int base = (int)(iw % nr);
+    for (int j = lane; j < nr; j += 32) {
+        df64 s = 0;
+        for (int l = (j - base + nr) % nr; l < 32; l += nr) s = s + wv[32 * w + l];
+        wacc[w][P.slot0 + j] = wacc[w][P.slot0 + j] + s;
+    }
+    __syncwarp();
+}
+
+template <int BLOCK = BT_BLOCK>
+__device__ __forceinline__ void bt_zero_sums(df64 (*wacc)[BT_MAX_SLOTS]) {
+    for (int i = threadIdx.x; i < (BLOCK / 32) * BT_MAX_SLOTS; i += BLOCK)
+        wacc[i / BT_MAX_SLOTS][i % BT_MAX_SLOTS] = df64(0.0f, 0.0f);
+    __syncthreads();
+}
+
+// the block's slot sums: the warps' rows added in warp order
+template <int BLOCK = BT_BLOCK>
+__device__ __forceinline__ void bt_block_sums(df64 (*wacc)[BT_MAX_SLOTS], df64 *sacc, int nslots) {
+    __syncthreads();
+    for (int sl = threadIdx.x; sl < nslots; sl += BLOCK) {
+        df64 t = wacc[0][sl];
+#pragma unroll
+        for (int w = 1; w < BLOCK / 32; ++w) t = t + wacc[w][sl];
+        sacc[sl] = t;
+    }
+    __syncthreads();
+}
+
+// Grid-wide finish: per-block slot partials, then the last block adds them
+// in block order (one warp per slot) and applies the final operation.
+template <int BLOCK = BT_BLOCK>
+__device__ __forceinline__ void bt_finish(const BtArgs &a, const df64 *sacc) {
+    __shared__ bool last;
+    for (int s = threadIdx.x; s < a.nslots; s += BLOCK)
+        a.partials[(long)blockIdx.x * BT_MAX_SLOTS + s] = sacc[s];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = arrive_last(a.counter, gridDim.x, blockIdx.x);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = warp; s < a.nslots; s += BLOCK / 32) {
+        const df64 sum = warp_sum(strided_sum<32>(a.partials + s, gridDim.x, lane, BT_MAX_SLOTS));
+        if (lane == 0) apply_final(&a.scalars[s], a.fin, (double)sum);
+    }
+}
+
+// ------------------------------------------------------------------ hopping term
+template <typename S, typename R, int RECON, int MU, int DAG>
+__device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], long h, int r,
+                                            Acc<R> *acc) {
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    const long ss = P.g.stride * P.nrhs;
+    {
+        bool wrap;
+        const long hn = neighbour<MU, +1>(P.g, h, c, wrap);
+        R psi[24];
+        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
+        cx<Acc<R>> hs[2][3], u[2][3];
+        project<MU, SF>(psi, hs);
+        R U[18];
+        load_link<S, R, RECON>(P.gauge_out + MU * P.dir_bytes, P.g.stride, h, U);
+        su3_mul(U, hs, u);
+        if (wrap) phase_mul(u, (R)P.ph[2 * MU], (R)P.ph[2 * MU + 1]);
+        accumulate<MU, SF>(acc, u);
+    }
+    {
+        bool wrap;
+        const long hn = neighbour<MU, -1>(P.g, h, c, wrap);
+        R psi[24];
+        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
+        cx<Acc<R>> hs[2][3], u[2][3];
+        project<MU, SB>(psi, hs);
+        R U[18];
+        load_link<S, R, RECON>(P.gauge_in + MU * P.dir_bytes, P.g.stride, hn, U);
+        su3_adj_mul(U, hs, u);
+        if (wrap) phase_mul(u, (R)P.ph[2 * MU], -(R)P.ph[2 * MU + 1]);
+        accumulate<MU, SB>(acc, u);
+    }
+}
+
+// f[0] = out, f[1] = in, f[2] = x:  out = scale * H in  or  x + scale * H in.
+// Tiles of BLOCK items (one per thread); MINB resident blocks per SM set the
+// register cap, the parameter the autotuner picks per batch.  Double-float
+// instances run the hop loop of dslash_df.cuh (unrolled, their code
+// outgrows the instruction cache).
+template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_dslash_batch(const __grid_constant__ BtArgs a) {
+    __shared__ df64 wv[BLOCK];
+    __shared__ df64 wacc[BLOCK / 32][BT_MAX_SLOTS];
+    __shared__ df64 sacc[BT_MAX_SLOTS];
+    if (NORM) bt_zero_sums<BLOCK>(wacc);
+    for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const BtProb &P = a.p[bt_problem(a, t)];
+        const long item0 = (t - P.tile0) * BLOCK;
+        const long item = item0 + threadIdx.x;
+        df64 v = 0;
+        if (item < P.nitems) {
+            const int nr = P.nrhs;
+            const unsigned hu = (unsigned)item / (unsigned)nr;   // items < 2^31
+            const long h = hu;
+            const int r = (int)((unsigned)item - hu * (unsigned)nr);
+            int c[4];
+            site_coords(P.g, h, a.parity, c);
+            Acc<R> acc[24];
+#pragma unroll
+            for (int k = 0; k < 24; ++k) acc[k] = 0;
+            if constexpr (std::is_same<S, df64>::value) {
+                df_hops<DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                             P.g.stride * nr, nr, r, h, c, acc);
+            } else if constexpr (std::is_same<S, __half>::value) {
+                const long ss = P.g.stride * nr;
+                hop_pair_h2<RECON, 0, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
+                hop_pair_h2<RECON, 1, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
+                hop_pair_h2<RECON, 2, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
+                hop_pair_h2<RECON, 3, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
+                                           ss, nr, r, c, h, acc);
+            } else {
+                bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
+                bt_hop_pair<S, R, RECON, 1, DAG>(P, c, h, r, acc);
+                bt_hop_pair<S, R, RECON, 2, DAG>(P, c, h, r, acc);
+                bt_hop_pair<S, R, RECON, 3, DAG>(P, c, h, r, acc);
+            }
+            const long ss = P.g.stride * nr;
+            const R sc = (R)P.scale;
+            R o[24];
+            if (XPAY) {
+                R xv[24];
+                Rec<S, 24>::template load<R, 0>(P.f[2], ss, item, xv);
+#pragma unroll
+                for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + sc * acc[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) o[k] = settle(sc * acc[k]);
+            }
+            Rec<S, 24>::store(P.f[0], ss, item, o);
+            if (NORM) {
+                R sq = 0;
+#pragma unroll
+                for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
+                v = to_df(sq);
+            }
+        }
+        if (NORM) bt_warp_sums<BLOCK>(v, P, item0, wv, wacc);
+    }
+    if (NORM) {
+        bt_block_sums<BLOCK>(wacc, sacc, a.nslots);
+        bt_finish<BLOCK>(a, sacc);
+    }
+}
+
+// Launch configurations of the batched hopping term in storage precision
+// (FP32, FP16): threads per block (= items per tile) and minimum resident
+// blocks per SM (the register cap).  The grid is the kernel's resident
+// capacity on this GPU (SMs x blocks per SM), capped at the tile count.
+struct BtCfg { int block, minb; };
+constexpr int N_BT_CFG = 5;
+constexpr BtCfg BT_CFGS[N_BT_CFG] = {{128, 4}, {128, 5}, {128, 6}, {128, 8}, {256, 2}};
+
+// Variants of a batched hop: plain (out = scale H in) or xpay with the fused
+// per-system norm (the second hop of the Schur operator in the CGNR
+// iteration); residual-arithmetic handles also use xpay without a norm.
+enum BtVariant { BTV_PLAIN = 0, BTV_XPAY_NORM = 1, BTV_XPAY = 2 };
+
+// Resident capacity of a kernel with `block` threads: SMs x blocks per SM.
+template <typename K>
+inline unsigned bt_resident_grid(K kernel, int block) {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0) != cudaSuccess || per < 1)
+        per = 1;
+    cudaGetLastError();
+    return (unsigned)(sms * per);
+}
+
+// One launch of a batched hop: persistent grid = the kernel's resident
+// capacity on this device (looked up once per device), capped at the tile
+// count and at the partials buffer.
+template <typename S, typename R, int RECON, int DAG, int X, int N, int BLOCK, int MINB>
+cudaError_t bt_go(const BtArgs &a, cudaStream_t s, unsigned *grid_out) {
+    const auto k = k_dslash_batch<S, R, RECON, DAG, X, N, BLOCK, MINB>;
+    static unsigned cap[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    unsigned res = (dev >= 0 && dev < 64) ? cap[dev] : 0u;
+    if (!res) {
+        res = bt_resident_grid(k, BLOCK);
+        if (dev >= 0 && dev < 64) cap[dev] = res;
+    }
+    long g = a.ntiles < (long)res ? a.ntiles : (long)res;
+    if (g > a.max_grid) g = a.max_grid;
+    const unsigned grid = (unsigned)(g < 1 ? 1 : g);
+    k<<<grid, BLOCK, 0, s>>>(a);
+    if (grid_out) *grid_out = grid;
+    return cudaGetLastError();
+}
+
+template <typename S, typename R, int RECON, int DAG, int X, int N>
+cudaError_t bt_go_cfg(int cfg, const BtArgs &a, cudaStream_t s, unsigned *g) {
+#define WD_BT_CFG(C) bt_go<S, R, RECON, DAG, X, N, BT_CFGS[C].block, BT_CFGS[C].minb>(a, s, g)
+    switch (cfg) {
+    case 1: return WD_BT_CFG(1);
+    case 2: return WD_BT_CFG(2);
+    case 3: return WD_BT_CFG(3);
+    case 4: return WD_BT_CFG(4);
+    default: return WD_BT_CFG(0);
+    }
+#undef WD_BT_CFG
+}
+
+// Storage-precision hops (FP32, FP16): the plain and the norm-fused xpay
+// variants in every configuration; xpay without a norm (not on the solver's
+// storage-precision path) in one.
+template <typename S, typename R, int RECON>
+cudaError_t bt_launch_lo(int dagger, int variant, int cfg, const BtArgs &a, cudaStream_t s,
+                         unsigned *g) {
+    if (variant == BTV_XPAY)
+        return dagger ? bt_go<S, R, RECON, 1, 1, 0, 128, 4>(a, s, g)
+                      : bt_go<S, R, RECON, 0, 1, 0, 128, 4>(a, s, g);
+    if (variant == BTV_XPAY_NORM)
+        return dagger ? bt_go_cfg<S, R, RECON, 1, 1, 1>(cfg, a, s, g)
+                      : bt_go_cfg<S, R, RECON, 0, 1, 1>(cfg, a, s, g);
+    return dagger ? bt_go_cfg<S, R, RECON, 1, 0, 0>(cfg, a, s, g)
+                  : bt_go_cfg<S, R, RECON, 0, 0, 0>(cfg, a, s, g);
+}
+
+// FP64 storage and double-float residual hops: one configuration each
+// (FP64-pipe bound, and the double-float hop's register appetite).
+template <typename S, typename R, int RECON, int MINB>
+cudaError_t bt_launch_fixed(int dagger, int variant, const BtArgs &a, cudaStream_t s,
+                            unsigned *g) {
+#define WD_BT_V(D, X, N) bt_go<S, R, RECON, D, X, N, 128, MINB>(a, s, g)
+    if (variant == BTV_XPAY) return dagger ? WD_BT_V(1, 1, 0) : WD_BT_V(0, 1, 0);
+    if (variant == BTV_XPAY_NORM) return dagger ? WD_BT_V(1, 1, 1) : WD_BT_V(0, 1, 1);
+    return dagger ? WD_BT_V(1, 0, 0) : WD_BT_V(0, 0, 0);
+#undef WD_BT_V
+}
+
+// Per-precision launchers, one translation unit each (batch_hop_*.cu).
+#define WD_BT_DECL(NAME)                                                                   \
+    cudaError_t NAME(int dagger, int variant, int cfg, const BtArgs &a, cudaStream_t s,      \
+                     unsigned *grid_out);
+WD_BT_DECL(bt_launch_hop_f32_r18)
+WD_BT_DECL(bt_launch_hop_f32_r12)
+WD_BT_DECL(bt_launch_hop_f16_r18)
+WD_BT_DECL(bt_launch_hop_f16_r12)
+WD_BT_DECL(bt_launch_hop_f64_r18)
+WD_BT_DECL(bt_launch_hop_f64_r12)
+WD_BT_DECL(bt_launch_hop_df64_r18)
+#undef WD_BT_DECL
+
+}  // namespace wd

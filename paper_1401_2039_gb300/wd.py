@@ -359,6 +359,16 @@ class WilsonBatch:
             raise WDError(rc, self.lib.wd_batch_last_error().decode())
         return outs
 
+    def tuning(self, norm: bool = False) -> dict:
+        """The autotuner's choice for the batched hop (norm=True: the xpay hop
+        with fused norms) and every candidate's microseconds per launch."""
+        us = (ctypes.c_double * 8)()
+        blk, mb, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        k = self.lib.wd_batch_tuning(self.handle, int(bool(norm)), us, 8, ctypes.byref(blk),
+                                     ctypes.byref(mb), ctypes.byref(gr))
+        return {"index": k, "block": blk.value, "min_blocks": mb.value, "grid": gr.value,
+                "us": [us[i] for i in range(5)]}
+
     def dslash_resident(self, out_parity: int, dagger: bool = False):
         rc = self.lib.wd_batch_dslash_resident(self.handle, int(out_parity), int(bool(dagger)))
         if rc != WD_OK:
@@ -393,6 +403,8 @@ def _setup_batch_signatures(lib):
         "wd_batch_destroy": (None, [vp]),
         "wd_batch_dslash": (i, [vp, pp, pp, i, i]),
         "wd_batch_dslash_resident": (i, [vp, i, i]),
+        "wd_batch_tuning": (i, [vp, i, ctypes.POINTER(d), i, ctypes.POINTER(i),
+                                ctypes.POINTER(i), ctypes.POINTER(i)]),
         "wd_batch_solve": (i, [vp, pp, pp, d, i, i, ctypes.POINTER(SolveInfo)]),
         "wd_batch_last_error": (ctypes.c_char_p, []),
         "wd_solve_cg_multi": (i, [pp, i, pp, pp, ctypes.POINTER(i), d, i, i,

@@ -128,3 +128,20 @@ def test_one_call_multi_solve_equals_the_batch_handle():
     ops[0].set_twisted_mass(0.1)   # batches have no twisted mass: an argument error
     with pytest.raises(WDError):
         solve_cg_multi(ops, [n for _, n, _ in PROBLEMS], bs, tol=1e-10)
+
+
+@pytest.mark.parametrize("prec,recon", [("f32", 18), ("f16", 12)])
+def test_batch_autotuner_keeps_the_fastest_configuration(prec, recon):
+    """The batched hop's launch configuration (block, register cap, grid) is
+    picked per batch by timing every candidate on its own lattices; the
+    choice is the fastest candidate and its grid is a resident-capacity grid
+    (a multiple of the SM count) no larger than needed."""
+    bt, ops, Us = make(prec, recon)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for norm in (False, True):
+        t = bt.tuning(norm=norm)
+        us = t["us"]
+        assert all(u > 0 for u in us), t
+        assert t["index"] == int(np.argmin(us)), t
+        assert t["block"] in (128, 256) and t["min_blocks"] >= 1, t
+        assert t["grid"] >= 1 and (t["grid"] % sms == 0 or t["grid"] < sms * t["min_blocks"]), t
