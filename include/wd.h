@@ -330,6 +330,14 @@ long wd_ptc_weight_count(const wd_ptc *net);              /* complex weights in 
 int wd_ptc_set_weights(wd_ptc *net, const double *W);
 int wd_ptc_get_weights(wd_ptc *net, double *W);
 int wd_ptc_apply(wd_ptc *net, double *y, const double *r);  /* y = N(r), synchronous */
+/* How wd_ptc_apply runs a layer with 16 input and 16 or 1 output channels:
+ * on = 1 (default) as one fused kernel that computes the transports straight
+ * into the tensor cores' shared-memory operand tiles (nothing of the
+ * gathered operand goes to HBM); on = 0 as a gather of the transported
+ * operand into device memory followed by the tensor-core GEMM (the form
+ * training always uses: its weight gradient needs that operand).  The two
+ * differ only in the order of the FP32 accumulation. */
+int wd_ptc_set_fused(wd_ptc *net, int on);
 /* Loss L = sum_i ||N(r_i) - e_i||^2 / ||e_i||^2 over nsamples fields r, e
  * ([nsamples][V][3][4]) and its gradient (grad: device, weight layout, or NULL). */
 int wd_ptc_loss_grad(wd_ptc *net, const double *r, const double *e, int nsamples,

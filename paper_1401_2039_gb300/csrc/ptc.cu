@@ -109,6 +109,12 @@ __device__ __forceinline__ void store_bf16x4(__nv_bfloat16 *p, float a, float b,
     *reinterpret_cast<uint2 *>(p) = w;
 }
 
+}  // namespace wd
+
+#include "ptc_fused.cuh"
+
+namespace wd {
+
 // Gather: one thread per (site x, input channel c).  F_in row stride ldf holds
 // [Re (c, s)][Im (c, s)] blocks of 4*C_in values; A row stride lda.
 __global__ void __launch_bounds__(PTC_BLOCK)
@@ -448,6 +454,10 @@ struct wd_ptc {
     // that makes the GEMMs issue no MMA (their waits then run out)
     unsigned spin_limit = TC_SPIN_LIMIT;
     int withhold = 0;
+    // layers with 16 input channels (16 or 1 output channels) of forward-only
+    // applications run as one fused transport + tensor-core kernel
+    // (wd_ptc_set_fused)
+    int fused = 1;
     std::vector<void *> allocs;
 };
 
@@ -592,14 +602,61 @@ static int ptc_check_err(wd_ptc *n) {
     return WD_OK;
 }
 
-// forward through every layer, activations left in F[0..nl]
-static int ptc_forward(wd_ptc *n, const double *r, double in_scale) {
+// One fused layer with 16 input channels (ptc_fused.cuh): F[l + 1] from
+// F[l], no gathered operand.
+template <int COUT>
+static int ptc_layer_fused_t(wd_ptc *n, int l) {
+    static bool attr_done[64] = {};
+    int dev = 0;
+    PTC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        PTC_CUDA(cudaFuncSetAttribute(k_ptc_layer_fused<COUT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      pf_smem_bytes<COUT>()));
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    if (n->Np[l] != pf_n<COUT>()) return ptc_fail(WD_ERR_ARG, "fused layer: output width");
+    int sms = 1;
+    PTC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PfArgs a;
+    a.g = n->g;
+    a.F = n->F[l];
+    a.ldf = n->ldF[l];
+    a.U = n->U;
+    a.B = n->B[l];
+    a.ldb = n->Kp[l];
+    a.out = n->F[l + 1];
+    a.ldo = n->ldF[l + 1];
+    a.ntiles = (n->g.V + PF_SITES - 1) / PF_SITES;
+    a.err = n->err;
+    a.spin_limit = n->spin_limit;
+    a.withhold = n->withhold;
+    const unsigned grid = (unsigned)std::min<long>(a.ntiles, sms);
+    k_ptc_layer_fused<COUT><<<grid, PF_ALL_THREADS, pf_smem_bytes<COUT>(), n->stream>>>(a);
+    PTC_CUDA(cudaGetLastError());
+    return WD_OK;
+}
+
+static int ptc_layer_fused(wd_ptc *n, int l) {
+    return n->ch[l + 1] == 1 ? ptc_layer_fused_t<1>(n, l) : ptc_layer_fused_t<16>(n, l);
+}
+
+// forward through every layer, activations left in F[0..nl]; with
+// keep_operands (training: the weight gradient needs them) every layer
+// gathers its operand into A[l], otherwise layers with 16 input channels
+// (and 16 or 1 output channels) run fused
+static int ptc_forward(wd_ptc *n, const double *r, double in_scale, bool keep_operands = false) {
     const long V = n->g.V;
     k_ptc_in<<<grid_for(3 * V), PTC_BLOCK, 0, n->stream>>>(V, (const double2 *)r, n->F[0],
                                                             n->ldF[0], (float)in_scale);
     PTC_CUDA(cudaGetLastError());
     for (int l = 0; l < n->nl; ++l) {
         const int cin = n->ch[l];
+        if (!keep_operands && n->fused && cin == PF_CIN &&
+            (n->ch[l + 1] == 16 || n->ch[l + 1] == 1)) {
+            PTC_TRY(ptc_layer_fused(n, l));
+            continue;
+        }
         k_ptc_gather<<<grid_for(V * cin), PTC_BLOCK, 0, n->stream>>>(n->g, cin, n->F[l], n->ldF[l],
                                                                       n->U, n->A[l], n->Kp[l]);
         PTC_CUDA(cudaGetLastError());
@@ -767,7 +824,7 @@ static int ptc_accumulate(wd_ptc *n, const double *r, const double *e, int ns, d
     PTC_TRY(ptc_inv_norms(n, e, ns));
     for (int i = 0; i < ns; ++i) {
         const double2 *ei = (const double2 *)e + i * fs;
-        PTC_TRY(ptc_forward(n, r + i * fs * 2, 1.0));
+        PTC_TRY(ptc_forward(n, r + i * fs * 2, 1.0, true));
         k_ptc_loss_grad<<<nbl, PTC_BLOCK, 0, n->stream>>>(V, n->F[L_], n->ldF[L_], ei, n->inv_ne + i,
                                                           n->dF[L_], n->dFb[L_], n->Rp[L_],
                                                           n->partials);
@@ -900,6 +957,12 @@ int wd_ptc_set_wait_limit(wd_ptc *n, unsigned polls, int withhold_mma) {
         return ptc_fail(WD_ERR_ARG, "bad argument");
     n->spin_limit = polls;
     n->withhold = withhold_mma;
+    return WD_OK;
+}
+
+int wd_ptc_set_fused(wd_ptc *n, int on) {
+    if (!n || (on != 0 && on != 1)) return ptc_fail(WD_ERR_ARG, "bad argument");
+    n->fused = on;
     return WD_OK;
 }
 

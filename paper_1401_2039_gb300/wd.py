@@ -517,6 +517,11 @@ class PtcNet:
                                               ctypes.c_void_p(D.data_ptr()), R, M, N))
         return D
 
+    def set_fused(self, on: bool = True):
+        """Layers of apply() with 16 input channels as one fused transport +
+        tensor-core kernel (default), or gathered operand + GEMM (on=False)."""
+        self._chk(self.lib.wd_ptc_set_fused(self.handle, int(bool(on))))
+
     def set_wait_limit(self, polls: int = 1 << 26, withhold_mma: bool = False):
         """Polls per bounded GEMM wait; withhold_mma (tests) makes the GEMMs issue no MMA."""
         self._chk(self.lib.wd_ptc_set_wait_limit(self.handle, int(polls), int(withhold_mma)))
@@ -553,6 +558,7 @@ def _setup_ptc_signatures(lib):
         "wd_tc_gemm_bf16": (i, [vp, vp, vp, vp, l, i, i]),
         "wd_tc_gemm_bf16_tn": (i, [vp, vp, vp, vp, l, i, i]),
         "wd_ptc_set_wait_limit": (i, [vp, ctypes.c_uint, i]),
+        "wd_ptc_set_fused": (i, [vp, i]),
         "wd_ptc_loss_grad": (i, [vp, vp, vp, i, ctypes.POINTER(d), vp]),
         "wd_ptc_train_step": (i, [vp, vp, vp, i, d, ctypes.POINTER(d)]),
         "wd_ptc_last_error": (ctypes.c_char_p, []),

@@ -74,6 +74,55 @@ def test_gemm_bounded_wait_runs_out_and_the_gpu_stays_usable():
     net.close()
 
 
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 6, 2, 4), (4, 4, 4, 4)])
+@pytest.mark.parametrize("channels,norm_tol,site_tol", [((1, 16, 16, 1), 1e-4, 5e-3),
+                                                        ((1, 16, 16, 16, 1), 1e-3, 1e-2)])
+def test_fused_layers_match_the_gathered_layers(dims, channels, norm_tol, site_tol):
+    """The fused 16 -> 16 layers (transports straight into the tensor cores'
+    shared-memory tiles, TMEM accumulators per colour) against the gathered
+    operand + GEMM form of the same network: the same BF16 products summed
+    in another FP32 order.  The order changes the FP32 output by ~1e-7; the
+    next layer rounds its operand to BF16 again, and a small fraction of
+    those roundings then lands one BF16 ulp (2^-8) apart, so the bound grows
+    with the layers that follow a fused one (one: 1e-4; two: 1e-3, measured
+    2e-4).  Shapes with a ragged last 128-site tile (V = 288) and a partial
+    one (4^4: V = 256 in two tiles)."""
+    from paper_1401_2039_gb300 import PtcNet
+    from parity import check
+    U = syn.su3_links(dims, eps=0.3, seed=9)
+    Ws = optc.identity_init(6, scale=0.5, layers=channels)
+    net = PtcNet(dims, APBC, channels)
+    net.set_gauge(torch.from_numpy(U).cuda())
+    net.set_weights(torch.from_numpy(_to_flat(Ws)).cuda())
+    r = torch.from_numpy(syn.gaussian_spinor(syn.volume(dims), 12)).cuda()
+    y_fused = net.apply(r).cpu().numpy()
+    net.set_fused(False)
+    y_gather = net.apply(r).cpu().numpy()
+    check(y_fused, y_gather, norm_tol=norm_tol, site_tol=site_tol)
+    net.set_fused(True)
+    assert np.array_equal(net.apply(r).cpu().numpy(), y_fused)   # deterministic
+    net.close()
+
+
+def test_fused_layer_bounded_wait_runs_out_and_the_gpu_stays_usable():
+    from paper_1401_2039_gb300 import PtcNet
+    from paper_1401_2039_gb300.wd import WD_ERR_TIMEOUT, WDError
+    dims = (8, 8, 8, 8)
+    U = syn.su3_links(dims, eps=0.3, seed=9)
+    net = PtcNet(dims, APBC, optc.LAYERS)
+    net.set_gauge(torch.from_numpy(U).cuda())
+    net.set_weights(torch.from_numpy(_to_flat(optc.identity_init(6, scale=0.5))).cuda())
+    r = torch.from_numpy(syn.gaussian_spinor(syn.volume(dims), 12)).cuda()
+    y = net.apply(r).cpu().numpy()
+    net.set_wait_limit(2000, withhold_mma=True)
+    with pytest.raises(WDError) as exc:
+        net.apply(r)
+    assert exc.value.status == WD_ERR_TIMEOUT
+    net.set_wait_limit()
+    assert np.array_equal(net.apply(r).cpu().numpy(), y)
+    net.close()
+
+
 def _to_flat(Ws):
     return np.concatenate([W.ravel() for W in Ws])
 
