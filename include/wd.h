@@ -183,6 +183,10 @@ double wd_op_twisted_mass(const wd_op *op);
  * host<->device copies go through buffers the handle owns. */
 int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
                      int maxiter, int parity, wd_solve_info *info);
+/* As wd_solve_cg_host from the initial guess x = 0: x_host is output only
+ * and is not read, so only b crosses to the device (and x back). */
+int wd_solve_cg_host_zero_guess(wd_op *op, double *x_host, const double *b_host, double tol,
+                                int maxiter, int parity, wd_solve_info *info);
 
 /* ---------------------------------------------------------------------------
  * Batches: several operators (lattices of any size, one storage precision

@@ -443,11 +443,81 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
     }
 }
 
-template <int RECON, int MU, int DAG>
-__device__ __forceinline__ void hop_pair_h2(const DslashArgs<float> &a, const int c[4], long h,
-                                            float *acc) {
-    hop_pair_h2<RECON, MU, DAG>(a.g, a.gauge_out, a.gauge_in, a.dir_bytes, a.ph, a.in, a.g.stride,
-                                1, 0, c, h, acc);
+// The single-system FP16 hop runs its eight hops software-pipelined: the
+// neighbour spinor and link words of hop i + 1 are loaded before the
+// arithmetic of hop i, so every hop's loads are in flight while the previous
+// hop computes (measured at 32^3 x 64: 70.3 against 73.5 us per launch, and
+// no spills at an 80-register cap, where the straight order spilled).
+struct HopH2 {
+    uint32_t p[12];
+    uint32_t U[9];
+    bool wrap;
+};
+
+template <int RECON, int MU, int DIR>
+__device__ __forceinline__ void load_hop_h2(const DslashArgs<float> &a, const int c[4], long h,
+                                            HopH2 &d) {
+    const long hn = neighbour<MU, DIR>(a.g, h, c, d.wrap);
+    Rec<__half, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, d.p);
+    if (DIR > 0)
+        Rec<__half, RECON>::template load_words<1>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, d.U);
+    else
+        Rec<__half, RECON>::template load_words<1>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, d.U);
+}
+
+template <int RECON, int MU, int DIR, int DAG>
+__device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, HopH2 &d, float *acc) {
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int S = DIR > 0 ? SF : -SF;
+    if (RECON == 12) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int k = (j + 1) % 3, l = (j + 2) % 3;
+            const uint32_t x = d.U[k], y = d.U[3 + l], z = d.U[l], w = d.U[3 + k];
+            const uint32_t yn = h2_neg(y), wn = h2_neg(w);
+            float re = mf_ll(x, y, 0.0f);
+            re = mf_hh(x, yn, re);
+            re = mf_ll(z, wn, re);
+            re = mf_hh(z, w, re);
+            float im = mf_lh(x, yn, 0.0f);
+            im = mf_hl(x, yn, im);
+            im = mf_lh(z, w, im);
+            im = mf_hl(z, w, im);
+            d.U[6 + j] = as_u32(__floats2half2_rn(re, im));
+        }
+    }
+    uint32_t hs[2][3];
+    project_h2<MU, S>(d.p, hs);
+    cx<float> u[2][3];
+    if (DIR > 0) su3_mul_h2(d.U, hs, u);
+    else su3_adj_mul_h2(d.U, hs, u);
+    if (d.wrap) {
+        const float pr = (float)a.ph[2 * MU], pi = (float)a.ph[2 * MU + 1];
+        phase_mul(u, pr, DIR > 0 ? pi : -pi);
+    }
+    accumulate<MU, S>(acc, u);
+}
+
+template <int RECON, int DAG>
+__device__ __forceinline__ void hops_h2_pipelined(const DslashArgs<float> &a, const int c[4], long h,
+                                                  float *acc) {
+    HopH2 d0, d1;
+    load_hop_h2<RECON, 0, +1>(a, c, h, d0);
+    load_hop_h2<RECON, 0, -1>(a, c, h, d1);
+    compute_hop_h2<RECON, 0, +1, DAG>(a, d0, acc);
+    load_hop_h2<RECON, 1, +1>(a, c, h, d0);
+    compute_hop_h2<RECON, 0, -1, DAG>(a, d1, acc);
+    load_hop_h2<RECON, 1, -1>(a, c, h, d1);
+    compute_hop_h2<RECON, 1, +1, DAG>(a, d0, acc);
+    load_hop_h2<RECON, 2, +1>(a, c, h, d0);
+    compute_hop_h2<RECON, 1, -1, DAG>(a, d1, acc);
+    load_hop_h2<RECON, 2, -1>(a, c, h, d1);
+    compute_hop_h2<RECON, 2, +1, DAG>(a, d0, acc);
+    load_hop_h2<RECON, 3, +1>(a, c, h, d0);
+    compute_hop_h2<RECON, 2, -1, DAG>(a, d1, acc);
+    load_hop_h2<RECON, 3, -1>(a, c, h, d1);
+    compute_hop_h2<RECON, 3, +1, DAG>(a, d0, acc);
+    compute_hop_h2<RECON, 3, -1, DAG>(a, d1, acc);
 }
 
 // One output site per (thread, i < SPT): site h = block base + i * BLOCK +
@@ -468,10 +538,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
             if constexpr (std::is_same<S, __half>::value) {
-                hop_pair_h2<RECON, 0, DAG>(a, c, h, acc);
-                hop_pair_h2<RECON, 1, DAG>(a, c, h, acc);
-                hop_pair_h2<RECON, 2, DAG>(a, c, h, acc);
-                hop_pair_h2<RECON, 3, DAG>(a, c, h, acc);
+                hops_h2_pipelined<RECON, DAG>(a, c, h, acc);
             } else {
                 hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
                 hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);

@@ -837,8 +837,9 @@ extern "C" int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, in
     return rc != WD_OK ? rc : rj;
 }
 
-extern "C" int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
-                                int maxiter, int parity, wd_solve_info *info) {
+// Host-memory solve; with_guess = 0 starts from x = 0 without reading x_host.
+static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, double tol,
+                           int maxiter, int parity, int with_guess, wd_solve_info *info) {
     auto t0 = std::chrono::steady_clock::now();
     WD_TRY(check_op(op));
     if (!x_host || !b_host) return fail(WD_ERR_ARG, "null spinor");
@@ -848,7 +849,10 @@ extern "C" int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host,
     const size_t bytes = (size_t)2 * op->g.vh * 24 * sizeof(double);
     WD_TRY(fork(op));
     WD_CUDA(cudaMemcpyAsync(op->stage_b, b_host, bytes, cudaMemcpyHostToDevice, op->stream));
-    WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
+    if (with_guess)
+        WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
+    else
+        WD_CUDA(cudaMemsetAsync(op->stage_x, 0, bytes, op->stream));
     int rc = solve_impl(op, op->stage_x, op->stage_b, tol, maxiter, parity, info);
     if (rc == WD_OK || rc == WD_ERR_NOT_CONVERGED) {
         WD_CUDA(cudaMemcpyAsync(x_host, op->stage_x, bytes, cudaMemcpyDeviceToHost, op->stream));
@@ -859,4 +863,15 @@ extern "C" int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host,
         info->seconds =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return rc != WD_OK ? rc : rj;
+}
+
+extern "C" int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
+                                int maxiter, int parity, wd_solve_info *info) {
+    return solve_host_impl(op, x_host, b_host, tol, maxiter, parity, 1, info);
+}
+
+extern "C" int wd_solve_cg_host_zero_guess(wd_op *op, double *x_host, const double *b_host,
+                                           double tol, int maxiter, int parity,
+                                           wd_solve_info *info) {
+    return solve_host_impl(op, x_host, b_host, tol, maxiter, parity, 0, info);
 }

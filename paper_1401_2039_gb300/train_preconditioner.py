@@ -205,6 +205,7 @@ def main():
     summary["kept"] = "initial" if best_dirs == validation[0] and validation.index(best_dirs) == 0 \
         else f"epoch {validation.index(best_dirs) - 1}"
     W = best_w
+    summary["W0"] = W0
     v_solver.close()
     v_net.close()
     v_lo.close()
@@ -234,6 +235,7 @@ def evaluate(args, summary, channels, ph, W):
     evals = []
     cases = [((16, 16, 16, 32), 11)] + ([((32, 32, 32, 64), 12)] if args.eval_large else [])
     W_start = torch.from_numpy(neumann_weights(channels, args.kappa, 7, scale=0.0)).cuda()
+    W0 = summary.pop("W0", None)     # the training run's own starting weights
     for edims, seed in cases:
         Ue = torch.from_numpy(syn.su3_links(edims, eps=0.3, seed=seed)).cuda()
         lo = WilsonDirac(edims, args.kappa, ph, prec="f32")
@@ -257,8 +259,14 @@ def evaluate(args, summary, channels, ph, W):
             torch.cuda.synchronize()
             return out, (time.perf_counter() - t) * 1e3
 
-        for name, pre in (("fgcr_learned", enet), ("fgcr_neumann4_untrained", nnet),
-                          ("gcr_plain", None)):
+        cases_pre = [("fgcr_learned", enet), ("fgcr_neumann4_untrained", nnet), ("gcr_plain", None)]
+        snet = None
+        if W0 is not None and args.init != "neumann":   # the untrained start of this run
+            snet = PtcNet(edims, ph, channels)
+            snet.set_gauge(Ue)
+            snet.set_weights(W0)
+            cases_pre.insert(1, (f"fgcr_{args.init}_untrained", snet))
+        for name, pre in cases_pre:
             fg = Fgcr(lo, hi, pre, nkrylov=16)
             res, ms = timed(lambda: fg.solve(b, tol=1e-10, maxiter=args.max_directions,
                                              check=False))
@@ -276,6 +284,8 @@ def evaluate(args, summary, channels, ph, W):
         print(json.dumps(row), flush=True)
         enet.close()
         nnet.close()
+        if snet is not None:
+            snet.close()
         lo.close()
         hi.close()
         torch.cuda.empty_cache()

@@ -63,6 +63,7 @@ def load_library() -> ctypes.CDLL:
             "wd_dslash_eo": (i, [vp, vp, vp, i, i]),
             "wd_solve_cg": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
             "wd_solve_cg_host": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
+            "wd_solve_cg_host_zero_guess": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
             "wd_field_load": (i, [vp, i, vp]),
             "wd_field_store": (i, [vp, i, vp]),
             "wd_dslash_resident": (i, [vp, i, i, i]),
@@ -208,16 +209,17 @@ class WilsonDirac:
         return SolveResult(x, rc, info.as_dict())
 
     def solve_host(self, x_host: torch.Tensor, b_host: torch.Tensor, tol: float = 1e-10,
-                   maxiter: int = 20000, parity: int = 1) -> SolveResult:
-        """Solve with x and b in host memory (pinned for asynchronous copies)."""
+                   maxiter: int = 20000, parity: int = 1, guess: bool = True) -> SolveResult:
+        """Solve with x and b in host memory (pinned for asynchronous copies).
+        guess=False starts from x = 0 and never reads x_host (output only)."""
         for t, n in ((x_host, "x"), (b_host, "b")):
             if t.is_cuda or t.dtype != torch.complex128 or tuple(t.shape) != (self.V, 3, 4) \
                     or not t.is_contiguous():
                 raise ValueError(f"{n} must be a contiguous complex128 host tensor [V, 3, 4]")
         info = SolveInfo()
-        rc = self.lib.wd_solve_cg_host(self.handle, ctypes.c_void_p(x_host.data_ptr()),
-                                       ctypes.c_void_p(b_host.data_ptr()), float(tol),
-                                       int(maxiter), int(parity), ctypes.byref(info))
+        fn = self.lib.wd_solve_cg_host if guess else self.lib.wd_solve_cg_host_zero_guess
+        rc = fn(self.handle, ctypes.c_void_p(x_host.data_ptr()), ctypes.c_void_p(b_host.data_ptr()),
+                float(tol), int(maxiter), int(parity), ctypes.byref(info))
         _check(rc)
         return SolveResult(x_host, rc, info.as_dict())
 

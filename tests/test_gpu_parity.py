@@ -242,6 +242,10 @@ def test_host_memory_solve_matches_device_solve():
     res = op.solve_host(xh, bh, tol=1e-10)
     assert np.array_equal(res.x.numpy(), host(dev.x))   # same kernels, same order: bitwise
     assert res.info["iters"] == dev.info["iters"]
+    # no initial guess: x_host is not read (garbage in it changes nothing)
+    xg = torch.full_like(bh, complex(float("nan"), 1.0)).pin_memory()
+    res0 = op.solve_host(xg, bh, tol=1e-10, guess=False)
+    assert np.array_equal(res0.x.numpy(), host(dev.x))
 
 
 def test_resident_dslash_matches_canonical():
