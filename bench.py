@@ -386,15 +386,16 @@ def small_config_comparison():
     return row
 
 
-def batch_measurement(prec: str, recon: int):
+def batch_measurement(prec: str, recon: int, recovery=("reliable", 0.1)):
     """Batched solves against the same systems solved one at a time:
     12 point sources (every spin and colour) on 24^3 x 48, and 4 Gaussian
     sources on each of 8^4, 12^3 x 24, 16^3 x 32 in one persistent batch
-    (storage precision prec, recon-real links)."""
+    (storage precision prec, recon-real links; recovery = (mode, inner
+    tolerance) for both forms)."""
     import torch
     from paper_1401_2039_gb300 import WilsonBatch, WilsonDirac
     ph = syn.workloads.APBC_T
-    out = {"storage": prec, "link_reals": recon}
+    out = {"storage": prec, "link_reals": recon, "recovery": list(recovery)}
 
     def timed(fn, reps=2):
         fn()
@@ -408,6 +409,7 @@ def batch_measurement(prec: str, recon: int):
     dims = (24, 24, 24, 48)
     op = WilsonDirac(dims, 0.12, ph, prec=prec, recon=recon)
     op.set_gauge(torch.from_numpy(syn.su3_links(dims)).cuda())
+    op.set_recovery(*recovery)
     B = torch.from_numpy(np.stack([syn.point_source(dims, 0, c, s)
                                    for c in range(3) for s in range(4)])).cuda()
     bt = WilsonBatch([op], [12])
@@ -415,13 +417,16 @@ def batch_measurement(prec: str, recon: int):
     ts, _ = timed(lambda: [op.solve(B[k].contiguous(), tol=1e-10) for k in range(12)], reps=1)
     out["point_sources_24x24x24x48"] = {
         "systems": 12, "batched_ms": tb, "sequential_ms": ts, "speedup": ts / tb,
-        "max_true_rel_resid": max(i["true_rel_resid"] for i in infos)}
+        "iters": max(i["iters"] for i in infos), "refreshes": infos[0]["reliable_updates"],
+        "max_true_rel_resid": max(i["true_rel_resid"] for i in infos),
+        "hop_tuning": {"plain": bt.tuning(), "xpay_norm": bt.tuning(norm=True)}}
     bt.close()
     op.close()
     ops, Bs = [], []
     for k, d in enumerate([(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32)]):
         o = WilsonDirac(d, 0.12, ph, prec=prec, recon=recon)
         o.set_gauge(torch.from_numpy(syn.su3_links(d, seed=1 + k)).cuda())
+        o.set_recovery(*recovery)
         ops.append(o)
         Bs.append(torch.from_numpy(np.stack([syn.gaussian_spinor(syn.volume(d), 2 + 10 * k + r)
                                              for r in range(4)])).cuda())
@@ -630,8 +635,10 @@ def main():
     # ---- batched solves (the multi-source and uneven-lattice workloads)
     batch = None
     if rank == 0 and not args.no_batch:
-        # the batched configuration: FP32 inner iterations, FP64-class residuals
-        batch = batch_measurement("f32", 18)
+        # the batched configuration: FP32 inner iterations, FP64-class residuals,
+        # with reliable updates and with defect correction (inner tol 1e-5)
+        batch = {"reliable_updates": batch_measurement("f32", 18, ("reliable", 0.1)),
+                 "defect_correction": batch_measurement("f32", 18, ("defect", 1e-5))}
 
     # ---- hopping-term sweep over storage precisions, and the small configuration
     sweep = small = None

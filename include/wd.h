@@ -195,7 +195,9 @@ int wd_solve_cg_host_zero_guess(wd_op *op, double *x_host, const double *b_host,
  * systems (right-hand-side index innermost, so the links of a site are read
  * once for all of its right-hand sides) and advances every system in
  * lockstep with persistent kernels that walk a table of tiles over all
- * lattices; each system keeps its own CGNR scalars, reliable updates are
+ * lattices; each system keeps its own CGNR scalars, residual refreshes
+ * (reliable updates, or the outer steps of defect correction: the recovery
+ * mode and tolerances of the first operator apply to every system) are
  * taken together, and converged systems are frozen.  The operators must
  * outlive the batch.  Not in the paper: it batches the paper's solve (goal
  * with templates "CGNR schur") over many right-hand sides and lattices. */

@@ -633,7 +633,12 @@ int bt_solve_impl(wd_batch *bt, double *const *x, const double *const *b, double
     }
     int iters = 0, ru = 0, status = WD_OK;
     bool th_valid = any_guess;
-    double delta = bt->ops[0]->ru_delta;
+    // accuracy recovery of the first operator for every system: reliable
+    // updates (refresh after a residual drop of ru_delta, Krylov directions
+    // kept) or defect correction (after a drop of the inner tolerance, and
+    // every system restarts its inner CGNR on the new residual)
+    const bool defect = mixed && bt->ops[0]->recovery == WD_RECOVER_DEFECT;
+    const double delta = defect ? bt->ops[0]->dc_delta : bt->ops[0]->ru_delta;
     int batch = 8;
     while (n_active > 0) {
         const int n = std::min(batch, maxiter - iters);
@@ -685,11 +690,21 @@ int bt_solve_impl(wd_batch *bt, double *const *x, const double *const *b, double
             if (status != WD_OK) break;
             if (n_active == 0) break;
             if (iters >= maxiter) { status = WD_ERR_NOT_CONVERGED; break; }
+            if (defect)   // restart: p = 0 and nz = +inf make the next direction z itself
+                for (int s = 0; s < S; ++s)
+                    if (active[s]) bt->sc_host[s].nz = INFINITY;
             BT_TRY(bt_write(bt));
             BT_TRY(bt_conv(bt, false, F_RL, F_RH));
-            BT_TRY(bt_vec<BT_RESCALE>(bt, false, FIN_NONE, {F_PL}));
-            k_bt_rescale_nz<<<1, BT_MAX_SLOTS, 0, st>>>(bt->sc, bt->consts, S);
-            BT_CUDA(cudaGetLastError());
+            if (defect) {
+                for (int p = 0; p < bt->nprob; ++p)
+                    BT_CUDA(cudaMemsetAsync(bt->fl[p].f[F_PL], 0,
+                                            field_bytes(bt->prec, bt->ops[p]->g.stride, 24) *
+                                                bt->nrhs[p], st));
+            } else {
+                BT_TRY(bt_vec<BT_RESCALE>(bt, false, FIN_NONE, {F_PL}));
+                k_bt_rescale_nz<<<1, BT_MAX_SLOTS, 0, st>>>(bt->sc, bt->consts, S);
+                BT_CUDA(cudaGetLastError());
+            }
             batch = 4;
             continue;
         }

@@ -145,3 +145,24 @@ def test_batch_autotuner_keeps_the_fastest_configuration(prec, recon):
         assert t["index"] == int(np.argmin(us)), t
         assert t["block"] in (128, 256) and t["min_blocks"] >= 1, t
         assert t["grid"] >= 1 and (t["grid"] % sms == 0 or t["grid"] < sms * t["min_blocks"]), t
+
+
+@pytest.mark.parametrize("prec,recon", [("f32", 18), ("f16", 12)])
+def test_batch_solve_with_defect_correction(prec, recon):
+    """Batched systems with defect correction (every refresh restarts all
+    inner CGNRs): each system meets the oracle's FP64 true residual and lies
+    within 1e-8 of the oracle's solution."""
+    bt, ops, Us = make(prec, recon)
+    ops[0].set_recovery("defect", 1e-3)
+    bs = []
+    for k, (dims, n, _) in enumerate(PROBLEMS):
+        bs.append(np.stack([syn.gaussian_spinor(syn.volume(dims), 300 + 5 * k + r) for r in range(n)]))
+    xs, status, infos = bt.solve([torch.from_numpy(b).cuda() for b in bs], tol=1e-10)
+    assert status == 0
+    for k, (dims, n, kappa) in enumerate(PROBLEMS):
+        x = xs[k].cpu().numpy()
+        for r in range(n):
+            res = np.linalg.norm(bs[k][r] - oracle.apply(x[r], Us[k], dims, kappa, APBC))
+            assert res <= 1.05e-10 * np.linalg.norm(bs[k][r]), (k, r, res)
+            x_ref, _, ok = oracle.solve(bs[k][r], Us[k], dims, kappa, APBC, parity=1, tol=1e-13)
+            assert ok and rel(x[r], x_ref) < 1e-8
