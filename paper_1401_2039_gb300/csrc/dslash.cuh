@@ -206,6 +206,20 @@ __device__ __forceinline__ void twist_site(R *v, R t) {
         }
 }
 
+// The same factor on K consecutive reals of a site record starting at real
+// index base (base even): the pair at index k is spin (k % 8) / 2.
+template <int K, typename R>
+__device__ __forceinline__ void twist_reals(R *v, int base, R t) {
+#pragma unroll
+    for (int m = 0; m < K / 2; ++m) {
+        const int s = ((base + 2 * m) & 7) >> 1;
+        const R ts = s < 2 ? t : -t;
+        const R re = v[2 * m], im = v[2 * m + 1];
+        v[2 * m] = re - ts * im;
+        v[2 * m + 1] = im + ts * re;
+    }
+}
+
 // Half-lattice index of the neighbour x +- mu of site h (coordinates c),
 // from offsets: h = ((t*Lz + z)*Ly + y)*(Lx/2) + x/2.
 template <int MU, int DIR>
@@ -545,25 +559,37 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
                 hop_pair<S, R, RECON, 2, DAG>(a, c, h, acc);
                 hop_pair<S, R, RECON, 3, DAG>(a, c, h, acc);
             }
-            R o[24];
-            if (EPI == EPI_XPAY) {
-                R xv[24];
-                Rec<S, 24>::template load<R, 0>(a.x, a.g.stride, h, xv);
-                if (a.twist_on) twist_site(xv, a.twist);
+            // epilogue one 16-byte plane (K reals) of the output record at a
+            // time: only one plane's inputs and outputs are live, which keeps
+            // the xpay and norm variants within the register cap
+            constexpr int K = 16 / (int)sizeof(S);
+            R sq = 0;
 #pragma unroll
-                for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + a.scale * acc[k]);
-            } else {
+            for (int j = 0; j < 24 / K; ++j) {
+                R ov[K];
+                if (EPI == EPI_XPAY) {
+                    R xv[K];
+                    const uint4 w = ld_nc_v4((const char *)a.x + ((long)j * a.g.stride + h) * 16);
+                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+                    Words<S, R>::unpack(ww, xv, K);
+                    if (a.twist_on) twist_reals<K>(xv, j * K, a.twist);
 #pragma unroll
-                for (int k = 0; k < 24; ++k) o[k] = settle(a.scale * acc[k]);
-                if (a.twist_on) twist_site(o, -a.twist);
+                    for (int t = 0; t < K; ++t) ov[t] = settle(xv[t] + a.scale * acc[j * K + t]);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < K; ++t) ov[t] = settle(a.scale * acc[j * K + t]);
+                    if (a.twist_on) twist_reals<K>(ov, j * K, -a.twist);
+                }
+                uint32_t ow[4];
+                Words<S, R>::pack(ov, ow, K);
+                st_v4((char *)a.out + ((long)j * a.g.stride + h) * 16,
+                      make_uint4(ow[0], ow[1], ow[2], ow[3]));
+                if (NORM) {
+#pragma unroll
+                    for (int t = 0; t < K; ++t) sq += ov[t] * ov[t];
+                }
             }
-            Rec<S, 24>::store(a.out, a.g.stride, h, o);
-            if (NORM) {
-                R sq = 0;
-#pragma unroll
-                for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-                nrm[i] = to_df(sq);
-            }
+            if (NORM) nrm[i] = to_df(sq);
         }
     }
     if (NORM) warp_partials<BLOCK, SPT>(nrm, a.g.vh, a.red.partials);
