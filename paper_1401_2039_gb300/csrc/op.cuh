@@ -28,6 +28,9 @@ struct wd_op {
     cudaStream_t user = nullptr;   // caller's stream (nullptr = legacy)
     cudaStream_t stream = nullptr; // work stream owned by the handle
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // host-memory solves: the solution's download overlaps the final residual
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_x = nullptr;
     bool gauge_loaded = false;
 
     GaugeSet gauge_lo;             // storage precision, recon

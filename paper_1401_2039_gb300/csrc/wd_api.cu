@@ -291,6 +291,11 @@ void wd_op_destroy(wd_op *op) {
     if (op->ev_t1) cudaEventDestroy(op->ev_t1);
     if (op->ev_fork) cudaEventDestroy(op->ev_fork);
     if (op->ev_join) cudaEventDestroy(op->ev_join);
+    if (op->ev_x) cudaEventDestroy(op->ev_x);
+    if (op->copy_stream) {
+        cudaStreamSynchronize(op->copy_stream);
+        cudaStreamDestroy(op->copy_stream);
+    }
     if (op->stream) cudaStreamDestroy(op->stream);
     delete op;
 }
@@ -301,6 +306,8 @@ static int create_impl(wd_op *op) {
     WD_CUDA(cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming));
     WD_CUDA(cudaEventCreate(&op->ev_t0));
     WD_CUDA(cudaEventCreate(&op->ev_t1));
+    WD_CUDA(cudaStreamCreateWithFlags(&op->copy_stream, cudaStreamNonBlocking));
+    WD_CUDA(cudaEventCreateWithFlags(&op->ev_x, cudaEventDisableTiming));
 
     const Geom &g = op->g;
     // gauge fields
@@ -576,9 +583,11 @@ int set_consts(wd_op *op, double scale, double inv_scale, double ratio) {
 }
 
 // x_in: the initial guess (read once, at the start); x_out: the solution
-// (written once, at the end); they may be the same array.
+// (written once, at the end); they may be the same array.  x_host (optional):
+// host memory the solution is also copied to, on the handle's copy stream as
+// soon as it is complete, so that the copy overlaps the final true residual.
 int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, double tol,
-               int maxiter, int parity, wd_solve_info *info) {
+               int maxiter, int parity, wd_solve_info *info, double *x_host = nullptr) {
     SolveState st{};
     st.p = parity;
     st.q = 1 - parity;
@@ -776,6 +785,18 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
             st.bytes += 2 * field_b(op, WD_F64);
         }
     }
+    // x is complete: unpack it now (the residual below reads but never
+    // writes xh and xq) and start its download if the caller wants it
+    {
+        double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
+        WD_CUDA(launch_unpack_full(op->hi_prec, g, x_out, xe, xo, op->stream));
+    }
+    if (x_host) {
+        WD_CUDA(cudaEventRecord(op->ev_x, op->stream));
+        WD_CUDA(cudaStreamWaitEvent(op->copy_stream, op->ev_x, 0));
+        WD_CUDA(cudaMemcpyAsync(x_host, x_out, (size_t)2 * g.vh * 24 * sizeof(double),
+                                cudaMemcpyDeviceToHost, op->copy_stream));
+    }
     WD_TRY(dslash(op, true, st.p, 0, op->axh, op->xq, op->xh, -op->kappa, nullptr, tw));
     WD_CUDA(launch_xmy_norm(op->hi_prec, g, op->rh, op->hb[st.p], op->axh, r0, op->stream));
     if (reuse) {
@@ -792,10 +813,6 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
         st.bytes += dslash_b(op, true, true);
     }
     WD_CUDA(launch_xmy_norm(op->hi_prec, g, op->th, op->hb[st.q], op->axh, r1, op->stream));
-    {
-        double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
-        WD_CUDA(launch_unpack_full(op->hi_prec, g, x_out, xe, xo, op->stream));
-    }
     WD_TRY(read_scalars(op));
     st.dslash_hi += 1;
     st.launches += 6;
@@ -841,9 +858,10 @@ extern "C" int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, in
 
 // Host-memory solve; with_guess = 0 starts from x = 0 without reading x_host.
 // The copies go through the handle's staging buffers with cudaMemcpyAsync
-// (DMA, 200 GB/s each way on GB300); reading b and writing x from the layout
-// kernels through the mapping of pinned host memory was measured slower
-// (55.2 against 49.8 ms per solve at 32^3 x 64).
+// (DMA, 200 GB/s each way on GB300); the solution's copy runs on a second
+// stream while the final true residual is computed.  Reading b and writing x
+// from the layout kernels through the mapping of pinned host memory was
+// measured slower (55.2 against 49.8 ms per solve at 32^3 x 64).
 static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, double tol,
                            int maxiter, int parity, int with_guess, wd_solve_info *info) {
     auto t0 = std::chrono::steady_clock::now();
@@ -859,11 +877,10 @@ static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, doub
         WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
     else
         WD_CUDA(cudaMemsetAsync(op->stage_x, 0, bytes, op->stream));
-    int rc = solve_impl(op, op->stage_x, op->stage_x, op->stage_b, tol, maxiter, parity, info);
-    if (rc == WD_OK || rc == WD_ERR_NOT_CONVERGED) {
-        WD_CUDA(cudaMemcpyAsync(x_host, op->stage_x, bytes, cudaMemcpyDeviceToHost, op->stream));
-        WD_CUDA(cudaStreamSynchronize(op->stream));
-    }
+    // the solution's download starts inside the solve, once x is complete
+    int rc = solve_impl(op, op->stage_x, op->stage_x, op->stage_b, tol, maxiter, parity, info,
+                        x_host);
+    WD_CUDA(cudaStreamSynchronize(op->copy_stream));
     int rj = join(op);
     if (info)
         info->seconds =
