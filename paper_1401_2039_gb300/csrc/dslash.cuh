@@ -273,27 +273,37 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
     }
 }
 
-// ---------------------------------------------------------------- FP16 storage
-// With FP16 storage the generic hop spends about a sixth of its instructions
-// converting halves to FP32 (one conversion per stored element).  This
-// variant keeps spinors and links in their packed half2 words (one complex
-// number each, real part in the low half): the spin projection adds half2
-// words in FP16 arithmetic, and every product of the SU(3) multiply is a
-// mixed-precision FMA, f16 x f16 -> f32 (PTX fma.rn.f32.f16), accumulating in
-// FP32.  The product of two halves is exact in FP32, so the one new rounding
-// is the FP16 projection sum (relative 2^-11, the size of the storage
-// rounding).  The twelve-real links rebuild row 2 = conj(row0 x row1) with the
-// same mixed FMAs and round it to FP16, as an 18-real FP16 link would store it.
+// ------------------------------------------------------ FP16 and BF16 storage
+// With 16-bit storage the generic hop spends about a sixth of its
+// instructions converting elements to FP32 (one conversion per stored
+// element).  This variant keeps spinors and links in their packed 32-bit
+// words (one complex number each, real part in the low half): the spin
+// projection adds packed words in 16-bit arithmetic, and every product of the
+// SU(3) multiply is a mixed-precision FMA, 16-bit x 16-bit -> f32 (PTX
+// fma.rn.f32.f16 or fma.rn.f32.bf16), accumulating in FP32.  The product of
+// two FP16 (or two BF16) numbers is exact in FP32, so the one new rounding is
+// the projection sum (relative 2^-11 for FP16, 2^-8 for BF16: the size of the
+// storage rounding).  The twelve-real links rebuild row 2 = conj(row0 x row1)
+// with the same mixed FMAs and round it to the storage type, as an 18-real
+// link would store it.
 #define WD_MIXED_FMA(NAME, SA, SB)                                                           \
+    template <typename HT>                                                                   \
     __device__ __forceinline__ float NAME(uint32_t a, uint32_t b, float c) {                 \
         float d;                                                                             \
-        asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"                                             \
-            "mov.b32 {a0, a1}, %1;\n\tmov.b32 {b0, b1}, %2;\n\t"                             \
-            "fma.rn.f32.f16 %0, " SA ", " SB ", %3;\n\t}"                                    \
-            : "=f"(d) : "r"(a), "r"(b), "f"(c));                                             \
+        if constexpr (std::is_same<HT, __half>::value)                                       \
+            asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"                                         \
+                "mov.b32 {a0, a1}, %1;\n\tmov.b32 {b0, b1}, %2;\n\t"                         \
+                "fma.rn.f32.f16 %0, " SA ", " SB ", %3;\n\t}"                                \
+                : "=f"(d) : "r"(a), "r"(b), "f"(c));                                         \
+        else                                                                                 \
+            asm("{\n\t.reg .b16 a0, a1, b0, b1;\n\t"                                         \
+                "mov.b32 {a0, a1}, %1;\n\tmov.b32 {b0, b1}, %2;\n\t"                         \
+                "fma.rn.f32.bf16 %0, " SA ", " SB ", %3;\n\t}"                               \
+                : "=f"(d) : "r"(a), "r"(b), "f"(c));                                         \
         return d;                                                                            \
     }
-// mf_XY(a, b, c) = a.X * b.Y + c with X, Y in {l = real, h = imaginary}
+// mf_XY<HT>(a, b, c) = a.X * b.Y + c with X, Y in {l = real, h = imaginary}, for
+// packed words of HT = __half (fma.rn.f32.f16) or __nv_bfloat16 (fma.rn.f32.bf16)
 WD_MIXED_FMA(mf_ll, "a0", "b0")
 WD_MIXED_FMA(mf_lh, "a0", "b1")
 WD_MIXED_FMA(mf_hl, "a1", "b0")
@@ -301,22 +311,38 @@ WD_MIXED_FMA(mf_hh, "a1", "b1")
 #undef WD_MIXED_FMA
 
 __device__ __forceinline__ uint32_t h2_neg(uint32_t a) { return a ^ 0x80008000u; }
-__device__ __forceinline__ __half2 as_h2(uint32_t a) { return *reinterpret_cast<__half2 *>(&a); }
-__device__ __forceinline__ uint32_t as_u32(__half2 a) { return *reinterpret_cast<uint32_t *>(&a); }
 
-// p + F q on half2 complex words, F = +1, -1, +i, -i (codes 0..3)
-template <int F>
+// the packed two-element type of HT, and its words
+template <typename HT> struct Pair2;
+template <> struct Pair2<__half> {
+    using T = __half2;
+    __device__ static T of(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <> struct Pair2<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    __device__ static T of(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <typename HT>
+__device__ __forceinline__ typename Pair2<HT>::T as_p2(uint32_t a) {
+    return *reinterpret_cast<typename Pair2<HT>::T *>(&a);
+}
+template <typename P2> __device__ __forceinline__ uint32_t as_u32(P2 a) {
+    return *reinterpret_cast<uint32_t *>(&a);
+}
+
+// p + F q on packed complex words (HT pairs), F = +1, -1, +i, -i (codes 0..3)
+template <typename HT, int F>
 __device__ __forceinline__ uint32_t h2_comb(uint32_t p, uint32_t q) {
-    if (F == 0) return as_u32(__hadd2(as_h2(p), as_h2(q)));
-    if (F == 1) return as_u32(__hsub2(as_h2(p), as_h2(q)));
+    if (F == 0) return as_u32(__hadd2(as_p2<HT>(p), as_p2<HT>(q)));
+    if (F == 1) return as_u32(__hsub2(as_p2<HT>(p), as_p2<HT>(q)));
     // i q = (-q.im, q.re), -i q = (q.im, -q.re): swap the halves, then one FMA
-    const __half2 sq = __lowhigh2highlow(as_h2(q));
-    const __half2 sg = F == 2 ? __floats2half2_rn(-1.0f, 1.0f) : __floats2half2_rn(1.0f, -1.0f);
-    return as_u32(__hfma2(sq, sg, as_h2(p)));
+    const auto sq = __lowhigh2highlow(as_p2<HT>(q));
+    const auto sg = F == 2 ? Pair2<HT>::of(-1.0f, 1.0f) : Pair2<HT>::of(1.0f, -1.0f);
+    return as_u32(__hfma2(sq, sg, as_p2<HT>(p)));
 }
 
 // half spinor h[k][colour] (half2 words) of the site's 12 words (word 4 c + s)
-template <int MU, int SGN>
+template <typename HT, int MU, int SGN>
 __device__ __forceinline__ void project_h2(const uint32_t *p, uint32_t h[2][3]) {
     constexpr int PI = SGN > 0 ? 2 : 3, MI = SGN > 0 ? 3 : 2;   // SGN i, -SGN i
     constexpr int P1 = SGN > 0 ? 0 : 1, M1 = SGN > 0 ? 1 : 0;   // SGN, -SGN
@@ -324,26 +350,26 @@ __device__ __forceinline__ void project_h2(const uint32_t *p, uint32_t h[2][3]) 
     for (int c = 0; c < 3; ++c) {
         const uint32_t p0 = p[4 * c], p1 = p[4 * c + 1], p2 = p[4 * c + 2], p3 = p[4 * c + 3];
         if (MU == 0) {
-            h[0][c] = h2_comb<PI>(p0, p3);
-            h[1][c] = h2_comb<PI>(p1, p2);
+            h[0][c] = h2_comb<HT, PI>(p0, p3);
+            h[1][c] = h2_comb<HT, PI>(p1, p2);
         } else if (MU == 1) {
-            h[0][c] = h2_comb<M1>(p0, p3);
-            h[1][c] = h2_comb<P1>(p1, p2);
+            h[0][c] = h2_comb<HT, M1>(p0, p3);
+            h[1][c] = h2_comb<HT, P1>(p1, p2);
         } else if (MU == 2) {
-            h[0][c] = h2_comb<PI>(p0, p2);
-            h[1][c] = h2_comb<MI>(p1, p3);
+            h[0][c] = h2_comb<HT, PI>(p0, p2);
+            h[1][c] = h2_comb<HT, MI>(p1, p3);
         } else {
-            h[0][c] = h2_comb<P1>(p0, p2);
-            h[1][c] = h2_comb<P1>(p1, p3);
+            h[0][c] = h2_comb<HT, P1>(p0, p2);
+            h[1][c] = h2_comb<HT, P1>(p1, p3);
         }
     }
 }
 
 // link as 9 half2 words (row-major); 12-real records rebuild row 2
-template <int RECON>
+template <typename HT, int RECON>
 __device__ __forceinline__ void load_link_h2(const char *base, long stride, long site,
                                              uint32_t U[9]) {
-    Rec<__half, RECON>::template load_words<1>(base, stride, site, U);
+    Rec<HT, RECON>::template load_words<1>(base, stride, site, U);
     if (RECON == 12) {
         // row2_j = conj(row0_k row1_l - row0_l row1_k), (j, k, l) cyclic
 #pragma unroll
@@ -351,20 +377,21 @@ __device__ __forceinline__ void load_link_h2(const char *base, long stride, long
             const int k = (j + 1) % 3, l = (j + 2) % 3;
             const uint32_t x = U[k], y = U[3 + l], z = U[l], w = U[3 + k];
             const uint32_t yn = h2_neg(y), wn = h2_neg(w);
-            float re = mf_ll(x, y, 0.0f);
-            re = mf_hh(x, yn, re);
-            re = mf_ll(z, wn, re);
-            re = mf_hh(z, w, re);
-            float im = mf_lh(x, yn, 0.0f);
-            im = mf_hl(x, yn, im);
-            im = mf_lh(z, w, im);
-            im = mf_hl(z, w, im);
-            U[6 + j] = as_u32(__floats2half2_rn(re, im));
+            float re = mf_ll<HT>(x, y, 0.0f);
+            re = mf_hh<HT>(x, yn, re);
+            re = mf_ll<HT>(z, wn, re);
+            re = mf_hh<HT>(z, w, re);
+            float im = mf_lh<HT>(x, yn, 0.0f);
+            im = mf_hl<HT>(x, yn, im);
+            im = mf_lh<HT>(z, w, im);
+            im = mf_hl<HT>(z, w, im);
+            U[6 + j] = as_u32(Pair2<HT>::of(re, im));
         }
     }
 }
 
 // u[k][a] = sum_b U[a][b] h[k][b]
+template <typename HT>
 __device__ __forceinline__ void su3_mul_h2(const uint32_t U[9], const uint32_t h[2][3],
                                            cx<float> u[2][3]) {
 #pragma unroll
@@ -374,16 +401,16 @@ __device__ __forceinline__ void su3_mul_h2(const uint32_t U[9], const uint32_t h
         for (int b = 0; b < 3; ++b) hn[b] = h2_neg(h[k][b]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float re = mf_ll(U[3 * a], h[k][0], 0.0f);
-            float im = mf_lh(U[3 * a], h[k][0], 0.0f);
-            re = mf_hh(U[3 * a], hn[0], re);
-            im = mf_hl(U[3 * a], h[k][0], im);
+            float re = mf_ll<HT>(U[3 * a], h[k][0], 0.0f);
+            float im = mf_lh<HT>(U[3 * a], h[k][0], 0.0f);
+            re = mf_hh<HT>(U[3 * a], hn[0], re);
+            im = mf_hl<HT>(U[3 * a], h[k][0], im);
 #pragma unroll
             for (int b = 1; b < 3; ++b) {
-                re = mf_ll(U[3 * a + b], h[k][b], re);
-                re = mf_hh(U[3 * a + b], hn[b], re);
-                im = mf_lh(U[3 * a + b], h[k][b], im);
-                im = mf_hl(U[3 * a + b], h[k][b], im);
+                re = mf_ll<HT>(U[3 * a + b], h[k][b], re);
+                re = mf_hh<HT>(U[3 * a + b], hn[b], re);
+                im = mf_lh<HT>(U[3 * a + b], h[k][b], im);
+                im = mf_hl<HT>(U[3 * a + b], h[k][b], im);
             }
             u[k][a] = {re, im};
         }
@@ -391,6 +418,7 @@ __device__ __forceinline__ void su3_mul_h2(const uint32_t U[9], const uint32_t h
 }
 
 // u[k][a] = sum_b conj(U[b][a]) h[k][b]
+template <typename HT>
 __device__ __forceinline__ void su3_adj_mul_h2(const uint32_t U[9], const uint32_t h[2][3],
                                                cx<float> u[2][3]) {
 #pragma unroll
@@ -400,16 +428,16 @@ __device__ __forceinline__ void su3_adj_mul_h2(const uint32_t U[9], const uint32
         for (int b = 0; b < 3; ++b) hn[b] = h2_neg(h[k][b]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float re = mf_ll(U[a], h[k][0], 0.0f);
-            float im = mf_lh(U[a], h[k][0], 0.0f);
-            re = mf_hh(U[a], h[k][0], re);
-            im = mf_hl(U[a], hn[0], im);
+            float re = mf_ll<HT>(U[a], h[k][0], 0.0f);
+            float im = mf_lh<HT>(U[a], h[k][0], 0.0f);
+            re = mf_hh<HT>(U[a], h[k][0], re);
+            im = mf_hl<HT>(U[a], hn[0], im);
 #pragma unroll
             for (int b = 1; b < 3; ++b) {
-                re = mf_ll(U[3 * b + a], h[k][b], re);
-                re = mf_hh(U[3 * b + a], h[k][b], re);
-                im = mf_lh(U[3 * b + a], h[k][b], im);
-                im = mf_hl(U[3 * b + a], hn[b], im);
+                re = mf_ll<HT>(U[3 * b + a], h[k][b], re);
+                re = mf_hh<HT>(U[3 * b + a], h[k][b], re);
+                im = mf_lh<HT>(U[3 * b + a], h[k][b], im);
+                im = mf_hl<HT>(U[3 * b + a], hn[b], im);
             }
             u[k][a] = {re, im};
         }
@@ -433,11 +461,11 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
         uint32_t p[12];
         Rec<__half, 24>::template load_words<0>((const char *)in, in_stride, hn * nrhs + r, p);
         uint32_t hs[2][3];
-        project_h2<MU, SF>(p, hs);
+        project_h2<__half, MU, SF>(p, hs);
         uint32_t U[9];
-        load_link_h2<RECON>(gauge_out + MU * dir_bytes, g.stride, h, U);
+        load_link_h2<__half, RECON>(gauge_out + MU * dir_bytes, g.stride, h, U);
         cx<float> u[2][3];
-        su3_mul_h2(U, hs, u);
+        su3_mul_h2<__half>(U, hs, u);
         if (wrap) phase_mul(u, pr, pi);
         accumulate<MU, SF>(acc, u);
     }
@@ -447,17 +475,17 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
         uint32_t p[12];
         Rec<__half, 24>::template load_words<0>((const char *)in, in_stride, hn * nrhs + r, p);
         uint32_t hs[2][3];
-        project_h2<MU, SB>(p, hs);
+        project_h2<__half, MU, SB>(p, hs);
         uint32_t U[9];
-        load_link_h2<RECON>(gauge_in + MU * dir_bytes, g.stride, hn, U);
+        load_link_h2<__half, RECON>(gauge_in + MU * dir_bytes, g.stride, hn, U);
         cx<float> u[2][3];
-        su3_adj_mul_h2(U, hs, u);
+        su3_adj_mul_h2<__half>(U, hs, u);
         if (wrap) phase_mul(u, pr, -pi);
         accumulate<MU, SB>(acc, u);
     }
 }
 
-// The single-system FP16 hop runs its eight hops software-pipelined: the
+// The single-system FP16/BF16 hop runs its eight hops software-pipelined: the
 // neighbour spinor and link words of hop i + 1 are loaded before the
 // arithmetic of hop i, so every hop's loads are in flight while the previous
 // hop computes (measured at 32^3 x 64: 70.3 against 73.5 us per launch, and
@@ -468,18 +496,18 @@ struct HopH2 {
     bool wrap;
 };
 
-template <int RECON, int MU, int DIR>
+template <typename HT, int RECON, int MU, int DIR>
 __device__ __forceinline__ void load_hop_h2(const DslashArgs<float> &a, const int c[4], long h,
                                             HopH2 &d) {
     const long hn = neighbour<MU, DIR>(a.g, h, c, d.wrap);
-    Rec<__half, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, d.p);
+    Rec<HT, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, d.p);
     if (DIR > 0)
-        Rec<__half, RECON>::template load_words<1>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, d.U);
+        Rec<HT, RECON>::template load_words<1>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, d.U);
     else
-        Rec<__half, RECON>::template load_words<1>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, d.U);
+        Rec<HT, RECON>::template load_words<1>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, d.U);
 }
 
-template <int RECON, int MU, int DIR, int DAG>
+template <typename HT, int RECON, int MU, int DIR, int DAG>
 __device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, HopH2 &d, float *acc) {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int S = DIR > 0 ? SF : -SF;
@@ -489,22 +517,22 @@ __device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, HopH2
             const int k = (j + 1) % 3, l = (j + 2) % 3;
             const uint32_t x = d.U[k], y = d.U[3 + l], z = d.U[l], w = d.U[3 + k];
             const uint32_t yn = h2_neg(y), wn = h2_neg(w);
-            float re = mf_ll(x, y, 0.0f);
-            re = mf_hh(x, yn, re);
-            re = mf_ll(z, wn, re);
-            re = mf_hh(z, w, re);
-            float im = mf_lh(x, yn, 0.0f);
-            im = mf_hl(x, yn, im);
-            im = mf_lh(z, w, im);
-            im = mf_hl(z, w, im);
-            d.U[6 + j] = as_u32(__floats2half2_rn(re, im));
+            float re = mf_ll<HT>(x, y, 0.0f);
+            re = mf_hh<HT>(x, yn, re);
+            re = mf_ll<HT>(z, wn, re);
+            re = mf_hh<HT>(z, w, re);
+            float im = mf_lh<HT>(x, yn, 0.0f);
+            im = mf_hl<HT>(x, yn, im);
+            im = mf_lh<HT>(z, w, im);
+            im = mf_hl<HT>(z, w, im);
+            d.U[6 + j] = as_u32(Pair2<HT>::of(re, im));
         }
     }
     uint32_t hs[2][3];
-    project_h2<MU, S>(d.p, hs);
+    project_h2<HT, MU, S>(d.p, hs);
     cx<float> u[2][3];
-    if (DIR > 0) su3_mul_h2(d.U, hs, u);
-    else su3_adj_mul_h2(d.U, hs, u);
+    if (DIR > 0) su3_mul_h2<HT>(d.U, hs, u);
+    else su3_adj_mul_h2<HT>(d.U, hs, u);
     if (d.wrap) {
         const float pr = (float)a.ph[2 * MU], pi = (float)a.ph[2 * MU + 1];
         phase_mul(u, pr, DIR > 0 ? pi : -pi);
@@ -512,26 +540,26 @@ __device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, HopH2
     accumulate<MU, S>(acc, u);
 }
 
-template <int RECON, int DAG>
+template <typename HT, int RECON, int DAG>
 __device__ __forceinline__ void hops_h2_pipelined(const DslashArgs<float> &a, const int c[4], long h,
                                                   float *acc) {
     HopH2 d0, d1;
-    load_hop_h2<RECON, 0, +1>(a, c, h, d0);
-    load_hop_h2<RECON, 0, -1>(a, c, h, d1);
-    compute_hop_h2<RECON, 0, +1, DAG>(a, d0, acc);
-    load_hop_h2<RECON, 1, +1>(a, c, h, d0);
-    compute_hop_h2<RECON, 0, -1, DAG>(a, d1, acc);
-    load_hop_h2<RECON, 1, -1>(a, c, h, d1);
-    compute_hop_h2<RECON, 1, +1, DAG>(a, d0, acc);
-    load_hop_h2<RECON, 2, +1>(a, c, h, d0);
-    compute_hop_h2<RECON, 1, -1, DAG>(a, d1, acc);
-    load_hop_h2<RECON, 2, -1>(a, c, h, d1);
-    compute_hop_h2<RECON, 2, +1, DAG>(a, d0, acc);
-    load_hop_h2<RECON, 3, +1>(a, c, h, d0);
-    compute_hop_h2<RECON, 2, -1, DAG>(a, d1, acc);
-    load_hop_h2<RECON, 3, -1>(a, c, h, d1);
-    compute_hop_h2<RECON, 3, +1, DAG>(a, d0, acc);
-    compute_hop_h2<RECON, 3, -1, DAG>(a, d1, acc);
+    load_hop_h2<HT, RECON, 0, +1>(a, c, h, d0);
+    load_hop_h2<HT, RECON, 0, -1>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 0, +1, DAG>(a, d0, acc);
+    load_hop_h2<HT, RECON, 1, +1>(a, c, h, d0);
+    compute_hop_h2<HT, RECON, 0, -1, DAG>(a, d1, acc);
+    load_hop_h2<HT, RECON, 1, -1>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 1, +1, DAG>(a, d0, acc);
+    load_hop_h2<HT, RECON, 2, +1>(a, c, h, d0);
+    compute_hop_h2<HT, RECON, 1, -1, DAG>(a, d1, acc);
+    load_hop_h2<HT, RECON, 2, -1>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 2, +1, DAG>(a, d0, acc);
+    load_hop_h2<HT, RECON, 3, +1>(a, c, h, d0);
+    compute_hop_h2<HT, RECON, 2, -1, DAG>(a, d1, acc);
+    load_hop_h2<HT, RECON, 3, -1>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 3, +1, DAG>(a, d0, acc);
+    compute_hop_h2<HT, RECON, 3, -1, DAG>(a, d1, acc);
 }
 
 // One output site per (thread, i < SPT): site h = block base + i * BLOCK +
@@ -551,8 +579,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
             Acc<R> acc[24];
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
-            if constexpr (std::is_same<S, __half>::value) {
-                hops_h2_pipelined<RECON, DAG>(a, c, h, acc);
+            if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
+                hops_h2_pipelined<S, RECON, DAG>(a, c, h, acc);
             } else {
                 hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
                 hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
