@@ -73,6 +73,7 @@ def main():
     us = e0.elapsed_time(e1) * 1e3 / max(1, args.launches)
     print(f"{w.name} prec={prec} recon={recon}: {args.launches} launches, {us:.1f} us each, "
           f"{op.dslash_bytes / (us * 1e-6) / 1e9:.0f} GB/s algorithmic")
+    print("launch configuration:", op.dslash_tuning())
     op.close()
 
 
