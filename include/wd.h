@@ -252,12 +252,15 @@ int wd_dslash_resident(wd_op *op, int in_slot, int out_parity, int dagger);
  * hi = 2: the storage-precision kernel with the xpay epilogue and fused norm
  * that ends each Schur operator of the CGNR iteration (tuned on its own: its
  * register demand differs).  us (optional, n entries) receives the
- * measured microseconds per launch of every candidate; block, min_blocks and
- * sites_per_thread (optional) describe the chosen one.  Returns its index,
- * or -1 for a null handle.  Setting WD_DSLASH_CFG=k in the environment
- * forces candidate k, WD_TUNE=0 keeps candidate 0. */
+ * measured microseconds per launch of every candidate (0 for a candidate
+ * that was not timed: link staging applies to FP16/BF16 storage only, and
+ * entries past the candidate count); block, min_blocks, sites_per_thread and
+ * staged (optional; staged = 1: the link records of the eight hops are copied
+ * into shared memory at kernel start) describe the chosen one.  Returns its
+ * index, or -1 for a null handle.  Setting WD_DSLASH_CFG=k in the
+ * environment forces candidate k, WD_TUNE=0 keeps candidate 0. */
 int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,
-                     int *sites_per_thread);
+                     int *sites_per_thread, int *staged);
 
 /* Stream the handle queues its work on (a cudaStream_t). */
 void *wd_op_stream(wd_op *op);

@@ -230,12 +230,10 @@ __device__ __forceinline__ long neighbour(const Geom &g, long h, const int c[4],
         if (wrap) xn = DIR > 0 ? 0 : g.L[0] - 1;
         return h + ((xn >> 1) - (c[0] >> 1));
     }
-    long step = g.hx;
-    if (MU >= 2) step *= g.L[1];
-    if (MU >= 3) step *= g.L[2];
+    const long step = g.step[MU], back = g.back[MU];
     wrap = DIR > 0 ? (c[MU] == g.L[MU] - 1) : (c[MU] == 0);
-    if (DIR > 0) return wrap ? h - (long)(g.L[MU] - 1) * step : h + step;
-    return wrap ? h + (long)(g.L[MU] - 1) * step : h - step;
+    if (DIR > 0) return wrap ? h - back : h + step;
+    return wrap ? h + back : h - step;
 }
 
 template <typename S, typename R, int RECON, int MU, int DAG>
@@ -485,37 +483,96 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
     }
 }
 
-// The single-system FP16/BF16 hop runs its eight hops software-pipelined: the
-// neighbour spinor and link words of hop i + 1 are loaded before the
-// arithmetic of hop i, so every hop's loads are in flight while the previous
-// hop computes (measured at 32^3 x 64: 70.3 against 73.5 us per launch, and
-// no spills at an 80-register cap, where the straight order spilled).
-struct HopH2 {
+// The single-system FP16/BF16 hop computes in 32-bit site indices and byte
+// offsets from precomputed hop steps (Geom::step, Geom::back), and runs its
+// eight hops in one of two ways, both measured and offered to the autotuner:
+//  * pipelined: the neighbour spinor and link words of hop i + 1 are loaded
+//    into registers before the arithmetic of hop i, so every hop's loads are
+//    in flight while the previous hop computes;
+//  * staged: at kernel start every thread copies the link records of all
+//    eight hops into shared memory with cp.async (global -> shared, no
+//    registers held), one commit group per hop, so the block's link bytes
+//    are all requested at once and each hop waits for its own group only;
+//    the neighbour spinors (read by eight sites, mostly from L1/L2) still go
+//    through registers one hop ahead.
+// Measured at 32^3 x 64: the plain hop is fastest pipelined (64 against
+// 67 us), the xpay hop with fused norm staged (82 against 88 us).
+template <int MU, int DIR>
+__device__ __forceinline__ unsigned neighbour32(const Geom &g, unsigned h, const int c[4],
+                                                bool &wrap) {
+    if (MU == 0) {
+        int xn = c[0] + DIR;
+        wrap = DIR > 0 ? (xn == g.L[0]) : (xn < 0);
+        if (wrap) xn = DIR > 0 ? 0 : g.L[0] - 1;
+        return h + (unsigned)((xn >> 1) - (c[0] >> 1));
+    }
+    const unsigned step = g.step[MU], back = g.back[MU];
+    wrap = DIR > 0 ? (c[MU] == g.L[MU] - 1) : (c[MU] == 0);
+    if (DIR > 0) return wrap ? h - back : h + step;
+    return wrap ? h + back : h - step;
+}
+
+// 16-bit link records: NF 16-byte planes and a TAIL-byte plane
+template <int RECON> struct LinkPlanes {
+    static constexpr int NF = RECON == 12 ? 1 : 2;
+    static constexpr int TAIL = RECON == 12 ? 8 : 4;
+};
+
+struct SpinorH2 {
     uint32_t p[12];
-    uint32_t U[9];
     bool wrap;
 };
 
-template <typename HT, int RECON, int MU, int DIR>
-__device__ __forceinline__ void load_hop_h2(const DslashArgs<float> &a, const int c[4], long h,
-                                            HopH2 &d) {
-    const long hn = neighbour<MU, DIR>(a.g, h, c, d.wrap);
-    Rec<HT, 24>::template load_words<0>((const char *)a.in, a.g.stride, hn, d.p);
-    if (DIR > 0)
-        Rec<HT, RECON>::template load_words<1>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, d.U);
-    else
-        Rec<HT, RECON>::template load_words<1>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, d.U);
+template <int MU, int DIR>
+__device__ __forceinline__ void load_spinor_h2(const DslashArgs<float> &a, const int c[4],
+                                               unsigned h, SpinorH2 &d) {
+    const unsigned hn = neighbour32<MU, DIR>(a.g, h, c, d.wrap);
+    const size_t plane = (size_t)a.g.stride * 16;
+    const char *p0 = (const char *)a.in + (size_t)hn * 16;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const uint4 v = ld_nc_v4(p0 + j * plane);
+        d.p[4 * j] = v.x; d.p[4 * j + 1] = v.y; d.p[4 * j + 2] = v.z; d.p[4 * j + 3] = v.w;
+    }
 }
 
+// the link record of hop (MU, DIR): U_mu(x) forward, U_mu(x - mu) backward
+template <int MU, int DIR>
+__device__ __forceinline__ const char *link_base(const DslashArgs<float> &a) {
+    return (DIR > 0 ? a.gauge_out : a.gauge_in) + MU * a.dir_bytes;
+}
+
+template <int RECON, int MU, int DIR>
+__device__ __forceinline__ void load_link_words(const DslashArgs<float> &a, unsigned site,
+                                                uint32_t U[9]) {
+    constexpr int NF = LinkPlanes<RECON>::NF;
+    const char *base = link_base<MU, DIR>(a);
+    const size_t plane = (size_t)a.g.stride * 16;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        const uint4 v = ld_stream_v4(base + (size_t)site * 16 + j * plane);
+        U[4 * j] = v.x; U[4 * j + 1] = v.y; U[4 * j + 2] = v.z; U[4 * j + 3] = v.w;
+    }
+    if (RECON == 12) {
+        const uint2 v = ld_stream_v2(base + NF * plane + (size_t)site * 8);
+        U[4] = v.x; U[5] = v.y;
+    } else {
+        U[8] = ld_stream_u32(base + NF * plane + (size_t)site * 4);
+    }
+}
+
+// acc += hop (MU, DIR) of the neighbour words p with the link words U
+// (12-real records: words 0..5, row 2 rebuilt here)
 template <typename HT, int RECON, int MU, int DIR, int DAG>
-__device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, HopH2 &d, float *acc) {
+__device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, const uint32_t p[12],
+                                               bool wrap, uint32_t U[9], float *acc) {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int S = DIR > 0 ? SF : -SF;
     if (RECON == 12) {
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int k = (j + 1) % 3, l = (j + 2) % 3;
-            const uint32_t x = d.U[k], y = d.U[3 + l], z = d.U[l], w = d.U[3 + k];
+            const uint32_t x = U[k], y = U[3 + l], z = U[l], w = U[3 + k];
             const uint32_t yn = h2_neg(y), wn = h2_neg(w);
             float re = mf_ll<HT>(x, y, 0.0f);
             re = mf_hh<HT>(x, yn, re);
@@ -525,48 +582,155 @@ __device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, HopH2
             im = mf_hl<HT>(x, yn, im);
             im = mf_lh<HT>(z, w, im);
             im = mf_hl<HT>(z, w, im);
-            d.U[6 + j] = as_u32(Pair2<HT>::of(re, im));
+            U[6 + j] = as_u32(Pair2<HT>::of(re, im));
         }
     }
     uint32_t hs[2][3];
-    project_h2<HT, MU, S>(d.p, hs);
+    project_h2<HT, MU, S>(p, hs);
     cx<float> u[2][3];
-    if (DIR > 0) su3_mul_h2<HT>(d.U, hs, u);
-    else su3_adj_mul_h2<HT>(d.U, hs, u);
-    if (d.wrap) {
+    if (DIR > 0) su3_mul_h2<HT>(U, hs, u);
+    else su3_adj_mul_h2<HT>(U, hs, u);
+    if (wrap) {
         const float pr = (float)a.ph[2 * MU], pi = (float)a.ph[2 * MU + 1];
         phase_mul(u, pr, DIR > 0 ? pi : -pi);
     }
     accumulate<MU, S>(acc, u);
 }
 
+// ---- pipelined: spinor and link words of the next hop in registers
+struct HopH2 {
+    SpinorH2 s;
+    uint32_t U[9];
+};
+
+template <int RECON, int I>
+__device__ __forceinline__ void load_hop_h2(const DslashArgs<float> &a, const int c[4], unsigned h,
+                                            HopH2 &d) {
+    constexpr int MU = I / 2, DIR = (I & 1) ? -1 : +1;
+    load_spinor_h2<MU, DIR>(a, c, h, d.s);
+    bool wrap;
+    const unsigned site = DIR > 0 ? h : neighbour32<MU, DIR>(a.g, h, c, wrap);
+    load_link_words<RECON, MU, DIR>(a, site, d.U);
+}
+
 template <typename HT, int RECON, int DAG>
-__device__ __forceinline__ void hops_h2_pipelined(const DslashArgs<float> &a, const int c[4], long h,
-                                                  float *acc) {
+__device__ __forceinline__ void hops_h2_pipelined(const DslashArgs<float> &a, const int c[4],
+                                                  unsigned h, float *acc) {
     HopH2 d0, d1;
-    load_hop_h2<HT, RECON, 0, +1>(a, c, h, d0);
-    load_hop_h2<HT, RECON, 0, -1>(a, c, h, d1);
-    compute_hop_h2<HT, RECON, 0, +1, DAG>(a, d0, acc);
-    load_hop_h2<HT, RECON, 1, +1>(a, c, h, d0);
-    compute_hop_h2<HT, RECON, 0, -1, DAG>(a, d1, acc);
-    load_hop_h2<HT, RECON, 1, -1>(a, c, h, d1);
-    compute_hop_h2<HT, RECON, 1, +1, DAG>(a, d0, acc);
-    load_hop_h2<HT, RECON, 2, +1>(a, c, h, d0);
-    compute_hop_h2<HT, RECON, 1, -1, DAG>(a, d1, acc);
-    load_hop_h2<HT, RECON, 2, -1>(a, c, h, d1);
-    compute_hop_h2<HT, RECON, 2, +1, DAG>(a, d0, acc);
-    load_hop_h2<HT, RECON, 3, +1>(a, c, h, d0);
-    compute_hop_h2<HT, RECON, 2, -1, DAG>(a, d1, acc);
-    load_hop_h2<HT, RECON, 3, -1>(a, c, h, d1);
-    compute_hop_h2<HT, RECON, 3, +1, DAG>(a, d0, acc);
-    compute_hop_h2<HT, RECON, 3, -1, DAG>(a, d1, acc);
+    load_hop_h2<RECON, 0>(a, c, h, d0);
+    load_hop_h2<RECON, 1>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 0, +1, DAG>(a, d0.s.p, d0.s.wrap, d0.U, acc);
+    load_hop_h2<RECON, 2>(a, c, h, d0);
+    compute_hop_h2<HT, RECON, 0, -1, DAG>(a, d1.s.p, d1.s.wrap, d1.U, acc);
+    load_hop_h2<RECON, 3>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 1, +1, DAG>(a, d0.s.p, d0.s.wrap, d0.U, acc);
+    load_hop_h2<RECON, 4>(a, c, h, d0);
+    compute_hop_h2<HT, RECON, 1, -1, DAG>(a, d1.s.p, d1.s.wrap, d1.U, acc);
+    load_hop_h2<RECON, 5>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 2, +1, DAG>(a, d0.s.p, d0.s.wrap, d0.U, acc);
+    load_hop_h2<RECON, 6>(a, c, h, d0);
+    compute_hop_h2<HT, RECON, 2, -1, DAG>(a, d1.s.p, d1.s.wrap, d1.U, acc);
+    load_hop_h2<RECON, 7>(a, c, h, d1);
+    compute_hop_h2<HT, RECON, 3, +1, DAG>(a, d0.s.p, d0.s.wrap, d0.U, acc);
+    compute_hop_h2<HT, RECON, 3, -1, DAG>(a, d1.s.p, d1.s.wrap, d1.U, acc);
+}
+
+// ---- staged: the eight link records in shared memory, [hop][plane][thread]
+template <int RECON, int BLOCK> struct LinkStage {
+    uint4 w[8][LinkPlanes<RECON>::NF][BLOCK];
+    typename std::conditional<RECON == 12, uint2, uint32_t>::type tail[8][BLOCK];
+};
+
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+
+// copy the link record of hop I into the stage as commit group I
+template <int RECON, int I, int BLOCK>
+__device__ __forceinline__ void stage_link_h2(const DslashArgs<float> &a, const int c[4],
+                                              unsigned h, LinkStage<RECON, BLOCK> &st) {
+    constexpr int MU = I / 2, DIR = (I & 1) ? -1 : +1;
+    constexpr int NF = LinkPlanes<RECON>::NF, TAIL = LinkPlanes<RECON>::TAIL;
+    bool wrap;
+    const unsigned site = DIR > 0 ? h : neighbour32<MU, DIR>(a.g, h, c, wrap);
+    const char *base = link_base<MU, DIR>(a);
+    const size_t plane = (size_t)a.g.stride * 16;
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+        cp_async_16(&st.w[I][j][threadIdx.x], base + (size_t)site * 16 + j * plane);
+    cp_async_small<TAIL>(&st.tail[I][threadIdx.x], base + NF * plane + (size_t)site * TAIL);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// wait for group I (groups I + 1 .. 7 may still be in flight), then compute
+template <typename HT, int RECON, int I, int DAG, int BLOCK>
+__device__ __forceinline__ void compute_staged_h2(const DslashArgs<float> &a, const SpinorH2 &d,
+                                                  const LinkStage<RECON, BLOCK> &st, float *acc) {
+    asm volatile("cp.async.wait_group %0;" :: "n"(7 - I) : "memory");
+    uint32_t U[9];
+#pragma unroll
+    for (int j = 0; j < LinkPlanes<RECON>::NF; ++j) {
+        const uint4 v = st.w[I][j][threadIdx.x];
+        U[4 * j] = v.x; U[4 * j + 1] = v.y; U[4 * j + 2] = v.z; U[4 * j + 3] = v.w;
+    }
+    if constexpr (RECON == 12) {
+        const uint2 t = st.tail[I][threadIdx.x];
+        U[4] = t.x; U[5] = t.y;
+    } else {
+        U[8] = st.tail[I][threadIdx.x];
+    }
+    compute_hop_h2<HT, RECON, I / 2, (I & 1) ? -1 : +1, DAG>(a, d.p, d.wrap, U, acc);
+}
+
+template <typename HT, int RECON, int DAG, int BLOCK>
+__device__ __forceinline__ void hops_h2_staged(const DslashArgs<float> &a, const int c[4],
+                                               unsigned h, LinkStage<RECON, BLOCK> &st,
+                                               float *acc) {
+    stage_link_h2<RECON, 0>(a, c, h, st);
+    stage_link_h2<RECON, 1>(a, c, h, st);
+    stage_link_h2<RECON, 2>(a, c, h, st);
+    stage_link_h2<RECON, 3>(a, c, h, st);
+    stage_link_h2<RECON, 4>(a, c, h, st);
+    stage_link_h2<RECON, 5>(a, c, h, st);
+    stage_link_h2<RECON, 6>(a, c, h, st);
+    stage_link_h2<RECON, 7>(a, c, h, st);
+    SpinorH2 d0, d1;
+    load_spinor_h2<0, +1>(a, c, h, d0);
+    load_spinor_h2<0, -1>(a, c, h, d1);
+    compute_staged_h2<HT, RECON, 0, DAG>(a, d0, st, acc);
+    load_spinor_h2<1, +1>(a, c, h, d0);
+    compute_staged_h2<HT, RECON, 1, DAG>(a, d1, st, acc);
+    load_spinor_h2<1, -1>(a, c, h, d1);
+    compute_staged_h2<HT, RECON, 2, DAG>(a, d0, st, acc);
+    load_spinor_h2<2, +1>(a, c, h, d0);
+    compute_staged_h2<HT, RECON, 3, DAG>(a, d1, st, acc);
+    load_spinor_h2<2, -1>(a, c, h, d1);
+    compute_staged_h2<HT, RECON, 4, DAG>(a, d0, st, acc);
+    load_spinor_h2<3, +1>(a, c, h, d0);
+    compute_staged_h2<HT, RECON, 5, DAG>(a, d1, st, acc);
+    load_spinor_h2<3, -1>(a, c, h, d1);
+    compute_staged_h2<HT, RECON, 6, DAG>(a, d0, st, acc);
+    compute_staged_h2<HT, RECON, 7, DAG>(a, d1, st, acc);
+}
+
+template <typename S> constexpr bool packed16() {
+    return std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
 }
 
 // One output site per (thread, i < SPT): site h = block base + i * BLOCK +
-// thread, so each of a warp's loads stays one contiguous request.
+// thread, so each of a warp's loads stays one contiguous request.  STAGE
+// (16-bit storage, one site per thread): links staged in shared memory.
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK, int MINB,
-          int SPT>
+          int SPT, int STAGE>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
+    static_assert(!STAGE || (packed16<S>() && SPT == 1), "staging: 16-bit storage, one site");
     df64 nrm[SPT];
 #pragma unroll
     for (int i = 0; i < SPT; ++i) nrm[i] = df64(0.0f, 0.0f);
@@ -579,8 +743,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
             Acc<R> acc[24];
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
-            if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
-                hops_h2_pipelined<S, RECON, DAG>(a, c, h, acc);
+            if constexpr (STAGE) {
+                __shared__ LinkStage<RECON, BLOCK> stage;
+                hops_h2_staged<S, RECON, DAG>(a, c, (unsigned)h, stage, acc);
+            } else if constexpr (packed16<S>()) {
+                hops_h2_pipelined<S, RECON, DAG>(a, c, (unsigned)h, acc);
             } else {
                 hop_pair<S, R, RECON, 0, DAG>(a, c, h, acc);
                 hop_pair<S, R, RECON, 1, DAG>(a, c, h, acc);
@@ -624,25 +791,34 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
 }
 
 // Launch configurations the tuner chooses from: threads per block, the
-// minimum resident blocks per SM handed to the register allocator, and
-// output sites per thread.  A fused norm adds in the same order under every
-// configuration (warp_partials), so every variant can take its own tuned one.
-struct DslashCfg { int block, minb, spt; };
-constexpr int N_DSLASH_CFG = 5;
+// minimum resident blocks per SM handed to the register allocator, output
+// sites per thread, and (16-bit storage only) links staged in shared memory.
+// A fused norm adds in the same order under every configuration
+// (warp_partials), so every variant can take its own tuned one.
+struct DslashCfg { int block, minb, spt, stage; };
+constexpr int N_DSLASH_CFG = 8;
 constexpr DslashCfg DSLASH_CFGS[N_DSLASH_CFG] = {
-    {128, 1, 1}, {128, 8, 1}, {128, 6, 1}, {256, 4, 1}, {128, 1, 2}};
+    {128, 1, 1, 0}, {128, 8, 1, 0}, {128, 6, 1, 0}, {256, 4, 1, 0},
+    {128, 1, 2, 0}, {128, 8, 1, 1}, {128, 6, 1, 1}, {256, 4, 1, 1}};
+// whether candidate k is distinct for storage precision prec (staging
+// applies to 16-bit storage only; elsewhere it repeats an unstaged entry)
+inline bool dslash_cfg_applies(int k, int prec) {
+    return !DSLASH_CFGS[k].stage || prec == WD_F16 || prec == WD_BF16;
+}
 // The double-float hopping term (one site per thread, a loop over the hops)
 // has its own table: its register appetite makes the minimum resident blocks,
 // i.e. the register cap, the parameter that matters.
-constexpr DslashCfg DSLASH_DF_CFGS[N_DSLASH_CFG] = {
-    {128, 3, 1}, {128, 1, 1}, {128, 2, 1}, {128, 4, 1}, {256, 2, 1}};
+constexpr int N_DSLASH_DF_CFG = 5;
+constexpr DslashCfg DSLASH_DF_CFGS[N_DSLASH_DF_CFG] = {
+    {128, 3, 1, 0}, {128, 1, 1, 0}, {128, 2, 1, 0}, {128, 4, 1, 0}, {256, 2, 1, 0}};
 
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int CFG>
 void launch_cfg(const DslashArgs<R> &a, cudaStream_t s) {
     constexpr DslashCfg C = DSLASH_CFGS[CFG];
+    constexpr int STAGE = packed16<S>() ? C.stage : 0;
     const long per_block = (long)C.block * C.spt;
     const unsigned grid = (unsigned)((a.g.vh + per_block - 1) / per_block);
-    k_dslash<S, R, RECON, DAG, EPI, NORM, C.block, C.minb, C.spt><<<grid, C.block, 0, s>>>(a);
+    k_dslash<S, R, RECON, DAG, EPI, NORM, C.block, C.minb, C.spt, STAGE><<<grid, C.block, 0, s>>>(a);
 }
 
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM>
@@ -652,6 +828,9 @@ void launch_any_cfg(int cfg, const DslashArgs<R> &a, cudaStream_t s) {
     case 2: launch_cfg<S, R, RECON, DAG, EPI, NORM, 2>(a, s); break;
     case 3: launch_cfg<S, R, RECON, DAG, EPI, NORM, 3>(a, s); break;
     case 4: launch_cfg<S, R, RECON, DAG, EPI, NORM, 4>(a, s); break;
+    case 5: launch_cfg<S, R, RECON, DAG, EPI, NORM, 5>(a, s); break;
+    case 6: launch_cfg<S, R, RECON, DAG, EPI, NORM, 6>(a, s); break;
+    case 7: launch_cfg<S, R, RECON, DAG, EPI, NORM, 7>(a, s); break;
     default: launch_cfg<S, R, RECON, DAG, EPI, NORM, 0>(a, s); break;
     }
 }

@@ -171,11 +171,7 @@ extern "C" int wd_apply_eo_noalloc(double *out, const double *in, const double *
         }
         tmp = g_noalloc_addr[dev];
     }
-    Geom g{};
-    for (int m = 0; m < 4; ++m) g.L[m] = dims[m];
-    g.hx = dims[0] / 2;
-    g.vh = V / 2;
-    g.stride = g.vh;
+    const Geom g = make_geom(dims, V / 2);
     Phase8 ph{};
     for (int i = 0; i < 8; ++i) ph.v[i] = phase[i];
     cudaStream_t s = (cudaStream_t)stream;

@@ -136,16 +136,19 @@ static int check_op(const wd_op *op) {
 static int tune_dslash(wd_op *op, int variant) {
     const char *force = getenv("WD_DSLASH_CFG");
     const char *tune = getenv("WD_TUNE");
+    const bool hi = variant == 1;
+    const int prec = hi ? op->hi_prec : op->prec;
+    const int n_cfg = prec == WD_DF64 ? N_DSLASH_DF_CFG : N_DSLASH_CFG;
+    auto applies = [&](int k) { return prec == WD_DF64 || dslash_cfg_applies(k, prec); };
     if (force) {
         int k = atoi(force);
-        op->cfg[variant] = (k >= 0 && k < N_DSLASH_CFG) ? k : 0;
+        op->cfg[variant] = (k >= 0 && k < n_cfg && applies(k)) ? k : 0;
         return WD_OK;
     }
     if (tune && tune[0] == '0') {
         op->cfg[variant] = 0;
         return WD_OK;
     }
-    const bool hi = variant == 1;
     void *in = hi ? (void *)op->th : op->slot[0];
     void *out = hi ? (void *)op->axh : op->slot[1];
     Reduction red = reduction(op, FIN_STORE0);
@@ -156,7 +159,9 @@ static int tune_dslash(wd_op *op, int variant) {
     };
     int best = 0;
     float best_ms = 1e30f;
-    for (int k = 0; k < N_DSLASH_CFG; ++k) {
+    for (int k = 0; k < n_cfg; ++k) {
+        op->tune_us[variant][k] = 0.0;
+        if (!applies(k)) continue;   // the same kernel as an unstaged candidate
         op->cfg[variant] = k;
         for (int w = 0; w < 2; ++w) WD_TRY(launch(w & 1));
         WD_CUDA(cudaEventRecord(op->ev_t0, op->stream));
@@ -241,14 +246,17 @@ int wd_op_set_twisted_mass(wd_op *op, double mu) {
 double wd_op_twisted_mass(const wd_op *op) { return op ? op->mu : 0.0; }
 
 int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,
-                     int *sites_per_thread) {
+                     int *sites_per_thread, int *staged) {
     if (!op || hi < 0 || hi > 2) return -1;
     const int k = op->cfg[hi];
-    for (int i = 0; us && i < n && i < N_DSLASH_CFG; ++i) us[i] = op->tune_us[hi][i];
-    const DslashCfg &C = (hi == 1 && op->hi_prec == WD_DF64) ? DSLASH_DF_CFGS[k] : DSLASH_CFGS[k];
+    const bool df = hi == 1 && op->hi_prec == WD_DF64;
+    const int n_cfg = df ? N_DSLASH_DF_CFG : N_DSLASH_CFG;
+    for (int i = 0; us && i < n; ++i) us[i] = i < n_cfg ? op->tune_us[hi][i] : 0.0;
+    const DslashCfg &C = df ? DSLASH_DF_CFGS[k] : DSLASH_CFGS[k];
     if (block) *block = C.block;
     if (min_blocks) *min_blocks = C.minb;
     if (sites_per_thread) *sites_per_thread = C.spt;
+    if (staged) *staged = C.stage;
     return k;
 }
 
@@ -368,10 +376,7 @@ int wd_op_create(wd_op **out, const int dims[4], double kappa, const double phas
         if (!std::isfinite(phase[i])) return fail(WD_ERR_ARG, "phases must be finite");
 
     wd_op *op = new wd_op();
-    for (int m = 0; m < 4; ++m) op->g.L[m] = dims[m];
-    op->g.hx = dims[0] / 2;
-    op->g.vh = V / 2;
-    op->g.stride = pad_stride(op->g.vh);
+    op->g = make_geom(dims, pad_stride(V / 2));
     op->kappa = kappa;
     memcpy(op->phase, phase, sizeof(op->phase));
     op->prec = prec;

@@ -288,7 +288,29 @@ struct Geom {
     int hx;         // Lx / 2
     long vh;        // V / 2
     long stride;    // padded plane stride (sites)
+    // half-lattice index step of a hop in direction mu = 1, 2, 3 (entry 0
+    // unused: x hops depend on the site's parity) and the step back across
+    // the periodic boundary, (L_mu - 1) * step
+    unsigned step[4];
+    unsigned back[4];
 };
+
+// Geometry of a dims[0] x ... x dims[3] lattice (dims[0] even) whose fields
+// have plane stride stride.
+inline Geom make_geom(const int dims[4], long stride) {
+    Geom g{};
+    for (int m = 0; m < 4; ++m) g.L[m] = dims[m];
+    g.hx = dims[0] / 2;
+    g.vh = (long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
+    g.stride = stride;
+    unsigned st = (unsigned)g.hx;
+    for (int m = 1; m < 4; ++m) {
+        g.step[m] = st;
+        g.back[m] = (unsigned)(dims[m] - 1) * st;
+        st *= (unsigned)dims[m];
+    }
+    return g;
+}
 
 // Coordinates of half-lattice site h of parity p (32-bit arithmetic: the
 // volume is limited to 2^31 sites).

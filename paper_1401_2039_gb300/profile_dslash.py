@@ -74,6 +74,7 @@ def main():
     print(f"{w.name} prec={prec} recon={recon}: {args.launches} launches, {us:.1f} us each, "
           f"{op.dslash_bytes / (us * 1e-6) / 1e9:.0f} GB/s algorithmic")
     print("launch configuration:", op.dslash_tuning())
+    print("xpay + norm variant:", op.dslash_tuning(norm=True))
     op.close()
 
 

@@ -73,7 +73,7 @@ def load_library() -> ctypes.CDLL:
             "wd_op_set_recovery": (i, [vp, i, d]),
             "wd_op_recovery": (i, [vp, dp]),
             "wd_op_set_residual_precision": (i, [vp, i]),
-            "wd_dslash_tuning": (i, [vp, i, dp, i, ip, ip, ip]),
+            "wd_dslash_tuning": (i, [vp, i, dp, i, ip, ip, ip, ip]),
             "wd_dslash_bytes": (d, [vp]),
             "wd_status_string": (ctypes.c_char_p, [i]),
             "wd_last_error": (ctypes.c_char_p, []),
@@ -258,12 +258,13 @@ class WilsonDirac:
         (hi=True), or the storage-precision variant with xpay and fused norm
         (norm=True)."""
         us = (ctypes.c_double * 8)()
-        blk, mb, spt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        blk, mb, spt, stg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         variant = 2 if norm else int(bool(hi))
         k = self.lib.wd_dslash_tuning(self.handle, variant, us, 8, ctypes.byref(blk),
-                                      ctypes.byref(mb), ctypes.byref(spt))
+                                      ctypes.byref(mb), ctypes.byref(spt), ctypes.byref(stg))
         return {"index": k, "block": blk.value, "min_blocks": mb.value,
-                "sites_per_thread": spt.value, "us": [round(v, 2) for v in us[:5]]}
+                "sites_per_thread": spt.value, "staged": bool(stg.value),
+                "us": [round(v, 2) for v in us]}
 
     # resident fields, for timing the hopping term alone
     def field_load(self, slot: int, half: torch.Tensor):

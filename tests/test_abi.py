@@ -95,8 +95,9 @@ def test_null_handles_are_rejected(lib):
     lib.wd_op_twisted_mass.restype = ctypes.c_double
     assert lib.wd_op_twisted_mass(None) == 0.0
     lib.wd_dslash_tuning.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
-                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-    assert lib.wd_dslash_tuning(None, 0, None, 0, None, None, None) == -1
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]
+    assert lib.wd_dslash_tuning(None, 0, None, 0, None, None, None, None) == -1
     lib.wd_krylov_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     assert lib.wd_krylov_create(None, None, 1) == 1
     h = ctypes.c_void_p()

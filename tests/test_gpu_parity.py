@@ -79,6 +79,29 @@ def test_dslash_eo(dims, prec, recon):
         op.close()
 
 
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("cfg", [1, 5, 7])
+def test_dslash_eo_each_16bit_path(monkeypatch, prec, recon, cfg):
+    """Both hop paths of 16-bit storage against the oracle, site by site:
+    link and spinor words in registers one hop ahead (candidate 1), and the
+    eight link records staged in shared memory by cp.async (candidates 5,
+    7: 128 and 256 threads).  Lattices: odd Lx/2 with a ragged last block,
+    2^4 (x + mu = x - mu), and an anisotropic one; twisted boundary phases."""
+    monkeypatch.setenv("WD_DSLASH_CFG", str(cfg))
+    for dims in [(6, 6, 2, 4), (2, 2, 2, 2), (8, 4, 6, 10)]:
+        U, psi = fields(dims)
+        op = make_op(dims, 0.12, PHASES["twisted"], prec, recon, U)
+        assert op.dslash_tuning()["staged"] == (cfg >= 5)
+        for out_parity in (0, 1):
+            src = syn.to_half(psi, dims, 1 - out_parity)
+            for dagger in (False, True):
+                ref = oracle.hop_eo(src, U, dims, PHASES["twisted"], out_parity, dagger)
+                got = host(op.dslash_eo(cuda(src), out_parity, dagger))
+                check(got, ref, prec, what=(dims, cfg, out_parity, dagger))
+        op.close()
+
+
 def test_dslash_generic_links_f64():
     """18-real links need not be unitary: random complex matrices."""
     dims = (6, 4, 2, 4)
@@ -310,19 +333,23 @@ def test_residual_arithmetic_schur_operator(dims, mode):
         op.close()
 
 
-@pytest.mark.parametrize("prec,recon", [("f16", 12), ("f32", 18)])
+@pytest.mark.parametrize("prec,recon", [("f16", 12), ("bf16", 18), ("f32", 18)])
 def test_solve_bitwise_identical_across_launch_configurations(monkeypatch, prec, recon):
     """Fused norms add in one order under every launch configuration, so
     the iterates and the solution are bitwise identical whichever
-    configuration the tuner picks (ragged last chunk: Vh = 1440)."""
+    configuration the tuner picks (ragged last chunk: Vh = 1440).  The
+    link-staging candidates (5..7) apply to 16-bit storage only; elsewhere
+    forcing one falls back to candidate 0."""
     dims = (8, 6, 6, 10)
     U, _ = fields(dims)
     b = syn.gaussian_spinor(syn.volume(dims), 3)
     runs = []
-    for k in range(5):
+    for k in range(8):
         monkeypatch.setenv("WD_DSLASH_CFG", str(k))
         op = make_op(dims, 0.124, PHASES["apbc"], prec, recon, U)
-        assert op.dslash_tuning()["index"] == k
+        t = op.dslash_tuning()
+        assert t["index"] == (k if prec in ("f16", "bf16") or k < 5 else 0)
+        assert t["staged"] == (prec in ("f16", "bf16") and k >= 5)
         res = op.solve(cuda(b), tol=1e-10)
         runs.append((host(res.x), res.info["iters"], res.info["reliable_updates"]))
         op.close()
