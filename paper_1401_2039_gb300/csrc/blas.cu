@@ -60,47 +60,50 @@ template <typename R> using ThreadAcc = typename ThreadAccOf<R>::T;
 template <typename R> __device__ __forceinline__ ThreadAcc<R> thread_term(R s) { return to_df(s); }
 template <> __device__ __forceinline__ double thread_term<double>(double s) { return s; }
 
-// x += alpha p;  r -= alpha Ap;  ||r||^2  (alpha from the device scalars)
+// r -= alpha Ap;  ||r||^2  (alpha from the device scalars).  The matching
+// x += alpha p is deferred to the next p update (k_cg_update_px), which reads
+// the same p anyway: one field pass fewer per iteration.
 template <typename S, typename R>
 __global__ void __launch_bounds__(BLAS_BLOCK)
-k_cg_update_xr(long n, void *x, void *r, const void *p, const void *Ap, Reduction red) {
+k_cg_update_r(long n, void *r, const void *Ap, Reduction red) {
     using C = Chunk<S, R>;
     const R alpha = (R)red.scalars->alpha;
     ThreadAcc<R> acc = 0;
     for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
          i += (long)gridDim.x * BLAS_BLOCK) {
-        R xv[C::K], rv[C::K], pv[C::K], av[C::K];
-        C::load(x, i, xv);
+        R rv[C::K], av[C::K];
         C::load(r, i, rv);
-        C::load(p, i, pv);
         C::load(Ap, i, av);
         R s = 0;
 #pragma unroll
         for (int k = 0; k < C::K; ++k) {
-            xv[k] += alpha * pv[k];
             rv[k] -= alpha * av[k];
             s += rv[k] * rv[k];
         }
-        C::store(x, i, xv);
         C::store(r, i, rv);
         acc = acc + thread_term<R>(s);
     }
     block_reduce_finish<BLAS_BLOCK>(acc, red);
 }
 
-// p = z + beta p
+// x += alpha_x p (the previous iteration's step);  p = z + beta p
 template <typename S, typename R>
 __global__ void __launch_bounds__(BLAS_BLOCK)
-k_cg_update_p(long n, void *p, const void *z, const SolverScalars *sc) {
+k_cg_update_px(long n, void *x, void *p, const void *z, const SolverScalars *sc) {
     using C = Chunk<S, R>;
-    const R beta = (R)sc->beta;
+    const R alpha = (R)sc->alpha_x, beta = (R)sc->beta;
     for (long i = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; i < n;
          i += (long)gridDim.x * BLAS_BLOCK) {
-        R pv[C::K], zv[C::K];
+        R xv[C::K], pv[C::K], zv[C::K];
+        C::load(x, i, xv);
         C::load(p, i, pv);
         C::load(z, i, zv);
 #pragma unroll
-        for (int k = 0; k < C::K; ++k) pv[k] = zv[k] + beta * pv[k];
+        for (int k = 0; k < C::K; ++k) {
+            xv[k] = fma(alpha, pv[k], xv[k]);
+            pv[k] = zv[k] + beta * pv[k];
+        }
+        C::store(x, i, xv);
         C::store(p, i, pv);
     }
 }
@@ -154,20 +157,34 @@ k_xpay_df(long n, void *out, const void *y, df64 a, const void *x) {
     }
 }
 
+// x_lo + alpha p rounded to storage precision S, as k_cg_update_px would
+// have stored it (the same FMA in the same arithmetic, then one rounding)
+template <typename S, typename R> __device__ __forceinline__ R owed_step(R lo, R a, R p) {
+    const R v = fma(a, p, lo);
+    if constexpr (std::is_same<S, __half>::value) return __half2float(__float2half_rn(v));
+    else if constexpr (std::is_same<S, __nv_bfloat16>::value)
+        return __bfloat162float(__float2bfloat16_rn(v));
+    else return v;
+}
+
+// x_lo += alpha_x p (the step the last iteration still owes x), then
 // x_hi (double-float) += inv_scale * x_lo;  x_lo = 0
 template <typename S>
 __global__ void __launch_bounds__(BLAS_BLOCK)
-k_fold_x_df(long vh, long stride, void *x_hi, void *x_lo, const double *inv_scale) {
+k_fold_x_df(long vh, long stride, void *x_hi, void *x_lo, const void *p,
+            const SolverScalars *sc, const double *inv_scale) {
     const df64 is = df64(*inv_scale);
+    const float a = (float)sc->alpha_x;
     for (long h = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; h < vh;
          h += (long)gridDim.x * BLAS_BLOCK) {
-        float lo[24];
+        float lo[24], pv[24];
         df64 hi[24];
         Rec<S, 24>::template load_coherent<float>(x_lo, stride, h, lo);
+        Rec<S, 24>::template load_coherent<float>(p, stride, h, pv);
         Rec<df64, 24>::template load_coherent<df64>(x_hi, stride, h, hi);
 #pragma unroll
         for (int i = 0; i < 24; ++i) {
-            hi[i] += is * df64(lo[i], 0.0f);
+            hi[i] += is * df64(owed_step<S>(lo[i], a, pv[i]), 0.0f);
             lo[i] = 0.0f;
         }
         Rec<df64, 24>::store(x_hi, stride, h, hi);
@@ -268,17 +285,22 @@ k_convert_scaled(long vh, long stride, void *out, const void *in, const double *
 // x_hi += inv_scale * x_lo;  x_lo = 0
 template <typename S>
 __global__ void __launch_bounds__(BLAS_BLOCK)
-k_fold_x(long vh, long stride, double *x_hi, void *x_lo, const double *inv_scale) {
+k_fold_x(long vh, long stride, double *x_hi, void *x_lo, const void *p, const SolverScalars *sc,
+         const double *inv_scale) {
+    using R = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
     const double is = *inv_scale;
+    const R a = (R)sc->alpha_x;
     for (long h = (long)blockIdx.x * BLAS_BLOCK + threadIdx.x; h < vh;
          h += (long)gridDim.x * BLAS_BLOCK) {
-        double lo[24], hi[24];
-        Rec<S, 24>::template load_coherent<double>(x_lo, stride, h, lo);
+        R lo[24], pv[24];
+        double hi[24];
+        Rec<S, 24>::template load_coherent<R>(x_lo, stride, h, lo);
+        Rec<S, 24>::template load_coherent<R>(p, stride, h, pv);
         Rec<double, 24>::template load_coherent<double>(x_hi, stride, h, hi);
 #pragma unroll
         for (int i = 0; i < 24; ++i) {
-            hi[i] += is * lo[i];
-            lo[i] = 0.0;
+            hi[i] += is * (double)owed_step<S>(lo[i], a, pv[i]);
+            lo[i] = 0;
         }
         Rec<double, 24>::store(x_hi, stride, h, hi);
         Rec<S, 24>::store(x_lo, stride, h, lo);
@@ -313,18 +335,19 @@ k_rescale(long n, void *p, SolverScalars *sc, const double *ratio_dev) {
     default: return cudaErrorInvalidValue;                                              \
     }
 
-cudaError_t launch_cg_update_xr(int prec, const Geom &g, void *x, void *r, const void *p,
-                                const void *Ap, const Reduction &red, cudaStream_t s) {
+cudaError_t launch_cg_update_r(int prec, const Geom &g, void *r, const void *Ap,
+                               const Reduction &red, cudaStream_t s) {
     const long n = spinor_chunks(prec, g);
-    WD_PREC_DISPATCH(prec, (k_cg_update_xr<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(
-                               n, x, r, p, Ap, red)));
+    WD_PREC_DISPATCH(prec, (k_cg_update_r<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(
+                               n, r, Ap, red)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update_p(int prec, const Geom &g, void *p, const void *z,
-                               const SolverScalars *sc, cudaStream_t s) {
+cudaError_t launch_cg_update_px(int prec, const Geom &g, void *x, void *p, const void *z,
+                                const SolverScalars *sc, cudaStream_t s) {
     const long n = spinor_chunks(prec, g);
-    WD_PREC_DISPATCH(prec, (k_cg_update_p<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(n, p, z, sc)));
+    WD_PREC_DISPATCH(prec, (k_cg_update_px<S, R><<<blas_grid(n), BLAS_BLOCK, 0, s>>>(
+                               n, x, p, z, sc)));
     return cudaGetLastError();
 }
 
@@ -433,21 +456,25 @@ cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const vo
 }
 
 cudaError_t launch_fold_x(int prec_lo, int prec_hi, const Geom &g, void *x_hi, void *x_lo,
-                          const double *inv_scale_dev, cudaStream_t s) {
+                          const void *p, SolverScalars *sc, const double *inv_scale_dev,
+                          cudaStream_t s) {
     const unsigned grid = blas_grid(g.vh);
     if (prec_hi == WD_DF64) {
         switch (prec_lo) {
-        case WD_F32: k_fold_x_df<float><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, inv_scale_dev); break;
-        case WD_F16: k_fold_x_df<__half><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, inv_scale_dev); break;
-        case WD_BF16: k_fold_x_df<__nv_bfloat16><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, inv_scale_dev); break;
+        case WD_F32: k_fold_x_df<float><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, p, sc, inv_scale_dev); break;
+        case WD_F16: k_fold_x_df<__half><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, p, sc, inv_scale_dev); break;
+        case WD_BF16: k_fold_x_df<__nv_bfloat16><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride, x_hi, x_lo, p, sc, inv_scale_dev); break;
         default: return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
+    } else {
+        WD_PREC_DISPATCH(prec_lo, (k_fold_x<S><<<grid, BLAS_BLOCK, 0, s>>>(
+                                      g.vh, g.stride, (double *)x_hi, x_lo, p, sc,
+                                      inv_scale_dev)));
     }
-    WD_PREC_DISPATCH(prec_lo, (k_fold_x<S><<<grid, BLAS_BLOCK, 0, s>>>(g.vh, g.stride,
-                                                                         (double *)x_hi, x_lo,
-                                                                         inv_scale_dev)));
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the owed step is settled: the next p update must not add it again
+    return cudaMemsetAsync(&sc->alpha_x, 0, sizeof(double), s);
 }
 
 cudaError_t launch_rescale_lo(int prec_lo, const Geom &g, void *p, SolverScalars *sc,

@@ -21,27 +21,73 @@ __device__ __forceinline__ void load_canonical(const double *src, long site, dou
     }
 }
 
-__device__ __forceinline__ void store_canonical(double *dst, long site, const double *v, int n) {
-    double2 *p = reinterpret_cast<double2 *>(dst + (long)site * n);
-    for (int i = 0; i < n / 2; ++i) p[i] = make_double2(v[2 * i], v[2 * i + 1]);
+// Spinor records (24 doubles, 12 chunks of 16 bytes) of a block's
+// LAYOUT_BLOCK consecutive sites pass through shared memory: the canonical
+// side moves the block's contiguous chunks with consecutive threads on
+// consecutive chunks (coalesced), the internal side handles one record per
+// thread.  Records are padded to 13 chunks in shared memory, so that the
+// per-record accesses of 8 consecutive threads fall in distinct banks.
+constexpr int SPIN_CHUNKS = 12, SPIN_PAD = 13;
+
+__device__ __forceinline__ void canonical_block_in(const double *src, long first, long n,
+                                                   double2 *sm) {
+    const double2 *g = reinterpret_cast<const double2 *>(src) + first * SPIN_CHUNKS;
+    const long left = n - first;
+    const int avail = (int)((left < LAYOUT_BLOCK ? left : LAYOUT_BLOCK) * SPIN_CHUNKS);
+#pragma unroll 4
+    for (int c = threadIdx.x; c < avail; c += LAYOUT_BLOCK)
+        sm[(c / SPIN_CHUNKS) * SPIN_PAD + c % SPIN_CHUNKS] = __ldcs(g + c);
+}
+
+__device__ __forceinline__ void canonical_block_out(double *dst, long first, long n,
+                                                    const double2 *sm) {
+    double2 *g = reinterpret_cast<double2 *>(dst) + first * SPIN_CHUNKS;
+    const long left = n - first;
+    const int avail = (int)((left < LAYOUT_BLOCK ? left : LAYOUT_BLOCK) * SPIN_CHUNKS);
+#pragma unroll 4
+    for (int c = threadIdx.x; c < avail; c += LAYOUT_BLOCK)
+        __stcs(g + c, sm[(c / SPIN_CHUNKS) * SPIN_PAD + c % SPIN_CHUNKS]);
+}
+
+__device__ __forceinline__ void record_from_smem(const double2 *sm, double *v) {
+    const double2 *p = sm + threadIdx.x * SPIN_PAD;
+#pragma unroll
+    for (int i = 0; i < SPIN_CHUNKS; ++i) {
+        const double2 d = p[i];
+        v[2 * i] = d.x;
+        v[2 * i + 1] = d.y;
+    }
+}
+
+__device__ __forceinline__ void record_to_smem(double2 *sm, const double *v) {
+    double2 *p = sm + threadIdx.x * SPIN_PAD;
+#pragma unroll
+    for (int i = 0; i < SPIN_CHUNKS; ++i) p[i] = make_double2(v[2 * i], v[2 * i + 1]);
 }
 
 template <typename S>
-__global__ void k_pack_half(Geom g, void *dst, const double *src) {
-    const long h = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
+__global__ void __launch_bounds__(LAYOUT_BLOCK) k_pack_half(Geom g, void *dst, const double *src) {
+    __shared__ double2 sm[LAYOUT_BLOCK * SPIN_PAD];
+    const long first = (long)blockIdx.x * LAYOUT_BLOCK, h = first + threadIdx.x;
+    canonical_block_in(src, first, g.vh, sm);
+    __syncthreads();
     if (h >= g.vh) return;
     double v[24];
-    load_canonical(src, h, v, 24);
+    record_from_smem(sm, v);
     Rec<S, 24>::store(dst, g.stride, h, v);
 }
 
 template <typename S>
-__global__ void k_unpack_half(Geom g, double *dst, const void *src) {
-    const long h = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
-    if (h >= g.vh) return;
-    double v[24];
-    Rec<S, 24>::template load_coherent<double>(src, g.stride, h, v);
-    store_canonical(dst, h, v, 24);
+__global__ void __launch_bounds__(LAYOUT_BLOCK) k_unpack_half(Geom g, double *dst, const void *src) {
+    __shared__ double2 sm[LAYOUT_BLOCK * SPIN_PAD];
+    const long first = (long)blockIdx.x * LAYOUT_BLOCK, h = first + threadIdx.x;
+    if (h < g.vh) {
+        double v[24];
+        Rec<S, 24>::template load_coherent<double>(src, g.stride, h, v);
+        record_to_smem(sm, v);
+    }
+    __syncthreads();
+    canonical_block_out(dst, first, g.vh, sm);
 }
 
 // parity of lexicographic site lex (32-bit arithmetic: volumes stay below 2^31;
@@ -58,22 +104,31 @@ __device__ __forceinline__ int lex_parity(const Geom &g, long lex) {
 }
 
 template <typename S>
-__global__ void k_pack_full(Geom g, void *even, void *odd, const double *src) {
-    const long lex = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
+__global__ void __launch_bounds__(LAYOUT_BLOCK) k_pack_full(Geom g, void *even, void *odd,
+                                                            const double *src) {
+    __shared__ double2 sm[LAYOUT_BLOCK * SPIN_PAD];
+    const long first = (long)blockIdx.x * LAYOUT_BLOCK, lex = first + threadIdx.x;
+    canonical_block_in(src, first, 2 * g.vh, sm);
+    __syncthreads();
     if (lex >= 2 * g.vh) return;
     double v[24];
-    load_canonical(src, lex, v, 24);
+    record_from_smem(sm, v);
     Rec<S, 24>::store(lex_parity(g, lex) ? odd : even, g.stride, lex >> 1, v);
 }
 
 template <typename S>
-__global__ void k_unpack_full(Geom g, double *dst, const void *even, const void *odd) {
-    const long lex = (long)blockIdx.x * LAYOUT_BLOCK + threadIdx.x;
-    if (lex >= 2 * g.vh) return;
-    double v[24];
-    Rec<S, 24>::template load_coherent<double>(lex_parity(g, lex) ? odd : even, g.stride,
-                                                lex >> 1, v);
-    store_canonical(dst, lex, v, 24);
+__global__ void __launch_bounds__(LAYOUT_BLOCK) k_unpack_full(Geom g, double *dst, const void *even,
+                                                              const void *odd) {
+    __shared__ double2 sm[LAYOUT_BLOCK * SPIN_PAD];
+    const long first = (long)blockIdx.x * LAYOUT_BLOCK, lex = first + threadIdx.x;
+    if (lex < 2 * g.vh) {
+        double v[24];
+        Rec<S, 24>::template load_coherent<double>(lex_parity(g, lex) ? odd : even, g.stride,
+                                                    lex >> 1, v);
+        record_to_smem(sm, v);
+    }
+    __syncthreads();
+    canonical_block_out(dst, first, 2 * g.vh, sm);
 }
 
 // One thread per (site, direction): the link's first RECON reals (row-major,

@@ -516,14 +516,16 @@ double dslash_b(const wd_op *op, bool hi, bool xpay) {
 //   z = A^dag r; beta = |z|^2 / nz; nz = |z|^2; p = z + beta p;
 //   Ap = A p; alpha = nz / |Ap|^2; x += alpha p; r -= alpha Ap; nr = |r|^2
 // (Alg. "CGNR", rotated so that the host may refresh r between iterations).
+// The step x += alpha p only feeds x, so it runs one iteration late, in the
+// pass that reads p anyway (p = z + beta p), and the fold of a refresh
+// settles the step still owed.
 int cg_iteration(wd_op *op, int p) {
     Reduction rb = reduction(op, FIN_BETA), ra = reduction(op, FIN_ALPHA),
               rn = reduction(op, FIN_NR);
     WD_TRY(schur(op, false, p, 1, op->zl, op->rl, op->tl, &rb));
-    WD_CUDA(launch_cg_update_p(op->prec, op->g, op->pl, op->zl, op->sc, op->stream));
+    WD_CUDA(launch_cg_update_px(op->prec, op->g, op->xl, op->pl, op->zl, op->sc, op->stream));
     WD_TRY(schur(op, false, p, 0, op->apl, op->pl, op->tl, &ra));
-    WD_CUDA(launch_cg_update_xr(op->prec, op->g, op->xl, op->rl, op->pl, op->apl, rn,
-                                op->stream));
+    WD_CUDA(launch_cg_update_r(op->prec, op->g, op->rl, op->apl, rn, op->stream));
     return WD_OK;
 }
 
@@ -587,8 +589,8 @@ int set_consts(wd_op *op, double scale, double inv_scale, double ratio) {
     return WD_OK;
 }
 
-// x_in: the initial guess (read once, at the start); x_out: the solution
-// (written once, at the end); they may be the same array.  x_host (optional):
+// x_in: the initial guess (read once, at the start; nullptr: x = 0); x_out:
+// the solution (written once, at the end); they may be the same array.  x_host (optional):
 // host memory the solution is also copied to, on the handle's copy stream as
 // soon as it is complete, so that the copy overlaps the final true residual.
 int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, double tol,
@@ -603,9 +605,11 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
     // Alg. schur: split b and the initial guess by parity,
     // bhat_p = b_p + kappa H_pq A^-1 b_q  (A = 1 + i t gamma5, t = 2 kappa mu)
     WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));
-    {
+    if (x_in) {
         double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
         WD_CUDA(launch_pack_full(op->hi_prec, g, xe, xo, x_in, op->stream));
+    } else {   // all-zero bytes are a zero in FP64 and in double-float
+        WD_CUDA(cudaMemsetAsync(op->xh, 0, op->hi_field_bytes(), op->stream));
     }
     const double tw = op->twist(0);
     const double inv_norm = 1.0 / (1.0 + tw * tw);
@@ -621,15 +625,17 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
               r2 = reduction(op, FIN_STORE2), r3 = reduction(op, FIN_STORE3);
     WD_CUDA(launch_norm2(op->hi_prec, g, op->hb[st.q], r1, op->stream));
     WD_CUDA(launch_norm2(op->hi_prec, g, op->hb[st.p], r0, op->stream));
-    WD_CUDA(launch_norm2(op->hi_prec, g, op->xh, r2, op->stream));
+    if (x_in) WD_CUDA(launch_norm2(op->hi_prec, g, op->xh, r2, op->stream));
     WD_CUDA(launch_norm2(op->hi_prec, g, op->bh, r3, op->stream));
     WD_TRY(read_scalars(op));
+    if (!x_in) op->sc_host->scratch[2] = 0.0;
     const double nb2 = op->sc_host->scratch[0] + op->sc_host->scratch[1];
     st.nb = std::sqrt(nb2);
     st.target = tol * st.nb;
     st.dslash_hi += 1;
-    st.launches += 7;   // two packs, the bhat hop, four norms
-    st.bytes += dslash_b(op, true, true) + 8 * field_b(op, WD_F64);
+    // packs of b (and the guess), the bhat hop, the norms
+    st.launches += x_in ? 7 : 5;
+    st.bytes += dslash_b(op, true, true) + (x_in ? 8 : 5) * field_b(op, WD_F64);
 
     if (op->sc_host->scratch[2] == 0.0) {
         // zero initial guess: r = bhat exactly, no operator application
@@ -668,7 +674,7 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
 
         const double per_iter_bytes =
             2 * (dslash_b(op, false, false) + dslash_b(op, false, true)) +
-            9 * field_b(op, op->prec);
+            8 * field_b(op, op->prec);
         double r_max_lo = st.r_hi * st.scale;   // iterated residual at the last refresh
         double last_lognr = 2 * std::log(r_max_lo);
         int last_it = 0;
@@ -699,10 +705,10 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
             const bool out_of_iters = iters >= maxiter;
             if (want_conv || want_ru || stalled || out_of_iters) {
                 // reliable update: fold x_lo into x_hi, recompute r_hi in FP64
-                WD_CUDA(launch_fold_x(op->prec, op->hi_prec, g, op->xh, op->xl, op->dev_consts + 1,
-                                      op->stream));
+                WD_CUDA(launch_fold_x(op->prec, op->hi_prec, g, op->xh, op->xl, op->pl, op->sc,
+                                      op->dev_consts + 1, op->stream));
                 st.th_valid = false;
-                st.bytes += field_b(op, op->prec) * 2 + field_b(op, WD_F64) * 2;
+                st.bytes += field_b(op, op->prec) * 3 + field_b(op, WD_F64) * 2;
                 st.launches += 1;
                 WD_TRY(true_residual(op, st));
                 WD_TRY(read_scalars(op));
@@ -880,11 +886,9 @@ static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, doub
     WD_CUDA(cudaMemcpyAsync(op->stage_b, b_host, bytes, cudaMemcpyHostToDevice, op->stream));
     if (with_guess)
         WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
-    else
-        WD_CUDA(cudaMemsetAsync(op->stage_x, 0, bytes, op->stream));
     // the solution's download starts inside the solve, once x is complete
-    int rc = solve_impl(op, op->stage_x, op->stage_x, op->stage_b, tol, maxiter, parity, info,
-                        x_host);
+    int rc = solve_impl(op, with_guess ? op->stage_x : nullptr, op->stage_x, op->stage_b, tol,
+                        maxiter, parity, info, x_host);
     WD_CUDA(cudaStreamSynchronize(op->copy_stream));
     int rj = join(op);
     if (info)

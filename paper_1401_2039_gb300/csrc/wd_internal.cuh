@@ -337,6 +337,8 @@ struct SolverScalars {
     double nz;          // ||z||^2 of the current z = A^dag r
     double pAp;         // ||A p||^2
     double alpha, beta;
+    double alpha_x;     // step still owed to x: the x += alpha p of the last
+                        // iteration runs in the next p update (or the fold)
     double nr;          // ||r||^2 of the iterated residual
     double scratch[4];  // results of plain reductions
     int iter;           // iterations completed
@@ -379,6 +381,7 @@ __device__ __forceinline__ void apply_final(SolverScalars *s, int op, double sum
             if (!(sum > 0.0) || !isfinite(a)) { s->flags |= 1; a = 0.0; }
         }
         s->alpha = a;
+        s->alpha_x = a;
         break;
     }
     case FIN_BETA: {
@@ -565,10 +568,12 @@ struct DslashLaunch {
 cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s);
 
 // blas.cu
-cudaError_t launch_cg_update_xr(int prec, const Geom &g, void *x, void *r, const void *p,
-                                const void *Ap, const Reduction &red, cudaStream_t s);
-cudaError_t launch_cg_update_p(int prec, const Geom &g, void *p, const void *z,
-                               const SolverScalars *sc, cudaStream_t s);
+// r -= alpha Ap and ||r||^2; then, next iteration, x += alpha_x p and
+// p = z + beta p (the x step deferred into the pass over p)
+cudaError_t launch_cg_update_r(int prec, const Geom &g, void *r, const void *Ap,
+                               const Reduction &red, cudaStream_t s);
+cudaError_t launch_cg_update_px(int prec, const Geom &g, void *x, void *p, const void *z,
+                                const SolverScalars *sc, cudaStream_t s);
 cudaError_t launch_norm2(int prec, const Geom &g, const void *v, const Reduction &red,
                          cudaStream_t s);
 cudaError_t launch_xmy_norm(int prec, const Geom &g, void *out, const void *x, const void *y,
@@ -585,8 +590,11 @@ cudaError_t launch_f64_df64(void *buf, long n_reals, int to_df, cudaStream_t s);
 cudaError_t launch_convert_scaled(int prec_out, void *out, int prec_in, const void *in,
                                   const Geom &g, const double *scale_dev, double scale_host,
                                   cudaStream_t s);
+// x_lo += alpha_x p (the owed step, then alpha_x = 0); x_hi += x_lo / scale;
+// x_lo = 0
 cudaError_t launch_fold_x(int prec_lo, int prec_hi, const Geom &g, void *x_hi, void *x_lo,
-                          const double *inv_scale_dev, cudaStream_t s);
+                          const void *p, SolverScalars *sc, const double *inv_scale_dev,
+                          cudaStream_t s);
 cudaError_t launch_rescale_lo(int prec_lo, const Geom &g, void *p, SolverScalars *sc,
                               const double *ratio_dev, cudaStream_t s);
 int reduction_blocks(const Geom &g);
