@@ -807,10 +807,12 @@ inline bool dslash_cfg_applies(int k, int prec) {
 }
 // The double-float hopping term (one site per thread, a loop over the hops)
 // has its own table: its register appetite makes the minimum resident blocks,
-// i.e. the register cap, the parameter that matters.
-constexpr int N_DSLASH_DF_CFG = 5;
+// i.e. the register cap, the parameter that matters; stage = 1 copies each
+// hop's link into shared memory one hop ahead (36 KB per 128-thread block).
+constexpr int N_DSLASH_DF_CFG = 8;
 constexpr DslashCfg DSLASH_DF_CFGS[N_DSLASH_DF_CFG] = {
-    {128, 3, 1, 0}, {128, 1, 1, 0}, {128, 2, 1, 0}, {128, 4, 1, 0}, {256, 2, 1, 0}};
+    {128, 3, 1, 0}, {128, 1, 1, 0}, {128, 2, 1, 0}, {128, 4, 1, 0},
+    {256, 2, 1, 0}, {128, 3, 1, 1}, {128, 4, 1, 1}, {128, 2, 1, 1}};
 
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int CFG>
 void launch_cfg(const DslashArgs<R> &a, cudaStream_t s) {

@@ -33,43 +33,83 @@ __device__ __forceinline__ cdf times(cdf q, bool im, float s) {
 
 __device__ __forceinline__ cdf sel(bool first, cdf a, cdf b) { return first ? a : b; }
 
+// neighbour x +- mu of half-lattice site h (coordinates c) for hop
+// 2 mu + (0 forward | 1 backward), and whether the hop wraps
+__device__ __forceinline__ long df_neighbour(const Geom &g, long h, const int c[4], int hop,
+                                             bool &wrap) {
+    const int mu = hop >> 1;
+    const bool fwd = (hop & 1) == 0;
+    if (mu == 0) {
+        int xn = c[0] + (fwd ? 1 : -1);
+        wrap = fwd ? (xn == g.L[0]) : (xn < 0);
+        if (wrap) xn = fwd ? 0 : g.L[0] - 1;
+        return h + ((xn >> 1) - (c[0] >> 1));
+    }
+    const long step = g.step[mu], back = g.back[mu];
+    const int cm = mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+    wrap = fwd ? (cm == g.L[mu] - 1) : (cm == 0);
+    return fwd ? (wrap ? h - back : h + step) : (wrap ? h + back : h - step);
+}
+
+// Link staging of the single-field kernel: the next hop's link record (nine
+// 16-byte planes) is copied into shared memory by cp.async while the
+// current hop computes; two buffers, laid out [buffer][plane][thread].
+constexpr int DF_LINK_PLANES = 9;
+template <int BLOCK>
+__device__ __forceinline__ void df_stage_link(const Geom &g, const char *gauge_out,
+                                              const char *gauge_in, size_t dir_bytes, long h,
+                                              const int c[4], int hop, uint4 *stage) {
+    bool wrap;
+    const bool fwd = (hop & 1) == 0;
+    const long site = fwd ? h : df_neighbour(g, h, c, hop, wrap);
+    const char *base = (fwd ? gauge_out : gauge_in) + (hop >> 1) * dir_bytes + site * 16;
+    uint4 *dst = stage + (hop & 1) * DF_LINK_PLANES * BLOCK + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < DF_LINK_PLANES; ++j)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                     :: "r"((uint32_t)__cvta_generic_to_shared(dst + j * BLOCK)),
+                        "l"(base + (long)j * g.stride * 16)
+                     : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // acc += H in at output site h (coordinates c, 18-real double-float links).
 // The input field holds nrhs right-hand sides with the rhs index innermost:
 // site s, rhs r at record s * nrhs + r of plane stride in_stride.  ph: the
-// boundary phases (re, im per direction), double or df64.
-template <int DAG, typename PH>
+// boundary phases (re, im per direction), double or df64.  stage (BLOCK
+// threads, 2 x 9 x BLOCK chunks of shared memory): links staged one hop ahead.
+template <int DAG, int BLOCK = 0, typename PH>
 __device__ __forceinline__ void df_hops(const Geom &g, const char *gauge_out, const char *gauge_in,
                                         size_t dir_bytes, const PH *ph, const void *in,
                                         long in_stride, int nrhs, int r, long h, const int c[4],
-                                        dfl acc[24]) {
-    const long s1 = g.hx, s2 = s1 * g.L[1], s3 = s2 * g.L[2];
+                                        dfl acc[24], uint4 *stage = nullptr) {
+    if constexpr (BLOCK > 0) df_stage_link<BLOCK>(g, gauge_out, gauge_in, dir_bytes, h, c, 0, stage);
 #pragma unroll 1
     for (int hop = 0; hop < 8; ++hop) {
         const int mu = hop >> 1;
         const bool fwd = (hop & 1) == 0;
         // projector 1 + sgn gamma_mu: forward (1 - gamma) for H, (1 + gamma) for H^dag
         const float sgn = (fwd == (DAG != 0)) ? 1.0f : -1.0f;
-        // neighbour x +- mu and whether the hop wraps
-        long hn;
         bool wrap;
-        if (mu == 0) {
-            int xn = c[0] + (fwd ? 1 : -1);
-            wrap = fwd ? (xn == g.L[0]) : (xn < 0);
-            if (wrap) xn = fwd ? 0 : g.L[0] - 1;
-            hn = h + ((xn >> 1) - (c[0] >> 1));
-        } else {
-            const long step = mu == 1 ? s1 : mu == 2 ? s2 : s3;
-            const int cm = mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
-            const int Lm = g.L[mu];
-            wrap = fwd ? (cm == Lm - 1) : (cm == 0);
-            const long jump = (long)(Lm - 1) * step;
-            hn = fwd ? (wrap ? h - jump : h + step) : (wrap ? h + jump : h - step);
-        }
+        const long hn = df_neighbour(g, h, c, hop, wrap);
         df64 psi[24];
         Rec<df64, 24>::template load<df64, 0>(in, in_stride, hn * nrhs + r, psi);
         df64 U[18];
-        Rec<df64, 18>::template load<df64, 1>((fwd ? gauge_out : gauge_in) + mu * dir_bytes,
-                                             g.stride, fwd ? h : hn, U);
+        if constexpr (BLOCK > 0) {
+            if (hop < 7) df_stage_link<BLOCK>(g, gauge_out, gauge_in, dir_bytes, h, c, hop + 1, stage);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this hop's link is in
+            const uint4 *src = stage + (hop & 1) * DF_LINK_PLANES * BLOCK + threadIdx.x;
+#pragma unroll
+            for (int j = 0; j < DF_LINK_PLANES; ++j) {
+                const uint4 v = src[j * BLOCK];
+                U[2 * j] = df64(__uint_as_float(v.x), __uint_as_float(v.y));
+                U[2 * j + 1] = df64(__uint_as_float(v.z), __uint_as_float(v.w));
+            }
+        } else {
+            Rec<df64, 18>::template load<df64, 1>((fwd ? gauge_out : gauge_in) + mu * dir_bytes,
+                                                 g.stride, fwd ? h : hn, U);
+        }
 
         const bool swap = mu < 2;          // rows (0,3)(1,2), else (0,2)(1,3)
         const bool im = (mu & 1) == 0;     // coefficients +-i, else +-1

@@ -6,7 +6,9 @@
 namespace wd {
 namespace {
 
-template <int DAG, int EPI, int NORM, int BLOCK, int MINB>
+// STAGE: each hop's link record is copied into shared memory by cp.async
+// while the previous hop computes (df_hops)
+template <int DAG, int EPI, int NORM, int BLOCK, int MINB, int STAGE>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64> a) {
     df64 nrm[1] = {df64(0.0f, 0.0f)};
     const long h = (long)blockIdx.x * BLOCK + threadIdx.x;
@@ -16,8 +18,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64
         dfl acc[24];
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] = 0;
-        df_hops<DAG>(a.g, a.gauge_out, a.gauge_in, a.dir_bytes, a.ph, a.in, a.g.stride, 1, 0, h, c,
-                     acc);
+        if constexpr (STAGE) {
+            __shared__ uint4 stage[2 * DF_LINK_PLANES * BLOCK];
+            df_hops<DAG, BLOCK>(a.g, a.gauge_out, a.gauge_in, a.dir_bytes, a.ph, a.in, a.g.stride,
+                                1, 0, h, c, acc, stage);
+        } else {
+            df_hops<DAG>(a.g, a.gauge_out, a.gauge_in, a.dir_bytes, a.ph, a.in, a.g.stride, 1, 0,
+                         h, c, acc);
+        }
         df64 o[24];
         if (EPI == EPI_XPAY) {
             df64 xv[24];
@@ -45,7 +53,7 @@ template <int DAG, int EPI, int NORM, int CFG>
 void launch_df(const DslashArgs<df64> &a, cudaStream_t s) {
     constexpr DslashCfg C = DSLASH_DF_CFGS[CFG];
     const unsigned grid = (unsigned)((a.g.vh + C.block - 1) / C.block);
-    k_dslash_df<DAG, EPI, NORM, C.block, C.minb><<<grid, C.block, 0, s>>>(a);
+    k_dslash_df<DAG, EPI, NORM, C.block, C.minb, C.stage><<<grid, C.block, 0, s>>>(a);
 }
 
 template <int DAG, int EPI>
@@ -55,6 +63,9 @@ void launch_df_cfg(int cfg, const DslashArgs<df64> &a, cudaStream_t s) {
     case 2: launch_df<DAG, EPI, 0, 2>(a, s); break;
     case 3: launch_df<DAG, EPI, 0, 3>(a, s); break;
     case 4: launch_df<DAG, EPI, 0, 4>(a, s); break;
+    case 5: launch_df<DAG, EPI, 0, 5>(a, s); break;
+    case 6: launch_df<DAG, EPI, 0, 6>(a, s); break;
+    case 7: launch_df<DAG, EPI, 0, 7>(a, s); break;
     default: launch_df<DAG, EPI, 0, 0>(a, s); break;
     }
 }

@@ -57,6 +57,7 @@ def main():
         us = e0.elapsed_time(e1) * 1e3 / max(1, args.launches)
         print(f"{w.name} Mhat in {args.residual} arithmetic: {args.launches} applications, "
               f"{us:.1f} us each")
+        print("launch configuration:", op.dslash_tuning(hi=True))
         op.close()
         return
     op.field_load(0, half)
