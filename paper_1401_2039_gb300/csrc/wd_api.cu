@@ -568,12 +568,47 @@ int read_scalars(wd_op *op) {
     return WD_OK;
 }
 
-// r_hi = bhat - Mhat x_hi in FP64 and ||r_hi||^2 -> scratch[0]
+// x_q = A^-1 b_q + kappa th on stream s, where th = A^-1 H_qp x_p is the
+// first hop of the last residual-arithmetic refresh (A = 1 + i t gamma5)
+int reconstruct_from_th(wd_op *op, SolveState &st, cudaStream_t s) {
+    const double tw = op->twist(0);
+    const void *bq = op->hb[st.q];
+    if (tw != 0.0) {
+        WD_CUDA(launch_twist_hi(op->hi_prec, op->g, op->xq, op->hb[st.q], -tw, 1.0 / (1.0 + tw * tw),
+                                s));
+        bq = op->xq;
+        st.launches += 1;
+        st.bytes += 2 * field_b(op, WD_F64);
+    }
+    WD_CUDA(launch_xpay_hi(op->hi_prec, op->g, op->xq, bq, op->kappa, op->th, s));
+    st.bytes += 3 * field_b(op, WD_F64);
+    st.launches += 1;
+    return WD_OK;
+}
+
+// unpack x = (x_p, x_q) into x_out on stream s and, with x_host, queue its
+// download on the copy stream behind it
+int unpack_and_download(wd_op *op, SolveState &st, double *x_out, double *x_host,
+                        cudaStream_t s) {
+    double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
+    WD_CUDA(launch_unpack_full(op->hi_prec, op->g, x_out, xe, xo, s));
+    st.launches += 1;
+    if (x_host) {
+        WD_CUDA(cudaEventRecord(op->ev_x, s));
+        WD_CUDA(cudaStreamWaitEvent(op->copy_stream, op->ev_x, 0));
+        WD_CUDA(cudaMemcpyAsync(x_host, x_out, (size_t)2 * op->g.vh * 24 * sizeof(double),
+                                cudaMemcpyDeviceToHost, op->copy_stream));
+    }
+    return WD_OK;
+}
+
+// r_hi = bhat - Mhat x_hi in residual arithmetic and ||r_hi||^2 -> scratch[0]
+// (the Schur operator's first hop leaves th = A^-1 H_qp x_hi)
 int true_residual(wd_op *op, SolveState &st) {
     Reduction r0 = reduction(op, FIN_STORE0);
     WD_TRY(schur(op, true, st.p, 0, op->axh, op->xh, op->th, nullptr));
-    WD_CUDA(launch_xmy_norm(op->hi_prec, op->g, op->rh, op->bh, op->axh, r0, op->stream));
     st.th_valid = true;
+    WD_CUDA(launch_xmy_norm(op->hi_prec, op->g, op->rh, op->bh, op->axh, r0, op->stream));
     st.dslash_hi += 2;
     st.launches += 3;
     st.bytes += dslash_b(op, true, false) + dslash_b(op, true, true) + 3 * field_b(op, WD_F64);
@@ -776,16 +811,7 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
     // x_q = A^-1 b_q + kappa th and A x_q - kappa H_qp x_p = A (x_q - kappa th).
     const bool reuse = st.th_valid;
     if (reuse) {
-        const void *bq = op->hb[st.q];
-        if (tw != 0.0) {
-            WD_CUDA(launch_twist_hi(op->hi_prec, g, op->xq, op->hb[st.q], -tw, inv_norm,
-                                    op->stream));
-            bq = op->xq;
-            st.launches += 1;
-            st.bytes += 2 * field_b(op, WD_F64);
-        }
-        WD_CUDA(launch_xpay_hi(op->hi_prec, g, op->xq, bq, op->kappa, op->th, op->stream));
-        st.bytes += 3 * field_b(op, WD_F64);
+        WD_TRY(reconstruct_from_th(op, st, op->stream));
     } else {
         WD_TRY(dslash(op, true, st.q, 0, op->xq, op->xh, op->hb[st.q], op->kappa, nullptr));
         st.dslash_hi += 1;
@@ -798,16 +824,7 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
     }
     // x is complete: unpack it now (the residual below reads but never
     // writes xh and xq) and start its download if the caller wants it
-    {
-        double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
-        WD_CUDA(launch_unpack_full(op->hi_prec, g, x_out, xe, xo, op->stream));
-    }
-    if (x_host) {
-        WD_CUDA(cudaEventRecord(op->ev_x, op->stream));
-        WD_CUDA(cudaStreamWaitEvent(op->copy_stream, op->ev_x, 0));
-        WD_CUDA(cudaMemcpyAsync(x_host, x_out, (size_t)2 * g.vh * 24 * sizeof(double),
-                                cudaMemcpyDeviceToHost, op->copy_stream));
-    }
+    WD_TRY(unpack_and_download(op, st, x_out, x_host, op->stream));
     WD_TRY(dslash(op, true, st.p, 0, op->axh, op->xq, op->xh, -op->kappa, nullptr, tw));
     WD_CUDA(launch_xmy_norm(op->hi_prec, g, op->rh, op->hb[st.p], op->axh, r0, op->stream));
     if (reuse) {

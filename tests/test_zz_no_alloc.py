@@ -92,3 +92,48 @@ def test_noalloc_matches_apply_eo_on_consecutive_calls(dims):
         torch.cuda.synchronize()
         check(out.cpu().numpy(), ref.cpu().numpy(), "f64", what=(parity, dagger))
     op.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_calls_captured_in_a_cuda_graph():
+    """The call allocates nothing and, after one call outside the capture
+    has loaded its kernels, makes no call that a stream capture forbids:
+    calls with both dagger flags captured in one torch.cuda.graph and
+    replayed give the results of wd_apply_eo."""
+    import torch
+    from paper_1401_2039_gb300 import WilsonDirac
+    lib = _lib()
+    dims = (6, 6, 2, 4)
+    U_np = syn.su3_links(dims, eps=0.3, seed=9)
+    U = torch.from_numpy(U_np).cuda()
+    op = WilsonDirac(dims, KAPPA, PHASE, prec="f64", recon=18)
+    op.set_gauge(U)
+    dims_c = (ctypes.c_int * 4)(*dims)
+    V = syn.volume(dims)
+    cases = ((1, 0, 31), (0, 1, 32))
+    ins = [torch.from_numpy(syn.gaussian_spinor(V // 2, seed)).cuda() for _, _, seed in cases]
+    outs = [torch.empty_like(t) for t in ins]
+    refs = [op.apply_eo(t, parity, bool(dagger)) for t, (parity, dagger, _) in zip(ins, cases)]
+
+    def call(i, stream):
+        parity, dagger, _ = cases[i]
+        return lib.wd_apply_eo_noalloc(ctypes.c_void_p(outs[i].data_ptr()),
+                                       ctypes.c_void_p(ins[i].data_ptr()),
+                                       ctypes.c_void_p(U.data_ptr()), dims_c, KAPPA, _phase8(),
+                                       parity, dagger, ctypes.c_void_p(stream))
+
+    assert call(0, torch.cuda.current_stream().cuda_stream) == 0   # warm call, not captured
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    rcs = []
+    with torch.cuda.graph(graph):
+        s = torch.cuda.current_stream().cuda_stream
+        rcs = [call(0, s), call(1, s)]
+    assert rcs == [0, 0], lib.wd_noalloc_last_error()
+    for o in outs:
+        o.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    for i, (parity, dagger, _) in enumerate(cases):
+        check(outs[i].cpu().numpy(), refs[i].cpu().numpy(), "f64", what=(parity, dagger))
+    op.close()
