@@ -189,6 +189,7 @@ template <typename R> struct DslashArgs {
     Reduction red;
     R twist;                 // twisted mass factor t (twist_on != 0)
     int twist_on;
+    long h0, h1;             // output sites [h0, h1)
 };
 
 // v <- (1 + i t gamma5) v on one site's 24 reals.  gamma5 = diag(1, 1, -1, -1)
@@ -736,8 +737,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
     for (int i = 0; i < SPT; ++i) nrm[i] = df64(0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
-        const long h = (long)blockIdx.x * (BLOCK * SPT) + i * BLOCK + threadIdx.x;
-        if (h < a.g.vh) {
+        const long h = a.h0 + (long)blockIdx.x * (BLOCK * SPT) + i * BLOCK + threadIdx.x;
+        if (h < a.h1) {
             int c[4];
             site_coords(a.g, h, a.parity, c);
             Acc<R> acc[24];
@@ -819,7 +820,7 @@ void launch_cfg(const DslashArgs<R> &a, cudaStream_t s) {
     constexpr DslashCfg C = DSLASH_CFGS[CFG];
     constexpr int STAGE = packed16<S>() ? C.stage : 0;
     const long per_block = (long)C.block * C.spt;
-    const unsigned grid = (unsigned)((a.g.vh + per_block - 1) / per_block);
+    const unsigned grid = (unsigned)((a.h1 - a.h0 + per_block - 1) / per_block);
     k_dslash<S, R, RECON, DAG, EPI, NORM, C.block, C.minb, C.spt, STAGE><<<grid, C.block, 0, s>>>(a);
 }
 
@@ -855,7 +856,14 @@ cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
     else a.red = Reduction{nullptr, nullptr, nullptr, FIN_NONE};
     a.twist = (R)L.twist;
     a.twist_on = L.twist != 0.0;
+    a.h0 = L.h_begin;
+    a.h1 = L.h_end < 0 ? L.g.vh : L.h_end;
+    if (a.h0 < 0 || a.h1 > L.g.vh || a.h0 > a.h1) return cudaErrorInvalidValue;
+    if (a.h1 == a.h0) return cudaSuccess;
     const int cfg = L.cfg;
+    if (L.red) {   // the per-warp partials assume a launch over every site
+        if (a.h0 != 0 || a.h1 != L.g.vh) return cudaErrorInvalidValue;
+    }
     if (L.red) {   // fused norm (after an xpay epilogue), then the fixed-order finish
         if (L.dagger) launch_any_cfg<S, R, RECON, 1, EPI_XPAY, 1>(cfg, a, s);
         else launch_any_cfg<S, R, RECON, 0, EPI_XPAY, 1>(cfg, a, s);

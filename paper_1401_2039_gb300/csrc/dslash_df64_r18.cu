@@ -11,8 +11,8 @@ namespace {
 template <int DAG, int EPI, int NORM, int BLOCK, int MINB, int STAGE>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64> a) {
     df64 nrm[1] = {df64(0.0f, 0.0f)};
-    const long h = (long)blockIdx.x * BLOCK + threadIdx.x;
-    if (h < a.g.vh) {
+    const long h = a.h0 + (long)blockIdx.x * BLOCK + threadIdx.x;
+    if (h < a.h1) {
         int c[4];
         site_coords(a.g, h, a.parity, c);
         dfl acc[24];
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64
 template <int DAG, int EPI, int NORM, int CFG>
 void launch_df(const DslashArgs<df64> &a, cudaStream_t s) {
     constexpr DslashCfg C = DSLASH_DF_CFGS[CFG];
-    const unsigned grid = (unsigned)((a.g.vh + C.block - 1) / C.block);
+    const unsigned grid = (unsigned)((a.h1 - a.h0 + C.block - 1) / C.block);
     k_dslash_df<DAG, EPI, NORM, C.block, C.minb, C.stage><<<grid, C.block, 0, s>>>(a);
 }
 
@@ -87,6 +87,11 @@ cudaError_t launch_dslash_df64_r18(const DslashLaunch &L, cudaStream_t s) {
     a.red = L.red ? *L.red : Reduction{nullptr, nullptr, nullptr, FIN_NONE};
     a.twist = df64(L.twist);
     a.twist_on = L.twist != 0.0;
+    a.h0 = L.h_begin;
+    a.h1 = L.h_end < 0 ? L.g.vh : L.h_end;
+    if (a.h0 < 0 || a.h1 > L.g.vh || a.h0 > a.h1) return cudaErrorInvalidValue;
+    if (a.h1 == a.h0) return cudaSuccess;
+    if (L.red && (a.h0 != 0 || a.h1 != L.g.vh)) return cudaErrorInvalidValue;
     if (L.red) {   // fused norm; the residuals never use it: one configuration
         if (L.dagger) launch_df<1, EPI_XPAY, 1, 0>(a, s);
         else launch_df<0, EPI_XPAY, 1, 0>(a, s);

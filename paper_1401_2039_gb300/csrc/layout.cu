@@ -103,14 +103,16 @@ __device__ __forceinline__ int lex_parity(const Geom &g, long lex) {
     return par & 1;
 }
 
+// canonical sites [lex0, lex1) of the full lattice
 template <typename S>
 __global__ void __launch_bounds__(LAYOUT_BLOCK) k_pack_full(Geom g, void *even, void *odd,
-                                                            const double *src) {
+                                                            const double *src, long lex0,
+                                                            long lex1) {
     __shared__ double2 sm[LAYOUT_BLOCK * SPIN_PAD];
-    const long first = (long)blockIdx.x * LAYOUT_BLOCK, lex = first + threadIdx.x;
-    canonical_block_in(src, first, 2 * g.vh, sm);
+    const long first = lex0 + (long)blockIdx.x * LAYOUT_BLOCK, lex = first + threadIdx.x;
+    canonical_block_in(src, first, lex1, sm);
     __syncthreads();
-    if (lex >= 2 * g.vh) return;
+    if (lex >= lex1) return;
     double v[24];
     record_from_smem(sm, v);
     Rec<S, 24>::store(lex_parity(g, lex) ? odd : even, g.stride, lex >> 1, v);
@@ -170,9 +172,12 @@ cudaError_t launch_unpack_half(int prec, const Geom &g, double *dst, const void 
 }
 
 cudaError_t launch_pack_full(int prec, const Geom &g, void *dst_even, void *dst_odd,
-                             const double *src, cudaStream_t s) {
-    const unsigned grid = layout_grid(2 * g.vh);
-    WD_STORE_DISPATCH(prec, k_pack_full, g, dst_even, dst_odd, src);
+                             const double *src, cudaStream_t s, long lex0, long lex1) {
+    if (lex1 < 0) lex1 = 2 * g.vh;
+    if (lex0 < 0 || lex1 > 2 * g.vh || lex0 > lex1) return cudaErrorInvalidValue;
+    if (lex0 == lex1) return cudaSuccess;
+    const unsigned grid = layout_grid(lex1 - lex0);
+    WD_STORE_DISPATCH(prec, k_pack_full, g, dst_even, dst_odd, src, lex0, lex1);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,9 @@ struct wd_op {
     // host-memory solves: the solution's download overlaps the final residual
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_x = nullptr;
+    // host-memory solves: b arrives in t-slabs, one event per slab
+    static constexpr int B_SLABS = 4;
+    cudaEvent_t ev_b[B_SLABS] = {};
     bool gauge_loaded = false;
 
     GaugeSet gauge_lo;             // storage precision, recon

@@ -90,7 +90,8 @@ static Reduction reduction(wd_op *op, int fin) {
 // out = scale * H_{p,q} in  (PLAIN) or  x + scale * H_{p,q} in  (XPAY), optional norm.
 // twist t != 0: out = scale (1 - i t gamma5) H in  or  (1 + i t gamma5) x + scale H in.
 static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, const void *in,
-                  const void *x, double scale, const Reduction *red, double twist = 0.0) {
+                  const void *x, double scale, const Reduction *red, double twist = 0.0,
+                  long h_begin = 0, long h_end = -1) {
     DslashLaunch L;
     L.g = op->g;
     L.gauge = hi ? &op->gauge_hi : &op->gauge_lo;
@@ -105,6 +106,8 @@ static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, con
     L.red = red;
     L.cfg = hi ? op->cfg[1] : red ? op->cfg[2] : op->cfg[0];
     L.twist = twist;
+    L.h_begin = h_begin;
+    L.h_end = h_end;
     WD_CUDA(launch_dslash(L, hi ? op->hi_prec : op->prec, op->stream));
     return WD_OK;
 }
@@ -300,6 +303,8 @@ void wd_op_destroy(wd_op *op) {
     if (op->ev_fork) cudaEventDestroy(op->ev_fork);
     if (op->ev_join) cudaEventDestroy(op->ev_join);
     if (op->ev_x) cudaEventDestroy(op->ev_x);
+    for (cudaEvent_t e : op->ev_b)
+        if (e) cudaEventDestroy(e);
     if (op->copy_stream) {
         cudaStreamSynchronize(op->copy_stream);
         cudaStreamDestroy(op->copy_stream);
@@ -316,6 +321,7 @@ static int create_impl(wd_op *op) {
     WD_CUDA(cudaEventCreate(&op->ev_t1));
     WD_CUDA(cudaStreamCreateWithFlags(&op->copy_stream, cudaStreamNonBlocking));
     WD_CUDA(cudaEventCreateWithFlags(&op->ev_x, cudaEventDisableTiming));
+    for (cudaEvent_t &e : op->ev_b) WD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
     const Geom &g = op->g;
     // gauge fields
@@ -624,12 +630,49 @@ int set_consts(wd_op *op, double scale, double inv_scale, double ratio) {
     return WD_OK;
 }
 
+// The t-slabs b arrives in from host memory: slab k holds the time slices
+// [slab_t(k), slab_t(k + 1)), canonical sites [2 S slab_t(k), 2 S slab_t(k + 1))
+// with S = Lx Ly Lz / 2 sites per slice and parity.
+int slab_t(const wd_op *op, int k) {
+    return (int)((long)op->g.L[3] * k / wd_op::B_SLABS);
+}
+
+// bhat_p = b_p + kappa H_pq b_q (Wilson operator) while b arrives slab by
+// slab (event ev_b[k] on the copy stream): each slab is packed as soon as it
+// is in, and the hop computes the output slices whose neighbours in t have
+// all arrived, so that most of the packing and of the hop overlap the
+// upload.  Slice 0 needs slice Lt - 1 and goes last.
+int prepare_from_slabs(wd_op *op, SolveState &st, const double *b) {
+    const Geom &g = op->g;
+    const long S = (long)g.hx * g.L[1] * g.L[2];
+    const int T = g.L[3];
+    int done = 1;   // output slices [1, done) are computed
+    for (int k = 0; k < wd_op::B_SLABS; ++k) {
+        const int ta = slab_t(op, k), tb = slab_t(op, k + 1);
+        WD_CUDA(cudaStreamWaitEvent(op->stream, op->ev_b[k], 0));
+        WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream,
+                                 2 * S * ta, 2 * S * tb));
+        const int hi = k + 1 == wd_op::B_SLABS ? T : tb - 1;
+        if (hi > done) {
+            WD_TRY(dslash(op, true, st.p, 0, op->bh, op->hb[st.q], op->hb[st.p], op->kappa,
+                          nullptr, 0.0, S * done, S * hi));
+            done = hi;
+        }
+    }
+    WD_TRY(dslash(op, true, st.p, 0, op->bh, op->hb[st.q], op->hb[st.p], op->kappa, nullptr,
+                  0.0, 0, S));
+    st.launches += wd_op::B_SLABS + 1;
+    return WD_OK;
+}
+
 // x_in: the initial guess (read once, at the start; nullptr: x = 0); x_out:
 // the solution (written once, at the end); they may be the same array.  x_host (optional):
 // host memory the solution is also copied to, on the handle's copy stream as
 // soon as it is complete, so that the copy overlaps the final true residual.
+// b_slabs: b is still arriving, in the t-slabs of slab_t (events ev_b).
 int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, double tol,
-               int maxiter, int parity, wd_solve_info *info, double *x_host = nullptr) {
+               int maxiter, int parity, wd_solve_info *info, double *x_host = nullptr,
+               bool b_slabs = false) {
     SolveState st{};
     st.p = parity;
     st.q = 1 - parity;
@@ -639,16 +682,21 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
 
     // Alg. schur: split b and the initial guess by parity,
     // bhat_p = b_p + kappa H_pq A^-1 b_q  (A = 1 + i t gamma5, t = 2 kappa mu)
-    WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));
+    const double tw = op->twist(0);
+    const double inv_norm = 1.0 / (1.0 + tw * tw);
     if (x_in) {
         double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
         WD_CUDA(launch_pack_full(op->hi_prec, g, xe, xo, x_in, op->stream));
     } else {   // all-zero bytes are a zero in FP64 and in double-float
         WD_CUDA(cudaMemsetAsync(op->xh, 0, op->hi_field_bytes(), op->stream));
     }
-    const double tw = op->twist(0);
-    const double inv_norm = 1.0 / (1.0 + tw * tw);
-    if (tw != 0.0) {   // A^-1 b_q = (1 - i t gamma5) b_q / (1 + t^2)
+    const bool pipelined = b_slabs && tw == 0.0 && g.L[3] >= 2 * wd_op::B_SLABS;
+    if (b_slabs && !pipelined)
+        for (cudaEvent_t e : op->ev_b) WD_CUDA(cudaStreamWaitEvent(op->stream, e, 0));
+    if (!pipelined) WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));
+    if (pipelined) {
+        WD_TRY(prepare_from_slabs(op, st, b));
+    } else if (tw != 0.0) {   // A^-1 b_q = (1 - i t gamma5) b_q / (1 + t^2)
         WD_CUDA(launch_twist_hi(op->hi_prec, g, op->axh, op->hb[st.q], -tw, inv_norm, op->stream));
         WD_TRY(dslash(op, true, st.p, 0, op->bh, op->axh, op->hb[st.p], op->kappa, nullptr));
         st.launches += 1;
@@ -900,12 +948,22 @@ static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, doub
     if (info) memset(info, 0, sizeof(*info));
     const size_t bytes = (size_t)2 * op->g.vh * 24 * sizeof(double);
     WD_TRY(fork(op));
-    WD_CUDA(cudaMemcpyAsync(op->stage_b, b_host, bytes, cudaMemcpyHostToDevice, op->stream));
+    // b goes up in t-slabs on the copy stream; the solve packs each slab as
+    // soon as its event fires
+    WD_CUDA(cudaStreamWaitEvent(op->copy_stream, op->ev_fork, 0));
+    const size_t slice = (size_t)op->g.vh / op->g.L[3] * 2 * 24;   // doubles per time slice
+    for (int k = 0; k < wd_op::B_SLABS; ++k) {
+        const size_t d0 = slice * slab_t(op, k), d1 = slice * slab_t(op, k + 1);
+        if (d1 > d0)
+            WD_CUDA(cudaMemcpyAsync(op->stage_b + d0, b_host + d0, (d1 - d0) * sizeof(double),
+                                    cudaMemcpyHostToDevice, op->copy_stream));
+        WD_CUDA(cudaEventRecord(op->ev_b[k], op->copy_stream));
+    }
     if (with_guess)
         WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
     // the solution's download starts inside the solve, once x is complete
     int rc = solve_impl(op, with_guess ? op->stage_x : nullptr, op->stage_x, op->stage_b, tol,
-                        maxiter, parity, info, x_host);
+                        maxiter, parity, info, x_host, true);
     WD_CUDA(cudaStreamSynchronize(op->copy_stream));
     int rj = join(op);
     if (info)

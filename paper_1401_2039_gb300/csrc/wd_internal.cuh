@@ -562,6 +562,9 @@ struct DslashLaunch {
     // twisted mass: t != 0 makes the xpay epilogue out = (1 + i t gamma5) x +
     // scale H in, and the plain one out = scale (1 - i t gamma5) H in
     double twist = 0.0;
+    // output sites [h_begin, h_end) only (h_end < 0: to the end); a launch
+    // with a fused norm covers every site
+    long h_begin = 0, h_end = -1;
 };
 
 // dslash.cu
@@ -604,8 +607,9 @@ cudaError_t launch_pack_half(int prec, const Geom &g, void *dst, const double *s
                              cudaStream_t s);
 cudaError_t launch_unpack_half(int prec, const Geom &g, double *dst, const void *src,
                                cudaStream_t s);
+// canonical sites [lex0, lex1) (lex1 < 0: to the end)
 cudaError_t launch_pack_full(int prec, const Geom &g, void *dst_even, void *dst_odd,
-                             const double *src, cudaStream_t s);
+                             const double *src, cudaStream_t s, long lex0 = 0, long lex1 = -1);
 cudaError_t launch_unpack_full(int prec, const Geom &g, double *dst, const void *src_even,
                                const void *src_odd, cudaStream_t s);
 cudaError_t launch_pack_gauge(const GaugeSet &gs, const Geom &g, const double *U,

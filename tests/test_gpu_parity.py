@@ -277,6 +277,22 @@ def test_host_memory_solve_matches_device_solve():
     assert np.array_equal(resp.x.numpy(), host(dev.x))
     resq = op.solve_host(torch.zeros_like(bp), bp, tol=1e-10)
     assert np.array_equal(resq.x.numpy(), host(dev.x))
+    # b arrives in four t-slabs and the first hop runs slab by slab (Lt = 8);
+    # with the twisted mass, and with Lt < 8, the solve waits for all of b
+    op.set_twisted_mass(0.05)
+    dev_tm = op.solve(cuda(b), tol=1e-10)
+    res_tm = op.solve_host(xh, bh, tol=1e-10, guess=False)
+    assert np.array_equal(res_tm.x.numpy(), host(dev_tm.x))
+    op.close()
+    dims4 = (4, 4, 4, 6)
+    U4, _ = fields(dims4)
+    b4 = syn.gaussian_spinor(syn.volume(dims4), 2)
+    op4 = make_op(dims4, kappa, PHASES["apbc"], "f16", 12, U4)
+    dev4 = op4.solve(cuda(b4), tol=1e-10)
+    b4h = torch.from_numpy(b4).pin_memory()
+    res4 = op4.solve_host(torch.zeros_like(b4h).pin_memory(), b4h, tol=1e-10, guess=False)
+    assert np.array_equal(res4.x.numpy(), host(dev4.x))
+    op4.close()
 
 
 def test_resident_dslash_matches_canonical():
