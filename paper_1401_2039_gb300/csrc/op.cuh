@@ -32,7 +32,7 @@ struct wd_op {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_x = nullptr;
     // host-memory solves: b arrives in t-slabs, one event per slab
-    static constexpr int B_SLABS = 4;
+    static constexpr int B_SLABS = 8;
     cudaEvent_t ev_b[B_SLABS] = {};
     bool gauge_loaded = false;
 

@@ -690,7 +690,7 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
     } else {   // all-zero bytes are a zero in FP64 and in double-float
         WD_CUDA(cudaMemsetAsync(op->xh, 0, op->hi_field_bytes(), op->stream));
     }
-    const bool pipelined = b_slabs && tw == 0.0 && g.L[3] >= 2 * wd_op::B_SLABS;
+    const bool pipelined = b_slabs && tw == 0.0;   // (slabs may be empty when Lt < 8)
     if (b_slabs && !pipelined)
         for (cudaEvent_t e : op->ev_b) WD_CUDA(cudaStreamWaitEvent(op->stream, e, 0));
     if (!pipelined) WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));

@@ -277,8 +277,9 @@ def test_host_memory_solve_matches_device_solve():
     assert np.array_equal(resp.x.numpy(), host(dev.x))
     resq = op.solve_host(torch.zeros_like(bp), bp, tol=1e-10)
     assert np.array_equal(resq.x.numpy(), host(dev.x))
-    # b arrives in four t-slabs and the first hop runs slab by slab (Lt = 8);
-    # with the twisted mass, and with Lt < 8, the solve waits for all of b
+    # b arrives in eight t-slabs and the first hop runs slab by slab (one
+    # slice each at Lt = 8; some empty at Lt = 6); with the twisted mass the
+    # solve waits for all of b
     op.set_twisted_mass(0.05)
     dev_tm = op.solve(cuda(b), tol=1e-10)
     res_tm = op.solve_host(xh, bh, tol=1e-10, guess=False)
