@@ -180,7 +180,10 @@ int wd_op_set_twisted_mass(wd_op *op, double mu);
 double wd_op_twisted_mass(const wd_op *op);
 
 /* The same solve with x and b in HOST memory (pageable or pinned); the
- * host<->device copies go through buffers the handle owns. */
+ * host<->device copies go through buffers the handle owns.  b goes up in
+ * eight slabs of time slices, and the solve's preparation starts on each
+ * slab as it lands; x comes down as soon as it is complete, while the final
+ * true residual is computed.  The call returns when x_host holds x. */
 int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol,
                      int maxiter, int parity, wd_solve_info *info);
 /* As wd_solve_cg_host from the initial guess x = 0: x_host is output only
