@@ -95,6 +95,14 @@ int wd_apply_eo(wd_op *op, double *out, const double *in, int parity, int dagger
  * Same layout, ownership and errors as wd_apply_eo.  Lets a caller check
  * residuals, or the double-float arithmetic, against an FP64 reference. */
 int wd_apply_eo_residual(wd_op *op, double *out, const double *in, int parity, int dagger);
+/* As wd_apply_eo_residual in the arithmetic of the early refreshes of a
+ * mixed-precision solve (those whose residual is still above 1e-5 of ||b||):
+ * the double-float fields and links read in FP32 arithmetic, each
+ * double-float rounded to one float on load (relative rounding ~1e-7).
+ * Handles with FP64 residuals have no early form: the call is
+ * wd_apply_eo_residual. */
+int wd_apply_eo_residual_early(wd_op *op, double *out, const double *in, int parity,
+                               int dagger);
 
 /* out = P_p H P_q^t in (dagger: the same with H^dag): the hopping term from
  * parity q = 1 - p onto parity p, half-lattice canonical spinors. */

@@ -15,6 +15,9 @@ constexpr int STALL_ITERS_DEFAULT = 200;
 constexpr int MAX_BATCH_LOG2 = 5;  // graph batches of 1, 2, ..., 32 iterations
 // Defect correction: each inner solve reduces its residual by this factor.
 constexpr double DC_DELTA_DEFAULT = 0.1;
+// Refreshes whose expected residual is above this fraction of ||b|| compute
+// it in FP32 arithmetic (the next refreshes recompute it in double-float).
+constexpr double EARLY_REFRESH_REL = 1e-5;
 
 struct wd_op {
     using Geom = wd::Geom;

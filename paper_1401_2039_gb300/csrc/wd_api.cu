@@ -18,6 +18,7 @@ namespace wd {
 WD_DECL(f64) WD_DECL(f32) WD_DECL(f16) WD_DECL(bf16)
 #undef WD_DECL
 cudaError_t launch_dslash_df64_r18(const DslashLaunch &L, cudaStream_t s);
+cudaError_t launch_dslash_df64f32_r18(const DslashLaunch &L, cudaStream_t s);
 
 cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s) {
     const bool r12 = L.gauge->recon == 12;
@@ -27,6 +28,7 @@ cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s) {
     case WD_F16: return r12 ? launch_dslash_f16_r12(L, s) : launch_dslash_f16_r18(L, s);
     case WD_BF16: return r12 ? launch_dslash_bf16_r12(L, s) : launch_dslash_bf16_r18(L, s);
     case WD_DF64: return r12 ? cudaErrorInvalidValue : launch_dslash_df64_r18(L, s);
+    case WD_DF64_F32: return r12 ? cudaErrorInvalidValue : launch_dslash_df64f32_r18(L, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -89,9 +91,10 @@ static Reduction reduction(wd_op *op, int fin) {
 
 // out = scale * H_{p,q} in  (PLAIN) or  x + scale * H_{p,q} in  (XPAY), optional norm.
 // twist t != 0: out = scale (1 - i t gamma5) H in  or  (1 + i t gamma5) x + scale H in.
+// early: (hi only, double-float residuals) the same fields in FP32 arithmetic
 static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, const void *in,
                   const void *x, double scale, const Reduction *red, double twist = 0.0,
-                  long h_begin = 0, long h_end = -1) {
+                  long h_begin = 0, long h_end = -1, bool early = false) {
     DslashLaunch L;
     L.g = op->g;
     L.gauge = hi ? &op->gauge_hi : &op->gauge_lo;
@@ -108,7 +111,14 @@ static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, con
     L.twist = twist;
     L.h_begin = h_begin;
     L.h_end = h_end;
-    WD_CUDA(launch_dslash(L, hi ? op->hi_prec : op->prec, op->stream));
+    int prec = hi ? op->hi_prec : op->prec;
+    if (early && hi && prec == WD_DF64) {
+        prec = WD_DF64_F32;
+        // (128 threads, no register cap): measured 766 us per application
+        // at 32^3 x 64 against 847-860 us under the 64- and 80-register caps
+        L.cfg = 0;
+    }
+    WD_CUDA(launch_dslash(L, prec, op->stream));
     return WD_OK;
 }
 
@@ -116,10 +126,11 @@ static int dslash(wd_op *op, bool hi, int out_parity, int dagger, void *out, con
 // A = 1 + i t gamma5, t = 2 kappa mu (A = 1 for the Wilson operator), so that
 // A^-1 = (1 - i t gamma5) / (1 + t^2).  Mhat_p^dag: H^dag and -t.
 static int schur(wd_op *op, bool hi, int p, int dagger, void *out, const void *in, void *tmp,
-                 const Reduction *red) {
+                 const Reduction *red, bool early = false) {
     const double t = op->twist(dagger);
-    WD_TRY(dslash(op, hi, 1 - p, dagger, tmp, in, nullptr, 1.0 / (1.0 + t * t), nullptr, t));
-    WD_TRY(dslash(op, hi, p, dagger, out, tmp, in, -op->kappa * op->kappa, red, t));
+    WD_TRY(dslash(op, hi, 1 - p, dagger, tmp, in, nullptr, 1.0 / (1.0 + t * t), nullptr, t, 0,
+                  -1, early));
+    WD_TRY(dslash(op, hi, p, dagger, out, tmp, in, -op->kappa * op->kappa, red, t, 0, -1, early));
     return WD_OK;
 }
 
@@ -442,16 +453,26 @@ int wd_apply_eo(wd_op *op, double *out, const double *in, int parity, int dagger
     return join(op);
 }
 
-int wd_apply_eo_residual(wd_op *op, double *out, const double *in, int parity, int dagger) {
+static int apply_eo_hi(wd_op *op, double *out, const double *in, int parity, int dagger,
+                       bool early) {
     WD_TRY(check_op(op));
     if (!out || !in) return fail(WD_ERR_ARG, "null spinor");
     if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
     if (dagger != 0 && dagger != 1) return fail(WD_ERR_ARG, "dagger must be 0 or 1");
     WD_TRY(fork(op));
     WD_CUDA(launch_pack_half(op->hi_prec, op->g, op->xh, in, op->stream));
-    WD_TRY(schur(op, true, parity, dagger, op->axh, op->xh, op->th, nullptr));
+    WD_TRY(schur(op, true, parity, dagger, op->axh, op->xh, op->th, nullptr, early));
     WD_CUDA(launch_unpack_half(op->hi_prec, op->g, out, op->axh, op->stream));
     return join(op);
+}
+
+int wd_apply_eo_residual(wd_op *op, double *out, const double *in, int parity, int dagger) {
+    return apply_eo_hi(op, out, in, parity, dagger, false);
+}
+
+int wd_apply_eo_residual_early(wd_op *op, double *out, const double *in, int parity,
+                               int dagger) {
+    return apply_eo_hi(op, out, in, parity, dagger, true);
 }
 
 int wd_dslash_eo(wd_op *op, double *out, const double *in, int out_parity, int dagger) {
@@ -609,11 +630,16 @@ int unpack_and_download(wd_op *op, SolveState &st, double *x_out, double *x_host
 }
 
 // r_hi = bhat - Mhat x_hi in residual arithmetic and ||r_hi||^2 -> scratch[0]
-// (the Schur operator's first hop leaves th = A^-1 H_qp x_hi)
-int true_residual(wd_op *op, SolveState &st) {
+// (the Schur operator's first hop leaves th = A^-1 H_qp x_hi).  early: Mhat
+// x_hi in FP32 arithmetic on the double-float fields, for a refresh whose
+// residual is still large (relative rounding ~1e-7 of ||Mhat|| ||x||, small
+// against ||r_hi||; the next double-float refresh recomputes r_hi from x_hi
+// and so corrects it).  th is then not accurate enough for the
+// reconstruction.
+int true_residual(wd_op *op, SolveState &st, bool early = false) {
     Reduction r0 = reduction(op, FIN_STORE0);
-    WD_TRY(schur(op, true, st.p, 0, op->axh, op->xh, op->th, nullptr));
-    st.th_valid = true;
+    WD_TRY(schur(op, true, st.p, 0, op->axh, op->xh, op->th, nullptr, early));
+    st.th_valid = !early;
     WD_CUDA(launch_xmy_norm(op->hi_prec, op->g, op->rh, op->bh, op->axh, r0, op->stream));
     st.dslash_hi += 2;
     st.launches += 3;
@@ -793,7 +819,11 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
                 st.th_valid = false;
                 st.bytes += field_b(op, op->prec) * 3 + field_b(op, WD_F64) * 2;
                 st.launches += 1;
-                WD_TRY(true_residual(op, st));
+                // the residual this refresh expects, r_lo / scale, is still
+                // above EARLY_REFRESH_REL ||b||: FP32 arithmetic suffices
+                const bool early = mixed && !want_conv && !out_of_iters &&
+                                   r_lo > EARLY_REFRESH_REL * st.nb * st.scale;
+                WD_TRY(true_residual(op, st, early));
                 WD_TRY(read_scalars(op));
                 st.r_hi = std::sqrt(op->sc_host->scratch[0]);
                 st.ru += 1;

@@ -33,6 +33,8 @@ template <> struct Prec<WD_BF16> { using S = __nv_bfloat16; using R = float; };
 
 // Internal precision code of double-float fields (FP64-sized, FP32 pipes).
 constexpr int WD_DF64 = 4;
+// hop launches only: double-float fields and links read in FP32 arithmetic
+constexpr int WD_DF64_F32 = 5;
 template <> struct Prec<WD_DF64> { using S = df64; using R = df64; };
 
 inline size_t prec_bytes(int p) {

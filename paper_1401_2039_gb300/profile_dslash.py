@@ -33,8 +33,9 @@ def main():
     ap.add_argument("--recon", type=int, default=None)
     ap.add_argument("--launches", type=int, default=5)
     ap.add_argument("--dagger", action="store_true")
-    ap.add_argument("--residual", choices=["df64", "f64"], default=None,
-                    help="apply Mhat in this residual arithmetic instead")
+    ap.add_argument("--residual", choices=["df64", "f64", "early"], default=None,
+                    help="apply Mhat in this residual arithmetic instead (early: FP32 "
+                         "arithmetic on the double-float fields)")
     args = ap.parse_args()
     w = syn.WORKLOADS[args.workload]
     prec = args.prec or w.prec
@@ -44,14 +45,15 @@ def main():
     op = WilsonDirac(w.dims, w.kappa, w.phase, prec=prec, recon=recon)
     op.set_gauge(U)
     if args.residual:
-        op.set_residual_precision(args.residual)
+        op.set_residual_precision("df64" if args.residual == "early" else args.residual)
         out = torch.empty_like(half)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.launches):
-            op.apply_eo(half, 1, args.dagger, out=out, residual=True)
+            op.apply_eo(half, 1, args.dagger, out=out,
+                        residual="early" if args.residual == "early" else True)
         e1.record()
         torch.cuda.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / max(1, args.launches)

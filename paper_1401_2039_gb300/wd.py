@@ -58,6 +58,7 @@ def load_library() -> ctypes.CDLL:
             "wd_apply": (i, [vp, vp, vp, i]),
             "wd_apply_eo": (i, [vp, vp, vp, i, i]),
             "wd_apply_eo_residual": (i, [vp, vp, vp, i, i]),
+            "wd_apply_eo_residual_early": (i, [vp, vp, vp, i, i]),
             "wd_op_set_twisted_mass": (i, [vp, ctypes.c_double]),
             "wd_op_twisted_mass": (ctypes.c_double, [vp]),
             "wd_dslash_eo": (i, [vp, vp, vp, i, i]),
@@ -179,10 +180,12 @@ class WilsonDirac:
                  out=None, residual: bool = False) -> torch.Tensor:
         """Mhat_p psi; residual=True evaluates it in the residual arithmetic
         of the reliable updates (FP64 or double-float) instead of storage
-        precision."""
+        precision, residual="early" in that of the early refreshes (FP32 on
+        the double-float fields)."""
         _dev(psi, (self.Vh, 3, 4), "psi")
         out = torch.empty_like(psi) if out is None else _dev(out, (self.Vh, 3, 4), "out")
-        fn = self.lib.wd_apply_eo_residual if residual else self.lib.wd_apply_eo
+        fn = (self.lib.wd_apply_eo_residual_early if residual == "early" else
+              self.lib.wd_apply_eo_residual if residual else self.lib.wd_apply_eo)
         _check(fn(self.handle, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(psi.data_ptr()),
                   int(parity), int(bool(dagger))))
         return out

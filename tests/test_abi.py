@@ -89,6 +89,8 @@ def test_null_handles_are_rejected(lib):
     lib.wd_op_destroy(None)   # no-op
     lib.wd_apply_eo_residual.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int]
     assert lib.wd_apply_eo_residual(None, None, None, 1, 0) == 1
+    lib.wd_apply_eo_residual_early.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int]
+    assert lib.wd_apply_eo_residual_early(None, None, None, 1, 0) == 1
     lib.wd_op_set_twisted_mass.argtypes = [ctypes.c_void_p, ctypes.c_double]
     assert lib.wd_op_set_twisted_mass(None, 0.1) == 1
     lib.wd_op_twisted_mass.argtypes = [ctypes.c_void_p]
