@@ -212,13 +212,14 @@ __global__ void __launch_bounds__(PF_ALL_THREADS, 1) k_ptc_layer_fused(const __g
                                     "l"(p.B + (long)row * p.ldb + col) : "memory");
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
-                // transported operand: items (site, channel 8 grp + cl), one after the
-                // other (the stage lookahead of the other warps hides the latency);
-                // the item's loads go out together on the read-only path
+                // transported operand: items (site, channel 8 grp + cl), unrolled so
+                // that both items' loads go out together on the read-only path
+                // (96 registers, no spill; 1.80 -> 1.66 ms per network
+                // application at 16^3 x 32 against one item after the other)
                 const int c = grp * 8 + cl;
                 const int mu = (k - 1) & 3;
                 const bool fwd = k <= 4;
-#pragma unroll 1
+#pragma unroll
                 for (int j = 0; j < PF_ITEMS; ++j) {
                     const long x = xs[j] < p.g.V ? xs[j] : 0;
                     long xn = x;
