@@ -118,34 +118,74 @@ __device__ __forceinline__ void bt_finish(const BtArgs &a, const df64 *sacc) {
 }
 
 // ------------------------------------------------------------------ hopping term
+// N reals of storage S at record rec of a field with plane stride `plane`
+// bytes, in 32-bit record arithmetic (records < 2^32)
+template <typename S, int N, int KIND, typename R>
+__device__ __forceinline__ void bt_load(const void *base, size_t plane, unsigned rec, R *r) {
+    using Q = Rec<S, N>;
+    uint32_t w[Q::WORDS];
+    const char *p0 = (const char *)base + (size_t)rec * 16;
+#pragma unroll
+    for (int j = 0; j < Q::NF; ++j) {
+        const uint4 v = KIND ? ld_stream_v4(p0 + j * plane) : ld_nc_v4(p0 + j * plane);
+        w[4 * j] = v.x; w[4 * j + 1] = v.y; w[4 * j + 2] = v.z; w[4 * j + 3] = v.w;
+    }
+    if (Q::TAIL == 8) {
+        const uint2 v = ld_stream_v2((const char *)base + Q::NF * plane + (size_t)rec * 8);
+        w[4 * Q::NF] = v.x; w[4 * Q::NF + 1] = v.y;
+    } else if (Q::TAIL == 4) {
+        w[4 * Q::NF] = ld_stream_u32((const char *)base + Q::NF * plane + (size_t)rec * 4);
+    }
+    Words<S, R>::unpack(w, r, N);
+}
+
+// 12-real links: row 2 = conj(row0 x row1) in the arithmetic R
+template <typename R> __device__ __forceinline__ void bt_rebuild_row2(R *U) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        const R xr = U[2 * k], xi = U[2 * k + 1], yr = U[6 + 2 * l], yi = U[6 + 2 * l + 1];
+        const R zr = U[2 * l], zi = U[2 * l + 1], wr = U[6 + 2 * k], wi = U[6 + 2 * k + 1];
+        R t = xr * yr;
+        t -= xi * yi; t -= zr * wr; t += zi * wi;
+        U[12 + 2 * j] = t;
+        t = zr * wi;
+        t += zi * wr; t -= xr * yi; t -= xi * yr;
+        U[12 + 2 * j + 1] = t;
+    }
+}
+
 template <typename S, typename R, int RECON, int MU, int DAG>
 __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], long h, int r,
                                             Acc<R> *acc) {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-    const long ss = P.g.stride * P.nrhs;
+    const size_t splane = (size_t)P.g.stride * P.nrhs * 16, lplane = (size_t)P.g.stride * 16;
+    const unsigned hu = (unsigned)h;
     {
         bool wrap;
-        const long hn = neighbour<MU, +1>(P.g, h, c, wrap);
+        const unsigned hn = neighbour32<MU, +1>(P.g, hu, c, wrap);
         R psi[24];
-        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
+        bt_load<S, 24, 0>(P.f[1], splane, hn * (unsigned)P.nrhs + (unsigned)r, psi);
         cx<Acc<R>> hs[2][3], u[2][3];
         project<MU, SF>(psi, hs);
         R U[18];
-        load_link<S, R, RECON>(P.gauge_out + MU * P.dir_bytes, P.g.stride, h, U);
+        bt_load<S, RECON, 1>(P.gauge_out + MU * P.dir_bytes, lplane, hu, U);
+        if (RECON == 12) bt_rebuild_row2(U);
         su3_mul(U, hs, u);
         if (wrap) phase_mul(u, (R)P.ph[2 * MU], (R)P.ph[2 * MU + 1]);
         accumulate<MU, SF>(acc, u);
     }
     {
         bool wrap;
-        const long hn = neighbour<MU, -1>(P.g, h, c, wrap);
+        const unsigned hn = neighbour32<MU, -1>(P.g, hu, c, wrap);
         R psi[24];
-        Rec<S, 24>::template load<R, 0>(P.f[1], ss, hn * P.nrhs + r, psi);
+        bt_load<S, 24, 0>(P.f[1], splane, hn * (unsigned)P.nrhs + (unsigned)r, psi);
         cx<Acc<R>> hs[2][3], u[2][3];
         project<MU, SB>(psi, hs);
         R U[18];
-        load_link<S, R, RECON>(P.gauge_in + MU * P.dir_bytes, P.g.stride, hn, U);
+        bt_load<S, RECON, 1>(P.gauge_in + MU * P.dir_bytes, lplane, hn, U);
+        if (RECON == 12) bt_rebuild_row2(U);
         su3_adj_mul(U, hs, u);
         if (wrap) phase_mul(u, (R)P.ph[2 * MU], -(R)P.ph[2 * MU + 1]);
         accumulate<MU, SB>(acc, u);
