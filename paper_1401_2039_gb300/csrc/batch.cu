@@ -34,7 +34,15 @@ namespace wd {
 // ------------------------------------------------------------------ vector kernels
 // Element-wise kernels walk 16-byte chunks; chunk i of a problem belongs to
 // rhs i % nrhs (planes hold stride * nrhs chunks, a multiple of nrhs).
-enum BtOp { BT_XR = 0, BT_P = 1, BT_NORM = 2, BT_RESCALE = 3 };
+// BT_R:  f = {r, Ap}: r -= a Ap, |r|^2
+// BT_PX: f = {p, z, x}: x += a_x p (the step the last iteration still owes
+//        x, deferred into this pass over p, as in the single-system
+//        solver), then p = z + b p
+enum BtOp { BT_R = 0, BT_PX = 1, BT_NORM = 2, BT_RESCALE = 3 };
+
+// c + a b with one rounding where the type has a fused multiply-add
+template <typename R> __device__ __forceinline__ R bt_fma(R a, R b, R c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ df64 bt_fma<df64>(df64 a, df64 b, df64 c) { return c + a * b; }
 
 template <typename S, typename R, int OP>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtArgs a) {
@@ -42,7 +50,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtA
     __shared__ df64 wv[BT_BLOCK];
     __shared__ df64 wacc[BT_WARPS][BT_MAX_SLOTS];
     __shared__ df64 sacc[BT_MAX_SLOTS];
-    constexpr bool RED = OP == BT_XR || OP == BT_NORM;
+    constexpr bool RED = OP == BT_R || OP == BT_NORM;
     if (RED) bt_zero_sums(wacc);
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
@@ -51,30 +59,31 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_vec(const __grid_constant__ BtA
         df64 v = 0;
         if (i < P.nitems) {
             SolverScalars *s = &a.scalars[P.slot0 + (int)((unsigned)i % (unsigned)P.nrhs)];
-            if (OP == BT_XR) {          // f = {x, r, p, Ap}: x += a p, r -= a Ap, |r|^2
+            if (OP == BT_R) {           // f = {r, Ap}: r -= a Ap, |r|^2
                 const R al = (R)s->alpha;
-                R xv[C::K], rv[C::K], pv[C::K], av[C::K];
-                C::load(P.f[0], i, xv);
-                C::load(P.f[1], i, rv);
-                C::load(P.f[2], i, pv);
-                C::load(P.f[3], i, av);
+                R rv[C::K], av[C::K];
+                C::load(P.f[0], i, rv);
+                C::load(P.f[1], i, av);
                 R sq = 0;
 #pragma unroll
                 for (int k = 0; k < C::K; ++k) {
-                    xv[k] += al * pv[k];
                     rv[k] -= al * av[k];
                     sq += rv[k] * rv[k];
                 }
-                C::store(P.f[0], i, xv);
-                C::store(P.f[1], i, rv);
+                C::store(P.f[0], i, rv);
                 v = to_df(sq);
-            } else if (OP == BT_P) {    // f = {p, z}: p = z + b p
-                const R be = (R)s->beta;
-                R pv[C::K], zv[C::K];
+            } else if (OP == BT_PX) {   // f = {p, z, x}: x += a_x p, p = z + b p
+                const R ax = (R)s->alpha_x, be = (R)s->beta;
+                R pv[C::K], zv[C::K], xv[C::K];
                 C::load(P.f[0], i, pv);
                 C::load(P.f[1], i, zv);
+                C::load(P.f[2], i, xv);
 #pragma unroll
-                for (int k = 0; k < C::K; ++k) pv[k] = zv[k] + be * pv[k];
+                for (int k = 0; k < C::K; ++k) {
+                    xv[k] = bt_fma(ax, pv[k], xv[k]);
+                    pv[k] = zv[k] + be * pv[k];
+                }
+                C::store(P.f[2], i, xv);
                 C::store(P.f[0], i, pv);
             } else if (OP == BT_NORM) { // f = {v}
                 R vv[C::K];
@@ -142,7 +151,9 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_hi(const __grid_constant__ BtAr
 
 // Conversions over (site, rhs) items, with per-slot constants:
 //   CONV: f = {out (SO), in (SI)}: out = consts[0][slot] * in
-//   FOLD: f = {x_hi (H), x_lo (SI)}: x_hi += consts[1][slot] * x_lo; x_lo = 0
+//   FOLD: f = {x_hi (H), x_lo (SI), p (SI)}: x_lo += alpha_x[slot] p (the owed
+//         step, with the FMA and rounding of BT_PX), then x_hi +=
+//         consts[1][slot] * x_lo; x_lo = 0
 template <typename H, typename T> __device__ __forceinline__ H widen(T v) { return H(v); }
 template <> __device__ __forceinline__ df64 widen<df64, float>(float v) { return df64(v, 0.0f); }
 
@@ -164,11 +175,16 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_conv(const __grid_constant__ Bt
         Rec<SI, 24>::template load_coherent<T>(P.f[1], ss, i, v);
         if constexpr (FOLD != 0) {
             H hi[24];
+            T pv[24];
             Rec<H, 24>::template load_coherent<H>(P.f[0], ss, i, hi);
+            Rec<SI, 24>::template load_coherent<T>(P.f[2], ss, i, pv);
             const H is = H(a.consts[BT_MAX_SLOTS + slot]);
+            const T ax = (T)a.scalars[slot].alpha_x;
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
-                hi[k] += is * widen<H>(v[k]);
+                T xl = bt_fma(ax, pv[k], v[k]);
+                if constexpr (std::is_same<SI, __half>::value) xl = __half2float(__float2half_rn(xl));
+                hi[k] += is * widen<H>(xl);
                 v[k] = T(0);
             }
             Rec<H, 24>::store(P.f[0], ss, i, hi);
@@ -470,9 +486,11 @@ int bt_f64(wd_batch *bt, int fin, std::initializer_list<int> fields, int scale_m
     return WD_OK;
 }
 
-// lo <- consts[0] * hi  (FOLD = 0)   or   hi += consts[1] * lo, lo = 0  (FOLD = 1)
+// lo <- consts[0] * hi  (FOLD = 0)   or   lo += alpha_x p, hi += consts[1] * lo,
+// lo = 0  (FOLD = 1; the caller then zeroes alpha_x)
 int bt_conv(wd_batch *bt, bool fold, int dst, int src) {
-    BtArgs a = make_args(bt, IT_SITES, FIN_NONE, {dst, src}, SC_ONE, false, 0);
+    BtArgs a = fold ? make_args(bt, IT_SITES, FIN_NONE, {dst, src, F_PL}, SC_ONE, false, 0)
+                    : make_args(bt, IT_SITES, FIN_NONE, {dst, src}, SC_ONE, false, 0);
     const unsigned gr = grid_of(bt, a);
     cudaStream_t s = bt->stream;
     const bool df = bt->hi_prec == WD_DF64;
@@ -518,9 +536,9 @@ int bt_write(wd_batch *bt) {
 // single-system solver)
 int bt_iteration(wd_batch *bt, int p) {
     BT_TRY(bt_schur(bt, false, p, 1, F_ZL, F_RL, F_TL, FIN_BETA));
-    BT_TRY(bt_vec<BT_P>(bt, false, FIN_NONE, {F_PL, F_ZL}));
+    BT_TRY(bt_vec<BT_PX>(bt, false, FIN_NONE, {F_PL, F_ZL, F_XL}));
     BT_TRY(bt_schur(bt, false, p, 0, F_APL, F_PL, F_TL, FIN_ALPHA));
-    BT_TRY(bt_vec<BT_XR>(bt, false, FIN_NR, {F_XL, F_RL, F_PL, F_APL}));
+    BT_TRY(bt_vec<BT_R>(bt, false, FIN_NR, {F_RL, F_APL}));
     return WD_OK;
 }
 
@@ -664,6 +682,7 @@ int bt_solve_impl(wd_batch *bt, double *const *x, const double *const *b, double
             BT_TRY(bt_read(bt));
             th_valid = true;
             ru += 1;
+            for (int s = 0; s < S; ++s) bt->sc_host[s].alpha_x = 0.0;   // settled by the fold
             for (int s = 0; s < S; ++s) {
                 if (!active[s]) continue;
                 r_hi[s] = std::sqrt(bt->sc_host[s].scratch[0]);
