@@ -294,6 +294,20 @@ def test_host_memory_solve_matches_device_solve():
     res4 = op4.solve_host(torch.zeros_like(b4h).pin_memory(), b4h, tol=1e-10, guess=False)
     assert np.array_equal(res4.x.numpy(), host(dev4.x))
     op4.close()
+    # Lt = 2: six of the eight slabs are empty, and the wrap-around slice 0
+    # needs slice 1 from the last one
+    dims2 = (2, 2, 2, 2)
+    U2, _ = fields(dims2)
+    b2 = syn.gaussian_spinor(syn.volume(dims2), 2)
+    op2 = make_op(dims2, kappa, PHASES["twisted"], "f32", 18, U2)
+    dev2 = op2.solve(cuda(b2), tol=1e-10)
+    b2h = torch.from_numpy(b2).pin_memory()
+    res2 = op2.solve_host(torch.zeros_like(b2h).pin_memory(), b2h, tol=1e-10, guess=False)
+    assert np.array_equal(res2.x.numpy(), host(dev2.x))
+    x2 = res2.x.numpy()
+    r2 = np.linalg.norm(b2 - oracle.apply(x2, U2, dims2, kappa, PHASES["twisted"])) / np.linalg.norm(b2)
+    assert r2 <= 1.05e-10, r2
+    op2.close()
 
 
 def test_resident_dslash_matches_canonical():
