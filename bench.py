@@ -397,14 +397,18 @@ def batch_measurement(prec: str, recon: int, recovery=("reliable", 0.1)):
     ph = syn.workloads.APBC_T
     out = {"storage": prec, "link_reals": recon, "recovery": list(recovery)}
 
-    def timed(fn, reps=2):
+    def timed(fn, reps=3):
+        # median wall time of reps runs after one warm-up run (the solves
+        # synchronise with the host, so host jitter enters single runs)
         fn()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ts = []
         for _ in range(reps):
+            t0 = time.perf_counter()
             r = fn()
-        torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / reps * 1e3, r
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts)), r
 
     dims = (24, 24, 24, 48)
     op = WilsonDirac(dims, 0.12, ph, prec=prec, recon=recon)
@@ -414,7 +418,7 @@ def batch_measurement(prec: str, recon: int, recovery=("reliable", 0.1)):
                                    for c in range(3) for s in range(4)])).cuda()
     bt = WilsonBatch([op], [12])
     tb, (_, _, infos) = timed(lambda: bt.solve([B], tol=1e-10))
-    ts, _ = timed(lambda: [op.solve(B[k].contiguous(), tol=1e-10) for k in range(12)], reps=1)
+    ts, _ = timed(lambda: [op.solve(B[k].contiguous(), tol=1e-10) for k in range(12)])
     out["point_sources_24x24x24x48"] = {
         "systems": 12, "batched_ms": tb, "sequential_ms": ts, "speedup": ts / tb,
         "iters": max(i["iters"] for i in infos), "refreshes": infos[0]["reliable_updates"],
@@ -433,7 +437,7 @@ def batch_measurement(prec: str, recon: int, recovery=("reliable", 0.1)):
     bt = WilsonBatch(ops, [4, 4, 4])
     tb, (_, _, infos) = timed(lambda: bt.solve(Bs, tol=1e-10))
     ts, _ = timed(lambda: [o.solve(b[r].contiguous(), tol=1e-10) for o, b in zip(ops, Bs)
-                           for r in range(4)], reps=1)
+                           for r in range(4)])
     out["uneven_8^4_12^3x24_16^3x32_x4"] = {
         "systems": 12, "batched_ms": tb, "sequential_ms": ts, "speedup": ts / tb,
         "max_true_rel_resid": max(i["true_rel_resid"] for i in infos)}

@@ -394,7 +394,9 @@ BtArgs make_args(wd_batch *bt, int kind, int fin, std::initializer_list<int> fie
         for (int fid : fields) P.f[k++] = bt->fl[p].f[fid];
         P.scale = scale_of(op, scale_mode);
         memcpy(P.ph, op->phase, sizeof(P.ph));
+        P.phase_on = phase_mask(op->phase);
         P.nrhs = bt->nrhs[p];
+        P.div_nrhs = make_divisor((unsigned)P.nrhs);
         P.slot0 = bt->slot0[p];
         P.tile0 = tile;
         P.nitems = items_of(bt, p, kind);

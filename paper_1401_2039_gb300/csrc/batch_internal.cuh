@@ -25,7 +25,9 @@ struct BtProb {
     void *f[4];              // fields of this launch (meaning set by the kernel)
     double scale;            // per-problem coefficient
     double ph[8];            // boundary phases
+    unsigned phase_on;       // bit mu set: direction mu's phase is not 1
     int nrhs;
+    Divisor div_nrhs;        // by nrhs (item -> site)
     int slot0;               // first solver slot of the problem
     long tile0;              // first tile of the problem
     long nitems;             // work items of the problem
@@ -173,8 +175,9 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
         bt_load<S, RECON, 1>(P.gauge_out + MU * P.dir_bytes, lplane, hu, U);
         if (RECON == 12) bt_rebuild_row2(U);
         su3_mul(U, hs, u);
-        if (wrap) phase_mul(u, (R)P.ph[2 * MU], (R)P.ph[2 * MU + 1]);
-        accumulate<MU, SF>(acc, u);
+        if (wrap && (P.phase_on >> MU & 1u)) phase_mul(u, (R)P.ph[2 * MU], (R)P.ph[2 * MU + 1]);
+        if constexpr (std::is_same<Acc<R>, float>::value) accumulate_x2<MU, SF>(acc, u);
+        else accumulate<MU, SF>(acc, u);
     }
     {
         bool wrap;
@@ -187,8 +190,9 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
         bt_load<S, RECON, 1>(P.gauge_in + MU * P.dir_bytes, lplane, hn, U);
         if (RECON == 12) bt_rebuild_row2(U);
         su3_adj_mul(U, hs, u);
-        if (wrap) phase_mul(u, (R)P.ph[2 * MU], -(R)P.ph[2 * MU + 1]);
-        accumulate<MU, SB>(acc, u);
+        if (wrap && (P.phase_on >> MU & 1u)) phase_mul(u, (R)P.ph[2 * MU], -(R)P.ph[2 * MU + 1]);
+        if constexpr (std::is_same<Acc<R>, float>::value) accumulate_x2<MU, SB>(acc, u);
+        else accumulate<MU, SB>(acc, u);
     }
 }
 
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_batch(const __grid_const
         df64 v = 0;
         if (item < P.nitems) {
             const int nr = P.nrhs;
-            const unsigned hu = (unsigned)item / (unsigned)nr;   // items < 2^31
+            const unsigned hu = udiv((unsigned)item, P.div_nrhs);   // items < 2^31
             const long h = hu;
             const int r = (int)((unsigned)item - hu * (unsigned)nr);
             int c[4];
@@ -220,17 +224,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_batch(const __grid_const
             for (int k = 0; k < 24; ++k) acc[k] = 0;
             if constexpr (std::is_same<S, df64>::value) {
                 df_hops<DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                             P.g.stride * nr, nr, r, h, c, acc);
+                             P.g.stride * nr, nr, r, h, c, acc, nullptr, P.phase_on);
             } else if constexpr (std::is_same<S, __half>::value) {
                 const long ss = P.g.stride * nr;
                 hop_pair_h2<RECON, 0, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
+                                           ss, nr, r, c, h, acc, P.phase_on);
                 hop_pair_h2<RECON, 1, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
+                                           ss, nr, r, c, h, acc, P.phase_on);
                 hop_pair_h2<RECON, 2, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
+                                           ss, nr, r, c, h, acc, P.phase_on);
                 hop_pair_h2<RECON, 3, DAG>(P.g, P.gauge_out, P.gauge_in, P.dir_bytes, P.ph, P.f[1],
-                                           ss, nr, r, c, h, acc);
+                                           ss, nr, r, c, h, acc, P.phase_on);
             } else {
                 bt_hop_pair<S, R, RECON, 0, DAG>(P, c, h, r, acc);
                 bt_hop_pair<S, R, RECON, 1, DAG>(P, c, h, r, acc);
@@ -243,18 +247,36 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_batch(const __grid_const
             if (XPAY) {
                 R xv[24];
                 Rec<S, 24>::template load<R, 0>(P.f[2], ss, item, xv);
+                if constexpr (std::is_same<R, float>::value) {
 #pragma unroll
-                for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + sc * acc[k]);
+                    for (int k = 0; k < 24; k += 2)
+                        scale_add_x2(o[k], o[k + 1], acc[k], acc[k + 1], sc, xv[k], xv[k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 24; ++k) o[k] = settle(xv[k] + sc * acc[k]);
+                }
             } else {
+                if constexpr (std::is_same<R, float>::value) {
 #pragma unroll
-                for (int k = 0; k < 24; ++k) o[k] = settle(sc * acc[k]);
+                    for (int k = 0; k < 24; k += 2) scale_x2(o[k], o[k + 1], acc[k], acc[k + 1], sc);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 24; ++k) o[k] = settle(sc * acc[k]);
+                }
             }
             Rec<S, 24>::store(P.f[0], ss, item, o);
             if (NORM) {
-                R sq = 0;
+                if constexpr (std::is_same<R, float>::value) {
+                    float sq = 0, sq1 = 0;
 #pragma unroll
-                for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
-                v = to_df(sq);
+                    for (int k = 0; k < 24; k += 2) sq_acc_x2(sq, sq1, o[k], o[k + 1]);
+                    v = to_df(sq + sq1);
+                } else {
+                    R sq = 0;
+#pragma unroll
+                    for (int k = 0; k < 24; ++k) sq += o[k] * o[k];
+                    v = to_df(sq);
+                }
             }
         }
         if (NORM) bt_warp_sums<BLOCK>(v, P, item0, wv, wacc);

@@ -98,6 +98,70 @@ __device__ __forceinline__ void accumulate(A *acc, const cx<A> u[2][3]) {
     }
 }
 
+// (a0, a1) +-= (b0, b1) as one packed FP32 pair operation (add.rn.f32x2 /
+// sub.rn.f32x2, each lane rounded as the scalar add)
+template <bool SUB>
+__device__ __forceinline__ void acc_x2(float &a0, float &a1, float b0, float b1) {
+    if constexpr (SUB)
+        asm("{\n\t.reg .b64 a, b;\n\tmov.b64 a, {%0, %1};\n\tmov.b64 b, {%2, %3};\n\t"
+            "sub.rn.f32x2 a, a, b;\n\tmov.b64 {%0, %1}, a;\n\t}"
+            : "+f"(a0), "+f"(a1) : "f"(b0), "f"(b1));
+    else
+        asm("{\n\t.reg .b64 a, b;\n\tmov.b64 a, {%0, %1};\n\tmov.b64 b, {%2, %3};\n\t"
+            "add.rn.f32x2 a, a, b;\n\tmov.b64 {%0, %1}, a;\n\t}"
+            : "+f"(a0), "+f"(a1) : "f"(b0), "f"(b1));
+}
+
+// (d0, d1) = s (a0, a1) [+ (x0, x1)] as one packed FP32 pair operation
+__device__ __forceinline__ void scale_x2(float &d0, float &d1, float a0, float a1, float s) {
+    asm("{\n\t.reg .b64 a, s, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 s, {%4, %4};\n\t"
+        "mul.rn.f32x2 d, s, a;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(d0), "=f"(d1) : "f"(a0), "f"(a1), "f"(s));
+}
+__device__ __forceinline__ void scale_add_x2(float &d0, float &d1, float a0, float a1, float s,
+                                             float x0, float x1) {
+    asm("{\n\t.reg .b64 a, s, x, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 s, {%4, %4};\n\t"
+        "mov.b64 x, {%5, %6};\n\tfma.rn.f32x2 d, s, a, x;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(d0), "=f"(d1) : "f"(a0), "f"(a1), "f"(s), "f"(x0), "f"(x1));
+}
+
+// (q0, q1) += (a0, a1)^2 elementwise, one packed FP32 pair FMA
+__device__ __forceinline__ void sq_acc_x2(float &q0, float &q1, float a0, float a1) {
+    asm("{\n\t.reg .b64 a, q;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 q, {%0, %1};\n\t"
+        "fma.rn.f32x2 q, a, a, q;\n\tmov.b64 {%0, %1}, q;\n\t}"
+        : "+f"(q0), "+f"(q1) : "f"(a0), "f"(a1));
+}
+
+// accumulate<MU, SGN> with the complex additions of real sign as packed pair
+// operations; the +-i terms (directions 0 and 2) stay scalar.  Same sums,
+// same roundings.
+template <int MU, int SGN>
+__device__ __forceinline__ void accumulate_x2(float *acc, const cx<float> u[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float *a = acc + 8 * c;
+        acc_x2<false>(a[0], a[1], u[0][c].re, u[0][c].im);
+        acc_x2<false>(a[2], a[3], u[1][c].re, u[1][c].im);
+        if (MU == 1) {          // spin 2 += SGN u1, spin 3 -= SGN u0
+            acc_x2<(SGN < 0)>(a[4], a[5], u[1][c].re, u[1][c].im);
+            acc_x2<(SGN > 0)>(a[6], a[7], u[0][c].re, u[0][c].im);
+        } else if (MU == 3) {   // spin 2 += SGN u0, spin 3 += SGN u1
+            acc_x2<(SGN < 0)>(a[4], a[5], u[0][c].re, u[0][c].im);
+            acc_x2<(SGN < 0)>(a[6], a[7], u[1][c].re, u[1][c].im);
+        } else {
+            // MU 0: spin 2 += -SGN i u1, spin 3 += -SGN i u0;
+            // MU 2: spin 2 += -SGN i u0, spin 3 += SGN i u1;  i v = (-v.im, v.re)
+            const cx<float> v2 = MU == 0 ? u[1][c] : u[0][c];
+            const cx<float> v3 = MU == 0 ? u[0][c] : u[1][c];
+            constexpr bool n3 = MU == 0 ? SGN > 0 : SGN < 0;   // spin 3 coefficient is -i
+            if (SGN > 0) { a[4] += v2.im; a[5] -= v2.re; }
+            else         { a[4] -= v2.im; a[5] += v2.re; }
+            if (n3) { a[6] += v3.im; a[7] -= v3.re; }
+            else    { a[6] -= v3.im; a[7] += v3.re; }
+        }
+    }
+}
+
 // Link as 18 reals (row-major, re/im); 12-real records rebuild row 2.
 template <typename S, typename R, int RECON>
 __device__ __forceinline__ void load_link(const void *base, long stride, long h, R *U) {
@@ -185,6 +249,7 @@ template <typename R> struct DslashArgs {
     const void *x;
     R scale;
     R ph[8];
+    unsigned phase_on;       // bit mu set: the boundary phase of direction mu is not 1
     int parity;              // output parity
     Reduction red;
     R twist;                 // twisted mass factor t (twist_on != 0)
@@ -253,8 +318,9 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
         R U[18];
         load_link<S, R, RECON>(a.gauge_out + MU * a.dir_bytes, a.g.stride, h, U);
         su3_mul(U, hs, u);
-        if (wrap) phase_mul(u, a.ph[2 * MU], a.ph[2 * MU + 1]);
-        accumulate<MU, SF>(acc, u);
+        if (wrap && (a.phase_on >> MU & 1u)) phase_mul(u, a.ph[2 * MU], a.ph[2 * MU + 1]);
+        if constexpr (std::is_same<Acc<R>, float>::value) accumulate_x2<MU, SF>(acc, u);
+        else accumulate<MU, SF>(acc, u);
     }
     // backward hop: U_mu(x - mu)^dag in(x - mu)
     {
@@ -267,8 +333,9 @@ __device__ __forceinline__ void hop_pair(const DslashArgs<R> &a, const int c[4],
         R U[18];
         load_link<S, R, RECON>(a.gauge_in + MU * a.dir_bytes, a.g.stride, hn, U);
         su3_adj_mul(U, hs, u);
-        if (wrap) phase_mul(u, a.ph[2 * MU], -a.ph[2 * MU + 1]);
-        accumulate<MU, SB>(acc, u);
+        if (wrap && (a.phase_on >> MU & 1u)) phase_mul(u, a.ph[2 * MU], -a.ph[2 * MU + 1]);
+        if constexpr (std::is_same<Acc<R>, float>::value) accumulate_x2<MU, SB>(acc, u);
+        else accumulate<MU, SB>(acc, u);
     }
 }
 
@@ -309,7 +376,6 @@ WD_MIXED_FMA(mf_hl, "a1", "b0")
 WD_MIXED_FMA(mf_hh, "a1", "b1")
 #undef WD_MIXED_FMA
 
-__device__ __forceinline__ uint32_t h2_neg(uint32_t a) { return a ^ 0x80008000u; }
 
 // the packed two-element type of HT, and its words
 template <typename HT> struct Pair2;
@@ -327,6 +393,17 @@ __device__ __forceinline__ typename Pair2<HT>::T as_p2(uint32_t a) {
 }
 template <typename P2> __device__ __forceinline__ uint32_t as_u32(P2 a) {
     return *reinterpret_cast<uint32_t *>(&a);
+}
+
+// -a on both halves of a packed word, written as the type's own negation so
+// that the compiler can fold it into the consuming multiply-add
+template <typename HT> __device__ __forceinline__ uint32_t h2_neg(uint32_t a) {
+    uint32_t d;
+    if constexpr (std::is_same<HT, __half>::value)
+        asm("neg.f16x2 %0, %1;" : "=r"(d) : "r"(a));
+    else
+        asm("neg.bf16x2 %0, %1;" : "=r"(d) : "r"(a));
+    return d;
 }
 
 // p + F q on packed complex words (HT pairs), F = +1, -1, +i, -i (codes 0..3)
@@ -375,7 +452,7 @@ __device__ __forceinline__ void load_link_h2(const char *base, long stride, long
         for (int j = 0; j < 3; ++j) {
             const int k = (j + 1) % 3, l = (j + 2) % 3;
             const uint32_t x = U[k], y = U[3 + l], z = U[l], w = U[3 + k];
-            const uint32_t yn = h2_neg(y), wn = h2_neg(w);
+            const uint32_t yn = h2_neg<HT>(y), wn = h2_neg<HT>(w);
             float re = mf_ll<HT>(x, y, 0.0f);
             re = mf_hh<HT>(x, yn, re);
             re = mf_ll<HT>(z, wn, re);
@@ -397,7 +474,7 @@ __device__ __forceinline__ void su3_mul_h2(const uint32_t U[9], const uint32_t h
     for (int k = 0; k < 2; ++k) {
         uint32_t hn[3];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) hn[b] = h2_neg(h[k][b]);
+        for (int b = 0; b < 3; ++b) hn[b] = h2_neg<HT>(h[k][b]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float re = mf_ll<HT>(U[3 * a], h[k][0], 0.0f);
@@ -424,7 +501,7 @@ __device__ __forceinline__ void su3_adj_mul_h2(const uint32_t U[9], const uint32
     for (int k = 0; k < 2; ++k) {
         uint32_t hn[3];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) hn[b] = h2_neg(h[k][b]);
+        for (int b = 0; b < 3; ++b) hn[b] = h2_neg<HT>(h[k][b]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float re = mf_ll<HT>(U[a], h[k][0], 0.0f);
@@ -445,12 +522,14 @@ __device__ __forceinline__ void su3_adj_mul_h2(const uint32_t U[9], const uint32
 
 // acc += the forward and backward hops in direction MU.  The input field
 // holds nrhs right-hand sides with the rhs index innermost (site s, rhs r at
-// record s * nrhs + r of plane stride in_stride); ph: the boundary phases.
+// record s * nrhs + r of plane stride in_stride); ph: the boundary phases,
+// phase_on: bit mu clear when direction mu's phase is exactly 1 (skipped).
 template <int RECON, int MU, int DAG, typename PH>
 __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out,
                                             const char *gauge_in, size_t dir_bytes, const PH *ph,
                                             const void *in, long in_stride, int nrhs, int r,
-                                            const int c[4], long h, float *acc) {
+                                            const int c[4], long h, float *acc,
+                                            unsigned phase_on) {
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
     const float pr = (float)ph[2 * MU], pi = (float)ph[2 * MU + 1];
@@ -465,8 +544,8 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
         load_link_h2<__half, RECON>(gauge_out + MU * dir_bytes, g.stride, h, U);
         cx<float> u[2][3];
         su3_mul_h2<__half>(U, hs, u);
-        if (wrap) phase_mul(u, pr, pi);
-        accumulate<MU, SF>(acc, u);
+        if (wrap && (phase_on >> MU & 1u)) phase_mul(u, pr, pi);
+        accumulate_x2<MU, SF>(acc, u);
     }
     {
         bool wrap;
@@ -479,8 +558,8 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
         load_link_h2<__half, RECON>(gauge_in + MU * dir_bytes, g.stride, hn, U);
         cx<float> u[2][3];
         su3_adj_mul_h2<__half>(U, hs, u);
-        if (wrap) phase_mul(u, pr, -pi);
-        accumulate<MU, SB>(acc, u);
+        if (wrap && (phase_on >> MU & 1u)) phase_mul(u, pr, -pi);
+        accumulate_x2<MU, SB>(acc, u);
     }
 }
 
@@ -574,7 +653,7 @@ __device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, const
         for (int j = 0; j < 3; ++j) {
             const int k = (j + 1) % 3, l = (j + 2) % 3;
             const uint32_t x = U[k], y = U[3 + l], z = U[l], w = U[3 + k];
-            const uint32_t yn = h2_neg(y), wn = h2_neg(w);
+            const uint32_t yn = h2_neg<HT>(y), wn = h2_neg<HT>(w);
             float re = mf_ll<HT>(x, y, 0.0f);
             re = mf_hh<HT>(x, yn, re);
             re = mf_ll<HT>(z, wn, re);
@@ -591,11 +670,11 @@ __device__ __forceinline__ void compute_hop_h2(const DslashArgs<float> &a, const
     cx<float> u[2][3];
     if (DIR > 0) su3_mul_h2<HT>(U, hs, u);
     else su3_adj_mul_h2<HT>(U, hs, u);
-    if (wrap) {
+    if (wrap && (a.phase_on >> MU & 1u)) {   // a phase of exactly 1 is skipped
         const float pr = (float)a.ph[2 * MU], pi = (float)a.ph[2 * MU + 1];
         phase_mul(u, pr, DIR > 0 ? pi : -pi);
     }
-    accumulate<MU, S>(acc, u);
+    accumulate_x2<MU, S>(acc, u);
 }
 
 // ---- pipelined: spinor and link words of the next hop in registers
@@ -759,7 +838,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
             // time: only one plane's inputs and outputs are live, which keeps
             // the xpay and norm variants within the register cap
             constexpr int K = 16 / (int)sizeof(S);
-            R sq = 0;
+            R sq = 0, sq1 = 0;   // FP32: even and odd reals in a packed pair
 #pragma unroll
             for (int j = 0; j < 24 / K; ++j) {
                 R ov[K];
@@ -769,11 +848,24 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
                     const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
                     Words<S, R>::unpack(ww, xv, K);
                     if (a.twist_on) twist_reals<K>(xv, j * K, a.twist);
+                    if constexpr (std::is_same<R, float>::value) {
 #pragma unroll
-                    for (int t = 0; t < K; ++t) ov[t] = settle(xv[t] + a.scale * acc[j * K + t]);
+                        for (int t = 0; t < K; t += 2)
+                            scale_add_x2(ov[t], ov[t + 1], acc[j * K + t], acc[j * K + t + 1],
+                                         a.scale, xv[t], xv[t + 1]);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < K; ++t) ov[t] = settle(xv[t] + a.scale * acc[j * K + t]);
+                    }
                 } else {
+                    if constexpr (std::is_same<R, float>::value) {
 #pragma unroll
-                    for (int t = 0; t < K; ++t) ov[t] = settle(a.scale * acc[j * K + t]);
+                        for (int t = 0; t < K; t += 2)
+                            scale_x2(ov[t], ov[t + 1], acc[j * K + t], acc[j * K + t + 1], a.scale);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < K; ++t) ov[t] = settle(a.scale * acc[j * K + t]);
+                    }
                     if (a.twist_on) twist_reals<K>(ov, j * K, -a.twist);
                 }
                 uint32_t ow[4];
@@ -781,11 +873,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
                 st_v4((char *)a.out + ((long)j * a.g.stride + h) * 16,
                       make_uint4(ow[0], ow[1], ow[2], ow[3]));
                 if (NORM) {
+                    if constexpr (std::is_same<R, float>::value) {
 #pragma unroll
-                    for (int t = 0; t < K; ++t) sq += ov[t] * ov[t];
+                        for (int t = 0; t < K; t += 2) sq_acc_x2(sq, sq1, ov[t], ov[t + 1]);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < K; ++t) sq += ov[t] * ov[t];
+                    }
                 }
             }
-            if (NORM) nrm[i] = to_df(sq);
+            if (NORM) {
+                if constexpr (std::is_same<R, float>::value) nrm[i] = to_df(sq + sq1);
+                else nrm[i] = to_df(sq);
+            }
         }
     }
     if (NORM) warp_partials<BLOCK, SPT>(nrm, a.g.vh, a.red.partials);
@@ -851,6 +951,7 @@ cudaError_t launch_dslash_t(const DslashLaunch &L, cudaStream_t s) {
     a.x = L.x;
     a.scale = (R)L.scale;
     for (int i = 0; i < 8; ++i) a.ph[i] = (R)L.phase[i];
+    a.phase_on = phase_mask(L.phase);
     a.parity = L.out_parity;
     if (L.red) a.red = *L.red;
     else a.red = Reduction{nullptr, nullptr, nullptr, FIN_NONE};

@@ -78,11 +78,13 @@ __device__ __forceinline__ void df_stage_link(const Geom &g, const char *gauge_o
 // site s, rhs r at record s * nrhs + r of plane stride in_stride.  ph: the
 // boundary phases (re, im per direction), double or df64.  stage (BLOCK
 // threads, 2 x 9 x BLOCK chunks of shared memory): links staged one hop ahead.
+// phase_on: bit mu clear when direction mu's phase is exactly 1 (skipped).
 template <int DAG, int BLOCK = 0, typename PH>
 __device__ __forceinline__ void df_hops(const Geom &g, const char *gauge_out, const char *gauge_in,
                                         size_t dir_bytes, const PH *ph, const void *in,
                                         long in_stride, int nrhs, int r, long h, const int c[4],
-                                        dfl acc[24], uint4 *stage = nullptr) {
+                                        dfl acc[24], uint4 *stage = nullptr,
+                                        unsigned phase_on = 0xFu) {
     if constexpr (BLOCK > 0) df_stage_link<BLOCK>(g, gauge_out, gauge_in, dir_bytes, h, c, 0, stage);
 #pragma unroll 1
     for (int hop = 0; hop < 8; ++hop) {
@@ -144,7 +146,7 @@ __device__ __forceinline__ void df_hops(const Geom &g, const char *gauge_out, co
         }
         cdf u[2][3];
         su3_mul(U, hs, u);
-        if (wrap) {
+        if (wrap && (phase_on >> mu & 1u)) {
             const df64 pr = df64(ph[2 * mu]), pi = df64(ph[2 * mu + 1]);
             phase_mul(u, pr, fwd ? pi : -pi);
         }

@@ -21,10 +21,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_df(const DslashArgs<df64
         if constexpr (STAGE) {
             __shared__ uint4 stage[2 * DF_LINK_PLANES * BLOCK];
             df_hops<DAG, BLOCK>(a.g, a.gauge_out, a.gauge_in, a.dir_bytes, a.ph, a.in, a.g.stride,
-                                1, 0, h, c, acc, stage);
+                                1, 0, h, c, acc, stage, a.phase_on);
         } else {
             df_hops<DAG>(a.g, a.gauge_out, a.gauge_in, a.dir_bytes, a.ph, a.in, a.g.stride, 1, 0,
-                         h, c, acc);
+                         h, c, acc, nullptr, a.phase_on);
         }
         df64 o[24];
         if (EPI == EPI_XPAY) {
@@ -83,6 +83,7 @@ cudaError_t launch_dslash_df64_r18(const DslashLaunch &L, cudaStream_t s) {
     a.x = L.x;
     a.scale = df64(L.scale);
     for (int i = 0; i < 8; ++i) a.ph[i] = df64(L.phase[i]);
+    a.phase_on = phase_mask(L.phase);
     a.parity = L.out_parity;
     a.red = L.red ? *L.red : Reduction{nullptr, nullptr, nullptr, FIN_NONE};
     a.twist = df64(L.twist);

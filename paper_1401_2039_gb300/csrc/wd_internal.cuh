@@ -285,6 +285,27 @@ template <typename S, typename R> struct Chunk16 {
 };
 
 // ---------------------------------------------------------------- geometry
+// Division of an index n < 2^31 by an invariant d >= 1 as one widening
+// multiply and a shift (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994, Thm. 4.2 with N = 31 bits):
+// with l = ceil(log2 d) and m = floor(2^(31 + l) / d) + 1, 2^(31+l) < m d <=
+// 2^(31+l) + 2^l, so floor(n / d) = floor(m n / 2^(31+l)); m < 2^32.
+struct Divisor {
+    unsigned m;     // multiplier
+    unsigned s;     // shift, 31 + l
+};
+
+inline Divisor make_divisor(unsigned d) {
+    unsigned l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    const unsigned s = 31 + l;
+    return Divisor{(unsigned)((1ull << s) / d + 1), s};
+}
+
+__host__ __device__ __forceinline__ unsigned udiv(unsigned n, Divisor d) {
+    return (unsigned)(((unsigned long long)n * d.m) >> d.s);
+}
+
 struct Geom {
     int L[4];       // Lx, Ly, Lz, Lt
     int hx;         // Lx / 2
@@ -295,6 +316,7 @@ struct Geom {
     // the periodic boundary, (L_mu - 1) * step
     unsigned step[4];
     unsigned back[4];
+    Divisor div_hx, div_y, div_z;   // by hx, L[1], L[2] (site_coords)
 };
 
 // Geometry of a dims[0] x ... x dims[3] lattice (dims[0] even) whose fields
@@ -311,6 +333,9 @@ inline Geom make_geom(const int dims[4], long stride) {
         g.back[m] = (unsigned)(dims[m] - 1) * st;
         st *= (unsigned)dims[m];
     }
+    g.div_hx = make_divisor((unsigned)g.hx);
+    g.div_y = make_divisor((unsigned)dims[1]);
+    g.div_z = make_divisor((unsigned)dims[2]);
     return g;
 }
 
@@ -318,11 +343,11 @@ inline Geom make_geom(const int dims[4], long stride) {
 // volume is limited to 2^31 sites).
 __device__ __forceinline__ void site_coords(const Geom &g, long h, int p, int c[4]) {
     const unsigned hu = (unsigned)h;
-    unsigned r = hu / (unsigned)g.hx;
+    unsigned r = udiv(hu, g.div_hx);
     const int xh = (int)(hu - r * (unsigned)g.hx);
-    const unsigned r1 = r / (unsigned)g.L[1];
+    const unsigned r1 = udiv(r, g.div_y);
     c[1] = (int)(r - r1 * (unsigned)g.L[1]);
-    const unsigned r2 = r1 / (unsigned)g.L[2];
+    const unsigned r2 = udiv(r1, g.div_z);
     c[2] = (int)(r1 - r2 * (unsigned)g.L[2]);
     c[3] = (int)r2;
     c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
@@ -568,6 +593,15 @@ struct DslashLaunch {
     // with a fused norm covers every site
     long h_begin = 0, h_end = -1;
 };
+
+// bit mu set unless direction mu's boundary phase (re, im) is exactly (1, 0):
+// the hop kernels skip the multiplication by a phase of 1
+inline unsigned phase_mask(const double phase[8]) {
+    unsigned m = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        if (phase[2 * mu] != 1.0 || phase[2 * mu + 1] != 0.0) m |= 1u << mu;
+    return m;
+}
 
 // dslash.cu
 cudaError_t launch_dslash(const DslashLaunch &L, int prec, cudaStream_t s);
