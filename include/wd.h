@@ -225,13 +225,16 @@ int wd_batch_dslash_resident(wd_batch *bt, int out_parity, int dagger);
  * when the batch was created (FP32/FP16 storage; every candidate is timed on
  * the batch's own lattices and right-hand sides): variant 0 = the plain hop,
  * 1 = the xpay hop with the fused per-system norms that ends each Schur
- * operator of the lockstep CGNR.  us (optional, n entries) receives each
- * candidate's microseconds per launch; block (threads per block = items per
- * tile), min_blocks (resident blocks per SM the register cap is set for) and
- * grid (the persistent grid launched: the kernel's resident capacity on this
- * GPU, at most the tile count) describe the chosen one.  Returns its index,
- * or -1 for a null batch or another variant.  WD_BATCH_CFG=k forces
- * candidate k, WD_TUNE=0 keeps candidate 0. */
+ * operator of the lockstep CGNR.  There are 9 candidates: 0-4 take one
+ * (site, rhs) item per thread, 5-8 two (rhs r and r + 1 of one site, FP32
+ * storage with an even number of right-hand sides in every problem; 0 us
+ * where they do not apply).  us (optional, n entries) receives each
+ * candidate's microseconds per launch; block (threads per block), min_blocks
+ * (resident blocks per SM the register cap is set for) and grid (the
+ * persistent grid launched: the kernel's resident capacity on this GPU, at
+ * most the tile count) describe the chosen one.  Returns its index, or -1
+ * for a null batch or another variant.  WD_BATCH_CFG=k forces candidate k
+ * (where it applies), WD_TUNE=0 keeps candidate 0. */
 int wd_batch_tuning(const wd_batch *bt, int variant, double *us, int n, int *block,
                     int *min_blocks, int *grid);
 /* x[k] (in: initial guesses or zeros, out: solutions), b[k]: device,

@@ -419,8 +419,20 @@ unsigned grid_of(const wd_batch *bt, const BtArgs &a) {
     return (unsigned)std::max<long>(1, std::min<long>(a.ntiles, bt->vec_grid));
 }
 
+// items per tile of the storage-precision hop in configuration cfg
 int bt_hop_block(int prec, int cfg) {
-    return (prec == WD_F32 || prec == WD_F16) ? BT_CFGS[cfg].block : 128;
+    if (prec != WD_F32 && prec != WD_F16) return 128;
+    return BT_CFGS[cfg].block * (BT_CFGS[cfg].pair ? 2 : 1);
+}
+
+// whether configuration cfg can run this batch: pair items need FP32
+// storage and an even number of right-hand sides in every problem
+bool bt_cfg_applies(const wd_batch *bt, int cfg) {
+    if (!BT_CFGS[cfg].pair) return true;
+    if (bt->prec != WD_F32) return false;
+    for (int p = 0; p < bt->nprob; ++p)
+        if (bt->nrhs[p] % 2) return false;
+    return true;
 }
 
 cudaError_t bt_launch_hop(int prec, int recon, int dagger, int variant, int cfg, const BtArgs &a,
@@ -816,7 +828,7 @@ static int bt_tune(wd_batch *bt) {
     const char *tune = getenv("WD_TUNE");
     if (force || (tune && tune[0] == '0')) {
         const int k = force ? atoi(force) : 0;
-        bt->cfg[0] = bt->cfg[1] = (k >= 0 && k < N_BT_CFG) ? k : 0;
+        bt->cfg[0] = bt->cfg[1] = (k >= 0 && k < N_BT_CFG && bt_cfg_applies(bt, k)) ? k : 0;
         return WD_OK;
     }
     cudaEvent_t e0, e1;
@@ -826,6 +838,8 @@ static int bt_tune(wd_batch *bt) {
     for (int v = 0; v < 2 && rc == WD_OK; ++v) {
         float best = 1e30f;
         for (int k = 0; k < N_BT_CFG && rc == WD_OK; ++k) {
+            bt->tune_us[v][k] = 0.0;
+            if (!bt_cfg_applies(bt, k)) continue;
             auto launch = [&](int par) {
                 return v == BTV_PLAIN
                            ? bt_hop(bt, false, par, 0, F_IO1, F_IO0, -1, SC_ONE, FIN_NONE, k,

@@ -196,17 +196,293 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
     }
 }
 
+// ---- two right-hand sides per thread (FP32 storage and arithmetic)
+// The pair item (site, rhs r, r + 1) shares the neighbour indices, the link
+// loads and the row-2 rebuild.  Each projected half spinor, SU(3) product and
+// accumulation is one packed FP32 pair operation over the two right-hand
+// sides (lane 0: rhs r, lane 1: rhs r + 1), each lane rounded as the scalar
+// operation of bt_hop_pair in the same order.
+typedef unsigned long long f2;   // two FP32 lanes in one 64-bit register pair
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// a b + c, one rounding per lane
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_neg(f2 a) { return f2_mul(a, f2_pack(-1.0f, -1.0f)); }
+__device__ __forceinline__ f2 f2_bcast(float a) { return f2_pack(a, a); }
+
+struct c2 {
+    f2 re, im;
+};
+
+// acc += (1 + SGN gamma_MU) expanded from u, lane-wise as accumulate<MU, SGN>
+template <int MU, int SGN>
+__device__ __forceinline__ void accumulate2(f2 *acc, const c2 u[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        f2 *q = acc + 8 * c;
+        q[0] = f2_add(q[0], u[0][c].re); q[1] = f2_add(q[1], u[0][c].im);
+        q[2] = f2_add(q[2], u[1][c].re); q[3] = f2_add(q[3], u[1][c].im);
+        if (MU == 1) {          // spin 2 += SGN u1, spin 3 -= SGN u0
+            if (SGN > 0) {
+                q[4] = f2_add(q[4], u[1][c].re); q[5] = f2_add(q[5], u[1][c].im);
+                q[6] = f2_sub(q[6], u[0][c].re); q[7] = f2_sub(q[7], u[0][c].im);
+            } else {
+                q[4] = f2_sub(q[4], u[1][c].re); q[5] = f2_sub(q[5], u[1][c].im);
+                q[6] = f2_add(q[6], u[0][c].re); q[7] = f2_add(q[7], u[0][c].im);
+            }
+        } else if (MU == 3) {   // spin 2 += SGN u0, spin 3 += SGN u1
+            if (SGN > 0) {
+                q[4] = f2_add(q[4], u[0][c].re); q[5] = f2_add(q[5], u[0][c].im);
+                q[6] = f2_add(q[6], u[1][c].re); q[7] = f2_add(q[7], u[1][c].im);
+            } else {
+                q[4] = f2_sub(q[4], u[0][c].re); q[5] = f2_sub(q[5], u[0][c].im);
+                q[6] = f2_sub(q[6], u[1][c].re); q[7] = f2_sub(q[7], u[1][c].im);
+            }
+        } else {
+            // MU 0: spin 2 += -SGN i u1, spin 3 += -SGN i u0;
+            // MU 2: spin 2 += -SGN i u0, spin 3 += SGN i u1;  i v = (-v.im, v.re)
+            const c2 v2 = MU == 0 ? u[1][c] : u[0][c];
+            const c2 v3 = MU == 0 ? u[0][c] : u[1][c];
+            constexpr bool n3 = MU == 0 ? SGN > 0 : SGN < 0;
+            if (SGN > 0) { q[4] = f2_add(q[4], v2.im); q[5] = f2_sub(q[5], v2.re); }
+            else         { q[4] = f2_sub(q[4], v2.im); q[5] = f2_add(q[5], v2.re); }
+            if (n3) { q[6] = f2_add(q[6], v3.im); q[7] = f2_sub(q[7], v3.re); }
+            else    { q[6] = f2_sub(q[6], v3.im); q[7] = f2_add(q[7], v3.re); }
+        }
+    }
+}
+
+// u[k][a] = sum_b U[a][b] h[k][b] (ADJ: conj(U[b][a])), the FMA chains of
+// su3_mul / su3_adj_mul with the link entries broadcast to both lanes
+template <int ADJ>
+__device__ __forceinline__ void su3_mul2(const float *U, const c2 h[2][3], c2 u[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        f2 hn[3];   // -h.im (U h) or -h.re (U^dag h): the negative products
+#pragma unroll
+        for (int b = 0; b < 3; ++b) hn[b] = f2_neg(ADJ ? h[k][b].re : h[k][b].im);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int e0 = ADJ ? a : 3 * a;
+            const f2 ur = f2_bcast(U[2 * e0]), ui = f2_bcast(U[2 * e0 + 1]);
+            f2 re = f2_mul(ur, h[k][0].re);
+            f2 im = f2_mul(ur, h[k][0].im);
+            if (ADJ) {
+                re = f2_fma(ui, h[k][0].im, re);
+                im = f2_fma(ui, hn[0], im);
+            } else {
+                re = f2_fma(ui, hn[0], re);
+                im = f2_fma(ui, h[k][0].re, im);
+            }
+#pragma unroll
+            for (int b = 1; b < 3; ++b) {
+                const int e = ADJ ? 3 * b + a : 3 * a + b;
+                const f2 vr = f2_bcast(U[2 * e]), vi = f2_bcast(U[2 * e + 1]);
+                re = f2_fma(vr, h[k][b].re, re);
+                re = f2_fma(vi, ADJ ? h[k][b].im : hn[b], re);
+                im = f2_fma(vr, h[k][b].im, im);
+                im = f2_fma(vi, ADJ ? hn[b] : h[k][b].re, im);
+            }
+            u[k][a] = {re, im};
+        }
+    }
+}
+
+// the half spinors of the two right-hand sides' neighbour records, paired
+template <int MU, int SGN>
+__device__ __forceinline__ void project2(const float *p0, const float *p1, c2 h[2][3]) {
+    cx<float> a[2][3], b[2][3];
+    project<MU, SGN>(p0, a);
+    project<MU, SGN>(p1, b);
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            h[k][c] = {f2_pack(a[k][c].re, b[k][c].re), f2_pack(a[k][c].im, b[k][c].im)};
+}
+
+// u *= phase (pr, pi), lane-wise
+__device__ __forceinline__ void phase_mul2(c2 u[2][3], float pr, float pi) {
+    const f2 r = f2_bcast(pr), i = f2_bcast(pi), ni = f2_bcast(-pi);
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const f2 re = f2_fma(u[k][a].re, r, f2_mul(u[k][a].im, ni));
+            const f2 im = f2_fma(u[k][a].re, i, f2_mul(u[k][a].im, r));
+            u[k][a] = {re, im};
+        }
+}
+
+// acc += the forward and backward hops of direction MU for the right-hand
+// sides r and r + 1 of site h (FP32 storage)
+template <int RECON, int MU, int DAG>
+__device__ __forceinline__ void bt_hop_pair2(const BtProb &P, const int c[4], unsigned hu, int r,
+                                             f2 *acc) {
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    const size_t splane = (size_t)P.g.stride * P.nrhs * 16, lplane = (size_t)P.g.stride * 16;
+    {
+        bool wrap;
+        const unsigned hn = neighbour32<MU, +1>(P.g, hu, c, wrap);
+        const unsigned rec = hn * (unsigned)P.nrhs + (unsigned)r;
+        float p0[24], p1[24];
+        bt_load<float, 24, 0>(P.f[1], splane, rec, p0);
+        bt_load<float, 24, 0>(P.f[1], splane, rec + 1, p1);
+        c2 hs[2][3], u[2][3];
+        project2<MU, SF>(p0, p1, hs);
+        float U[18];
+        bt_load<float, RECON, 1>(P.gauge_out + MU * P.dir_bytes, lplane, hu, U);
+        if (RECON == 12) bt_rebuild_row2(U);
+        su3_mul2<0>(U, hs, u);
+        if (wrap && (P.phase_on >> MU & 1u))
+            phase_mul2(u, (float)P.ph[2 * MU], (float)P.ph[2 * MU + 1]);
+        accumulate2<MU, SF>(acc, u);
+    }
+    {
+        bool wrap;
+        const unsigned hn = neighbour32<MU, -1>(P.g, hu, c, wrap);
+        const unsigned rec = hn * (unsigned)P.nrhs + (unsigned)r;
+        float p0[24], p1[24];
+        bt_load<float, 24, 0>(P.f[1], splane, rec, p0);
+        bt_load<float, 24, 0>(P.f[1], splane, rec + 1, p1);
+        c2 hs[2][3], u[2][3];
+        project2<MU, SB>(p0, p1, hs);
+        float U[18];
+        bt_load<float, RECON, 1>(P.gauge_in + MU * P.dir_bytes, lplane, hn, U);
+        if (RECON == 12) bt_rebuild_row2(U);
+        su3_mul2<1>(U, hs, u);
+        if (wrap && (P.phase_on >> MU & 1u))
+            phase_mul2(u, (float)P.ph[2 * MU], -(float)P.ph[2 * MU + 1]);
+        accumulate2<MU, SB>(acc, u);
+    }
+}
+
+// Per-rhs sums of a pair tile (2 BLOCK items, two per thread), with the
+// staging and summation order of bt_warp_sums over each warp's 64 items.
+template <int BLOCK>
+__device__ __forceinline__ void bt_warp_sums2(df64 v0, df64 v1, const BtProb &P, long item0,
+                                              df64 *wv, df64 (*wacc)[BT_MAX_SLOTS]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    wv[2 * threadIdx.x] = v0;
+    wv[2 * threadIdx.x + 1] = v1;
+    __syncwarp();
+    const int nr = P.nrhs;
+    const long iw = item0 + 64 * w;
+    const int base = (int)(iw % nr);
+    for (int j = lane; j < nr; j += 32) {
+        df64 s = 0;
+        for (int l = (j - base + nr) % nr; l < 64; l += nr) s = s + wv[64 * w + l];
+        wacc[w][P.slot0 + j] = wacc[w][P.slot0 + j] + s;
+    }
+    __syncwarp();
+}
+
 // f[0] = out, f[1] = in, f[2] = x:  out = scale * H in  or  x + scale * H in.
 // Tiles of BLOCK items (one per thread); MINB resident blocks per SM set the
 // register cap, the parameter the autotuner picks per batch.  Double-float
 // instances run the hop loop of dslash_df.cuh (unrolled, their code
 // outgrows the instruction cache).
-template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM, int BLOCK, int MINB>
+template <typename S, typename R, int RECON, int DAG, int XPAY, int NORM, int BLOCK, int MINB,
+          int PAIR = 0>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_batch(const __grid_constant__ BtArgs a) {
-    __shared__ df64 wv[BLOCK];
+    __shared__ df64 wv[PAIR ? 2 * BLOCK : BLOCK];
     __shared__ df64 wacc[BLOCK / 32][BT_MAX_SLOTS];
     __shared__ df64 sacc[BT_MAX_SLOTS];
     if (NORM) bt_zero_sums<BLOCK>(wacc);
+    if constexpr (PAIR) {
+        static_assert(std::is_same<S, float>::value && std::is_same<R, float>::value,
+                      "pair items: FP32 storage");
+        // tiles of 2 BLOCK items; thread t takes items item0 + 2 t and + 1,
+        // rhs r and r + 1 of one site (every nrhs of the batch is even)
+        for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+            const BtProb &P = a.p[bt_problem(a, t)];
+            const long item0 = (t - P.tile0) * (2 * BLOCK);
+            const long item = item0 + 2 * threadIdx.x;
+            df64 v0 = 0, v1 = 0;
+            if (item < P.nitems) {
+                const int nr = P.nrhs;
+                const unsigned hu = udiv((unsigned)item, P.div_nrhs);   // items < 2^31
+                const int r = (int)((unsigned)item - hu * (unsigned)nr);
+                int c[4];
+                site_coords(P.g, hu, a.parity, c);
+                f2 acc[24];
+#pragma unroll
+                for (int k = 0; k < 24; ++k) acc[k] = f2_pack(0.0f, 0.0f);
+                bt_hop_pair2<RECON, 0, DAG>(P, c, hu, r, acc);
+                bt_hop_pair2<RECON, 1, DAG>(P, c, hu, r, acc);
+                bt_hop_pair2<RECON, 2, DAG>(P, c, hu, r, acc);
+                bt_hop_pair2<RECON, 3, DAG>(P, c, hu, r, acc);
+                const long ss = P.g.stride * nr;
+                const float sc = (float)P.scale;
+                float o0[24], o1[24];
+                if (XPAY) {
+                    float x0[24], x1[24];
+                    Rec<float, 24>::template load<float, 0>(P.f[2], ss, item, x0);
+                    Rec<float, 24>::template load<float, 0>(P.f[2], ss, item + 1, x1);
+#pragma unroll
+                    for (int k = 0; k < 24; ++k) {
+                        float a0, a1;
+                        f2_unpack(acc[k], a0, a1);
+                        o0[k] = fmaf(sc, a0, x0[k]);
+                        o1[k] = fmaf(sc, a1, x1[k]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 24; ++k) {
+                        float a0, a1;
+                        f2_unpack(acc[k], a0, a1);
+                        o0[k] = sc * a0;
+                        o1[k] = sc * a1;
+                    }
+                }
+                Rec<float, 24>::store(P.f[0], ss, item, o0);
+                Rec<float, 24>::store(P.f[0], ss, item + 1, o1);
+                if (NORM) {
+                    float q0 = 0, q0b = 0, q1 = 0, q1b = 0;
+#pragma unroll
+                    for (int k = 0; k < 24; k += 2) {
+                        sq_acc_x2(q0, q0b, o0[k], o0[k + 1]);
+                        sq_acc_x2(q1, q1b, o1[k], o1[k + 1]);
+                    }
+                    v0 = to_df(q0 + q0b);
+                    v1 = to_df(q1 + q1b);
+                }
+            }
+            if (NORM) bt_warp_sums2<BLOCK>(v0, v1, P, item0, wv, wacc);
+        }
+        if (NORM) {
+            bt_block_sums<BLOCK>(wacc, sacc, a.nslots);
+            bt_finish<BLOCK>(a, sacc);
+        }
+        return;
+    }
     for (long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const BtProb &P = a.p[bt_problem(a, t)];
         const long item0 = (t - P.tile0) * BLOCK;
@@ -291,9 +567,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash_batch(const __grid_const
 // (FP32, FP16): threads per block (= items per tile) and minimum resident
 // blocks per SM (the register cap).  The grid is the kernel's resident
 // capacity on this GPU (SMs x blocks per SM), capped at the tile count.
-struct BtCfg { int block, minb; };
-constexpr int N_BT_CFG = 5;
-constexpr BtCfg BT_CFGS[N_BT_CFG] = {{128, 4}, {128, 5}, {128, 6}, {128, 8}, {256, 2}};
+// pair = 1: two right-hand sides per thread (FP32 storage, every nrhs even).
+struct BtCfg { int block, minb, pair; };
+constexpr int N_BT_CFG = 9;
+constexpr BtCfg BT_CFGS[N_BT_CFG] = {{128, 4, 0}, {128, 5, 0}, {128, 6, 0}, {128, 8, 0},
+                                     {256, 2, 0}, {128, 2, 1}, {128, 3, 1}, {128, 4, 1},
+                                     {256, 2, 1}};
 
 // Variants of a batched hop: plain (out = scale H in) or xpay with the fused
 // per-system norm (the second hop of the Schur operator in the CGNR
@@ -315,9 +594,10 @@ inline unsigned bt_resident_grid(K kernel, int block) {
 // One launch of a batched hop: persistent grid = the kernel's resident
 // capacity on this device (looked up once per device), capped at the tile
 // count and at the partials buffer.
-template <typename S, typename R, int RECON, int DAG, int X, int N, int BLOCK, int MINB>
+template <typename S, typename R, int RECON, int DAG, int X, int N, int BLOCK, int MINB,
+          int PAIR = 0>
 cudaError_t bt_go(const BtArgs &a, cudaStream_t s, unsigned *grid_out) {
-    const auto k = k_dslash_batch<S, R, RECON, DAG, X, N, BLOCK, MINB>;
+    const auto k = k_dslash_batch<S, R, RECON, DAG, X, N, BLOCK, MINB, PAIR>;
     static unsigned cap[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -336,7 +616,19 @@ cudaError_t bt_go(const BtArgs &a, cudaStream_t s, unsigned *grid_out) {
 
 template <typename S, typename R, int RECON, int DAG, int X, int N>
 cudaError_t bt_go_cfg(int cfg, const BtArgs &a, cudaStream_t s, unsigned *g) {
-#define WD_BT_CFG(C) bt_go<S, R, RECON, DAG, X, N, BT_CFGS[C].block, BT_CFGS[C].minb>(a, s, g)
+#define WD_BT_CFG(C)                                                                       \
+    bt_go<S, R, RECON, DAG, X, N, BT_CFGS[C].block, BT_CFGS[C].minb, BT_CFGS[C].pair>(a, s, g)
+    if constexpr (std::is_same<S, float>::value) {
+        switch (cfg) {
+        case 5: return WD_BT_CFG(5);
+        case 6: return WD_BT_CFG(6);
+        case 7: return WD_BT_CFG(7);
+        case 8: return WD_BT_CFG(8);
+        default: break;
+        }
+    } else if (cfg >= 5) {
+        return cudaErrorInvalidValue;   // pair items: FP32 storage only
+    }
     switch (cfg) {
     case 1: return WD_BT_CFG(1);
     case 2: return WD_BT_CFG(2);

@@ -180,6 +180,30 @@ __device__ __forceinline__ void load_link(const void *base, long stride, long h,
     }
 }
 
+// c + a b and c - a b with one rounding, and a b, spelled with the
+// round-to-nearest intrinsics in FP32 and FP64 so that the compiler cannot
+// pick which product of a chain to fuse: every kernel that forms these
+// products (the batched hop's one- and two-rhs forms among them) then rounds
+// them identically.  Other arithmetic types use their own operators.
+template <typename A, typename R>
+__device__ __forceinline__ A pmul(R a, A b) {
+    if constexpr (std::is_same<A, float>::value) return __fmul_rn(a, b);
+    else if constexpr (std::is_same<A, double>::value) return __dmul_rn(a, b);
+    else return a * b;
+}
+template <typename A, typename R>
+__device__ __forceinline__ A pmac(R a, A b, A c) {
+    if constexpr (std::is_same<A, float>::value) return __fmaf_rn(a, b, c);
+    else if constexpr (std::is_same<A, double>::value) return __fma_rn(a, b, c);
+    else return c + a * b;
+}
+template <typename A, typename R>
+__device__ __forceinline__ A pmsub(R a, A b, A c) {
+    if constexpr (std::is_same<A, float>::value) return __fmaf_rn(-a, b, c);
+    else if constexpr (std::is_same<A, double>::value) return __fma_rn(-a, b, c);
+    else return c - a * b;
+}
+
 // u[k][a] = sum_b U[a][b] h[k][b], written as chains of single
 // multiply-adds so that every real product becomes one FMA.
 template <typename R, typename A>
@@ -188,17 +212,17 @@ __device__ __forceinline__ void su3_mul(const R *U, const cx<A> h[2][3], cx<A> u
     for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            A re = U[6 * a] * h[k][0].re;
-            A im = U[6 * a] * h[k][0].im;
-            re -= U[6 * a + 1] * h[k][0].im;
-            im += U[6 * a + 1] * h[k][0].re;
+            A re = pmul(U[6 * a], h[k][0].re);
+            A im = pmul(U[6 * a], h[k][0].im);
+            re = pmsub(U[6 * a + 1], h[k][0].im, re);
+            im = pmac(U[6 * a + 1], h[k][0].re, im);
 #pragma unroll
             for (int b = 1; b < 3; ++b) {
                 const R ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
-                re += ur * h[k][b].re;
-                re -= ui * h[k][b].im;
-                im += ur * h[k][b].im;
-                im += ui * h[k][b].re;
+                re = pmac(ur, h[k][b].re, re);
+                re = pmsub(ui, h[k][b].im, re);
+                im = pmac(ur, h[k][b].im, im);
+                im = pmac(ui, h[k][b].re, im);
             }
             u[k][a] = {re, im};
         }
@@ -211,17 +235,17 @@ __device__ __forceinline__ void su3_adj_mul(const R *U, const cx<A> h[2][3], cx<
     for (int k = 0; k < 2; ++k)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            A re = U[2 * a] * h[k][0].re;
-            A im = U[2 * a] * h[k][0].im;
-            re += U[2 * a + 1] * h[k][0].im;
-            im -= U[2 * a + 1] * h[k][0].re;
+            A re = pmul(U[2 * a], h[k][0].re);
+            A im = pmul(U[2 * a], h[k][0].im);
+            re = pmac(U[2 * a + 1], h[k][0].im, re);
+            im = pmsub(U[2 * a + 1], h[k][0].re, im);
 #pragma unroll
             for (int b = 1; b < 3; ++b) {
                 const R ur = U[2 * (3 * b + a)], ui = U[2 * (3 * b + a) + 1];
-                re += ur * h[k][b].re;
-                re += ui * h[k][b].im;
-                im += ur * h[k][b].im;
-                im -= ui * h[k][b].re;
+                re = pmac(ur, h[k][b].re, re);
+                re = pmac(ui, h[k][b].im, re);
+                im = pmac(ur, h[k][b].im, im);
+                im = pmsub(ui, h[k][b].re, im);
             }
             u[k][a] = {re, im};
         }

@@ -21,6 +21,10 @@ WD_OK, WD_ERR_ARG, WD_ERR_DIMS, WD_ERR_CUDA, WD_ERR_NOMEM = 0, 1, 2, 3, 4
 WD_ERR_NOT_CONVERGED, WD_ERR_BREAKDOWN, WD_ERR_TIMEOUT, WD_ERR_STATE = 5, 6, 7, 8
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 RECOVERY = {"reliable": 0, "defect": 1}
+# launch candidates of the batched hop (include/wd.h, wd_batch_tuning): the
+# ones from BATCH_PAIR_FIRST on take two right-hand sides per thread
+BATCH_CANDIDATES = 9
+BATCH_PAIR_FIRST = 5
 
 
 class WDError(RuntimeError):
@@ -368,12 +372,13 @@ class WilsonBatch:
     def tuning(self, norm: bool = False) -> dict:
         """The autotuner's choice for the batched hop (norm=True: the xpay hop
         with fused norms) and every candidate's microseconds per launch."""
-        us = (ctypes.c_double * 8)()
+        us = (ctypes.c_double * BATCH_CANDIDATES)()
         blk, mb, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        k = self.lib.wd_batch_tuning(self.handle, int(bool(norm)), us, 8, ctypes.byref(blk),
-                                     ctypes.byref(mb), ctypes.byref(gr))
+        k = self.lib.wd_batch_tuning(self.handle, int(bool(norm)), us, BATCH_CANDIDATES,
+                                     ctypes.byref(blk), ctypes.byref(mb), ctypes.byref(gr))
         return {"index": k, "block": blk.value, "min_blocks": mb.value, "grid": gr.value,
-                "us": [us[i] for i in range(5)]}
+                "rhs_per_thread": 2 if k >= BATCH_PAIR_FIRST else 1,
+                "us": [us[i] for i in range(BATCH_CANDIDATES)]}
 
     def dslash_resident(self, out_parity: int, dagger: bool = False):
         rc = self.lib.wd_batch_dslash_resident(self.handle, int(out_parity), int(bool(dagger)))

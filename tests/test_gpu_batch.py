@@ -141,10 +141,81 @@ def test_batch_autotuner_keeps_the_fastest_configuration(prec, recon):
     for norm in (False, True):
         t = bt.tuning(norm=norm)
         us = t["us"]
-        assert all(u > 0 for u in us), t
-        assert t["index"] == int(np.argmin(us)), t
+        # one item per thread: always timed; two (rhs pairs): not for odd nrhs
+        assert len(us) == 9 and all(u > 0 for u in us[:5]) and all(u == 0 for u in us[5:]), t
+        assert t["index"] == int(np.argmin(us[:5])) and t["rhs_per_thread"] == 1, t
         assert t["block"] in (128, 256) and t["min_blocks"] >= 1, t
         assert t["grid"] >= 1 and (t["grid"] % sms == 0 or t["grid"] < sms * t["min_blocks"]), t
+
+
+# even right-hand-side counts: the pair candidates (two rhs per thread) apply
+PAIR_PROBLEMS = [((4, 4, 4, 4), 4, 0.12), ((6, 6, 2, 4), 2, 0.124), ((8, 4, 6, 10), 6, 0.13)]
+
+
+def test_batch_autotuner_times_the_pair_candidates():
+    """With FP32 storage and even nrhs everywhere, all nine candidates are
+    timed (five with one (site, rhs) item per thread, four with two) and the
+    fastest is kept."""
+    bt, ops, Us = make("f32", 18, PAIR_PROBLEMS)
+    for norm in (False, True):
+        t = bt.tuning(norm=norm)
+        us = t["us"]
+        assert len(us) == 9 and all(u > 0 for u in us), t
+        assert t["index"] == int(np.argmin(us)), t
+        assert t["rhs_per_thread"] == (2 if t["index"] >= 5 else 1), t
+
+
+@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("cfg", [5, 6, 7, 8])
+def test_batch_pair_dslash(monkeypatch, recon, cfg):
+    """Two right-hand sides per thread (packed FP32 pair arithmetic): every
+    site against the oracle at the FP32 tolerance, and bitwise the output of
+    the one-item-per-thread kernel (the same operations in the same order per
+    lane), on uneven lattices with ragged last tiles, both parities and both
+    daggers."""
+    ins = [np.stack([syn.gaussian_spinor(syn.volume(dims) // 2, 500 + 7 * k + r)
+                     for r in range(n)]) for k, (dims, n, _) in enumerate(PAIR_PROBLEMS)]
+    res = {}
+    for c in (0, cfg):
+        monkeypatch.setenv("WD_BATCH_CFG", str(c))
+        bt, ops, Us = make("f32", recon, PAIR_PROBLEMS)
+        assert bt.tuning()["index"] == c and bt.tuning(norm=True)["index"] == c
+        res[c] = {}
+        for out_parity in (0, 1):
+            for dagger in (False, True):
+                outs = bt.dslash([torch.from_numpy(a).cuda() for a in ins], out_parity, dagger)
+                torch.cuda.synchronize()
+                res[c][out_parity, dagger] = [o.cpu() for o in outs]
+        bt.close()
+    for (out_parity, dagger), outs in res[cfg].items():
+        for k, (dims, n, _) in enumerate(PAIR_PROBLEMS):
+            assert torch.equal(outs[k], res[0][out_parity, dagger][k]), (k, out_parity, dagger)
+            got = outs[k].numpy()
+            for r in range(n):
+                ref = oracle.hop_eo(ins[k][r], Us[k], dims, APBC, out_parity, dagger)
+                check(got[r], ref, "f32", what=(k, r, out_parity, dagger))
+
+
+@pytest.mark.parametrize("recovery", [("reliable", 0.1), ("defect", 1e-3)])
+def test_batch_pair_solve(monkeypatch, recovery):
+    """A batched solve whose hops take two right-hand sides per thread: every
+    system meets the oracle's FP64 true residual and lies within 1e-8 of the
+    oracle's solution."""
+    monkeypatch.setenv("WD_BATCH_CFG", "6")
+    bt, ops, Us = make("f32", 18, PAIR_PROBLEMS)
+    assert bt.tuning()["rhs_per_thread"] == 2
+    ops[0].set_recovery(*recovery)
+    bs = [np.stack([syn.gaussian_spinor(syn.volume(dims), 600 + 5 * k + r) for r in range(n)])
+          for k, (dims, n, _) in enumerate(PAIR_PROBLEMS)]
+    xs, status, infos = bt.solve([torch.from_numpy(b).cuda() for b in bs], tol=1e-10)
+    assert status == 0
+    for k, (dims, n, kappa) in enumerate(PAIR_PROBLEMS):
+        x = xs[k].cpu().numpy()
+        for r in range(n):
+            res = np.linalg.norm(bs[k][r] - oracle.apply(x[r], Us[k], dims, kappa, APBC))
+            assert res <= 1.05e-10 * np.linalg.norm(bs[k][r]), (k, r, res)
+            x_ref, _, ok = oracle.solve(bs[k][r], Us[k], dims, kappa, APBC, parity=1, tol=1e-13)
+            assert ok and rel(x[r], x_ref) < 1e-8
 
 
 @pytest.mark.parametrize("prec,recon", [("f32", 18), ("f16", 12)])
