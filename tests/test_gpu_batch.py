@@ -24,12 +24,12 @@ def rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
 
-def make(prec, recon, problems=PROBLEMS):
+def make(prec, recon, problems=PROBLEMS, phase=APBC):
     from paper_1401_2039_gb300 import WilsonBatch, WilsonDirac
     ops, Us = [], []
     for k, (dims, n, kappa) in enumerate(problems):
         U = syn.su3_links(dims, eps=0.3, seed=40 + k)
-        op = WilsonDirac(dims, kappa, APBC, prec=prec, recon=recon)
+        op = WilsonDirac(dims, kappa, phase, prec=prec, recon=recon)
         op.set_gauge(torch.from_numpy(U).cuda())
         ops.append(op)
         Us.append(U)
@@ -52,6 +52,29 @@ def test_batch_dslash(prec, recon):
                 got = outs[k].cpu().numpy()
                 for r in range(n):
                     ref = oracle.hop_eo(ins[k][r], Us[k], dims, APBC, out_parity, dagger)
+                    check(got[r], ref, prec, what=(k, r, out_parity, dagger))
+
+
+# trivial (exactly 1) and complex boundary phases mixed: the hop kernels skip
+# the multiplication only in the directions whose phase is 1
+TWISTED = tuple(np.exp(1j * np.array([0.0, 0.7, 0.0, -2.1])))
+
+
+@pytest.mark.parametrize("prec,recon,cfg", [("f64", 18, 0), ("f32", 18, 0), ("f32", 12, 5),
+                                            ("f16", 12, 0)])
+def test_batch_dslash_twisted_phases(monkeypatch, prec, recon, cfg):
+    monkeypatch.setenv("WD_BATCH_CFG", str(cfg))
+    bt, ops, Us = make(prec, recon, PAIR_PROBLEMS, phase=TWISTED)
+    ins = [np.stack([syn.gaussian_spinor(syn.volume(dims) // 2, 700 + 7 * k + r)
+                     for r in range(n)]) for k, (dims, n, _) in enumerate(PAIR_PROBLEMS)]
+    for out_parity in (0, 1):
+        for dagger in (False, True):
+            outs = bt.dslash([torch.from_numpy(a).cuda() for a in ins], out_parity, dagger)
+            torch.cuda.synchronize()
+            for k, (dims, n, _) in enumerate(PAIR_PROBLEMS):
+                got = outs[k].cpu().numpy()
+                for r in range(n):
+                    ref = oracle.hop_eo(ins[k][r], Us[k], dims, TWISTED, out_parity, dagger)
                     check(got[r], ref, prec, what=(k, r, out_parity, dagger))
 
 
