@@ -270,7 +270,9 @@ int wd_dslash_resident(wd_op *op, int in_slot, int out_parity, int dagger);
  * that was not timed: link staging applies to FP16/BF16 storage only, and
  * entries past the candidate count); block, min_blocks, sites_per_thread and
  * staged (optional; staged = 1: the link records of the eight hops are copied
- * into shared memory at kernel start) describe the chosen one.  Returns its
+ * into shared memory at kernel start and the neighbour spinors are loaded two
+ * hops ahead; staged = 2: the same with the spinors three hops ahead)
+ * describe the chosen one.  Returns its
  * index, or -1 for a null handle.  Setting WD_DSLASH_CFG=k in the
  * environment forces candidate k, WD_TUNE=0 keeps candidate 0. */
 int wd_dslash_tuning(const wd_op *op, int hi, double *us, int n, int *block, int *min_blocks,

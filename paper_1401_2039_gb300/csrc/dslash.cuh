@@ -589,7 +589,7 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
 
 // The single-system FP16/BF16 hop computes in 32-bit site indices and byte
 // offsets from precomputed hop steps (Geom::step, Geom::back), and runs its
-// eight hops in one of two ways, both measured and offered to the autotuner:
+// eight hops in one of three ways, all measured and offered to the autotuner:
 //  * pipelined: the neighbour spinor and link words of hop i + 1 are loaded
 //    into registers before the arithmetic of hop i, so every hop's loads are
 //    in flight while the previous hop computes;
@@ -597,10 +597,13 @@ __device__ __forceinline__ void hop_pair_h2(const Geom &g, const char *gauge_out
 //    eight hops into shared memory with cp.async (global -> shared, no
 //    registers held), one commit group per hop, so the block's link bytes
 //    are all requested at once and each hop waits for its own group only;
-//    the neighbour spinors (read by eight sites, mostly from L1/L2) still go
-//    through registers one hop ahead.
-// Measured at 32^3 x 64: the plain hop is fastest pipelined (64 against
-// 67 us), the xpay hop with fused norm staged (82 against 88 us).
+//    the neighbour spinors (read by eight sites, mostly from L1/L2) go
+//    through registers, two hops ahead;
+//  * staged, three ahead: as staged, with three spinor buffers in registers.
+// Measured at 32^3 x 64 (plain hop / xpay hop with fused norm): pipelined
+// 60.3 / 85.2 us, staged 59.1 / 76.2 us, staged three ahead 53.7-55.4 /
+// 72.2 us; the kernel waits mostly on the latency of the neighbour reads,
+// so more of them in flight pays.
 template <int MU, int DIR>
 __device__ __forceinline__ unsigned neighbour32(const Geom &g, unsigned h, const int c[4],
                                                 bool &wrap) {
@@ -824,13 +827,48 @@ __device__ __forceinline__ void hops_h2_staged(const DslashArgs<float> &a, const
     compute_staged_h2<HT, RECON, 7, DAG>(a, d1, st, acc);
 }
 
+// staged links, and the neighbour spinors three hops in flight: three
+// register buffers, each refilled (three hops ahead) as soon as its hop has
+// computed
+template <typename HT, int RECON, int DAG, int BLOCK>
+__device__ __forceinline__ void hops_h2_staged3(const DslashArgs<float> &a, const int c[4],
+                                                unsigned h, LinkStage<RECON, BLOCK> &st,
+                                                float *acc) {
+    stage_link_h2<RECON, 0>(a, c, h, st);
+    stage_link_h2<RECON, 1>(a, c, h, st);
+    stage_link_h2<RECON, 2>(a, c, h, st);
+    stage_link_h2<RECON, 3>(a, c, h, st);
+    stage_link_h2<RECON, 4>(a, c, h, st);
+    stage_link_h2<RECON, 5>(a, c, h, st);
+    stage_link_h2<RECON, 6>(a, c, h, st);
+    stage_link_h2<RECON, 7>(a, c, h, st);
+    SpinorH2 d0, d1, d2;
+    load_spinor_h2<0, +1>(a, c, h, d0);
+    load_spinor_h2<0, -1>(a, c, h, d1);
+    load_spinor_h2<1, +1>(a, c, h, d2);
+    compute_staged_h2<HT, RECON, 0, DAG>(a, d0, st, acc);
+    load_spinor_h2<1, -1>(a, c, h, d0);
+    compute_staged_h2<HT, RECON, 1, DAG>(a, d1, st, acc);
+    load_spinor_h2<2, +1>(a, c, h, d1);
+    compute_staged_h2<HT, RECON, 2, DAG>(a, d2, st, acc);
+    load_spinor_h2<2, -1>(a, c, h, d2);
+    compute_staged_h2<HT, RECON, 3, DAG>(a, d0, st, acc);
+    load_spinor_h2<3, +1>(a, c, h, d0);
+    compute_staged_h2<HT, RECON, 4, DAG>(a, d1, st, acc);
+    load_spinor_h2<3, -1>(a, c, h, d1);
+    compute_staged_h2<HT, RECON, 5, DAG>(a, d2, st, acc);
+    compute_staged_h2<HT, RECON, 6, DAG>(a, d0, st, acc);
+    compute_staged_h2<HT, RECON, 7, DAG>(a, d1, st, acc);
+}
+
 template <typename S> constexpr bool packed16() {
     return std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
 }
 
 // One output site per (thread, i < SPT): site h = block base + i * BLOCK +
 // thread, so each of a warp's loads stays one contiguous request.  STAGE
-// (16-bit storage, one site per thread): links staged in shared memory.
+// (16-bit storage, one site per thread): links staged in shared memory, with
+// the neighbour spinors two (STAGE 1) or three (STAGE 2) hops in flight.
 template <typename S, typename R, int RECON, int DAG, int EPI, int NORM, int BLOCK, int MINB,
           int SPT, int STAGE>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
@@ -847,7 +885,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
             Acc<R> acc[24];
 #pragma unroll
             for (int k = 0; k < 24; ++k) acc[k] = 0;
-            if constexpr (STAGE) {
+            if constexpr (STAGE == 2) {
+                __shared__ LinkStage<RECON, BLOCK> stage;
+                hops_h2_staged3<S, RECON, DAG>(a, c, (unsigned)h, stage, acc);
+            } else if constexpr (STAGE) {
                 __shared__ LinkStage<RECON, BLOCK> stage;
                 hops_h2_staged<S, RECON, DAG>(a, c, (unsigned)h, stage, acc);
             } else if constexpr (packed16<S>()) {
@@ -917,14 +958,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dslash(const DslashArgs<R> a) {
 
 // Launch configurations the tuner chooses from: threads per block, the
 // minimum resident blocks per SM handed to the register allocator, output
-// sites per thread, and (16-bit storage only) links staged in shared memory.
+// sites per thread, and (16-bit storage only) links staged in shared memory
+// with the neighbour spinors two (stage 1) or three (stage 2) hops ahead.
 // A fused norm adds in the same order under every configuration
 // (warp_partials), so every variant can take its own tuned one.
 struct DslashCfg { int block, minb, spt, stage; };
 constexpr int N_DSLASH_CFG = 8;
 constexpr DslashCfg DSLASH_CFGS[N_DSLASH_CFG] = {
     {128, 1, 1, 0}, {128, 8, 1, 0}, {128, 6, 1, 0}, {256, 4, 1, 0},
-    {128, 1, 2, 0}, {128, 8, 1, 1}, {128, 6, 1, 1}, {256, 4, 1, 1}};
+    {128, 1, 2, 0}, {128, 5, 1, 2}, {128, 6, 1, 1}, {128, 6, 1, 2}};
 // whether candidate k is distinct for storage precision prec (staging
 // applies to 16-bit storage only; elsewhere it repeats an unstaged entry)
 inline bool dslash_cfg_applies(int k, int prec) {

@@ -270,7 +270,7 @@ class WilsonDirac:
         k = self.lib.wd_dslash_tuning(self.handle, variant, us, 8, ctypes.byref(blk),
                                       ctypes.byref(mb), ctypes.byref(spt), ctypes.byref(stg))
         return {"index": k, "block": blk.value, "min_blocks": mb.value,
-                "sites_per_thread": spt.value, "staged": bool(stg.value),
+                "sites_per_thread": spt.value, "staged": bool(stg.value), "stage": stg.value,
                 "us": [round(v, 2) for v in us]}
 
     # resident fields, for timing the hopping term alone

@@ -59,11 +59,13 @@ def test_dslash_sampled_sites(field, prec, recon):
     op.close()
 
 
-@pytest.mark.parametrize("prec,recon,cfg", [("f16", 12, 6), ("bf16", 18, 6), ("f16", 12, 7)])
+@pytest.mark.parametrize("prec,recon,cfg", [("f16", 12, 6), ("bf16", 18, 6), ("f16", 12, 7),
+                                            ("bf16", 12, 5)])
 def test_dslash_sampled_sites_staged_links(monkeypatch, field, prec, recon, cfg):
     """At full size, the 16-bit hop with its eight link records staged in
-    shared memory (candidate 6, the norm-fused variant's pick at this size,
-    and 7 with 256-thread blocks)."""
+    shared memory: spinors two hops ahead (candidate 6) or three (7, the
+    pick of both FP16 variants at this size, and 5 with the register cap for
+    5 blocks, BF16's pick)."""
     from paper_1401_2039_gb300 import WilsonDirac
     monkeypatch.setenv("WD_DSLASH_CFG", str(cfg))
     U, psi = field

@@ -81,18 +81,20 @@ def test_dslash_eo(dims, prec, recon):
 
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
 @pytest.mark.parametrize("recon", [18, 12])
-@pytest.mark.parametrize("cfg", [1, 5, 7])
+@pytest.mark.parametrize("cfg", [1, 5, 6, 7])
 def test_dslash_eo_each_16bit_path(monkeypatch, prec, recon, cfg):
-    """Both hop paths of 16-bit storage against the oracle, site by site:
+    """Every hop path of 16-bit storage against the oracle, site by site:
     link and spinor words in registers one hop ahead (candidate 1), and the
-    eight link records staged in shared memory by cp.async (candidates 5,
-    7: 128 and 256 threads).  Lattices: odd Lx/2 with a ragged last block,
-    2^4 (x + mu = x - mu), and an anisotropic one; twisted boundary phases."""
+    eight link records staged in shared memory by cp.async with the spinors
+    two hops ahead (candidate 6) or three (candidates 5 and 7, register caps
+    for 5 and 6 blocks).  Lattices: odd Lx/2 with a ragged last block, 2^4
+    (x + mu = x - mu), and an anisotropic one; twisted boundary phases."""
     monkeypatch.setenv("WD_DSLASH_CFG", str(cfg))
     for dims in [(6, 6, 2, 4), (2, 2, 2, 2), (8, 4, 6, 10)]:
         U, psi = fields(dims)
         op = make_op(dims, 0.12, PHASES["twisted"], prec, recon, U)
-        assert op.dslash_tuning()["staged"] == (cfg >= 5)
+        t = op.dslash_tuning()
+        assert t["staged"] == (cfg >= 5) and t["stage"] == {1: 0, 5: 2, 6: 1, 7: 2}[cfg]
         for out_parity in (0, 1):
             src = syn.to_half(psi, dims, 1 - out_parity)
             for dagger in (False, True):
