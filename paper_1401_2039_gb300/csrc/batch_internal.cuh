@@ -202,40 +202,6 @@ __device__ __forceinline__ void bt_hop_pair(const BtProb &P, const int c[4], lon
 // accumulation is one packed FP32 pair operation over the two right-hand
 // sides (lane 0: rhs r, lane 1: rhs r + 1), each lane rounded as the scalar
 // operation of bt_hop_pair in the same order.
-typedef unsigned long long f2;   // two FP32 lanes in one 64-bit register pair
-
-__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
-    f2 d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-    return d;
-}
-__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-// a b + c, one rounding per lane
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 f2_neg(f2 a) { return f2_mul(a, f2_pack(-1.0f, -1.0f)); }
-__device__ __forceinline__ f2 f2_bcast(float a) { return f2_pack(a, a); }
-
 struct c2 {
     f2 re, im;
 };

@@ -125,6 +125,43 @@ __device__ __forceinline__ void scale_add_x2(float &d0, float &d1, float a0, flo
         : "=f"(d0), "=f"(d1) : "f"(a0), "f"(a1), "f"(s), "f"(x0), "f"(x1));
 }
 
+// Two FP32 lanes in one 64-bit register pair, and the packed FP32 pair
+// operations on them (add/sub/mul/fma .rn.f32x2: each lane rounded as the
+// scalar operation).
+typedef unsigned long long f2;   // two FP32 lanes in one 64-bit register pair
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// a b + c, one rounding per lane
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_neg(f2 a) { return f2_mul(a, f2_pack(-1.0f, -1.0f)); }
+__device__ __forceinline__ f2 f2_bcast(float a) { return f2_pack(a, a); }
+
 // (q0, q1) += (a0, a1)^2 elementwise, one packed FP32 pair FMA
 __device__ __forceinline__ void sq_acc_x2(float &q0, float &q1, float a0, float a1) {
     asm("{\n\t.reg .b64 a, q;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 q, {%0, %1};\n\t"

@@ -33,6 +33,83 @@ __device__ __forceinline__ cdf times(cdf q, bool im, float s) {
 
 __device__ __forceinline__ cdf sel(bool first, cdf a, cdf b) { return first ? a : b; }
 
+// A complex double-float value with its real and imaginary parts in the two
+// lanes of packed FP32 pairs: s = (re.s, im.s), e = (re.e, im.e).  Every
+// operation below is the scalar double-float operation of df64.cuh done on
+// both lanes at once, with the same FP32 roundings in the same order, so the
+// hop gives bitwise the scalar loop's result in about half the FP32
+// instructions.
+struct dfc2 {
+    f2 s, e;
+};
+
+__device__ __forceinline__ dfc2 dfc2_of(df64 re, df64 im) {
+    return {f2_pack(re.hi, im.hi), f2_pack(re.lo, im.lo)};
+}
+__device__ __forceinline__ cdf cdf_of(dfc2 a) {
+    cdf r;
+    f2_unpack(a.s, r.re.s, r.im.s);
+    f2_unpack(a.e, r.re.e, r.im.e);
+    return r;
+}
+__device__ __forceinline__ dfc2 dfc2_of(cdf a) {
+    return {f2_pack(a.re.s, a.im.s), f2_pack(a.re.e, a.im.e)};
+}
+__device__ __forceinline__ f2 f2_swap(f2 a) {
+    float lo, hi;
+    f2_unpack(a, lo, hi);
+    return f2_pack(hi, lo);
+}
+__device__ __forceinline__ f2 f2_sel(bool first, f2 a, f2 b) { return first ? a : b; }
+__device__ __forceinline__ dfc2 dfc2_sel(bool first, dfc2 a, dfc2 b) {
+    return {f2_sel(first, a.s, b.s), f2_sel(first, a.e, b.e)};
+}
+// a + b: lazy_add<1> on each lane
+__device__ __forceinline__ dfc2 dfc2_add(dfc2 a, dfc2 b) {
+    const f2 s = f2_add(a.s, b.s);
+    const f2 v = f2_sub(s, a.s);
+    const f2 t = f2_add(f2_sub(a.s, f2_sub(s, v)), f2_sub(b.s, v));
+    return {s, f2_add(a.e, f2_add(t, b.e))};
+}
+// a b for a real double-float a: operator*(df64, dfl) on each lane
+__device__ __forceinline__ dfc2 dfc2_scale(df64 a, dfc2 b) {
+    const f2 ah = f2_bcast(a.hi), al = f2_bcast(a.lo);
+    const f2 p = f2_mul(ah, b.s);
+    f2 c = f2_fma(ah, b.s, f2_neg(p));
+    c = f2_fma(ah, b.e, c);
+    c = f2_fma(al, b.s, c);
+    return {p, c};
+}
+// times(q, im, s) on the pair: s q, or s i q = (-s q.im, s q.re)
+__device__ __forceinline__ dfc2 dfc2_times(dfc2 q, bool im, float sg) {
+    const f2 m = im ? f2_pack(-sg, sg) : f2_pack(sg, sg);
+    return {f2_mul(im ? f2_swap(q.s) : q.s, m), f2_mul(im ? f2_swap(q.e) : q.e, m)};
+}
+// i a = (-a.im, a.re), exact
+__device__ __forceinline__ dfc2 dfc2_muli(dfc2 a) {
+    const f2 m = f2_pack(-1.0f, 1.0f);
+    return {f2_mul(f2_swap(a.s), m), f2_mul(f2_swap(a.e), m)};
+}
+
+// u[k][a] = sum_b U[a][b] h[k][b] with ih = i h: the chains of su3_mul, the
+// products U.im h.im entering as U.im (-h.im), i.e. through ih
+__device__ __forceinline__ void su3_mul_dfc2(const df64 *U, const dfc2 h[2][3],
+                                             const dfc2 ih[2][3], dfc2 u[2][3]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            dfc2 acc = dfc2_scale(U[6 * a], h[k][0]);
+            acc = dfc2_add(acc, dfc2_scale(U[6 * a + 1], ih[k][0]));
+#pragma unroll
+            for (int b = 1; b < 3; ++b) {
+                acc = dfc2_add(acc, dfc2_scale(U[2 * (3 * a + b)], h[k][b]));
+                acc = dfc2_add(acc, dfc2_scale(U[2 * (3 * a + b) + 1], ih[k][b]));
+            }
+            u[k][a] = acc;
+        }
+}
+
 // neighbour x +- mu of half-lattice site h (coordinates c) for hop
 // 2 mu + (0 forward | 1 backward), and whether the hop wraps
 __device__ __forceinline__ long df_neighbour(const Geom &g, long h, const int c[4], int hop,
@@ -86,6 +163,9 @@ __device__ __forceinline__ void df_hops(const Geom &g, const char *gauge_out, co
                                         dfl acc[24], uint4 *stage = nullptr,
                                         unsigned phase_on = 0xFu) {
     if constexpr (BLOCK > 0) df_stage_link<BLOCK>(g, gauge_out, gauge_in, dir_bytes, h, c, 0, stage);
+    dfc2 acc2[12];   // (spin, colour) 4 colour + spin: acc[2 k] + i acc[2 k + 1]
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc2[k] = dfc2_of(cdf{acc[2 * k], acc[2 * k + 1]});
 #pragma unroll 1
     for (int hop = 0; hop < 8; ++hop) {
         const int mu = hop >> 1;
@@ -120,15 +200,17 @@ __device__ __forceinline__ void df_hops(const Geom &g, const char *gauge_out, co
         const float g2 = (im ? -1.0f : 1.0f) * sgn;
         const float g3 = (swap ? -1.0f : 1.0f) * sgn;
 
-        cdf hs[2][3];
+        dfc2 hs[2][3], ihs[2][3];
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const cdf p0 = {psi[8 * cc + 0], psi[8 * cc + 1]};
-            const cdf p1 = {psi[8 * cc + 2], psi[8 * cc + 3]};
-            const cdf p2 = {psi[8 * cc + 4], psi[8 * cc + 5]};
-            const cdf p3 = {psi[8 * cc + 6], psi[8 * cc + 7]};
-            hs[0][cc] = cadd(p0, times(sel(swap, p3, p2), im, f0));
-            hs[1][cc] = cadd(p1, times(sel(swap, p2, p3), im, f1));
+            const dfc2 p0 = dfc2_of(psi[8 * cc + 0], psi[8 * cc + 1]);
+            const dfc2 p1 = dfc2_of(psi[8 * cc + 2], psi[8 * cc + 3]);
+            const dfc2 p2 = dfc2_of(psi[8 * cc + 4], psi[8 * cc + 5]);
+            const dfc2 p3 = dfc2_of(psi[8 * cc + 6], psi[8 * cc + 7]);
+            hs[0][cc] = dfc2_add(p0, dfc2_times(dfc2_sel(swap, p3, p2), im, f0));
+            hs[1][cc] = dfc2_add(p1, dfc2_times(dfc2_sel(swap, p2, p3), im, f1));
+            ihs[0][cc] = dfc2_muli(hs[0][cc]);
+            ihs[1][cc] = dfc2_muli(hs[1][cc]);
         }
         if (!fwd) {   // U <- U^dag
 #pragma unroll
@@ -144,21 +226,36 @@ __device__ __forceinline__ void df_hops(const Geom &g, const char *gauge_out, co
 #pragma unroll
             for (int k = 0; k < 9; ++k) U[2 * k + 1] = -U[2 * k + 1];
         }
-        cdf u[2][3];
-        su3_mul(U, hs, u);
-        if (wrap && (phase_on >> mu & 1u)) {
+        dfc2 u[2][3];
+        su3_mul_dfc2(U, hs, ihs, u);
+        if (wrap && (phase_on >> mu & 1u)) {   // rare: the scalar phase product
             const df64 pr = df64(ph[2 * mu]), pi = df64(ph[2 * mu + 1]);
-            phase_mul(u, pr, fwd ? pi : -pi);
+            cdf us[2][3];
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) us[k][a] = cdf_of(u[k][a]);
+            phase_mul(us, pr, fwd ? pi : -pi);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) u[k][a] = dfc2_of(us[k][a]);
         }
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const cdf r2 = times(sel(swap, u[1][cc], u[0][cc]), im, g2);
-            const cdf r3 = times(sel(swap, u[0][cc], u[1][cc]), im, g3);
-            acc[8 * cc + 0] += u[0][cc].re; acc[8 * cc + 1] += u[0][cc].im;
-            acc[8 * cc + 2] += u[1][cc].re; acc[8 * cc + 3] += u[1][cc].im;
-            acc[8 * cc + 4] += r2.re;       acc[8 * cc + 5] += r2.im;
-            acc[8 * cc + 6] += r3.re;       acc[8 * cc + 7] += r3.im;
+            const dfc2 r2 = dfc2_times(dfc2_sel(swap, u[1][cc], u[0][cc]), im, g2);
+            const dfc2 r3 = dfc2_times(dfc2_sel(swap, u[0][cc], u[1][cc]), im, g3);
+            acc2[4 * cc + 0] = dfc2_add(acc2[4 * cc + 0], u[0][cc]);
+            acc2[4 * cc + 1] = dfc2_add(acc2[4 * cc + 1], u[1][cc]);
+            acc2[4 * cc + 2] = dfc2_add(acc2[4 * cc + 2], r2);
+            acc2[4 * cc + 3] = dfc2_add(acc2[4 * cc + 3], r3);
         }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const cdf v = cdf_of(acc2[k]);
+        acc[2 * k] = v.re;
+        acc[2 * k + 1] = v.im;
     }
 }
 
