@@ -15,8 +15,10 @@ Printed as one JSON line:
                 wd_dslash_resident, CUDA events on its stream) against the
                 measured HBM copy bandwidth
   fp64_cg_ms    the same solve with plain FP64 even-odd CGNR on the same GPU
-  e2e           the solve through wd_solve_cg_host_zero_guess: b and x in pinned
-                host memory, b up and x down inside the timed region
+  e2e           nine solves through wd_solve_cg_host_stream: b and x in pinned
+                host memory, every step's b up and x down inside the timed
+                region (b_{k+1} during solve k, x_k during solve k+1); the
+                median one-call step of wd_solve_cg_host_zero_guess beside it
   twisted_mass  the same comparison with a twisted mass mu (Fig. dirac)
   recovery      reliable updates and defect correction (inner tolerances
                 0.1 ... 1e-4) on the same problem; the timed solve uses the
@@ -567,16 +569,17 @@ def main():
             tm_fp64 = (f0.elapsed_time(f1), r64.info["iters"])
         op64.close()
 
-    # ---- end to end through the host-memory entry point with no initial
-    # guess: every step uploads b from pinned host memory and reads x back
-    # into pinned host memory (host wall clock around the call).  The two
-    # host buffers are reused from step to step, as a serving loop would,
-    # after one untimed solve: a pinned buffer's first transfers pay the
-    # GPU's address translations of its pages (measured: with a fresh 402 MB
-    # buffer per step the steps took 65-69 ms, with a reused one 49.6 ms).
-    # The median of nine steps is reported: host-timed steps catch host
-    # jitter, and one step in a few can take 60-75 ms instead of 45 (seen
-    # only inside the full benchmark, after its other workloads).
+    # ---- end to end from host memory with no initial guess: every step
+    # uploads b from pinned host memory and reads x back into pinned host
+    # memory (host wall clock around the calls).  Host buffers are reused
+    # from step to step, as a serving loop would, after untimed solves: a
+    # pinned buffer's first transfers pay the GPU's address translations of
+    # its pages (measured: with a fresh 402 MB buffer per step the steps took
+    # 65-69 ms, with a reused one 49.6 ms).  Reported: nine steps as one
+    # stream call (the copies of one step overlap the neighbouring solves),
+    # and beside it the median of nine one-call steps (host-timed steps catch
+    # host jitter, and one in a few can take much longer inside the full
+    # benchmark, after its other workloads).
     n_e2e = 9
     bh = torch.from_numpy(b_np).pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
@@ -587,9 +590,25 @@ def main():
         t0 = time.perf_counter()
         e_bytes.append(op.solve_host(xh, bh, tol=w.tol, guess=False).info["bytes"])
         e_steps.append(time.perf_counter() - t0)
-    del xh
-    e2e_s = statistics.median(e_steps)
-    e2e_value = statistics.median(e_bytes) / e2e_s / 1e9
+    e2e_single_s = statistics.median(e_steps)
+    # the same steps as one stream of host-memory solves (wd_solve_cg_host_stream):
+    # each step still uploads its b and downloads its x, b_{k+1} during solve k
+    # and x_k during solve k+1; two pinned source and two solution buffers
+    # alternate (the sources hold the same b), warmed by an untimed stream
+    bh2 = bh.clone().pin_memory()
+    xh2 = torch.zeros_like(bh).pin_memory()
+    srcs = [bh if k % 2 == 0 else bh2 for k in range(n_e2e)]
+    sols = [xh if k % 2 == 0 else xh2 for k in range(n_e2e)]
+    op.solve_host_stream(sols[:2], srcs[:2], tol=w.tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rs = op.solve_host_stream(sols, srcs, tol=w.tol)
+    e2e_stream_s = (time.perf_counter() - t0) / n_e2e
+    s_bytes = sum(r.info["bytes"] for r in rs) / n_e2e
+    s_resid = max(r.info["true_rel_resid"] for r in rs)
+    del xh, xh2, bh2
+    e2e_s = e2e_stream_s
+    e2e_value = s_bytes / e2e_s / 1e9
     spinor_bytes = w.volume * 12 * 16
 
     # ---- twisted mass (Fig. dirac, 2 i kappa mu gamma5): the chosen solver on
@@ -696,8 +715,11 @@ def main():
             "dslash_gflops": 1320.0 * w.vh / (dslash_us * 1e-6) / 1e9,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": spinor_bytes,
                     "d2h_bytes_per_step": spinor_bytes, "ms_per_step": e2e_s * 1e3,
-                    "steps": n_e2e, "step_ms": [t * 1e3 for t in e_steps],
-                    "entry_point": "wd_solve_cg_host_zero_guess"},
+                    "steps": n_e2e, "entry_point": "wd_solve_cg_host_stream",
+                    "max_true_rel_resid": s_resid,
+                    "single_call": {"entry_point": "wd_solve_cg_host_zero_guess",
+                                    "ms_per_step": e2e_single_s * 1e3,
+                                    "step_ms": [t * 1e3 for t in e_steps]}},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "residual_arithmetic": "double-float (2 x FP32)" if w.prec != "f64" else "f64",

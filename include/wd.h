@@ -198,6 +198,20 @@ int wd_solve_cg_host(wd_op *op, double *x_host, const double *b_host, double tol
  * and is not read, so only b crosses to the device (and x back). */
 int wd_solve_cg_host_zero_guess(wd_op *op, double *x_host, const double *b_host, double tol,
                                 int maxiter, int parity, wd_solve_info *info);
+/* A stream of n host-memory solves D x_k = b_k (k = 0 .. n-1), each from the
+ * initial guess 0, one after another on the handle: b_{k+1} goes up (into a
+ * second device staging buffer, allocated at the first call: 384 x Vh bytes)
+ * while solve k runs, and x_k comes down while solve k+1 runs, so that a
+ * serving loop pays about one device solve per source.  x_host[k], b_host[k]
+ * as in wd_solve_cg_host_zero_guess (the x_host[k] must not overlap any
+ * b_host[j]); infos (optional) receives n entries, seconds being each solve's
+ * host time.  Every solution is bitwise the one wd_solve_cg_host_zero_guess
+ * gives.  The call returns when all x_host[k] hold their solutions, or at the
+ * first failing solve (its code; later ones are not run).  n = 0 does
+ * nothing; n < 0 or a null pointer among the first n is WD_ERR_ARG. */
+int wd_solve_cg_host_stream(wd_op *op, int n, double *const *x_host,
+                            const double *const *b_host, double tol, int maxiter, int parity,
+                            wd_solve_info *infos);
 
 /* ---------------------------------------------------------------------------
  * Batches: several operators (lattices of any size, one storage precision

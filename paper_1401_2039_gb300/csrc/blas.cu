@@ -6,6 +6,9 @@
 // kernels walk the flat array of 16-byte chunks (NF * stride of them;
 // the zero padding of each plane stays zero under every update).  Norms
 // accumulate in FP64 and finish with the deterministic last-block sum.
+#include <algorithm>
+#include <cstdint>
+
 #include "wd_internal.cuh"
 
 namespace wd {
@@ -44,6 +47,38 @@ __global__ void __launch_bounds__(FINISH_BLOCK) k_finish_partials(Reduction red,
         const df64 t = warp_sum(warp_sums[lane]);
         if (lane == 0) apply_final(red.scalars, red.op, (double)t);
     }
+}
+
+// Copies done by the SMs instead of the copy engines: a solve's small host
+// transfers (its scalars, per-refresh constants) then never queue behind a
+// large upload or download another stream has on the copy engines.  src and
+// dst may be host memory the device can address (mapped pinned buffers).
+__global__ void k_copy_u64(unsigned long long *dst, const unsigned long long *src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    __threadfence_system();
+}
+__global__ void k_copy_u4(uint4 *dst, const uint4 *src, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+cudaError_t launch_copy_small(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes % 8 || (uintptr_t)dst % 8 || (uintptr_t)src % 8) return cudaErrorInvalidValue;
+    k_copy_u64<<<1, 128, 0, s>>>((unsigned long long *)dst, (const unsigned long long *)src,
+                                 (int)(bytes / 8));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_field(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes % 16 || (uintptr_t)dst % 16 || (uintptr_t)src % 16) return cudaErrorInvalidValue;
+    const long n = (long)(bytes / 16);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long grid = std::min<long>((n + 255) / 256, (long)sms * 8);
+    k_copy_u4<<<(unsigned)std::max<long>(grid, 1), 256, 0, s>>>((uint4 *)dst, (const uint4 *)src, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_finish_partials(const Reduction &red, long n, cudaStream_t s) {

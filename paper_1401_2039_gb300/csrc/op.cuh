@@ -34,9 +34,17 @@ struct wd_op {
     // host-memory solves: the solution's download overlaps the final residual
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_x = nullptr;
+    // the last queued download of stage_x (xd_pending: one was queued); the
+    // next unpack into stage_x waits for it
+    cudaEvent_t ev_xd = nullptr;
+    bool xd_pending = false;
     // host-memory solves: b arrives in t-slabs, one event per slab
     static constexpr int B_SLABS = 8;
     cudaEvent_t ev_b[B_SLABS] = {};
+    // streams of host-memory solves: the second staging buffer for b and its
+    // slab events (created at the first such call)
+    double *stage_b2 = nullptr;
+    cudaEvent_t ev_b2[B_SLABS] = {};
     bool gauge_loaded = false;
 
     GaugeSet gauge_lo;             // storage precision, recon
@@ -57,9 +65,11 @@ struct wd_op {
     wd::df64 *partials = nullptr;
     unsigned int *counter = nullptr;
     SolverScalars *sc = nullptr;      // device
-    SolverScalars *sc_host = nullptr; // pinned mirror
+    SolverScalars *sc_host = nullptr; // pinned mirror (mapped)
+    SolverScalars *sc_host_dev = nullptr;   // its device address
     double *dev_consts = nullptr;     // [0] scale, [1] 1/scale, [2] ratio
-    double *host_consts = nullptr;    // pinned staging of dev_consts
+    double *host_consts = nullptr;    // pinned staging of dev_consts (mapped)
+    double *host_consts_dev = nullptr;      // its device address
 
     // solver parameters (FP32 inner iterations stay accurate over a deeper
     // residual drop than FP16/BF16 ones)

@@ -314,6 +314,9 @@ void wd_op_destroy(wd_op *op) {
     if (op->ev_fork) cudaEventDestroy(op->ev_fork);
     if (op->ev_join) cudaEventDestroy(op->ev_join);
     if (op->ev_x) cudaEventDestroy(op->ev_x);
+    if (op->ev_xd) cudaEventDestroy(op->ev_xd);
+    for (cudaEvent_t e : op->ev_b2)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : op->ev_b)
         if (e) cudaEventDestroy(e);
     if (op->copy_stream) {
@@ -332,6 +335,7 @@ static int create_impl(wd_op *op) {
     WD_CUDA(cudaEventCreate(&op->ev_t1));
     WD_CUDA(cudaStreamCreateWithFlags(&op->copy_stream, cudaStreamNonBlocking));
     WD_CUDA(cudaEventCreateWithFlags(&op->ev_x, cudaEventDisableTiming));
+    WD_CUDA(cudaEventCreateWithFlags(&op->ev_xd, cudaEventDisableTiming));
     for (cudaEvent_t &e : op->ev_b) WD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
     const Geom &g = op->g;
@@ -368,8 +372,12 @@ static int create_impl(wd_op *op) {
     WD_TRY(dev_alloc(op, (void **)&op->counter, sizeof(unsigned int) * ARRIVE_WORDS));
     WD_TRY(dev_alloc(op, (void **)&op->sc, sizeof(SolverScalars)));
     WD_TRY(dev_alloc(op, (void **)&op->dev_consts, sizeof(double) * 4));
-    WD_CUDA(cudaMallocHost((void **)&op->sc_host, sizeof(SolverScalars)));
-    WD_CUDA(cudaMallocHost((void **)&op->host_consts, sizeof(double) * 4));
+    // the solve's scalars and constants cross between host and device through
+    // mapped pinned buffers, copied by the SMs (launch_copy_small)
+    WD_CUDA(cudaHostAlloc((void **)&op->sc_host, sizeof(SolverScalars), cudaHostAllocMapped));
+    WD_CUDA(cudaHostAlloc((void **)&op->host_consts, sizeof(double) * 4, cudaHostAllocMapped));
+    WD_CUDA(cudaHostGetDevicePointer((void **)&op->sc_host_dev, op->sc_host, 0));
+    WD_CUDA(cudaHostGetDevicePointer((void **)&op->host_consts_dev, op->host_consts, 0));
     WD_CUDA(cudaDeviceSynchronize());
     return WD_OK;
 }
@@ -589,8 +597,9 @@ int run_iterations(wd_op *op, int p, int n) {
 }
 
 int read_scalars(wd_op *op) {
-    WD_CUDA(cudaMemcpyAsync(op->sc_host, op->sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost,
-                            op->stream));
+    // by the SMs: a copy-engine read would queue behind a large host copy
+    // (the next source's upload or the last solution's download)
+    WD_CUDA(launch_copy_small(op->sc_host_dev, op->sc, sizeof(SolverScalars), op->stream));
     WD_CUDA(cudaStreamSynchronize(op->stream));
     return WD_OK;
 }
@@ -618,6 +627,8 @@ int reconstruct_from_th(wd_op *op, SolveState &st, cudaStream_t s) {
 int unpack_and_download(wd_op *op, SolveState &st, double *x_out, double *x_host,
                         cudaStream_t s) {
     double *xe = st.p == 0 ? op->xh : op->xq, *xo = st.p == 0 ? op->xq : op->xh;
+    // a download of the previous solution from the same buffer may still run
+    if (op->xd_pending) WD_CUDA(cudaStreamWaitEvent(s, op->ev_xd, 0));
     WD_CUDA(launch_unpack_full(op->hi_prec, op->g, x_out, xe, xo, s));
     st.launches += 1;
     if (x_host) {
@@ -625,6 +636,8 @@ int unpack_and_download(wd_op *op, SolveState &st, double *x_out, double *x_host
         WD_CUDA(cudaStreamWaitEvent(op->copy_stream, op->ev_x, 0));
         WD_CUDA(cudaMemcpyAsync(x_host, x_out, (size_t)2 * op->g.vh * 24 * sizeof(double),
                                 cudaMemcpyDeviceToHost, op->copy_stream));
+        WD_CUDA(cudaEventRecord(op->ev_xd, op->copy_stream));
+        op->xd_pending = true;
     }
     return WD_OK;
 }
@@ -651,8 +664,8 @@ int set_consts(wd_op *op, double scale, double inv_scale, double ratio) {
     op->host_consts[0] = scale;
     op->host_consts[1] = inv_scale;
     op->host_consts[2] = ratio;
-    WD_CUDA(cudaMemcpyAsync(op->dev_consts, op->host_consts, 3 * sizeof(double),
-                            cudaMemcpyHostToDevice, op->stream));
+    WD_CUDA(launch_copy_small(op->dev_consts, op->host_consts_dev, 3 * sizeof(double),
+                              op->stream));
     return WD_OK;
 }
 
@@ -664,18 +677,18 @@ int slab_t(const wd_op *op, int k) {
 }
 
 // bhat_p = b_p + kappa H_pq b_q (Wilson operator) while b arrives slab by
-// slab (event ev_b[k] on the copy stream): each slab is packed as soon as it
+// slab (event slab_ev[k] on the copy stream): each slab is packed as soon as it
 // is in, and the hop computes the output slices whose neighbours in t have
 // all arrived, so that most of the packing and of the hop overlap the
 // upload.  Slice 0 needs slice Lt - 1 and goes last.
-int prepare_from_slabs(wd_op *op, SolveState &st, const double *b) {
+int prepare_from_slabs(wd_op *op, SolveState &st, const double *b, const cudaEvent_t *slab_ev) {
     const Geom &g = op->g;
     const long S = (long)g.hx * g.L[1] * g.L[2];
     const int T = g.L[3];
     int done = 1;   // output slices [1, done) are computed
     for (int k = 0; k < wd_op::B_SLABS; ++k) {
         const int ta = slab_t(op, k), tb = slab_t(op, k + 1);
-        WD_CUDA(cudaStreamWaitEvent(op->stream, op->ev_b[k], 0));
+        WD_CUDA(cudaStreamWaitEvent(op->stream, slab_ev[k], 0));
         WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream,
                                  2 * S * ta, 2 * S * tb));
         const int hi = k + 1 == wd_op::B_SLABS ? T : tb - 1;
@@ -695,10 +708,12 @@ int prepare_from_slabs(wd_op *op, SolveState &st, const double *b) {
 // the solution (written once, at the end); they may be the same array.  x_host (optional):
 // host memory the solution is also copied to, on the handle's copy stream as
 // soon as it is complete, so that the copy overlaps the final true residual.
-// b_slabs: b is still arriving, in the t-slabs of slab_t (events ev_b).
+// slab_ev (optional): b is still arriving, in the t-slabs of slab_t, slab k
+// complete at event slab_ev[k].
 int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, double tol,
                int maxiter, int parity, wd_solve_info *info, double *x_host = nullptr,
-               bool b_slabs = false) {
+               const cudaEvent_t *slab_ev = nullptr) {
+    const bool b_slabs = slab_ev != nullptr;
     SolveState st{};
     st.p = parity;
     st.q = 1 - parity;
@@ -718,10 +733,11 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
     }
     const bool pipelined = b_slabs && tw == 0.0;   // (slabs may be empty when Lt < 8)
     if (b_slabs && !pipelined)
-        for (cudaEvent_t e : op->ev_b) WD_CUDA(cudaStreamWaitEvent(op->stream, e, 0));
+        for (int k = 0; k < wd_op::B_SLABS; ++k)
+            WD_CUDA(cudaStreamWaitEvent(op->stream, slab_ev[k], 0));
     if (!pipelined) WD_CUDA(launch_pack_full(op->hi_prec, g, op->hb[0], op->hb[1], b, op->stream));
     if (pipelined) {
-        WD_TRY(prepare_from_slabs(op, st, b));
+        WD_TRY(prepare_from_slabs(op, st, b, slab_ev));
     } else if (tw != 0.0) {   // A^-1 b_q = (1 - i t gamma5) b_q / (1 + t^2)
         WD_CUDA(launch_twist_hi(op->hi_prec, g, op->axh, op->hb[st.q], -tw, inv_norm, op->stream));
         WD_TRY(dslash(op, true, st.p, 0, op->bh, op->axh, op->hb[st.p], op->kappa, nullptr));
@@ -748,8 +764,7 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
 
     if (op->sc_host->scratch[2] == 0.0) {
         // zero initial guess: r = bhat exactly, no operator application
-        WD_CUDA(cudaMemcpyAsync(op->rh, op->bh, op->hi_field_bytes(), cudaMemcpyDeviceToDevice,
-                                op->stream));
+        WD_CUDA(launch_copy_field(op->rh, op->bh, op->hi_field_bytes(), op->stream));
         st.r_hi = std::sqrt(op->sc_host->scratch[3]);
         st.bytes += 2 * field_b(op, WD_F64);
     } else {
@@ -775,8 +790,7 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
         SolverScalars init{};
         init.nz = INFINITY;
         *op->sc_host = init;
-        WD_CUDA(cudaMemcpyAsync(op->sc, op->sc_host, sizeof(SolverScalars),
-                                cudaMemcpyHostToDevice, op->stream));
+        WD_CUDA(launch_copy_small(op->sc, op->sc_host_dev, sizeof(SolverScalars), op->stream));
         WD_CUDA(cudaStreamSynchronize(op->stream));
         st.bytes += field_b(op, WD_F64) + field_b(op, op->prec) * 3;
         st.launches += 1;
@@ -842,8 +856,8 @@ int solve_impl(wd_op *op, const double *x_in, double *x_out, const double *b, do
                     // into x_hi and cleared) in a fresh Krylov space.
                     WD_CUDA(cudaMemsetAsync(op->pl, 0, op->lo_field_bytes(), op->stream));
                     op->host_consts[3] = INFINITY;
-                    WD_CUDA(cudaMemcpyAsync(&op->sc->nz, &op->host_consts[3], sizeof(double),
-                                            cudaMemcpyHostToDevice, op->stream));
+                    WD_CUDA(launch_copy_small(&op->sc->nz, op->host_consts_dev + 3,
+                                              sizeof(double), op->stream));
                     st.restarts += stalled ? 1 : 0;
                 } else if (ratio != 1.0) {
                     WD_CUDA(launch_rescale_lo(op->prec, g, op->pl, op->sc, op->dev_consts + 2,
@@ -962,6 +976,20 @@ extern "C" int wd_solve_cg(wd_op *op, double *x, const double *b, double tol, in
     return rc != WD_OK ? rc : rj;
 }
 
+// Queue the canonical field src (host) into dst (device) in the t-slabs of
+// slab_t on the copy stream, recording ev[k] after slab k.
+static int upload_slabs(wd_op *op, double *dst, const double *src, const cudaEvent_t *ev) {
+    const size_t slice = (size_t)op->g.vh / op->g.L[3] * 2 * 24;   // doubles per time slice
+    for (int k = 0; k < wd_op::B_SLABS; ++k) {
+        const size_t d0 = slice * slab_t(op, k), d1 = slice * slab_t(op, k + 1);
+        if (d1 > d0)
+            WD_CUDA(cudaMemcpyAsync(dst + d0, src + d0, (d1 - d0) * sizeof(double),
+                                    cudaMemcpyHostToDevice, op->copy_stream));
+        WD_CUDA(cudaEventRecord(ev[k], op->copy_stream));
+    }
+    return WD_OK;
+}
+
 // Host-memory solve; with_guess = 0 starts from x = 0 without reading x_host.
 // The copies go through the handle's staging buffers with cudaMemcpyAsync
 // (DMA, 200 GB/s each way on GB300); the solution's copy runs on a second
@@ -981,19 +1009,12 @@ static int solve_host_impl(wd_op *op, double *x_host, const double *b_host, doub
     // b goes up in t-slabs on the copy stream; the solve packs each slab as
     // soon as its event fires
     WD_CUDA(cudaStreamWaitEvent(op->copy_stream, op->ev_fork, 0));
-    const size_t slice = (size_t)op->g.vh / op->g.L[3] * 2 * 24;   // doubles per time slice
-    for (int k = 0; k < wd_op::B_SLABS; ++k) {
-        const size_t d0 = slice * slab_t(op, k), d1 = slice * slab_t(op, k + 1);
-        if (d1 > d0)
-            WD_CUDA(cudaMemcpyAsync(op->stage_b + d0, b_host + d0, (d1 - d0) * sizeof(double),
-                                    cudaMemcpyHostToDevice, op->copy_stream));
-        WD_CUDA(cudaEventRecord(op->ev_b[k], op->copy_stream));
-    }
+    WD_TRY(upload_slabs(op, op->stage_b, b_host, op->ev_b));
     if (with_guess)
         WD_CUDA(cudaMemcpyAsync(op->stage_x, x_host, bytes, cudaMemcpyHostToDevice, op->stream));
     // the solution's download starts inside the solve, once x is complete
     int rc = solve_impl(op, with_guess ? op->stage_x : nullptr, op->stage_x, op->stage_b, tol,
-                        maxiter, parity, info, x_host, true);
+                        maxiter, parity, info, x_host, op->ev_b);
     WD_CUDA(cudaStreamSynchronize(op->copy_stream));
     int rj = join(op);
     if (info)
@@ -1011,4 +1032,49 @@ extern "C" int wd_solve_cg_host_zero_guess(wd_op *op, double *x_host, const doub
                                            double tol, int maxiter, int parity,
                                            wd_solve_info *info) {
     return solve_host_impl(op, x_host, b_host, tol, maxiter, parity, 0, info);
+}
+
+// A stream of host-memory solves: source k + 1 goes up into the second
+// staging buffer while solve k runs, and solution k comes down while solve
+// k + 1 runs, so each step costs about one device solve.
+extern "C" int wd_solve_cg_host_stream(wd_op *op, int n, double *const *x_host,
+                                       const double *const *b_host, double tol, int maxiter,
+                                       int parity, wd_solve_info *infos) {
+    WD_TRY(check_op(op));
+    if (n < 0 || (n > 0 && (!x_host || !b_host)))
+        return fail(WD_ERR_ARG, "n must be >= 0 with n solution and source pointers");
+    for (int k = 0; k < n; ++k)
+        if (!x_host[k] || !b_host[k]) return fail(WD_ERR_ARG, "null spinor in the stream");
+    if (parity != 0 && parity != 1) return fail(WD_ERR_ARG, "parity must be 0 or 1");
+    if (!(tol > 0) || maxiter < 0) return fail(WD_ERR_ARG, "tol must be > 0, maxiter >= 0");
+    if (n == 0) return WD_OK;
+    if (!op->stage_b2) {
+        WD_TRY(dev_alloc(op, (void **)&op->stage_b2, (size_t)2 * op->g.vh * 24 * sizeof(double)));
+        for (cudaEvent_t &e : op->ev_b2)
+            WD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    double *stage[2] = {op->stage_b, op->stage_b2};
+    const cudaEvent_t *ev[2] = {op->ev_b, op->ev_b2};
+    WD_TRY(fork(op));
+    WD_CUDA(cudaStreamWaitEvent(op->copy_stream, op->ev_fork, 0));
+    WD_TRY(upload_slabs(op, stage[0], b_host[0], ev[0]));
+    int rc = WD_OK;
+    for (int k = 0; k < n && rc == WD_OK; ++k) {
+        auto t0 = std::chrono::steady_clock::now();
+        // solve k - 1 has returned, so its staging buffer is free for k + 1
+        if (k + 1 < n) rc = upload_slabs(op, stage[(k + 1) & 1], b_host[k + 1], ev[(k + 1) & 1]);
+        wd_solve_info *info = infos ? &infos[k] : nullptr;
+        if (info) memset(info, 0, sizeof(*info));
+        if (rc == WD_OK)
+            rc = solve_impl(op, nullptr, op->stage_x, stage[k & 1], tol, maxiter, parity, info,
+                            x_host[k], ev[k & 1]);
+        if (info)
+            info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0)
+                                .count();
+    }
+    cudaError_t e = cudaStreamSynchronize(op->copy_stream);
+    int rj = join(op);
+    if (rc != WD_OK) return rc;
+    if (e != cudaSuccess) return fail(WD_ERR_CUDA, std::string("copy stream: ") + cudaGetErrorString(e));
+    return rj;
 }

@@ -373,6 +373,7 @@ struct SolverScalars {
     int frozen;         // converged system of a batch: alpha = beta = 0 from now on
     double hist[64];    // ||r||^2 after iteration k at hist[k % 64]
 };
+static_assert(sizeof(SolverScalars) % 8 == 0, "copied in 8-byte words (launch_copy_small)");
 
 enum FinalOp {
     FIN_NONE = 0,
@@ -623,6 +624,10 @@ cudaError_t launch_twist_hi(int prec, const Geom &g, void *out, const void *in, 
                             cudaStream_t s);
 // Adds the n partials warp_partials wrote (fixed order) and applies red.op.
 cudaError_t launch_finish_partials(const Reduction &red, long n, cudaStream_t s);
+// copies by the SMs (not the copy engines): small (bytes, addresses multiples
+// of 8; either side may be mapped host memory) and whole fields (multiples of 16)
+cudaError_t launch_copy_small(void *dst, const void *src, size_t bytes, cudaStream_t s);
+cudaError_t launch_copy_field(void *dst, const void *src, size_t bytes, cudaStream_t s);
 cudaError_t launch_xpay_hi(int prec, const Geom &g, void *out, const void *y, double a,
                            const void *x, cudaStream_t s);
 cudaError_t launch_f64_df64(void *buf, long n_reals, int to_df, cudaStream_t s);

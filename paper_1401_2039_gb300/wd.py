@@ -69,6 +69,8 @@ def load_library() -> ctypes.CDLL:
             "wd_solve_cg": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
             "wd_solve_cg_host": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
             "wd_solve_cg_host_zero_guess": (i, [vp, vp, vp, d, i, i, ctypes.POINTER(SolveInfo)]),
+            "wd_solve_cg_host_stream": (i, [vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, i,
+                                            ctypes.POINTER(SolveInfo)]),
             "wd_field_load": (i, [vp, i, vp]),
             "wd_field_store": (i, [vp, i, vp]),
             "wd_dslash_resident": (i, [vp, i, i, i]),
@@ -229,6 +231,28 @@ class WilsonDirac:
                 float(tol), int(maxiter), int(parity), ctypes.byref(info))
         _check(rc)
         return SolveResult(x_host, rc, info.as_dict())
+
+    def solve_host_stream(self, xs_host, bs_host, tol: float = 1e-10, maxiter: int = 20000,
+                          parity: int = 1) -> list:
+        """A stream of host-memory solves from x = 0 (wd_solve_cg_host_stream):
+        b_{k+1} goes up while solve k runs and x_k comes down while solve k+1
+        runs.  xs_host[k], bs_host[k]: contiguous complex128 host tensors
+        [V, 3, 4] (pinned for asynchronous copies).  Returns one SolveResult
+        per source."""
+        n = len(bs_host)
+        if len(xs_host) != n:
+            raise ValueError("as many solution tensors as sources")
+        for t in list(xs_host) + list(bs_host):
+            if t.is_cuda or t.dtype != torch.complex128 or tuple(t.shape) != (self.V, 3, 4) \
+                    or not t.is_contiguous():
+                raise ValueError("spinors must be contiguous complex128 host tensors [V, 3, 4]")
+        xp = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in xs_host])
+        bp = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in bs_host])
+        infos = (SolveInfo * max(n, 1))()
+        rc = self.lib.wd_solve_cg_host_stream(self.handle, n, xp, bp, float(tol), int(maxiter),
+                                              int(parity), infos)
+        _check(rc)
+        return [SolveResult(xs_host[k], rc, infos[k].as_dict()) for k in range(n)]
 
     def set_solver(self, ru_delta: float = 0.1, stall_iters: int = 200):
         """Reliable-update threshold and stagnation restart of the mixed-precision solve."""

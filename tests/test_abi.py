@@ -114,6 +114,10 @@ def test_null_handles_are_rejected(lib):
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
     assert lib.wd_solve_cg_multi(None, 1, None, None, None, 1e-10, 100, 1, None) == 1
+    lib.wd_solve_cg_host_stream.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_void_p]
+    assert lib.wd_solve_cg_host_stream(None, 1, None, None, 1e-10, 100, 1, None) == 1
 
 
 def test_product_path_has_no_cpu_fallback():

@@ -11,6 +11,8 @@ Lattices span several 128-site thread blocks with a ragged last block
 (e.g. 6x6x2x4: Vh = 144), the 2^4 lattice where x+mu and x-mu coincide,
 anisotropic shapes and both boundary-phase kinds.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -254,6 +256,43 @@ def test_solve_reports_not_converged():
     assert res.status == WD_ERR_NOT_CONVERGED
     assert res.info["iters"] == 5
     assert 1e-10 < res.info["true_rel_resid"] < 1.0
+
+
+@pytest.mark.parametrize("prec,recon", [("f32", 18), ("f16", 12)])
+def test_host_stream_solves_match_single_host_solves(prec, recon):
+    """A stream of host-memory solves (b_{k+1} uploaded during solve k, x_k
+    downloaded during solve k+1, two device staging buffers for b) gives
+    bitwise the solutions of one-at-a-time zero-guess host solves, each at
+    the oracle's FP64 true residual; pinned and pageable buffers, both
+    staging buffers reused (five sources), n = 0, and a null pointer."""
+    dims, kappa = (8, 6, 6, 10), 0.124
+    U, _ = fields(dims)
+    op = make_op(dims, kappa, PHASES["twisted"], prec, recon, U)
+    bs = [syn.gaussian_spinor(syn.volume(dims), 40 + k) for k in range(5)]
+    singles = []
+    for b in bs:
+        bh = torch.from_numpy(b).pin_memory()
+        xh = torch.zeros_like(bh).pin_memory()
+        r = op.solve_host(xh, bh, tol=1e-10, guess=False)
+        singles.append((xh.numpy().copy(), r.info["iters"]))
+    bhs = [torch.from_numpy(b).pin_memory() for b in bs]
+    bhs[3] = torch.from_numpy(bs[3].copy())   # one pageable source
+    xhs = [torch.full_like(bhs[0], complex(float("nan"), 1.0)) for _ in bs]
+    xhs = [x.pin_memory() if k != 1 else x for k, x in enumerate(xhs)]
+    res = op.solve_host_stream(xhs, bhs, tol=1e-10)
+    assert len(res) == 5
+    for k, (r, (xs, it)) in enumerate(zip(res, singles)):
+        assert np.array_equal(r.x.numpy(), xs), k
+        assert r.info["iters"] == it and r.info["seconds"] > 0
+        rt = np.linalg.norm(bs[k] - oracle.apply(r.x.numpy(), U, dims, kappa, PHASES["twisted"]))
+        assert rt <= 1.05e-10 * np.linalg.norm(bs[k])
+    assert op.solve_host_stream([], [], tol=1e-10) == []
+    lib, n = op.lib, 2
+    xp = (ctypes.c_void_p * n)(xhs[0].data_ptr(), None)
+    bp = (ctypes.c_void_p * n)(bhs[0].data_ptr(), bhs[1].data_ptr())
+    assert lib.wd_solve_cg_host_stream(op.handle, n, xp, bp, 1e-10, 100, 1, None) == 1
+    assert lib.wd_solve_cg_host_stream(op.handle, -1, xp, bp, 1e-10, 100, 1, None) == 1
+    op.close()
 
 
 def test_host_memory_solve_matches_device_solve():
