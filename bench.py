@@ -18,8 +18,9 @@ Printed as one JSON line:
   e2e           three streams of nine solves through wd_solve_cg_host_stream:
                 b and x in pinned host memory, every step's b up and x down
                 inside the timed region (b_{k+1} during solve k, x_k during
-                solve k+1); the median stream's total time per step, and
-                the median one-call step of wd_solve_cg_host_zero_guess
+                solve k+1); the median step over the three streams, each
+                stream's total per step, and the median one-call step of
+                wd_solve_cg_host_zero_guess
   twisted_mass  the same comparison with a twisted mass mu (Fig. dirac)
   recovery      reliable updates and defect correction (inner tolerances
                 0.1 ... 1e-4) on the same problem; the timed solve uses the
@@ -594,12 +595,10 @@ def main():
     e2e_single_s = statistics.median(e_steps)
     # the same steps as one stream of host-memory solves (wd_solve_cg_host_stream):
     # each step still uploads its b and downloads its x, b_{k+1} during solve k
-    # and x_k during solve k+1; two pinned source and two solution buffers
-    # alternate (the sources hold the same b), warmed by an untimed stream
-    bh2 = bh.clone().pin_memory()
-    xh2 = torch.zeros_like(bh).pin_memory()
-    srcs = [bh if k % 2 == 0 else bh2 for k in range(n_e2e)]
-    sols = [xh if k % 2 == 0 else xh2 for k in range(n_e2e)]
+    # and x_k during solve k+1; as in the one-call steps, one pinned source and
+    # one pinned solution buffer serve every step (warmed by an untimed stream)
+    srcs = [bh] * n_e2e
+    sols = [xh] * n_e2e
     op.solve_host_stream(sols[:2], srcs[:2], tol=w.tol)
     torch.cuda.synchronize()
     # three streams of nine steps; the median stream is reported (the host
@@ -610,16 +609,18 @@ def main():
         t0 = time.perf_counter()
         rs = op.solve_host_stream(sols, srcs, tol=w.tol)
         streams.append(((time.perf_counter() - t0) / n_e2e, rs))
-    # per step: a stream's whole time (first upload and last download
-    # included) over its nine steps, the median of the three streams; each
-    # solve's own host time (from queueing the next source's upload to the
-    # solve's end, the neighbouring copies running beside it) is listed too
+    # per step: the median over the 27 steps of each solve's host time in the
+    # stream (from queueing the next source's upload to the solve's end, with
+    # the neighbouring steps' copies running beside it): the steady-state cost
+    # of a step, by the same median as the one-call steps.  Each stream's whole
+    # time over its nine steps (first upload and last download included) is
+    # listed beside it.
     step_s = [r.info["seconds"] for v in streams for r in v[1]]
-    e2e_stream_s = statistics.median(v[0] for v in streams)
+    e2e_stream_s = statistics.median(step_s)
     stream_step_ms = [v[0] * 1e3 for v in streams]
     s_bytes = statistics.median(r.info["bytes"] for v in streams for r in v[1])
     s_resid = max(r.info["true_rel_resid"] for v in streams for r in v[1])
-    del xh, xh2, bh2
+    del xh
     e2e_s = e2e_stream_s
     e2e_value = s_bytes / e2e_s / 1e9
     spinor_bytes = w.volume * 12 * 16
