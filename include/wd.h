@@ -204,8 +204,10 @@ int wd_solve_cg_host_zero_guess(wd_op *op, double *x_host, const double *b_host,
  * while solve k runs, and x_k comes down while solve k+1 runs, so that a
  * serving loop pays about one device solve per source.  x_host[k], b_host[k]
  * as in wd_solve_cg_host_zero_guess (the x_host[k] must not overlap any
- * b_host[j]); infos (optional) receives n entries, seconds being each solve's
- * host time.  Every solution is bitwise the one wd_solve_cg_host_zero_guess
+ * b_host[j]; entries may repeat: a repeated x_host holds the last of its
+ * solutions, a repeated b_host is read again); infos (optional) receives n
+ * entries, seconds being each solve's host time (from queueing the next
+ * source's upload to the solve's end).  Every solution is bitwise the one wd_solve_cg_host_zero_guess
  * gives.  The call returns when all x_host[k] hold their solutions, or at the
  * first failing solve (its code; later ones are not run).  n = 0 does
  * nothing; n < 0 or a null pointer among the first n is WD_ERR_ARG. */
